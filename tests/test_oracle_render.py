@@ -1,0 +1,62 @@
+"""Pins of the oracle's cameras, ray-box test and first-hit search (reading R12), and of
+the weight blob the inputs module writes."""
+import math
+import struct
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+
+def test_ray_box():
+    o = np.array([[-1.0, 0.5, 0.5], [-1.0, 2.0, 0.5], [0.5, 0.5, 0.5], [0.5, 0.5, 2.0]])
+    d = np.array([[1.0, 0, 0], [1.0, 0, 0], [0, 1.0, 0], [0, 0, -1.0]])
+    t0, t1 = O.ray_box(o, d)
+    assert (t0[0], t1[0]) == (1.0, 2.0)
+    assert not t1[1] > t0[1]
+    assert (t0[2], t1[2]) == (0.0, 0.5)
+    assert (t0[3], t1[3]) == (1.0, 2.0)
+
+
+def test_camera_centre_and_edge_rays():
+    cam = synth.persp_camera(np.array([0.0, 0, 1]), 3, 3, fov_y_deg=40.0)
+    o, d = O.camera_rays(cam)
+    np.testing.assert_allclose(d[1, 1], [0, 0, 1], atol=1e-15)
+    # top-centre pixel: screen y = 2/3 of the half-height
+    ang = math.acos(d[0, 1] @ np.array([0, 0, 1.0]))
+    assert ang == pytest.approx(math.atan(2 / 3 * math.tan(math.radians(20))), rel=1e-12)
+    assert d[0, 1, 1] > 0                        # row 0 is the top of the image
+    oc = synth.ortho_camera(np.array([1.0, 0, 0]), 5, 5)
+    o2, d2 = O.camera_rays(oc)
+    np.testing.assert_allclose(d2, np.broadcast_to([1.0, 0, 0], d2.shape))
+    np.testing.assert_allclose(o2[2, 2], oc["eye"], atol=1e-15)
+
+
+def test_first_hit_on_constant_cube():
+    n = 16
+    vol = np.full((n, n, n), 4.0)
+    o = np.array([[[-1.0, 0.5, 0.5]]])
+    d = np.array([[[1.0, 0.0, 0.0]]])
+    hit, p, margin = O.hit_search(vol, 4.0, o, d)
+    assert hit[0, 0]
+    # first sample half a step (0.25 / N) inside the face: zero-border lookup 0.75 sigma
+    np.testing.assert_allclose(p[0, 0], [0.25 / n, 0.5, 0.5], rtol=1e-14)
+    assert margin[0, 0] == pytest.approx(0.75 - 0.05)
+    miss, _, _ = O.hit_search(vol, 4.0, o, -d)
+    assert not miss[0, 0]
+
+
+def test_blob_header_and_checksum():
+    w = synth.make_weights(3)
+    blob = synth.pack_weights(w)
+    head = struct.unpack("<16IQQ", blob[:80])
+    assert head[0] == synth.BLOB_MAGIC and head[1] == 1 and head[3] == 80
+    assert head[4:13] == (12, 8, 225, 16, 2, 200, 5, 3, 80)
+    n = head[16]
+    assert n == synth.n_params() and len(blob) == 80 + 4 * n
+    assert head[17] == synth.blob_checksum(blob[80:])
+    payload = np.frombuffer(blob[80:], dtype="<f4")
+    np.testing.assert_array_equal(payload[:16 * 27], w["cnn"][0]["w1"].ravel())
+    np.testing.assert_array_equal(payload[-3:], w["head"][2]["b"])
