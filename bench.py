@@ -1,0 +1,394 @@
+#!/usr/bin/env python3
+"""Throughput of the neural in-scattering path: shaded points per second while rendering
+1920x1080 frames of a 256^3 FP32 cloud (g 0.85, albedo 0.999) on one GB300.
+
+One step = one pass of the whole path over the frame: density pyramid, transmittance
+fields toward the light, phase table, per-pixel first hits, template gathers + SE, 3D-CNN,
+backbone MLP and decode.  Inputs are resident in HBM when the timed region starts; L2 is
+flushed (256 MB write) between timed steps, outside the timed events.  ``e2e`` times the
+same step through the C ABI from page-locked host memory: the density upload and the
+image read-back are inside its timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl nis|reference]
+
+``--impl reference`` times the FP64 CPU oracle on the host cores (a bounded sample of the
+same frame per step).  Under torchrun each rank renders its own copy of the workload (weak
+scaling, no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "shaded points/sec (1080p frame of a 256^3 FP32 cloud)"
+UNIT = "points/s"
+
+# Algorithmic work per shading point (one light): FLOPs of the dense layers (backbone 12
+# blocks x 3 types, 3 merges, head) and of the 3D-CNN; bytes the gather must write.
+MLP_FLOP_PER_POINT = 2 * (24 * (230 * 200 + 200 * 200) + 12 * (85 * 200 + 200 * 200)
+                          + 3 * 400 * 200 + 600 * 200 + 200 * 200 + 200 * 3)
+CNN_FLOP_PER_POINT = 2 * 12 * (63 * 16 * 27 + 5 * 16 * 16 * 27)
+GATHER_BYTES_PER_POINT = 4 * (3 * 12 * 225 + 12 * 8 + 12 * 3 + 5 + 6)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("nis", "reference"), default="nis")
+    ap.add_argument("--workload", type=int, default=2, choices=(1, 2, 5))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---- distributed plumbing -------------------------------------------------------------
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def dist_init(backend):
+    rank, local, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend)
+    return rank, local, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---- clocks during the timed region --------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows),
+                "power_w_max": max((float(r[3]) for r in rows if r[3].replace(".", "").isdigit()),
+                                   default=None)}
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        d["source"] = "measured"
+        return d
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+def kernel_source_hash(files) -> str:
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2401_14051_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(family: str):
+    """DRAM bytes per launch of a kernel family from a committed ncu summary, if the kernel
+    source has not changed since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f).get(family)
+    if not rec or rec.get("source_hash") != kernel_source_hash(rec["files"]):
+        return None
+    return rec
+
+
+# ---- the oracle timed on the host (cpu_baseline and --impl reference) ------------------------
+def oracle_sample(cfg, vol, weights, n_pixels: int, seed: int):
+    """One bounded sample of the frame on the FP64 oracle: pyramid, lazily marched
+    transmittance, phase-table columns, first hits of n_pixels random pixels, shading.
+    Returns (shaded points, seconds)."""
+    import oracle as O
+    t0 = time.perf_counter()
+    levels = O.build_pyramid(vol)
+    o, d = O.camera_rays(cfg["camera"])
+    rng = np.random.default_rng(seed)
+    idx = rng.choice(o.shape[0] * o.shape[1], n_pixels, replace=False)
+    oo, dd = o.reshape(-1, 3)[idx], d.reshape(-1, 3)[idx]
+    hit, pts, _ = O.hit_search(levels[0], float(vol.max()), oo, dd)
+    if hit.any():
+        om = -dd[hit]
+        tl = O.LazyTransmittance(levels, cfg["light"])
+        table = O.phase_table(cfg["material"]["g"],
+                              columns=O.table_columns(O.view_angle(om, cfg["light"])))
+        O.shade_points(pts[hit], om, cfg["light"], levels, tl, table, weights, cfg["material"])
+    return int(hit.sum()), time.perf_counter() - t0
+
+
+def cpu_baseline(cfg, vol, weights, target_s: float = 12.0) -> dict:
+    pts_total, secs, rounds, pixels = 0, 0.0, 0, 0
+    while secs < target_s and rounds < 20:
+        n, s = oracle_sample(cfg, vol, weights, 160, seed=1000 + rounds)
+        pts_total += n
+        secs += s
+        rounds += 1
+        pixels += 160
+    return {"value": pts_total / secs if secs > 0 else 0.0, "unit": UNIT,
+            "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{rounds} rounds x 160 random pixels of the 1920x1080 frame "
+                      f"({pts_total} shading points): full pyramid, transmittance marched "
+                      f"only at the voxels the sample's gathers touch, phase-table columns of "
+                      f"the sample's angles; numpy float64 (BLAS may use all {os.cpu_count()} "
+                      f"cores, elementwise work one)",
+            "seconds": round(secs, 2)}
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    cfg = synth.config(args.workload)
+    vol = cfg["volume"]()
+    weights = synth.make_weights(cfg["weights_seed"], cfg["sigma_max"])
+    for i in range(args.warmup):
+        oracle_sample(cfg, vol, weights, 96, seed=i)
+    pts, secs = 0, 0.0
+    for i in range(args.steps):
+        n, s = oracle_sample(cfg, vol, weights, 96, seed=100 + i)
+        pts += n
+        secs += s
+    value = pts / secs
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": cfg["name"], "sample_per_step": "96 random pixels"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(),
+                             "kind": "oracle",
+                             "sample": f"{args.steps} steps x 96 random pixels ({pts} shading points)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---- the CUDA path ------------------------------------------------------------------------
+def run_nis(args):
+    import torch
+    rank, local, world = dist_init("nccl")
+    torch.cuda.set_device(local)
+    from paper_2401_14051_gb300 import nis
+    if not os.path.exists(nis.LIB_PATH):
+        from paper_2401_14051_gb300 import build
+        build.build()
+    dev = torch.device(f"cuda:{local}")
+    cfg = synth.config(args.workload)
+    vol_np = cfg["volume"]()
+    weights = synth.make_weights(cfg["weights_seed"], cfg["sigma_max"])
+    blob = synth.pack_weights(weights)
+    mat, cam, light = cfg["material"], cfg["camera"], cfg["light"]
+    ctx = nis.Context(local)
+    density = torch.from_numpy(vol_np).to(dev)
+    v = ctx.upload_volume(density)
+    w = ctx.load_weights(blob)
+    img = torch.empty((cam["height"], cam["width"], 3), dtype=torch.float32, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ctx.build_pyramid(v)
+        lt = ctx.build_transmittance(v, light, 0.6)
+        ctx.build_phase_table(mat["g"])
+        ctx.render_frame(v, lt, w, mat, cam, out=img)
+        return lt
+
+    for _ in range(args.warmup):
+        step()
+    ctx.sync(timeout_ms=120000)
+    hit, _, _ = ctx.find_hits(v, cam)
+    n_points = int(hit.sum().item())
+
+    # ---- device-resident timed region
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    ctx.profile(True)
+    launches0 = nis.kernel_launches()
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    launches = nis.kernel_launches() - launches0
+    ctx.profile(False)
+    barrier(world)
+    clk = clocks.stop()
+    fam = {f: ctx.profile_read(f) for f in nis.FAMILIES}
+    total_ms = max_over_ranks(sum(times), world)
+    ms_per_step = total_ms / args.steps
+    value = n_points * args.steps * world / (total_ms / 1e3)
+
+    # ---- end to end through the C ABI from page-locked host memory
+    host_vol = torch.from_numpy(vol_np).pin_memory()
+    host_img = torch.empty(img.shape, dtype=torch.float32).pin_memory()
+    e2e_times = []
+    barrier(world)
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.update_volume(v, host_vol)
+        step()
+        host_img.copy_(img, non_blocking=True)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e_times.append(time.perf_counter() - t0)
+    e2e_total = max_over_ranks(sum(e2e_times), world)
+    e2e_value = n_points * args.steps * world / e2e_total
+    ctx.sync(timeout_ms=120000)
+
+    if rank != 0:
+        ctx.close()
+        return
+
+    # ---- roofline of the dominant kernel family
+    peaks = measured_peaks()
+    dom = max(fam, key=lambda f: fam[f][0])
+    dom_ms, dom_n = fam[dom]
+    per_launch_s = dom_ms / 1e3 / max(dom_n, 1)
+    n_levels = len(range(int(math.log2(cfg["n"])) + 1))
+    if dom == "mlp":
+        work = MLP_FLOP_PER_POINT * n_points * args.steps / max(dom_n, 1)
+        achieved = work / per_launch_s / 1e12
+        peak = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+        roof = {"bound": "alu", "unit": "TFLOP/s", "kernel": "fc_f32_kernel (backbone, merges, head)",
+                "peak_source": "FP32 FFMA: 152 SMs x 128 lanes x 2 FLOP x max SM clock "
+                               f"{peaks['sm_max_mhz']:.0f} MHz (derived)"}
+    elif dom == "cnn":
+        work = CNN_FLOP_PER_POINT * n_points * args.steps / max(dom_n, 1)
+        achieved = work / per_launch_s / 1e12
+        peak = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+        roof = {"bound": "alu", "unit": "TFLOP/s", "kernel": "cnn_f32_kernel",
+                "peak_source": "FP32 FFMA derived peak"}
+    else:
+        if dom == "gather":
+            work = GATHER_BYTES_PER_POINT * n_points * args.steps / max(dom_n, 1)
+        else:
+            vox = sum(((cfg["n"] + (1 << m) - 1) >> m) ** 3 for m in range(n_levels))
+            work = 8.0 * vox / max(1, n_levels)
+        achieved = work / per_launch_s / 1e9
+        peak = peaks["hbm_gbs"]
+        roof = {"bound": "hbm", "unit": "GB/s", "kernel": dom,
+                "peak_source": f"{peaks['source']} STREAM copy"}
+    tr = recorded_traffic(dom)
+    roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak,
+                 "traffic": tr["bytes_per_launch"] if tr else None,
+                 "family": dom, "launches": dom_n, "avg_launch_ms": dom_ms / max(dom_n, 1),
+                 "work_per_launch": work})
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": cfg["name"], "volume": f"{cfg['n']}^3 float32",
+                       "image": f"{cam['width']}x{cam['height']} perspective",
+                       "shading_points_per_frame": n_points, "g": mat["g"],
+                       "albedo": mat["albedo"][0], "l2": "flushed between steps (256 MB write)",
+                       "step": "pyramid + transmittance + phase table + hits + gather/SE + "
+                               "3D-CNN + MLP + decode"},
+            "frame_ms": ms_per_step,
+            "gpu_launches": int(launches),
+            "step_breakdown_ms": {f: round(fam[f][0] / args.steps, 4) for f in nis.FAMILIES},
+            "roofline": roof,
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": int(vol_np.nbytes),
+                    "d2h_bytes_per_step": int(img.numel() * 4),
+                    "ms_per_step": 1e3 * e2e_total / args.steps},
+            "clocks": clk}
+    ctx.close()
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg, vol_np, weights)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_nis(args)
+
+
+if __name__ == "__main__":
+    main()

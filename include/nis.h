@@ -1,0 +1,230 @@
+/*
+ * nis.h -- C ABI of the neural in-scattering estimator of arXiv 2401.14051
+ * ("A real-time rendering method for high albedo anisotropic materials with multiple
+ * scattering"), built for one GB300 (sm_103a).
+ *
+ * The library runs the paper's inference path per shading point and per light:
+ *   1. density mip pyramid                         (Sec. III.B.1)
+ *   2. graded transmittance fields, Eq. 1          (Sec. III.B.1; Eq. 15)
+ *   3. diffuse + highlight template gathers of density, transmittance and
+ *      cone-integrated HG phase features           (Sec. III.B.2-5; Eq. 2-5, 8, 9)
+ *   4. per-layer 3D-CNN over the transmittance stencil (Sec. III.B.1, Fig. 3)
+ *   5. SE channel attention                        (Sec. III.C.3; Eq. 24-26)
+ *   6. backbone MLP + output decode                (Sec. III.C.2, Fig. 6; Eq. 21)
+ * Every step runs in this library's CUDA kernels; there is no CPU fallback.
+ *
+ * Conventions.  The medium occupies the unit cube [0,1]^3.  A grid of N^3 voxels is
+ * stored x-fastest (index (k*N + j)*N + i for voxel (i, j, k)), voxel centres at
+ * ((i+1/2)/N, (j+1/2)/N, (k+1/2)/N).  light_dir is the direction the light travels
+ * (unit or not; the library normalises it).  omega is the direction from a shading point
+ * toward the camera.  Images are row-major [height][width][3] float32, row 0 at the top.
+ *
+ * Errors.  Every call returns NIS_OK (0) or a negative nis_status; argument errors are
+ * reported synchronously and nis_last_error() gives a message.  Calls that enqueue GPU
+ * work return once it is enqueued on the caller's stream; device-side faults detected by
+ * the kernels' own checks are reported by nis_sync().  A context is not thread-safe:
+ * serialise calls on one context.
+ *
+ * Ownership.  The library copies volumes and weights into its own device memory and owns
+ * every pyramid, transmittance field, phase table and scratch buffer it builds.  Input and
+ * output buffers passed to a call stay owned by the caller.
+ */
+#ifndef NIS_H
+#define NIS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *nis_stream; /* a cudaStream_t; NULL = legacy default stream */
+typedef struct nis_ctx nis_ctx;
+typedef uint64_t nis_handle;            /* 0 is never a valid handle */
+typedef nis_handle nis_volume;
+typedef nis_handle nis_light;
+typedef nis_handle nis_weights;
+
+typedef int nis_status;
+#define NIS_OK 0
+#define NIS_ERR_INVALID_ARG -1   /* bad pointer, size, enum or handle */
+#define NIS_ERR_NOT_READY -2     /* handle released, or a cache the call may not build */
+#define NIS_ERR_BUDGET -3        /* allocation would exceed the context's HBM budget */
+#define NIS_ERR_OOM -4           /* the allocator failed */
+#define NIS_ERR_CUDA -5          /* a CUDA runtime call failed */
+#define NIS_ERR_TIMEOUT -6       /* a host wait passed its deadline */
+#define NIS_ERR_UNIMPLEMENTED -7
+#define NIS_ERR_BAD_BLOB -8      /* weight blob header, size or checksum mismatch */
+#define NIS_ERR_BAD_DATA -9      /* a kernel check failed (e.g. NaN/negative density) */
+
+#define NIS_DTYPE_F32 0
+#define NIS_DTYPE_F16 1
+
+#define NIS_PREC_F32 0           /* FP32 everywhere */
+#define NIS_PREC_BF16 1          /* CNN, SE and MLP in BF16 with FP32 accumulation */
+#define NIS_PREC_FP8 2           /* as BF16 with e4m3 operands and per-channel scales */
+
+#define NIS_CAMERA_ORTHO 0
+#define NIS_CAMERA_PERSP 1
+
+/* Optional device allocator (e.g. a framework's caching allocator).  alloc returns NULL
+ * on failure.  Either both callbacks are set or the library uses cudaMalloc/cudaFree. */
+typedef struct nis_allocator {
+    void *user;
+    void *(*alloc)(void *user, size_t bytes, nis_stream stream);
+    void (*free)(void *user, void *ptr, size_t bytes, nis_stream stream);
+} nis_allocator;
+
+/* Material: HG asymmetry g in (-1, 1) (Eq. 5), RGB albedo in (0, 1] (Sec. III.C.2) and
+ * RGB light intensity I (Eq. 16). */
+typedef struct nis_material {
+    float g;
+    float albedo[3];
+    float intensity[3];
+} nis_material;
+
+/* Pinhole (PERSP, vertical field of view fov_y in radians) or orthographic (ORTHO, view
+ * height ortho_height) camera at eye looking at target; up fixes the roll. */
+typedef struct nis_camera {
+    int type;
+    int width, height;
+    float eye[3], target[3], up[3];
+    float fov_y;
+    float ortho_height;
+} nis_camera;
+
+/* Creates a context on CUDA device `device`.  hbm_budget_bytes caps the device memory the
+ * context may hold (0 = no cap).  alloc may be NULL.  *out receives the context. */
+nis_status nis_create(nis_ctx **out, int device, size_t hbm_budget_bytes,
+                      const nis_allocator *alloc);
+
+/* Frees every buffer the context owns (after a device synchronise) and the context. */
+void nis_destroy(nis_ctx *ctx);
+
+/* Message of the last failed call on this context ("" if none).  Valid until the next
+ * call on the context.  A NULL ctx gives the message of the last failed nis_create. */
+const char *nis_last_error(const nis_ctx *ctx);
+
+/* Bytes of device memory the context holds now. */
+size_t nis_bytes_in_use(const nis_ctx *ctx);
+
+/* Copies an nx*ny*nz density grid (sigma_t per unit length, float32 or float16, x-fastest)
+ * from host or device memory (src_is_device) into a new volume, multiplied by
+ * sigma_scale.  The grid must be cubic (nx = ny = nz, 1..2048).  Values are checked on the
+ * device: NaN, infinite or negative densities make the next nis_sync return
+ * NIS_ERR_BAD_DATA.  The caller keeps ownership of `density`.  Host sources are copied
+ * before the call returns. */
+nis_status nis_upload_volume(nis_ctx *ctx, const void *density, int nx, int ny, int nz,
+                             int dtype, int src_is_device, float sigma_scale,
+                             nis_stream stream, nis_volume *out);
+
+/* Builds the density mip pyramid of `vol` (Sec. III.B.1): levels N, ceil(N/2), ..., 1,
+ * each voxel the mean of its in-range 2x2x2 children, plus sigma_max of level 0.
+ * Rebuilding an already built pyramid recomputes it in place. */
+nis_status nis_build_pyramid(nis_ctx *ctx, nis_volume vol, nis_stream stream);
+
+/* Marches the graded transmittance fields of `vol` toward a distant light (Eq. 1):
+ * T_m(x) = exp(-lambda^(m+1) * integral of level m's density from x to the cube exit along
+ * -light_dir), midpoint rule with step 1/N_m and a partial last step, stopping once the
+ * scaled optical depth exceeds 30.  lambda in (0, 1] (the paper uses 0.6).  Builds the
+ * pyramid first if needed.  A light with the same volume, direction and lambda is
+ * re-marched into its existing buffers and its handle returned again. */
+nis_status nis_build_transmittance(nis_ctx *ctx, nis_volume vol, const float light_dir[3],
+                                   float lambda, nis_stream stream, nis_light *out);
+
+/* Parses a weight blob (80-byte header, float32 tensors in the fixed order below, a
+ * position-weighted word checksum) and uploads it at `precision`.  The caller keeps the
+ * blob.  Tensor order: CNN[12]{w1 16x1x3x3x3, b1, w2 16x16x3x3x3, b2}, SE[12]{w1 2x8, b1,
+ * w2 3x2, b2}, blocks[type rho,f,T][layer 0..11]{W1 200x(d+5), b1, W2 200x200, b2} with
+ * d = 225, 225, 80, merge[3]{200x400, b}, head{200x600, b, 200x200, b, 3x200, b}. */
+nis_status nis_load_weights(nis_ctx *ctx, const void *blob, size_t bytes, int precision,
+                            nis_stream stream, nis_weights *out);
+
+/* Radiance at n shading points (steps 3-6; Sec. III.C.2 output layer): rgb[i] =
+ * I * albedo^4 * expm1(y_i) where y_i is the network output for point d_points[i] (x, y, z)
+ * seen along d_omega[i].  All three buffers are device float32 arrays of n*3 values.
+ * Builds the phase table for material->g if it is not cached. */
+nis_status nis_shade_points(nis_ctx *ctx, nis_volume vol, nis_light light, nis_weights w,
+                            const nis_material *m, const float *d_points,
+                            const float *d_omega, int n, float *d_rgb_out,
+                            nis_stream stream);
+
+/* Renders one frame: per pixel, the first sample along the camera ray (step 0.5/N from the
+ * cube entry) whose level-0 density reaches 0.05 sigma_max is the shading point; its
+ * radiance (as nis_shade_points, omega = -ray direction) is the pixel value, 0 for rays
+ * that find none.  d_rgb_out is a device float32 [height][width][3] buffer.  Waits once on
+ * the stream to read the number of shading points. */
+nis_status nis_render_frame(nis_ctx *ctx, nis_volume vol, nis_light light, nis_weights w,
+                            const nis_material *m, const nis_camera *cam, float *d_rgb_out,
+                            nis_stream stream);
+
+/* Overwrites the density of an existing volume with a grid of the same size (same
+ * conventions as nis_upload_volume) without allocating: device sources and page-locked
+ * host sources are read in place (a GB300 kernel reads pinned host memory over
+ * NVLink-C2C); pageable host sources go through a staging buffer the volume keeps.  The
+ * pyramid and every transmittance field of the volume become stale until rebuilt. */
+nis_status nis_update_volume(nis_ctx *ctx, nis_volume vol, const void *density, int dtype,
+                             int src_is_device, float sigma_scale, nis_stream stream);
+
+/* Frees a volume (and its lights), a light or a weight set. */
+nis_status nis_release(nis_ctx *ctx, nis_handle h);
+
+/* Waits for `stream` (polling, up to timeout_ms; <= 0 waits without limit) and reports
+ * any fault recorded by the kernels' own checks since the last nis_sync. */
+nis_status nis_sync(nis_ctx *ctx, nis_stream stream, int timeout_ms);
+
+/* ---- inspection (tests, benchmarks) ----------------------------------------------- */
+
+/* Number of pyramid levels, their sizes (sizes[0..levels-1]) and, after a nis_sync, the
+ * densest voxel of level 0. */
+nis_status nis_volume_info(nis_ctx *ctx, nis_volume vol, int *levels, int sizes[16],
+                           float *sigma_max);
+
+/* Copies pyramid level `level` (N_m^3 float32) or transmittance level `level` of `light`
+ * into a caller device buffer. */
+nis_status nis_copy_level(nis_ctx *ctx, nis_volume vol, int level, float *d_dst,
+                          nis_stream stream);
+nis_status nis_copy_transmittance(nis_ctx *ctx, nis_light light, int level, float *d_dst,
+                                  nis_stream stream);
+
+/* (Re)builds the phase table for asymmetry g (Sec. III.B.5): 1024 alpha nodes
+ * j*pi/1023 x 5 point sets (all diffuse layers; highlight layers 0..3) x 225 lattice points,
+ * alpha-major, float32, and copies it to d_dst (1024*1125 floats) if d_dst is not NULL.
+ * nis_shade_points builds a missing table itself; this call recomputes a cached one. */
+nis_status nis_build_phase_table(nis_ctx *ctx, float g, float *d_dst, nis_stream stream);
+
+/* Intermediate outputs of nis_shade_points for n points (any pointer may be NULL):
+ * H_rho, H_T, H_f [n][12][225]; v [n][12][8] (Eq. 24 squeeze vectors); X_T [n][12][80]
+ * (CNN output, position-major); w_se [n][12][3] (SE weights, order rho, f, T); y [n][3]
+ * (network output before the decode).  All device float32. */
+typedef struct nis_debug_out {
+    float *H_rho, *H_T, *H_f, *v, *X_T, *w_se, *y;
+} nis_debug_out;
+nis_status nis_shade_points_debug(nis_ctx *ctx, nis_volume vol, nis_light light,
+                                  nis_weights w, const nis_material *m,
+                                  const float *d_points, const float *d_omega, int n,
+                                  float *d_rgb_out, const nis_debug_out *dbg,
+                                  nis_stream stream);
+
+/* First-hit search alone: per pixel, hit flag (int32), shading point and omega (float32
+ * x3) into caller device buffers of width*height entries. */
+nis_status nis_find_hits(nis_ctx *ctx, nis_volume vol, const nis_camera *cam, int *d_hit,
+                         float *d_points, float *d_omega, nis_stream stream);
+
+/* Kernel timing: with profiling on, every kernel the context launches is bracketed by
+ * CUDA events on its stream, accumulated per kernel family.  nis_profile(ctx, 1) clears
+ * and starts, nis_profile(ctx, 0) stops.  nis_profile_read waits for the recorded events
+ * and returns the summed device time and launch count of one family: "pyramid", "march",
+ * "phase", "hits", "gather", "cnn", "mlp" or "other". */
+nis_status nis_profile(nis_ctx *ctx, int enable);
+nis_status nis_profile_read(nis_ctx *ctx, const char *family, double *total_ms,
+                            int *launches);
+
+/* Number of kernels this library has launched in the process (all contexts). */
+uint64_t nis_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NIS_H */

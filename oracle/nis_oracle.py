@@ -332,12 +332,23 @@ def alpha_nodes(n_alpha: int = N_ALPHA) -> np.ndarray:
     return np.arange(n_alpha) * (math.pi / (n_alpha - 1))
 
 
-def phase_table(g: float, n_alpha: int = N_ALPHA) -> np.ndarray:
+def phase_table(g: float, n_alpha: int = N_ALPHA, columns=None) -> np.ndarray:
     """Precomputed phase features over all light-view angles (Sec. III.B.5, R10):
-    table[set, point, alpha node]."""
+    table[set, point, alpha node].  With ``columns`` only those alpha nodes are filled
+    (the rest NaN), for callers that look up a few angles."""
     a = alpha_nodes(n_alpha)
-    return np.stack([phase_feature(phase_set_offsets(s)[:, None, :], a[None, :], g)
-                     for s in range(N_PHASE_SETS)])
+    cols = np.arange(n_alpha) if columns is None else np.unique(np.asarray(columns))
+    out = np.full((N_PHASE_SETS, N_LAT, n_alpha), np.nan)
+    for s in range(N_PHASE_SETS):
+        out[s][:, cols] = phase_feature(phase_set_offsets(s)[:, None, :], a[None, cols], g)
+    return out
+
+
+def table_columns(alpha: np.ndarray, n_alpha: int = N_ALPHA) -> np.ndarray:
+    """The alpha nodes a lookup at these angles reads."""
+    t = np.asarray(alpha) * ((n_alpha - 1) / math.pi)
+    j = np.minimum(np.floor(t).astype(np.int64), n_alpha - 2)
+    return np.unique(np.concatenate([j, j + 1]))
 
 
 def table_lookup(table: np.ndarray, phase_set: int, alpha: np.ndarray) -> np.ndarray:

@@ -1,0 +1,93 @@
+// Dense layers of the backbone (Sec. III.C.2, Fig. 6), FP32 SIMT path: a 64x64-tile GEMM
+// out = epilogue(A W^T + b) whose A operand is assembled on the fly -- the SE-scaled
+// template features concatenated with the configuration vector (FC-1), the running
+// state plus the block input (FC-2), or a concatenation of chain outputs (merge, head).
+#include "nis_internal.h"
+
+namespace nis {
+
+namespace {
+constexpr int BM = 64, BN = 64, BK = 16;
+
+template <int MODE>
+__device__ __forceinline__ float load_a(const FcArgs &a, int r, int kk) {
+    if (r >= a.count || kk >= a.K) return 0.f;
+    if (MODE == kFcFeat) {
+        if (kk < a.d)
+            return a.w_se[(size_t)r * (kLayers * 3) + a.layer * 3 + a.type] *
+                   a.X[(size_t)r * a.ldx + kk];
+        return a.cfg[(size_t)r * kCfg + (kk - a.d)];
+    } else if (MODE == kFcSum) {
+        float v = a.a1[(size_t)r * a.seg + kk];
+        if (a.a0) v += a.a0[(size_t)r * a.seg + kk];
+        return v;
+    } else {
+        int s = kk / a.seg, c = kk - s * a.seg;
+        const float *src = s == 0 ? a.a0 : (s == 1 ? a.a1 : a.a2);
+        return src[(size_t)r * a.seg + c];
+    }
+}
+}  // namespace
+
+template <int MODE>
+__global__ void __launch_bounds__(256) fc_f32_kernel(const FcArgs a) {
+    __shared__ float As[BK][BM + 4];
+    __shared__ float Bs[BK][BN + 4];
+    const int row0 = blockIdx.x * BM, col0 = blockIdx.y * BN;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < a.K; k0 += BK) {
+        for (int e = threadIdx.x; e < BM * BK; e += 256) {
+            int r = e / BK, kk = e % BK;
+            As[kk][r] = load_a<MODE>(a, row0 + r, k0 + kk);
+        }
+        for (int e = threadIdx.x; e < BN * BK; e += 256) {
+            int c = e / BK, kk = e % BK;
+            int gc = col0 + c, gk = k0 + kk;
+            Bs[kk][c] = (gc < a.N && gk < a.K) ? __ldg(a.W + (size_t)gc * a.K + gk) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            float av[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) av[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int r = row0 + ty * 4 + i;
+        if (r >= a.count) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int c = col0 + tx * 4 + j;
+            if (c >= a.N) continue;
+            float v = acc[i][j] + a.b[c];
+            if (a.relu) v = fmaxf(v, 0.f);
+            if (a.resid) v += a.resid[(size_t)r * a.ldo + c];
+            if (a.decode) {
+                if (a.y_out) a.y_out[(size_t)r * 3 + c] = v;
+                a.out[(size_t)r * 3 + c] = a.dec_scale[c] * expm1f(v);
+            } else {
+                a.out[(size_t)r * a.ldo + c] = v;
+            }
+        }
+    }
+}
+
+void launch_fc_f32(const FcArgs &a, cudaStream_t s) {
+    if (a.count <= 0) return;
+    dim3 grid((a.count + BM - 1) / BM, (a.N + BN - 1) / BN);
+    if (a.mode == kFcFeat) { note_launch(); fc_f32_kernel<kFcFeat><<<grid, 256, 0, s>>>(a); }
+    else if (a.mode == kFcSum) { note_launch(); fc_f32_kernel<kFcSum><<<grid, 256, 0, s>>>(a); }
+    else { note_launch(); fc_f32_kernel<kFcCat><<<grid, 256, 0, s>>>(a); }
+}
+
+}  // namespace nis

@@ -1,0 +1,77 @@
+// Density upload (conversion + checks) and the mip pyramid (Sec. III.B.1).
+#include <cuda_fp16.h>
+
+#include "nis_internal.h"
+
+namespace nis {
+
+// Converts the caller's density to float32 times `scale`, flags NaN/inf/negative values in
+// the error word and tracks the maximum (non-negative floats order like their bit patterns).
+template <typename T>
+__global__ void convert_density_kernel(const T *__restrict__ src, float scale, size_t count,
+                                       float *__restrict__ dst, unsigned *err,
+                                       float *sigma_max) {
+    float local_max = 0.f;
+    bool bad = false;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+         i += (size_t)gridDim.x * blockDim.x) {
+        float v = (float)src[i] * scale;
+        if (!(v >= 0.f) || isinf(v)) { bad = true; v = 0.f; }
+        dst[i] = v;
+        local_max = fmaxf(local_max, v);
+    }
+    for (int o = 16; o > 0; o >>= 1) local_max = fmaxf(local_max, __shfl_xor_sync(~0u, local_max, o));
+    unsigned any_bad = __any_sync(~0u, bad);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(reinterpret_cast<unsigned *>(sigma_max), __float_as_uint(local_max));
+        if (any_bad) atomicOr(err, kErrBadDensity);
+    }
+}
+
+void launch_convert_density(const void *src, int dtype, float scale, size_t count,
+                            float *dst, unsigned *err, float *sigma_max, cudaStream_t s) {
+    cudaMemsetAsync(sigma_max, 0, sizeof(float), s);
+    const int threads = 256;
+    size_t want = (count + threads - 1) / threads;
+    int blocks = (int)(want < 152 * 16 ? (want ? want : 1) : 152 * 16);
+    note_launch();
+    if (dtype == NIS_DTYPE_F16)
+        convert_density_kernel<<<blocks, threads, 0, s>>>(static_cast<const __half *>(src), scale,
+                                                          count, dst, err, sigma_max);
+    else
+        convert_density_kernel<<<blocks, threads, 0, s>>>(static_cast<const float *>(src), scale,
+                                                          count, dst, err, sigma_max);
+}
+
+// One level coarser: parent (i, j, k) of an m^3 grid averages its in-range children
+// (2i + a, 2j + b, 2k + c) < n of the n^3 grid (reading: box mean, ceil(n/2) for odd n).
+__global__ void downsample_kernel(const float *__restrict__ src, int n, float *__restrict__ dst,
+                                  int m) {
+    size_t total = (size_t)m * m * m;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        int i = (int)(idx % m), j = (int)((idx / m) % m), k = (int)(idx / ((size_t)m * m));
+        float sum = 0.f;
+        int cnt = 0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            int x = 2 * i + (c & 1), y = 2 * j + ((c >> 1) & 1), z = 2 * k + (c >> 2);
+            if (x < n && y < n && z < n) {
+                sum += __ldg(src + ((size_t)z * n + y) * n + x);
+                ++cnt;
+            }
+        }
+        dst[idx] = sum / (float)cnt;
+    }
+}
+
+void launch_downsample(const float *src, int n, float *dst, int m, cudaStream_t s) {
+    const int threads = 256;
+    size_t total = (size_t)m * m * m;
+    size_t want = (total + threads - 1) / threads;
+    int blocks = (int)(want < 152 * 32 ? want : 152 * 32);
+    note_launch();
+    downsample_kernel<<<blocks, threads, 0, s>>>(src, n, dst, m);
+}
+
+}  // namespace nis

@@ -1,0 +1,973 @@
+// The C ABI (include/nis.h): context, handle registries, HBM budget accounting, weight-blob
+// parsing and the stream-ordered orchestration of the kernels of the inference path.
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "nis_internal.h"
+
+using namespace nis;
+
+namespace {
+
+std::string g_create_error;
+
+struct Volume {
+    int n = 0, levels = 0;
+    int sizes[kMaxLevels] = {};
+    size_t off[kMaxLevels] = {};      // float offsets of each level in `data`
+    size_t total = 0;                 // floats in all levels
+    float *data = nullptr;
+    float *sigma_max = nullptr;       // device scalar (max of level 0)
+    void *staging = nullptr;          // pageable-host updates (nis_update_volume)
+    size_t staging_bytes = 0;
+    bool pyramid = false;
+};
+
+struct Light {
+    nis_handle vol = 0;
+    float dir[3] = {0, 0, 0};         // unit propagation direction
+    float lambda = 0.6f;
+    float *data = nullptr;            // same level layout as the volume
+};
+
+struct Weights {
+    int precision = NIS_PREC_F32;
+    float *f32 = nullptr;             // all tensors in blob order
+    WeightOffsets off;
+};
+
+struct Workspace {                    // scratch of nis_shade_points, grow-only
+    int cap = 0;
+    float *H_rho = nullptr, *H_T = nullptr, *H_f = nullptr, *v = nullptr, *w_se = nullptr,
+          *cfg = nullptr, *X_T = nullptr;
+    float *act = nullptr;             // activation buffers, kActBufs x cap x kWidth
+    int hit_cap = 0;                  // pixels
+    float *hit_pts = nullptr, *hit_omega = nullptr, *hit_rgb = nullptr;
+    int *hit_pix = nullptr, *hit_count = nullptr;
+    int *host_count = nullptr;        // pinned
+};
+constexpr int kActBufs = 15;          // e, h0, h1, 6 chain ends, 3 merges, z1, z2, spare
+constexpr int kChunk = 65536;         // shading points per pipeline pass
+
+}  // namespace
+
+struct nis_ctx {
+    int device = 0;
+    size_t budget = 0, in_use = 0;
+    nis_allocator alloc{};
+    bool custom_alloc = false;
+    std::string err;
+    unsigned *d_err = nullptr;
+    std::map<void *, size_t> allocs;
+    std::map<nis_handle, Volume> vols;
+    std::map<nis_handle, Light> lights;
+    std::map<nis_handle, Weights> weights;
+    std::map<uint32_t, float *> phase;   // by the bit pattern of g
+    Workspace ws;
+    nis_handle next = 1;
+    // kernel timing (nis_profile)
+    bool prof_on = false;
+    std::map<std::string, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>> prof;
+    std::vector<cudaEvent_t> event_pool;
+};
+
+namespace {
+
+nis_status fail(nis_ctx *c, nis_status s, const std::string &msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+nis_status cuda_fail(nis_ctx *c, cudaError_t e, const char *what) {
+    return fail(c, NIS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define NIS_CUDA(call)                                                 \
+    do {                                                               \
+        cudaError_t e_ = (call);                                       \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);       \
+    } while (0)
+
+std::atomic<uint64_t> g_launches{0};
+
+cudaEvent_t take_event(nis_ctx *c) {
+    if (!c->event_pool.empty()) {
+        cudaEvent_t e = c->event_pool.back();
+        c->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Brackets the kernel launches of its scope with events on `s` when profiling is on.
+struct ProfScope {
+    nis_ctx *c;
+    const char *family;
+    cudaStream_t s;
+    cudaEvent_t e0 = nullptr;
+    ProfScope(nis_ctx *c_, const char *f, cudaStream_t s_) : c(c_), family(f), s(s_) {
+        if (c->prof_on && (e0 = take_event(c))) cudaEventRecord(e0, s);
+    }
+    ~ProfScope() {
+        if (!e0) return;
+        cudaEvent_t e1 = take_event(c);
+        if (!e1) return;
+        cudaEventRecord(e1, s);
+        c->prof[family].push_back({e0, e1});
+    }
+};
+
+nis_status dev_alloc(nis_ctx *ctx, size_t bytes, void **out, cudaStream_t s) {
+    *out = nullptr;
+    if (bytes == 0) bytes = 256;
+    bytes = (bytes + 255) & ~size_t(255);
+    if (ctx->budget && ctx->in_use + bytes > ctx->budget)
+        return fail(ctx, NIS_ERR_BUDGET, "allocation of " + std::to_string(bytes) +
+                                             " bytes exceeds the HBM budget");
+    void *p = nullptr;
+    if (ctx->custom_alloc) {
+        p = ctx->alloc.alloc(ctx->alloc.user, bytes, s);
+        if (!p) return fail(ctx, NIS_ERR_OOM, "allocator returned NULL");
+    } else {
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, NIS_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+    }
+    ctx->allocs[p] = bytes;
+    ctx->in_use += bytes;
+    *out = p;
+    return NIS_OK;
+}
+
+template <typename T>
+nis_status dev_alloc_t(nis_ctx *ctx, size_t count, T **out, cudaStream_t s) {
+    void *p;
+    nis_status st = dev_alloc(ctx, count * sizeof(T), &p, s);
+    *out = static_cast<T *>(p);
+    return st;
+}
+
+void dev_free(nis_ctx *ctx, void *p) {
+    if (!p) return;
+    auto it = ctx->allocs.find(p);
+    if (it == ctx->allocs.end()) return;
+    if (ctx->custom_alloc) ctx->alloc.free(ctx->alloc.user, p, it->second, nullptr);
+    else cudaFree(p);
+    ctx->in_use -= it->second;
+    ctx->allocs.erase(it);
+}
+
+PyramidView view_of(const Volume &v, const float *base) {
+    PyramidView pv{};
+    pv.levels = v.levels;
+    for (int m = 0; m < v.levels; ++m) {
+        pv.lv[m] = base + v.off[m];
+        pv.n[m] = v.sizes[m];
+    }
+    return pv;
+}
+
+nis_status build_pyramid_impl(nis_ctx *ctx, Volume &v, cudaStream_t s) {
+    for (int m = 1; m < v.levels; ++m) {
+        ProfScope ps(ctx, "pyramid", s);
+        launch_downsample(v.data + v.off[m - 1], v.sizes[m - 1], v.data + v.off[m], v.sizes[m], s);
+    }
+    NIS_CUDA(cudaGetLastError());
+    v.pyramid = true;
+    return NIS_OK;
+}
+
+nis_status ensure_phase(nis_ctx *ctx, float g, cudaStream_t s, float **out, bool rebuild = false) {
+    uint32_t key;
+    std::memcpy(&key, &g, 4);
+    auto it = ctx->phase.find(key);
+    float *t;
+    if (it != ctx->phase.end()) {
+        *out = it->second;
+        if (!rebuild) return NIS_OK;
+        t = it->second;
+    } else {
+        nis_status st = dev_alloc_t(ctx, (size_t)kAlpha * kPhaseSets * kLat, &t, s);
+        if (st) return st;
+    }
+    {
+        ProfScope ps(ctx, "phase", s);
+        launch_phase_table(g, t, s);
+    }
+    NIS_CUDA(cudaGetLastError());
+    ctx->phase[key] = t;
+    *out = t;
+    return NIS_OK;
+}
+
+nis_status ensure_workspace(nis_ctx *ctx, int cap, cudaStream_t s) {
+    Workspace &w = ctx->ws;
+    if (w.cap >= cap) return NIS_OK;
+    float **bufs[] = {&w.H_rho, &w.H_T, &w.H_f, &w.v, &w.w_se, &w.cfg, &w.X_T, &w.act};
+    for (float **b : bufs) { dev_free(ctx, *b); *b = nullptr; }
+    w.cap = 0;
+    size_t n = (size_t)cap;
+    nis_status st;
+    if ((st = dev_alloc_t(ctx, n * kLayers * kLat, &w.H_rho, s))) return st;
+    if ((st = dev_alloc_t(ctx, n * kLayers * kLat, &w.H_T, s))) return st;
+    if ((st = dev_alloc_t(ctx, n * kLayers * kLat, &w.H_f, s))) return st;
+    if ((st = dev_alloc_t(ctx, n * kLayers * 8, &w.v, s))) return st;
+    if ((st = dev_alloc_t(ctx, n * kLayers * 3, &w.w_se, s))) return st;
+    if ((st = dev_alloc_t(ctx, n * kCfg, &w.cfg, s))) return st;
+    if ((st = dev_alloc_t(ctx, n * kLayers * kDT, &w.X_T, s))) return st;
+    if ((st = dev_alloc_t(ctx, n * kActBufs * kWidth, &w.act, s))) return st;
+    w.cap = cap;
+    return NIS_OK;
+}
+
+nis_status check_material(nis_ctx *ctx, const nis_material *m) {
+    if (!m) return fail(ctx, NIS_ERR_INVALID_ARG, "material is NULL");
+    if (!(m->g > -1.f && m->g < 1.f)) return fail(ctx, NIS_ERR_INVALID_ARG, "g must lie in (-1, 1)");
+    for (int c = 0; c < 3; ++c)
+        if (!(m->albedo[c] > 0.f && m->albedo[c] <= 1.f) || !std::isfinite(m->intensity[c]))
+            return fail(ctx, NIS_ERR_INVALID_ARG, "albedo must lie in (0, 1], intensity finite");
+    return NIS_OK;
+}
+
+// Runs steps 3-6 for `n` points already on the device.
+nis_status shade_impl(nis_ctx *ctx, const Volume &vol, const Light &light, const Weights &wt,
+                      const nis_material *m, const float *pts, const float *om, int n,
+                      float *rgb, const nis_debug_out *dbg, cudaStream_t s) {
+    float *table;
+    nis_status st = ensure_phase(ctx, m->g, s, &table);
+    if (st) return st;
+    int chunk = n < kChunk ? n : kChunk;
+    if (chunk <= 0) return NIS_OK;
+    if ((st = ensure_workspace(ctx, chunk, s))) return st;
+    Workspace &w = ctx->ws;
+    const WeightOffsets &o = wt.off;
+    const float *W = wt.f32;
+    const size_t act_stride = (size_t)w.cap * kWidth;
+    auto act = [&](int i) { return w.act + i * act_stride; };
+    float dec_scale[3];
+    for (int c = 0; c < 3; ++c) dec_scale[c] = m->intensity[c] * powf(m->albedo[c], 4.0f);
+
+    for (int off = 0; off < n; off += chunk) {
+        int cnt = n - off < chunk ? n - off : chunk;
+        GatherArgs ga{};
+        ga.rho = view_of(vol, vol.data);
+        ga.T = view_of(vol, light.data);
+        ga.table = table;
+        ga.points = pts + 3 * (size_t)off;
+        ga.omega = om + 3 * (size_t)off;
+        ga.count = cnt;
+        ga.lx = light.dir[0]; ga.ly = light.dir[1]; ga.lz = light.dir[2];
+        ga.g = m->g;
+        for (int c = 0; c < 3; ++c) ga.albedo[c] = m->albedo[c];
+        ga.se = W;
+        for (int k = 0; k < kLayers; ++k) {
+            ga.se_w1[k] = o.se_w1[k]; ga.se_b1[k] = o.se_b1[k];
+            ga.se_w2[k] = o.se_w2[k]; ga.se_b2[k] = o.se_b2[k];
+        }
+        ga.H_rho = w.H_rho; ga.H_T = w.H_T; ga.H_f = w.H_f;
+        ga.v = w.v; ga.w_se = w.w_se; ga.cfg = w.cfg;
+        {
+            ProfScope ps(ctx, "gather", s);
+            launch_gather(ga, s);
+        }
+        {
+            ProfScope ps(ctx, "cnn", s);
+            launch_cnn_f32(w.H_T, cnt, W, o, w.X_T, s);
+        }
+
+        // backbone: 3 types x (diffuse chain of 8, highlight chain of 4)
+        for (int t = 0; t < 3; ++t) {
+            const float *X = t == 0 ? w.H_rho : (t == 1 ? w.H_f : w.X_T);
+            const int d = feat_dim(t);
+            for (int chain = 0; chain < 2; ++chain) {
+                int k0 = chain == 0 ? 0 : kDiffuse, k1 = chain == 0 ? kDiffuse : kLayers;
+                float *h = nullptr;
+                int ping = 1;
+                for (int k = k0; k < k1; ++k) {
+                    FcArgs f1{};
+                    f1.mode = kFcFeat; f1.count = cnt; f1.K = d + kCfg; f1.N = kWidth;
+                    f1.X = X + (size_t)k * d; f1.ldx = kLayers * d; f1.d = d;
+                    f1.w_se = w.w_se; f1.layer = k; f1.type = t; f1.cfg = w.cfg;
+                    f1.W = W + o.blk_w1[t][k]; f1.b = W + o.blk_b1[t][k];
+                    f1.relu = 1; f1.out = act(0); f1.ldo = kWidth;
+                    { ProfScope ps(ctx, "mlp", s); launch_fc_f32(f1, s); }
+                    FcArgs f2{};
+                    f2.mode = kFcSum; f2.count = cnt; f2.K = kWidth; f2.N = kWidth;
+                    f2.a0 = h; f2.a1 = act(0); f2.seg = kWidth;
+                    f2.W = W + o.blk_w2[t][k]; f2.b = W + o.blk_b2[t][k];
+                    f2.relu = 1; f2.resid = act(0); f2.ldo = kWidth;
+                    float *dst = (k == k1 - 1) ? act(3 + 2 * t + chain) : act(ping);
+                    f2.out = dst;
+                    { ProfScope ps(ctx, "mlp", s); launch_fc_f32(f2, s); }
+                    h = dst;
+                    ping = 3 - ping;
+                }
+            }
+            FcArgs mg{};
+            mg.mode = kFcCat; mg.count = cnt; mg.K = 2 * kWidth; mg.N = kWidth;
+            mg.a0 = act(3 + 2 * t); mg.a1 = act(4 + 2 * t); mg.seg = kWidth;
+            mg.W = W + o.mrg_w[t]; mg.b = W + o.mrg_b[t]; mg.relu = 1;
+            mg.out = act(9 + t); mg.ldo = kWidth;
+            { ProfScope ps(ctx, "mlp", s); launch_fc_f32(mg, s); }
+        }
+        FcArgs h1{};
+        h1.mode = kFcCat; h1.count = cnt; h1.K = 3 * kWidth; h1.N = kWidth;
+        h1.a0 = act(9); h1.a1 = act(10); h1.a2 = act(11); h1.seg = kWidth;
+        h1.W = W + o.head_w[0]; h1.b = W + o.head_b[0]; h1.relu = 1;
+        h1.out = act(12); h1.ldo = kWidth;
+        { ProfScope ps(ctx, "mlp", s); launch_fc_f32(h1, s); }
+        FcArgs h2{};
+        h2.mode = kFcSum; h2.count = cnt; h2.K = kWidth; h2.N = kWidth;
+        h2.a1 = act(12); h2.seg = kWidth;
+        h2.W = W + o.head_w[1]; h2.b = W + o.head_b[1]; h2.relu = 1;
+        h2.out = act(13); h2.ldo = kWidth;
+        { ProfScope ps(ctx, "mlp", s); launch_fc_f32(h2, s); }
+        FcArgs h3{};
+        h3.mode = kFcSum; h3.count = cnt; h3.K = kWidth; h3.N = 3;
+        h3.a1 = act(13); h3.seg = kWidth;
+        h3.W = W + o.head_w[2]; h3.b = W + o.head_b[2];
+        h3.decode = 1;
+        for (int c = 0; c < 3; ++c) h3.dec_scale[c] = dec_scale[c];
+        h3.y_out = (dbg && dbg->y) ? dbg->y + 3 * (size_t)off : nullptr;
+        h3.out = rgb + 3 * (size_t)off; h3.ldo = 3;
+        { ProfScope ps(ctx, "mlp", s); launch_fc_f32(h3, s); }
+
+        if (dbg) {
+            auto cp = [&](float *dst, const float *src, size_t per) -> cudaError_t {
+                if (!dst) return cudaSuccess;
+                return cudaMemcpyAsync(dst + per * off, src, per * cnt * sizeof(float),
+                                       cudaMemcpyDeviceToDevice, s);
+            };
+            NIS_CUDA(cp(dbg->H_rho, w.H_rho, (size_t)kLayers * kLat));
+            NIS_CUDA(cp(dbg->H_T, w.H_T, (size_t)kLayers * kLat));
+            NIS_CUDA(cp(dbg->H_f, w.H_f, (size_t)kLayers * kLat));
+            NIS_CUDA(cp(dbg->v, w.v, (size_t)kLayers * 8));
+            NIS_CUDA(cp(dbg->X_T, w.X_T, (size_t)kLayers * kDT));
+            NIS_CUDA(cp(dbg->w_se, w.w_se, (size_t)kLayers * 3));
+        }
+        NIS_CUDA(cudaGetLastError());
+    }
+    return NIS_OK;
+}
+
+template <typename T>
+T *lookup(std::map<nis_handle, T> &m, nis_handle h) {
+    auto it = m.find(h);
+    return it == m.end() ? nullptr : &it->second;
+}
+
+nis_status resolve(nis_ctx *ctx, nis_volume vol, nis_light light, nis_weights w, Volume **pv,
+                   Light **pl, Weights **pw) {
+    *pv = lookup(ctx->vols, vol);
+    *pl = lookup(ctx->lights, light);
+    *pw = lookup(ctx->weights, w);
+    if (!*pv) return fail(ctx, NIS_ERR_NOT_READY, "unknown or released volume handle");
+    if (!*pl) return fail(ctx, NIS_ERR_NOT_READY, "unknown or released light handle");
+    if (!*pw) return fail(ctx, NIS_ERR_NOT_READY, "unknown or released weights handle");
+    if ((*pl)->vol != vol) return fail(ctx, NIS_ERR_INVALID_ARG, "light belongs to another volume");
+    if (!(*pv)->pyramid) return fail(ctx, NIS_ERR_NOT_READY, "pyramid not built");
+    return NIS_OK;
+}
+
+nis_status camera_args(nis_ctx *ctx, const nis_camera *cam, CameraArgs *c) {
+    if (!cam) return fail(ctx, NIS_ERR_INVALID_ARG, "camera is NULL");
+    if (cam->width <= 0 || cam->height <= 0 || (long long)cam->width * cam->height > (1LL << 27))
+        return fail(ctx, NIS_ERR_INVALID_ARG, "bad image size");
+    if (cam->type != NIS_CAMERA_ORTHO && cam->type != NIS_CAMERA_PERSP)
+        return fail(ctx, NIS_ERR_INVALID_ARG, "bad camera type");
+    for (int q = 0; q < 3; ++q)
+        if (!std::isfinite(cam->eye[q]) || !std::isfinite(cam->target[q]) || !std::isfinite(cam->up[q]) ||
+            std::fabs(cam->eye[q]) > 1e6f || std::fabs(cam->target[q]) > 1e6f)
+            return fail(ctx, NIS_ERR_INVALID_ARG, "camera vectors must be finite (|x| <= 1e6)");
+    double f[3], up[3], r[3], u[3];
+    for (int q = 0; q < 3; ++q) { f[q] = (double)cam->target[q] - cam->eye[q]; up[q] = cam->up[q]; }
+    double nf = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+    if (!(nf > 0)) return fail(ctx, NIS_ERR_INVALID_ARG, "eye equals target");
+    for (double &x : f) x /= nf;
+    r[0] = f[1] * up[2] - f[2] * up[1];
+    r[1] = f[2] * up[0] - f[0] * up[2];
+    r[2] = f[0] * up[1] - f[1] * up[0];
+    double nr = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    if (!(nr > 1e-12)) return fail(ctx, NIS_ERR_INVALID_ARG, "up is parallel to the view");
+    for (double &x : r) x /= nr;
+    u[0] = r[1] * f[2] - r[2] * f[1];
+    u[1] = r[2] * f[0] - r[0] * f[2];
+    u[2] = r[0] * f[1] - r[1] * f[0];
+    c->type = cam->type; c->width = cam->width; c->height = cam->height;
+    for (int q = 0; q < 3; ++q) {
+        c->eye[q] = cam->eye[q]; c->fwd[q] = (float)f[q]; c->right[q] = (float)r[q]; c->up[q] = (float)u[q];
+    }
+    c->tan_half = (float)std::tan(0.5 * (double)cam->fov_y);
+    c->aspect = (float)((double)cam->width / cam->height);
+    c->half_h = 0.5f * cam->ortho_height;
+    if (cam->type == NIS_CAMERA_PERSP && !(cam->fov_y > 0.f && cam->fov_y < 3.1f))
+        return fail(ctx, NIS_ERR_INVALID_ARG, "fov_y must lie in (0, 3.1) radians");
+    if (cam->type == NIS_CAMERA_ORTHO && !(cam->ortho_height > 0.f))
+        return fail(ctx, NIS_ERR_INVALID_ARG, "ortho_height must be positive");
+    return NIS_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+namespace nis {
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void weight_offsets(WeightOffsets *o) {
+    size_t p = 0;
+    for (int k = 0; k < kLayers; ++k) {
+        o->cnn_w1[k] = p; p += kCnnCh * 27;
+        o->cnn_b1[k] = p; p += kCnnCh;
+        o->cnn_w2[k] = p; p += kCnnCh * kCnnCh * 27;
+        o->cnn_b2[k] = p; p += kCnnCh;
+    }
+    for (int k = 0; k < kLayers; ++k) {
+        o->se_w1[k] = p; p += 2 * 8;
+        o->se_b1[k] = p; p += 2;
+        o->se_w2[k] = p; p += 3 * 2;
+        o->se_b2[k] = p; p += 3;
+    }
+    for (int t = 0; t < 3; ++t)
+        for (int k = 0; k < kLayers; ++k) {
+            int d = feat_dim(t);
+            o->blk_w1[t][k] = p; p += (size_t)kWidth * (d + kCfg);
+            o->blk_b1[t][k] = p; p += kWidth;
+            o->blk_w2[t][k] = p; p += (size_t)kWidth * kWidth;
+            o->blk_b2[t][k] = p; p += kWidth;
+        }
+    for (int t = 0; t < 3; ++t) {
+        o->mrg_w[t] = p; p += (size_t)kWidth * 2 * kWidth;
+        o->mrg_b[t] = p; p += kWidth;
+    }
+    o->head_w[0] = p; p += (size_t)kWidth * 3 * kWidth;
+    o->head_b[0] = p; p += kWidth;
+    o->head_w[1] = p; p += (size_t)kWidth * kWidth;
+    o->head_b[1] = p; p += kWidth;
+    o->head_w[2] = p; p += 3 * kWidth;
+    o->head_b[2] = p; p += 3;
+    o->total = p;
+}
+}  // namespace nis
+
+extern "C" {
+
+nis_status nis_create(nis_ctx **out, int device, size_t hbm_budget_bytes,
+                      const nis_allocator *alloc) {
+    if (!out) { g_create_error = "out is NULL"; return NIS_ERR_INVALID_ARG; }
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || device < 0 || device >= ndev) {
+        g_create_error = std::string("no CUDA device ") + std::to_string(device) +
+                         (e != cudaSuccess ? std::string(": ") + cudaGetErrorString(e) : "");
+        cudaGetLastError();
+        return NIS_ERR_CUDA;
+    }
+    if (alloc && (!alloc->alloc != !alloc->free)) {
+        g_create_error = "allocator needs both callbacks";
+        return NIS_ERR_INVALID_ARG;
+    }
+    nis_ctx *ctx = new nis_ctx();
+    ctx->device = device;
+    ctx->budget = hbm_budget_bytes;
+    if (alloc && alloc->alloc) { ctx->alloc = *alloc; ctx->custom_alloc = true; }
+    DeviceGuard g(device);
+    void *p;
+    if (dev_alloc(ctx, sizeof(unsigned), &p, nullptr) != NIS_OK) {
+        g_create_error = ctx->err;
+        delete ctx;
+        return NIS_ERR_OOM;
+    }
+    ctx->d_err = static_cast<unsigned *>(p);
+    if (cudaMemset(ctx->d_err, 0, sizeof(unsigned)) != cudaSuccess ||
+        cudaMallocHost(&ctx->ws.host_count, sizeof(int)) != cudaSuccess) {
+        g_create_error = "device set-up failed";
+        cudaGetLastError();
+        dev_free(ctx, ctx->d_err);
+        delete ctx;
+        return NIS_ERR_CUDA;
+    }
+    *out = ctx;
+    return NIS_OK;
+}
+
+void nis_destroy(nis_ctx *ctx) {
+    if (!ctx) return;
+    DeviceGuard g(ctx->device);
+    cudaDeviceSynchronize();
+    std::vector<void *> ptrs;
+    for (auto &kv : ctx->allocs) ptrs.push_back(kv.first);
+    for (void *p : ptrs) dev_free(ctx, p);
+    if (ctx->ws.host_count) cudaFreeHost(ctx->ws.host_count);
+    for (auto &kv : ctx->prof)
+        for (auto &e : kv.second) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+    for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+    delete ctx;
+}
+
+const char *nis_last_error(const nis_ctx *ctx) {
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+size_t nis_bytes_in_use(const nis_ctx *ctx) { return ctx ? ctx->in_use : 0; }
+
+nis_status nis_upload_volume(nis_ctx *ctx, const void *density, int nx, int ny, int nz,
+                             int dtype, int src_is_device, float sigma_scale, nis_stream stream,
+                             nis_volume *out) {
+    if (!ctx) return NIS_ERR_INVALID_ARG;
+    if (!density || !out) return fail(ctx, NIS_ERR_INVALID_ARG, "NULL density or out");
+    if (nx != ny || ny != nz) return fail(ctx, NIS_ERR_INVALID_ARG, "grid must be cubic");
+    if (nx < 1 || nx > 2048) return fail(ctx, NIS_ERR_INVALID_ARG, "grid size must be 1..2048");
+    if (dtype != NIS_DTYPE_F32 && dtype != NIS_DTYPE_F16)
+        return fail(ctx, NIS_ERR_INVALID_ARG, "dtype must be F32 or F16");
+    if (!(sigma_scale >= 0.f) || !std::isfinite(sigma_scale))
+        return fail(ctx, NIS_ERR_INVALID_ARG, "sigma_scale must be finite and >= 0");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Volume v;
+    v.n = nx;
+    int sz = nx;
+    size_t total = 0;
+    while (true) {
+        v.sizes[v.levels] = sz;
+        v.off[v.levels] = total;
+        total += (size_t)sz * sz * sz;
+        ++v.levels;
+        if (sz == 1) break;
+        sz = (sz + 1) / 2;
+    }
+    v.total = total;
+    nis_status st = dev_alloc_t(ctx, total, &v.data, s);
+    if (st) return st;
+    if ((st = dev_alloc_t(ctx, 1, &v.sigma_max, s))) { dev_free(ctx, v.data); return st; }
+    size_t count = (size_t)nx * nx * nx;
+    size_t elem = dtype == NIS_DTYPE_F16 ? 2 : 4;
+    const void *src = density;
+    void *staging = nullptr;
+    if (!src_is_device) {
+        if ((st = dev_alloc(ctx, count * elem, &staging, s))) {
+            dev_free(ctx, v.data); dev_free(ctx, v.sigma_max);
+            return st;
+        }
+        cudaError_t e = cudaMemcpyAsync(staging, density, count * elem, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) {
+            dev_free(ctx, staging); dev_free(ctx, v.data); dev_free(ctx, v.sigma_max);
+            return cuda_fail(ctx, e, "cudaMemcpyAsync(density)");
+        }
+        src = staging;
+    }
+    {
+        ProfScope ps(ctx, "other", s);
+        launch_convert_density(src, dtype, sigma_scale, count, v.data, ctx->d_err, v.sigma_max, s);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (staging) {
+        cudaStreamSynchronize(s);     // the staging copy is freed before returning
+        dev_free(ctx, staging);
+    }
+    if (e != cudaSuccess) {
+        dev_free(ctx, v.data); dev_free(ctx, v.sigma_max);
+        return cuda_fail(ctx, e, "convert_density");
+    }
+    nis_handle h = ctx->next++;
+    ctx->vols[h] = v;
+    *out = h;
+    return NIS_OK;
+}
+
+nis_status nis_build_pyramid(nis_ctx *ctx, nis_volume vol, nis_stream stream) {
+    if (!ctx) return NIS_ERR_INVALID_ARG;
+    Volume *v = lookup(ctx->vols, vol);
+    if (!v) return fail(ctx, NIS_ERR_NOT_READY, "unknown or released volume handle");
+    DeviceGuard g(ctx->device);
+    return build_pyramid_impl(ctx, *v, reinterpret_cast<cudaStream_t>(stream));
+}
+
+nis_status nis_build_transmittance(nis_ctx *ctx, nis_volume vol, const float light_dir[3],
+                                   float lambda, nis_stream stream, nis_light *out) {
+    if (!ctx) return NIS_ERR_INVALID_ARG;
+    if (!light_dir || !out) return fail(ctx, NIS_ERR_INVALID_ARG, "NULL light_dir or out");
+    if (!(lambda > 0.f && lambda <= 1.f)) return fail(ctx, NIS_ERR_INVALID_ARG, "lambda must lie in (0, 1]");
+    Volume *v = lookup(ctx->vols, vol);
+    if (!v) return fail(ctx, NIS_ERR_NOT_READY, "unknown or released volume handle");
+    double l[3] = {light_dir[0], light_dir[1], light_dir[2]};
+    double nl = std::sqrt(l[0] * l[0] + l[1] * l[1] + l[2] * l[2]);
+    if (!(nl > 0) || !std::isfinite(nl)) return fail(ctx, NIS_ERR_INVALID_ARG, "light_dir must be finite and non-zero");
+    float dir[3] = {(float)(l[0] / nl), (float)(l[1] / nl), (float)(l[2] / nl)};
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    nis_status st;
+    if (!v->pyramid && (st = build_pyramid_impl(ctx, *v, s))) return st;
+    nis_handle h = 0;
+    for (auto &kv : ctx->lights)
+        if (kv.second.vol == vol && kv.second.lambda == lambda &&
+            std::memcmp(kv.second.dir, dir, sizeof(dir)) == 0) { h = kv.first; break; }
+    if (!h) {
+        Light L;
+        L.vol = vol;
+        std::memcpy(L.dir, dir, sizeof(dir));
+        L.lambda = lambda;
+        if ((st = dev_alloc_t(ctx, v->total, &L.data, s))) return st;
+        h = ctx->next++;
+        ctx->lights[h] = L;
+    }
+    Light &L = ctx->lights[h];
+    // u = -l points toward the light
+    for (int m = 0; m < v->levels; ++m) {
+        ProfScope ps(ctx, "march", s);
+        launch_march(v->data + v->off[m], v->sizes[m], m, -dir[0], -dir[1], -dir[2], lambda,
+                     L.data + v->off[m], s);
+    }
+    NIS_CUDA(cudaGetLastError());
+    *out = h;
+    return NIS_OK;
+}
+
+nis_status nis_load_weights(nis_ctx *ctx, const void *blob, size_t bytes, int precision,
+                            nis_stream stream, nis_weights *out) {
+    if (!ctx) return NIS_ERR_INVALID_ARG;
+    if (!blob || !out) return fail(ctx, NIS_ERR_INVALID_ARG, "NULL blob or out");
+    if (precision != NIS_PREC_F32)
+        return fail(ctx, NIS_ERR_UNIMPLEMENTED, "only NIS_PREC_F32 is available");
+    if (bytes < 80) return fail(ctx, NIS_ERR_BAD_BLOB, "blob shorter than its header");
+    uint32_t hd[16];
+    uint64_t n_floats, checksum;
+    std::memcpy(hd, blob, 64);
+    std::memcpy(&n_floats, static_cast<const char *>(blob) + 64, 8);
+    std::memcpy(&checksum, static_cast<const char *>(blob) + 72, 8);
+    WeightOffsets o;
+    weight_offsets(&o);
+    const uint32_t expect[13] = {0x5753494Eu, 1u, 0u, 80u, (uint32_t)kLayers, (uint32_t)kDiffuse,
+                                 (uint32_t)kLat, (uint32_t)kCnnCh, 2u, (uint32_t)kWidth,
+                                 (uint32_t)kCfg, 3u, (uint32_t)kDT};
+    for (int i = 0; i < 13; ++i)
+        if (hd[i] != expect[i])
+            return fail(ctx, NIS_ERR_BAD_BLOB, "blob header field " + std::to_string(i) + " mismatch");
+    if (n_floats != o.total || bytes != 80 + 4 * n_floats)
+        return fail(ctx, NIS_ERR_BAD_BLOB, "blob size does not match the network shape");
+    const uint32_t *words = reinterpret_cast<const uint32_t *>(static_cast<const char *>(blob) + 80);
+    uint64_t sum = 0;
+    for (uint64_t i = 0; i < n_floats; ++i) sum += (uint64_t)words[i] * (2 * i + 1);
+    if (sum != checksum) return fail(ctx, NIS_ERR_BAD_BLOB, "blob checksum mismatch");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Weights w;
+    w.precision = precision;
+    w.off = o;
+    nis_status st = dev_alloc_t(ctx, o.total, &w.f32, s);
+    if (st) return st;
+    cudaError_t e = cudaMemcpyAsync(w.f32, words, o.total * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the caller may free the blob
+    if (e != cudaSuccess) { dev_free(ctx, w.f32); return cuda_fail(ctx, e, "weights upload"); }
+    nis_handle h = ctx->next++;
+    ctx->weights[h] = w;
+    *out = h;
+    return NIS_OK;
+}
+
+nis_status nis_shade_points_debug(nis_ctx *ctx, nis_volume vol, nis_light light, nis_weights w,
+                                  const nis_material *m, const float *d_points,
+                                  const float *d_omega, int n, float *d_rgb_out,
+                                  const nis_debug_out *dbg, nis_stream stream) {
+    if (!ctx) return NIS_ERR_INVALID_ARG;
+    if (n < 0) return fail(ctx, NIS_ERR_INVALID_ARG, "n must be >= 0");
+    if (n > 0 && (!d_points || !d_omega || !d_rgb_out))
+        return fail(ctx, NIS_ERR_INVALID_ARG, "NULL points, omega or output");
+    nis_status st = check_material(ctx, m);
+    if (st) return st;
+    Volume *pv; Light *pl; Weights *pw;
+    if ((st = resolve(ctx, vol, light, w, &pv, &pl, &pw))) return st;
+    if (n == 0) return NIS_OK;
+    DeviceGuard g(ctx->device);
+    return shade_impl(ctx, *pv, *pl, *pw, m, d_points, d_omega, n, d_rgb_out, dbg,
+                      reinterpret_cast<cudaStream_t>(stream));
+}
+
+nis_status nis_shade_points(nis_ctx *ctx, nis_volume vol, nis_light light, nis_weights w,
+                            const nis_material *m, const float *d_points, const float *d_omega,
+                            int n, float *d_rgb_out, nis_stream stream) {
+    return nis_shade_points_debug(ctx, vol, light, w, m, d_points, d_omega, n, d_rgb_out, nullptr,
+                                  stream);
+}
+
+nis_status nis_find_hits(nis_ctx *ctx, nis_volume vol, const nis_camera *cam, int *d_hit,
+                         float *d_points, float *d_omega, nis_stream stream) {
+    if (!ctx) return NIS_ERR_INVALID_ARG;
+    if (!d_hit || !d_points || !d_omega) return fail(ctx, NIS_ERR_INVALID_ARG, "NULL output");
+    Volume *v = lookup(ctx->vols, vol);
+    if (!v) return fail(ctx, NIS_ERR_NOT_READY, "unknown or released volume handle");
+    CameraArgs c;
+    nis_status st = camera_args(ctx, cam, &c);
+    if (st) return st;
+    DeviceGuard g(ctx->device);
+    launch_find_hits(v->data, v->n, v->sigma_max, c, d_hit, d_points, d_omega, nullptr, nullptr,
+                     reinterpret_cast<cudaStream_t>(stream));
+    NIS_CUDA(cudaGetLastError());
+    return NIS_OK;
+}
+
+nis_status nis_render_frame(nis_ctx *ctx, nis_volume vol, nis_light light, nis_weights w,
+                            const nis_material *m, const nis_camera *cam, float *d_rgb_out,
+                            nis_stream stream) {
+    if (!ctx) return NIS_ERR_INVALID_ARG;
+    if (!d_rgb_out) return fail(ctx, NIS_ERR_INVALID_ARG, "NULL output");
+    nis_status st = check_material(ctx, m);
+    if (st) return st;
+    CameraArgs c;
+    if ((st = camera_args(ctx, cam, &c))) return st;
+    Volume *pv; Light *pl; Weights *pw;
+    if ((st = resolve(ctx, vol, light, w, &pv, &pl, &pw))) return st;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Workspace &ws = ctx->ws;
+    int pixels = c.width * c.height;
+    if (ws.hit_cap < pixels) {
+        dev_free(ctx, ws.hit_pts); dev_free(ctx, ws.hit_omega); dev_free(ctx, ws.hit_rgb);
+        dev_free(ctx, ws.hit_pix); dev_free(ctx, ws.hit_count);
+        ws.hit_pts = ws.hit_omega = ws.hit_rgb = nullptr;
+        ws.hit_pix = ws.hit_count = nullptr;
+        ws.hit_cap = 0;
+        if ((st = dev_alloc_t(ctx, 3 * (size_t)pixels, &ws.hit_pts, s))) return st;
+        if ((st = dev_alloc_t(ctx, 3 * (size_t)pixels, &ws.hit_omega, s))) return st;
+        if ((st = dev_alloc_t(ctx, 3 * (size_t)pixels, &ws.hit_rgb, s))) return st;
+        if ((st = dev_alloc_t(ctx, (size_t)pixels, &ws.hit_pix, s))) return st;
+        if ((st = dev_alloc_t(ctx, 1, &ws.hit_count, s))) return st;
+        ws.hit_cap = pixels;
+    }
+    NIS_CUDA(cudaMemsetAsync(ws.hit_count, 0, sizeof(int), s));
+    {
+        ProfScope ps(ctx, "hits", s);
+        launch_find_hits(pv->data, pv->n, pv->sigma_max, c, nullptr, ws.hit_pts, ws.hit_omega,
+                         ws.hit_pix, ws.hit_count, s);
+    }
+    NIS_CUDA(cudaGetLastError());
+    NIS_CUDA(cudaMemcpyAsync(ws.host_count, ws.hit_count, sizeof(int), cudaMemcpyDeviceToHost, s));
+    NIS_CUDA(cudaStreamSynchronize(s));
+    int count = *ws.host_count;
+    NIS_CUDA(cudaMemsetAsync(d_rgb_out, 0, sizeof(float) * 3 * (size_t)pixels, s));
+    if (count > 0) {
+        if ((st = shade_impl(ctx, *pv, *pl, *pw, m, ws.hit_pts, ws.hit_omega, count, ws.hit_rgb,
+                             nullptr, s)))
+            return st;
+        {
+            ProfScope ps(ctx, "other", s);
+            launch_scatter_rgb(ws.hit_rgb, ws.hit_pix, count, d_rgb_out, s);
+        }
+        NIS_CUDA(cudaGetLastError());
+    }
+    return NIS_OK;
+}
+
+nis_status nis_release(nis_ctx *ctx, nis_handle h) {
+    if (!ctx) return NIS_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (Volume *v = lookup(ctx->vols, h)) {
+        cudaDeviceSynchronize();
+        std::vector<nis_handle> dead;
+        for (auto &kv : ctx->lights)
+            if (kv.second.vol == h) { dev_free(ctx, kv.second.data); dead.push_back(kv.first); }
+        for (nis_handle d : dead) ctx->lights.erase(d);
+        dev_free(ctx, v->data);
+        dev_free(ctx, v->sigma_max);
+        dev_free(ctx, v->staging);
+        ctx->vols.erase(h);
+        return NIS_OK;
+    }
+    if (Light *l = lookup(ctx->lights, h)) {
+        cudaDeviceSynchronize();
+        dev_free(ctx, l->data);
+        ctx->lights.erase(h);
+        return NIS_OK;
+    }
+    if (Weights *w = lookup(ctx->weights, h)) {
+        cudaDeviceSynchronize();
+        dev_free(ctx, w->f32);
+        ctx->weights.erase(h);
+        return NIS_OK;
+    }
+    return fail(ctx, NIS_ERR_INVALID_ARG, "unknown handle");
+}
+
+nis_status nis_sync(nis_ctx *ctx, nis_stream stream, int timeout_ms) {
+    if (!ctx) return NIS_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    auto start = std::chrono::steady_clock::now();
+    while (true) {
+        cudaError_t e = cudaStreamQuery(s);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) return cuda_fail(ctx, e, "stream");
+        if (timeout_ms > 0 &&
+            std::chrono::steady_clock::now() - start > std::chrono::milliseconds(timeout_ms))
+            return fail(ctx, NIS_ERR_TIMEOUT, "stream did not finish within the timeout");
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    unsigned err = 0;
+    NIS_CUDA(cudaMemcpy(&err, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (err) {
+        NIS_CUDA(cudaMemset(ctx->d_err, 0, sizeof(unsigned)));
+        if (err & kErrBadDensity)
+            return fail(ctx, NIS_ERR_BAD_DATA, "density contained NaN, infinite or negative values");
+        return fail(ctx, NIS_ERR_BAD_DATA, "a kernel bounds check failed");
+    }
+    return NIS_OK;
+}
+
+nis_status nis_volume_info(nis_ctx *ctx, nis_volume vol, int *levels, int sizes[16],
+                           float *sigma_max) {
+    if (!ctx) return NIS_ERR_INVALID_ARG;
+    Volume *v = lookup(ctx->vols, vol);
+    if (!v) return fail(ctx, NIS_ERR_NOT_READY, "unknown or released volume handle");
+    DeviceGuard g(ctx->device);
+    if (levels) *levels = v->levels;
+    if (sizes) for (int m = 0; m < kMaxLevels; ++m) sizes[m] = m < v->levels ? v->sizes[m] : 0;
+    if (sigma_max) NIS_CUDA(cudaMemcpy(sigma_max, v->sigma_max, sizeof(float), cudaMemcpyDeviceToHost));
+    return NIS_OK;
+}
+
+nis_status nis_copy_level(nis_ctx *ctx, nis_volume vol, int level, float *d_dst,
+                          nis_stream stream) {
+    if (!ctx) return NIS_ERR_INVALID_ARG;
+    Volume *v = lookup(ctx->vols, vol);
+    if (!v) return fail(ctx, NIS_ERR_NOT_READY, "unknown or released volume handle");
+    if (level < 0 || level >= v->levels || !d_dst) return fail(ctx, NIS_ERR_INVALID_ARG, "bad level or NULL dst");
+    DeviceGuard g(ctx->device);
+    size_t n = (size_t)v->sizes[level] * v->sizes[level] * v->sizes[level];
+    NIS_CUDA(cudaMemcpyAsync(d_dst, v->data + v->off[level], n * 4, cudaMemcpyDeviceToDevice,
+                             reinterpret_cast<cudaStream_t>(stream)));
+    return NIS_OK;
+}
+
+nis_status nis_copy_transmittance(nis_ctx *ctx, nis_light light, int level, float *d_dst,
+                                  nis_stream stream) {
+    if (!ctx) return NIS_ERR_INVALID_ARG;
+    Light *l = lookup(ctx->lights, light);
+    if (!l) return fail(ctx, NIS_ERR_NOT_READY, "unknown or released light handle");
+    Volume *v = lookup(ctx->vols, l->vol);
+    if (level < 0 || level >= v->levels || !d_dst) return fail(ctx, NIS_ERR_INVALID_ARG, "bad level or NULL dst");
+    DeviceGuard g(ctx->device);
+    size_t n = (size_t)v->sizes[level] * v->sizes[level] * v->sizes[level];
+    NIS_CUDA(cudaMemcpyAsync(d_dst, l->data + v->off[level], n * 4, cudaMemcpyDeviceToDevice,
+                             reinterpret_cast<cudaStream_t>(stream)));
+    return NIS_OK;
+}
+
+nis_status nis_build_phase_table(nis_ctx *ctx, float g, float *d_dst, nis_stream stream) {
+    if (!ctx) return NIS_ERR_INVALID_ARG;
+    if (!(g > -1.f && g < 1.f)) return fail(ctx, NIS_ERR_INVALID_ARG, "g must lie in (-1, 1)");
+    DeviceGuard gd(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    float *t;
+    nis_status st = ensure_phase(ctx, g, s, &t, /*rebuild=*/true);
+    if (st) return st;
+    if (d_dst)
+        NIS_CUDA(cudaMemcpyAsync(d_dst, t, sizeof(float) * kAlpha * kPhaseSets * kLat,
+                                 cudaMemcpyDeviceToDevice, s));
+    return NIS_OK;
+}
+
+nis_status nis_update_volume(nis_ctx *ctx, nis_volume vol, const void *density, int dtype,
+                             int src_is_device, float sigma_scale, nis_stream stream) {
+    if (!ctx) return NIS_ERR_INVALID_ARG;
+    if (!density) return fail(ctx, NIS_ERR_INVALID_ARG, "NULL density");
+    if (dtype != NIS_DTYPE_F32 && dtype != NIS_DTYPE_F16)
+        return fail(ctx, NIS_ERR_INVALID_ARG, "dtype must be F32 or F16");
+    if (!(sigma_scale >= 0.f) || !std::isfinite(sigma_scale))
+        return fail(ctx, NIS_ERR_INVALID_ARG, "sigma_scale must be finite and >= 0");
+    Volume *v = lookup(ctx->vols, vol);
+    if (!v) return fail(ctx, NIS_ERR_NOT_READY, "unknown or released volume handle");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    size_t count = (size_t)v->n * v->n * v->n;
+    size_t bytes = count * (dtype == NIS_DTYPE_F16 ? 2 : 4);
+    const void *src = density;
+    if (!src_is_device) {
+        cudaPointerAttributes attr{};
+        cudaError_t e = cudaPointerGetAttributes(&attr, density);
+        if (e != cudaSuccess) cudaGetLastError();
+        void *mapped = nullptr;
+        if (e == cudaSuccess && attr.type == cudaMemoryTypeHost &&
+            cudaHostGetDevicePointer(&mapped, const_cast<void *>(density), 0) == cudaSuccess) {
+            src = mapped;                       // page-locked: the kernel reads it in place
+        } else {
+            cudaGetLastError();
+            if (v->staging_bytes < bytes) {
+                dev_free(ctx, v->staging);
+                v->staging = nullptr;
+                v->staging_bytes = 0;
+                nis_status st = dev_alloc(ctx, bytes, &v->staging, s);
+                if (st) return st;
+                v->staging_bytes = bytes;
+            }
+            NIS_CUDA(cudaMemcpyAsync(v->staging, density, bytes, cudaMemcpyHostToDevice, s));
+            src = v->staging;
+        }
+    }
+    {
+        ProfScope ps(ctx, "other", s);
+        launch_convert_density(src, dtype, sigma_scale, count, v->data, ctx->d_err, v->sigma_max, s);
+    }
+    NIS_CUDA(cudaGetLastError());
+    v->pyramid = false;
+    return NIS_OK;
+}
+
+nis_status nis_profile(nis_ctx *ctx, int enable) {
+    if (!ctx) return NIS_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (enable) {
+        cudaDeviceSynchronize();
+        for (auto &kv : ctx->prof)
+            for (auto &e : kv.second) {
+                ctx->event_pool.push_back(e.first);
+                ctx->event_pool.push_back(e.second);
+            }
+        ctx->prof.clear();
+    }
+    ctx->prof_on = enable != 0;
+    return NIS_OK;
+}
+
+nis_status nis_profile_read(nis_ctx *ctx, const char *family, double *total_ms, int *launches) {
+    if (!ctx) return NIS_ERR_INVALID_ARG;
+    if (!family || !total_ms || !launches) return fail(ctx, NIS_ERR_INVALID_ARG, "NULL argument");
+    DeviceGuard g(ctx->device);
+    *total_ms = 0.0;
+    *launches = 0;
+    auto it = ctx->prof.find(family);
+    if (it == ctx->prof.end()) return NIS_OK;
+    for (auto &e : it->second) {
+        NIS_CUDA(cudaEventSynchronize(e.second));
+        float ms = 0.f;
+        NIS_CUDA(cudaEventElapsedTime(&ms, e.first, e.second));
+        *total_ms += ms;
+        ++*launches;
+    }
+    return NIS_OK;
+}
+
+uint64_t nis_kernel_launches(void) { return g_launches.load(); }
+
+}  // extern "C"

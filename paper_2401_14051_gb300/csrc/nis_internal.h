@@ -1,0 +1,181 @@
+// Internal declarations shared by the library's translation units: device-side helpers
+// (voxel lookups, geometry), the constants of the method, and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "nis.h"
+
+namespace nis {
+
+// ---- method constants (Sec. III.B-C) ----------------------------------------------------
+constexpr int kLayers = 12;          // 8 diffuse + 4 highlight template layers
+constexpr int kDiffuse = 8;
+constexpr int kHighlight = 4;
+constexpr int kLatA = 5, kLatB = 5, kLatC = 9;
+constexpr int kLat = 225;            // lattice points per layer
+constexpr int kPhaseSets = 5;        // all diffuse layers share one set; one per highlight
+constexpr int kAlpha = 1024;         // alpha nodes of the phase table
+constexpr int kRings = 16;           // cap quadrature: rings (angle midpoints) ...
+constexpr int kAzim = 24;            // ... times azimuths
+constexpr float kTauMax = 30.0f;     // march stops past this scaled optical depth
+constexpr float kHitFraction = 0.05f;
+constexpr int kWidth = 200;          // backbone width
+constexpr int kCnnCh = 16;
+constexpr int kDT = 80;              // CNN output per layer
+constexpr int kCfg = 5;              // [g, albedo rgb, alpha]
+constexpr int kMaxLevels = 16;
+
+// ---- weight blob layout ------------------------------------------------------------------
+struct WeightOffsets {                // float offsets into the FP32 weight buffer
+    size_t cnn_w1[kLayers], cnn_b1[kLayers], cnn_w2[kLayers], cnn_b2[kLayers];
+    size_t se_w1[kLayers], se_b1[kLayers], se_w2[kLayers], se_b2[kLayers];
+    size_t blk_w1[3][kLayers], blk_b1[3][kLayers], blk_w2[3][kLayers], blk_b2[3][kLayers];
+    size_t mrg_w[3], mrg_b[3];
+    size_t head_w[3], head_b[3];
+    size_t total;
+};
+void weight_offsets(WeightOffsets *o);   // fills the fixed blob order
+inline int feat_dim(int type) { return type == 2 ? kDT : kLat; }
+
+// ---- device helpers ---------------------------------------------------------------------
+struct Level {                       // one voxel-centred cubic grid level
+    const float *data;
+    int n;
+};
+
+// Trilinear lookup with clamp-to-edge indices (used by the march, inside the cube).
+__device__ __forceinline__ float sample_clamped(const float *__restrict__ g, int n, float x,
+                                                float y, float z) {
+    const float hi = (float)(n - 1);
+    float gx = fminf(fmaxf(x * n - 0.5f, 0.0f), hi);
+    float gy = fminf(fmaxf(y * n - 0.5f, 0.0f), hi);
+    float gz = fminf(fmaxf(z * n - 0.5f, 0.0f), hi);
+    const int top = n > 1 ? n - 2 : 0;
+    int ix = min((int)floorf(gx), top), iy = min((int)floorf(gy), top),
+        iz = min((int)floorf(gz), top);
+    float fx = gx - ix, fy = gy - iy, fz = gz - iz;
+    int dx = (ix + 1 < n) ? 1 : 0;
+    int dy = (iy + 1 < n) ? n : 0;
+    int dz = (iz + 1 < n) ? n * n : 0;
+    const float *p = g + ((size_t)iz * n + iy) * n + ix;
+    float c00 = __ldg(p) + fx * (__ldg(p + dx) - __ldg(p));
+    float c01 = __ldg(p + dy) + fx * (__ldg(p + dy + dx) - __ldg(p + dy));
+    float c10 = __ldg(p + dz) + fx * (__ldg(p + dz + dx) - __ldg(p + dz));
+    float c11 = __ldg(p + dz + dy) + fx * (__ldg(p + dz + dy + dx) - __ldg(p + dz + dy));
+    float c0 = c00 + fy * (c01 - c00);
+    float c1 = c10 + fy * (c11 - c10);
+    return c0 + fz * (c1 - c0);
+}
+
+// Trilinear lookup where voxels outside the grid read `border` (template gathers, hits).
+__device__ __forceinline__ float sample_border(const float *__restrict__ g, int n, float x,
+                                               float y, float z, float border) {
+    float gx = x * n - 0.5f, gy = y * n - 0.5f, gz = z * n - 0.5f;
+    float flx = floorf(gx), fly = floorf(gy), flz = floorf(gz);
+    float fx = gx - flx, fy = gy - fly, fz = gz - flz;
+    // coordinates far outside: clamp the integer base so index math cannot overflow
+    int ix = (int)fminf(fmaxf(flx, -2.0f), (float)n + 1.0f);
+    int iy = (int)fminf(fmaxf(fly, -2.0f), (float)n + 1.0f);
+    int iz = (int)fminf(fmaxf(flz, -2.0f), (float)n + 1.0f);
+    float v[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        int cx = ix + (c & 1), cy = iy + ((c >> 1) & 1), cz = iz + (c >> 2);
+        bool in = (unsigned)cx < (unsigned)n && (unsigned)cy < (unsigned)n &&
+                  (unsigned)cz < (unsigned)n;
+        v[c] = in ? __ldg(g + ((size_t)cz * n + cy) * n + cx) : border;
+    }
+    float c00 = v[0] + fx * (v[1] - v[0]);
+    float c01 = v[2] + fx * (v[3] - v[2]);
+    float c10 = v[4] + fx * (v[5] - v[4]);
+    float c11 = v[6] + fx * (v[7] - v[6]);
+    float c0 = c00 + fy * (c01 - c00);
+    float c1 = c10 + fy * (c11 - c10);
+    return c0 + fz * (c1 - c0);
+}
+
+// Distance from (x, y, z) along unit u to the boundary of the unit cube (>= 0).
+__device__ __forceinline__ float exit_distance(float x, float y, float z, float ux, float uy,
+                                               float uz) {
+    float t = 3.0e38f;
+    if (ux > 0.f) t = fminf(t, (1.f - x) / ux); else if (ux < 0.f) t = fminf(t, -x / ux);
+    if (uy > 0.f) t = fminf(t, (1.f - y) / uy); else if (uy < 0.f) t = fminf(t, -y / uy);
+    if (uz > 0.f) t = fminf(t, (1.f - z) / uz); else if (uz < 0.f) t = fminf(t, -z / uz);
+    return fmaxf(t, 0.f);
+}
+
+// ---- device-side error word bits (read back by nis_sync) ----------------------------------
+constexpr unsigned kErrBadDensity = 1u;
+constexpr unsigned kErrBadIndex = 2u;
+
+// ---- launchers (all enqueue on `s`) ----------------------------------------------------------
+void note_launch();                  // counts every kernel launch of the library
+// volume
+void launch_convert_density(const void *src, int dtype, float scale, size_t count,
+                            float *dst, unsigned *err, float *sigma_max, cudaStream_t s);
+void launch_downsample(const float *src, int n, float *dst, int m, cudaStream_t s);
+// transmittance of one level
+void launch_march(const float *level, int n, int m, float ux, float uy, float uz, float lam,
+                  float *out, cudaStream_t s);
+// phase table [kAlpha][kPhaseSets][kLat]
+void launch_phase_table(float g, float *table, cudaStream_t s);
+
+struct PyramidView {                 // device pointers of all levels of a pyramid
+    const float *lv[kMaxLevels];
+    int n[kMaxLevels];
+    int levels;
+};
+
+struct GatherArgs {
+    PyramidView rho, T;
+    const float *table;              // phase table of the material's g
+    const float *points, *omega;     // [n][3]
+    int count;
+    float lx, ly, lz;                // unit light propagation direction
+    float g;
+    float albedo[3];
+    const float *se;                 // FP32 weights base; SE offsets below
+    size_t se_w1[kLayers], se_b1[kLayers], se_w2[kLayers], se_b2[kLayers];
+    float *H_rho, *H_T, *H_f;        // [count][12][225]
+    float *v;                        // [count][12][8] (may be null)
+    float *w_se;                     // [count][12][3]
+    float *cfg;                      // [count][5]
+};
+void launch_gather(const GatherArgs &a, cudaStream_t s);
+
+void launch_cnn_f32(const float *H_T, int count, const float *wbase, const WeightOffsets &o,
+                    float *X_T, cudaStream_t s);
+
+// One dense layer out[r][j] = epilogue(sum_k A[r][k] W[j][k] + b[j]) over rows r < count.
+struct FcArgs {
+    int mode;                        // kFcFeat, kFcSum, kFcCat
+    int count, K, N;
+    // kFcFeat: A[r] = [ w_se[r*36 + layer*3 + type] * X[r*ldx + 0..d), cfg[r*5 + 0..5) ]
+    const float *X; int ldx; int d; const float *w_se; int layer, type; const float *cfg;
+    // kFcSum: A[r] = a0[r] + a1[r] (a0 may be null);  kFcCat: A[r] = [a0[r], a1[r], a2[r]]
+    const float *a0, *a1, *a2; int seg;
+    const float *W, *b;
+    int relu;                        // apply ReLU to acc + b
+    const float *resid;              // if set, out = act + resid[r][j]
+    float *out; int ldo;
+    // decode epilogue (last layer): rgb = intensity * albedo^4 * expm1(acc + b)
+    int decode; float dec_scale[3]; float *y_out;
+};
+constexpr int kFcFeat = 0, kFcSum = 1, kFcCat = 2;
+void launch_fc_f32(const FcArgs &a, cudaStream_t s);
+
+struct CameraArgs {
+    int type, width, height;
+    float eye[3], fwd[3], right[3], up[3];
+    float tan_half, aspect, half_h;
+};
+void launch_find_hits(const float *rho0, int n, const float *sigma_max, const CameraArgs &c,
+                      int *hit_flag, float *points, float *omega, int *pix_index,
+                      int *counter, cudaStream_t s);
+void launch_scatter_rgb(const float *rgb, const int *pix_index, int count, float *image,
+                        cudaStream_t s);
+
+}  // namespace nis

@@ -1,0 +1,345 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, step by step and end
+to end, on the 64^3 fBm workload and on ragged / degenerate cases.
+
+Tolerances (FP32 against FP64; derivations in the comments of each constant).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+# A box mean of 8 non-negative FP32 values costs <= 4 roundings relative to the result;
+# 11 levels compound to <= 44 * 2^-24 = 2.6e-6.
+RTOL_PYRAMID = 1e-5
+# Sample positions carry ~1e-6 voxel of FP32 position error at 64^3 and the optical
+# depth sums ~100 samples: optical depth to ~1e-5 relative plus a small absolute part.
+RTOL_TAU, ATOL_TAU = 2e-5, 2e-6
+# Gathered values: position error ~1e-5 voxel times the density jump between voxels
+# (<= sigma_max), plus FP32 rounding of the lerps; scaled by each feature's range.
+RTOL_FEAT, ATOL_FEAT_REL = 1e-5, 2e-5
+# Network outputs: ~60 dependent FP32 layers with sums of <= 600 terms; errors scale with
+# the activation magnitude, so they are compared against the output range.
+RTOL_OUT = 1e-4
+# The FP32 path must match the FP64 oracle at 1e-4 relative error.  For outputs near
+# zero a relative error is ill-conditioned (the network's FP32 sums carry absolute error
+# proportional to their terms, ~1e-6 of the output range), so the denominator is floored
+# at 1 % of the channel's largest magnitude.
+REL_FLOOR = 1e-2
+
+
+def rel_err(a, b, floor_frac=REL_FLOOR):
+    b = np.asarray(b, dtype=np.float64)
+    a = np.asarray(a, dtype=np.float64)
+    floor = floor_frac * np.abs(b).max(axis=0, keepdims=True)
+    return np.abs(a - b) / np.maximum(np.abs(b), np.maximum(floor, 1e-30))
+
+
+@pytest.fixture(scope="module")
+def nis():
+    from paper_2401_14051_gb300 import build, nis as N
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    return N
+
+
+@pytest.fixture(scope="module")
+def ctx(nis):
+    c = nis.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def w1():
+    """Workload 1: 64^3 fBm, g 0.6, albedo 0.99, seeded light, view, weights."""
+    cfg = synth.config(1)
+    vol = cfg["volume"]()
+    levels, tl, table = O.prepare(vol, cfg["light"], cfg["material"]["g"])
+    weights = synth.make_weights(cfg["weights_seed"], cfg["sigma_max"])
+    return {"cfg": cfg, "vol": vol, "levels": levels, "T": tl, "table": table,
+            "weights": weights, "blob": synth.pack_weights(weights)}
+
+
+@pytest.fixture(scope="module")
+def gpu1(ctx, w1):
+    cfg = w1["cfg"]
+    v = ctx.upload_volume(w1["vol"])
+    ctx.build_pyramid(v)
+    l = ctx.build_transmittance(v, cfg["light"], 0.6)
+    wt = ctx.load_weights(w1["blob"])
+    ctx.sync(timeout_ms=60000)
+    return {"vol": v, "light": l, "weights": wt}
+
+
+def _points(n, seed):
+    p, om = synth.shading_points(n, seed, -0.05, 1.05)
+    return p, om
+
+
+# ---- step 1: pyramid -------------------------------------------------------------------
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 37, 64])
+def test_pyramid_matches_oracle(ctx, n):
+    vol = synth.fbm_volume(n, 20 + n, 9.0) if n > 3 else \
+        np.random.default_rng(n).uniform(0, 5, (n, n, n)).astype(np.float32)
+    h = ctx.upload_volume(vol)
+    ctx.build_pyramid(h)
+    ref = O.build_pyramid(vol)
+    levels, sizes, smax = ctx.volume_info(h)
+    assert sizes == O.level_sizes(n)
+    ctx.sync(timeout_ms=30000)
+    assert smax == pytest.approx(float(vol.max()), rel=0, abs=0)
+    for m in range(levels):
+        got = ctx.copy_level(h, m).cpu().numpy()
+        np.testing.assert_allclose(got, ref[m], rtol=RTOL_PYRAMID, atol=1e-30)
+    ctx.release(h)
+
+
+def test_pyramid_and_march_from_float16(ctx):
+    vol = synth.fbm_volume(16, 3, 4.0).astype(np.float16)
+    h = ctx.upload_volume(vol)
+    ctx.build_pyramid(h)
+    ref = O.build_pyramid(vol.astype(np.float64))
+    for m in range(len(ref)):
+        np.testing.assert_allclose(ctx.copy_level(h, m).cpu().numpy(), ref[m], rtol=RTOL_PYRAMID)
+    ctx.release(h)
+
+
+# ---- step 2: transmittance ------------------------------------------------------------
+def _check_T(got, ref):
+    tau_ref = -np.log(ref)
+    tau_got = -np.log(np.maximum(got, 1e-45))
+    live = tau_ref < 29.0                  # past the early out both sides sit below e^-29
+    err = np.abs(tau_got - tau_ref)[live]
+    bound = (RTOL_TAU * tau_ref + ATOL_TAU)[live]
+    assert np.all(err <= bound), f"max tau err {err.max():.3g}, worst ratio {(err / bound).max():.3g}"
+    assert np.all(got[~live] <= math.exp(-28.0))
+
+
+def test_transmittance_matches_oracle(ctx, w1, gpu1):
+    for m, ref in enumerate(w1["T"]):
+        _check_T(ctx.copy_transmittance(gpu1["light"], gpu1["vol"], m).cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("n,seed", [(37, 1), (5, 2), (1, 3)])
+def test_transmittance_odd_grids(ctx, n, seed):
+    vol = np.random.default_rng(seed).uniform(0, 20, (n, n, n)).astype(np.float32)
+    l = synth.unit_vector(seed + 30)
+    h = ctx.upload_volume(vol)
+    lt = ctx.build_transmittance(h, l, 0.6)
+    ref = O.build_transmittance(O.build_pyramid(vol), l)
+    for m in range(len(ref)):
+        _check_T(ctx.copy_transmittance(lt, h, m).cpu().numpy(), ref[m])
+    ctx.release(h)
+
+
+def test_homogeneous_transmittance_closed_form(ctx):
+    n, sigma = 32, 3.0
+    l = synth.unit_vector(77)
+    h = ctx.upload_volume(np.full((n, n, n), sigma, dtype=np.float32))
+    lt = ctx.build_transmittance(h, l, 1.0)
+    got = ctx.copy_transmittance(lt, h, 0).cpu().numpy()
+    d = O.exit_distance(O.voxel_centres(n), -l)
+    np.testing.assert_allclose(got, np.exp(-sigma * d), rtol=5e-6, atol=1e-7)
+    ctx.release(h)
+
+
+def test_axis_light_is_exact_slab_sum(ctx):
+    n = 16
+    sig = np.random.default_rng(5).uniform(0, 3, n)
+    vol = np.broadcast_to(sig[:, None, None], (n, n, n)).astype(np.float32).copy()   # sigma(z)
+    h = ctx.upload_volume(vol)
+    lt = ctx.build_transmittance(h, [0.0, 0.0, -1.0], 1.0)    # light travels -z: u = +z
+    got = ctx.copy_transmittance(lt, h, 0).cpu().numpy()[:, 0, 0]
+    s32 = sig.astype(np.float32).astype(np.float64)
+    tau = np.array([(0.5 * s32[k] + s32[k + 1:].sum()) / n for k in range(n)])
+    np.testing.assert_allclose(got, np.exp(-tau), rtol=2e-6)
+    ctx.release(h)
+
+
+# ---- phase table ------------------------------------------------------------------------
+def test_phase_table_matches_oracle(ctx, w1):
+    got = ctx.build_phase_table(0.6).cpu().numpy()        # [alpha][set][point]
+    ref = w1["table"]                                      # [set][point][alpha]
+    cols = np.r_[0:1024:17, 1023]
+    np.testing.assert_allclose(got[cols].transpose(1, 2, 0), ref[:, :, cols], rtol=2e-5)
+    assert got[0, 0, 112] == pytest.approx(1 / (16 * math.pi ** 2), rel=1e-6)
+
+
+@pytest.mark.parametrize("g", [-0.5, 0.0, 0.9])
+def test_phase_table_other_g(ctx, g):
+    got = ctx.build_phase_table(g).cpu().numpy()
+    a = O.alpha_nodes()
+    for s in (0, 4):
+        for j in (0, 300, 1023):
+            ref = O.phase_feature(O.phase_set_offsets(s), a[j], g)
+            np.testing.assert_allclose(got[j, s], ref, rtol=3e-5)
+
+
+# ---- steps 3-6 ---------------------------------------------------------------------------
+def _oracle_features(w1, p, om):
+    cfg = w1["cfg"]
+    return O.gather(p, om, cfg["light"], w1["levels"], w1["T"], w1["table"], cfg["material"]["g"])
+
+
+def _ambiguous(w1, p):
+    """Points whose highlight mip choice sits within 1e-4 of a rounding tie."""
+    _, _, _, _, margin = O.layer_geometry(p.astype(np.float64), w1["cfg"]["light"], 64)
+    return margin.min(axis=1) < 1e-4
+
+
+def _check_feat(got, ref, scale, name):
+    err = np.abs(got - ref)
+    bound = RTOL_FEAT * np.abs(ref) + ATOL_FEAT_REL * scale
+    worst = (err / bound).max()
+    assert worst <= 1.0, f"{name}: max err {err.max():.3g}, worst ratio {worst:.3g}"
+
+
+def test_gather_and_squeeze_match_oracle(ctx, w1, gpu1):
+    p, om = _points(700, 101)
+    keep = ~_ambiguous(w1, p)
+    assert keep.mean() > 0.98
+    dev = torch.device("cuda:0")
+    r = ctx.shade_points_debug(gpu1["vol"], gpu1["light"], gpu1["weights"], w1["cfg"]["material"],
+                               torch.from_numpy(p).to(dev), torch.from_numpy(om).to(dev))
+    Hr, Ht, Hf, v = _oracle_features(w1, p[keep], om[keep])
+    g = {k: t.cpu().numpy()[keep] for k, t in r.items()}
+    _check_feat(g["H_rho"], Hr, 16.0, "H_rho")
+    _check_feat(g["H_T"], Ht, 1.0, "H_T")
+    _check_feat(g["H_f"], Hf, np.abs(Hf).max(), "H_f")
+    for q, sc in enumerate([16.0, Hf.max(), 1.0, 16.0, Hf.max(), 1.0, 1.0, math.pi]):
+        _check_feat(g["v"][..., q], v[..., q], sc, f"v[{q}]")
+    # SE, CNN and backbone checked on the GPU's own inputs: isolates each step
+    W = w1["weights"]
+    np.testing.assert_allclose(g["w_se"], O.se_weights(g["v"].astype(np.float64), W), atol=2e-6)
+    xt = O.cnn(g["H_T"].astype(np.float64), W)
+    np.testing.assert_allclose(g["X_T"], xt, rtol=1e-5, atol=1e-5 * np.abs(xt).max())
+    c = O.config_vector(0.6, [0.99] * 3, g["v"][:, 0, 7].astype(np.float64))
+    ws = g["w_se"].astype(np.float64)
+    y = O.backbone(ws[..., 0:1] * g["H_rho"], ws[..., 1:2] * g["H_f"], ws[..., 2:3] * g["X_T"], c, W)
+    np.testing.assert_allclose(g["y"], y, rtol=0, atol=RTOL_OUT * np.abs(y).max())
+    print(f"\n[parity] gather max|d| rho {np.abs(g['H_rho'] - Hr).max():.3g} "
+          f"T {np.abs(g['H_T'] - Ht).max():.3g} f {np.abs(g['H_f'] - Hf).max():.3g}; "
+          f"y max|d| {np.abs(g['y'] - y).max():.3g} of range {np.abs(y).max():.3g}")
+
+
+def test_shade_points_end_to_end(ctx, w1, gpu1):
+    p, om = _points(4096, 202)
+    keep = ~_ambiguous(w1, p)
+    dev = torch.device("cuda:0")
+    rgb = ctx.shade_points(gpu1["vol"], gpu1["light"], gpu1["weights"], w1["cfg"]["material"],
+                           torch.from_numpy(p).to(dev), torch.from_numpy(om).to(dev))
+    ctx.sync(timeout_ms=60000)
+    cfg = w1["cfg"]
+    ref = O.shade_points(p[keep], om[keep], cfg["light"], w1["levels"], w1["T"], w1["table"],
+                         w1["weights"], cfg["material"])
+    e = rel_err(rgb.cpu().numpy()[keep], ref)
+    print(f"\n[parity] shade_points 4096: max rel {e.max():.3g}, mean rel {e.mean():.3g}, "
+          f"excluded {int((~keep).sum())}")
+    assert e.max() <= 1e-4
+
+
+def test_ragged_and_degenerate_points(ctx, w1, gpu1):
+    cfg = w1["cfg"]
+    l = np.asarray(cfg["light"])
+    p = np.array([[0.5, 0.5, 0.5], [0.0, 0.0, 0.0], [1.0, 1.0, 1.0], [1.3, -0.2, 0.5],
+                  [0.2, 0.9, 0.4], [0.7, 0.1, 0.99]], dtype=np.float32)
+    om = np.array([l, -l, [0, 0, 1], [1, 0, 0], l, [0, 1, 0]], dtype=np.float64)
+    om = (om / np.linalg.norm(om, axis=1, keepdims=True)).astype(np.float32)
+    dev = torch.device("cuda:0")
+    for n in (1, 3, 6):
+        rgb = ctx.shade_points(gpu1["vol"], gpu1["light"], gpu1["weights"], cfg["material"],
+                               torch.from_numpy(p[:n]).to(dev), torch.from_numpy(om[:n]).to(dev))
+        ref = O.shade_points(p[:n], om[:n], cfg["light"], w1["levels"], w1["T"], w1["table"],
+                             w1["weights"], cfg["material"])
+        np.testing.assert_allclose(rgb.cpu().numpy(), ref, rtol=1e-4, atol=1e-4 * np.abs(ref).max())
+    empty = torch.empty((0, 3), device=dev)
+    assert ctx.shade_points(gpu1["vol"], gpu1["light"], gpu1["weights"], cfg["material"],
+                            empty, empty).shape == (0, 3)
+
+
+def test_chunked_batch_beyond_one_pass(ctx, w1, gpu1):
+    # more points than one pipeline pass (65536): the second pass is ragged
+    n = 65536 + 777
+    p, om = _points(n, 303)
+    dev = torch.device("cuda:0")
+    pt, ot = torch.from_numpy(p).to(dev), torch.from_numpy(om).to(dev)
+    cfg = w1["cfg"]
+    rgb = ctx.shade_points(gpu1["vol"], gpu1["light"], gpu1["weights"], cfg["material"], pt, ot)
+    tail = ctx.shade_points(gpu1["vol"], gpu1["light"], gpu1["weights"], cfg["material"],
+                            pt[-900:].contiguous(), ot[-900:].contiguous())
+    np.testing.assert_array_equal(rgb[-900:].cpu().numpy(), tail.cpu().numpy())
+    idx = np.r_[0:40, n - 40:n]
+    keep = idx[~_ambiguous(w1, p[idx])]
+    ref = O.shade_points(p[keep], om[keep], cfg["light"], w1["levels"], w1["T"], w1["table"],
+                         w1["weights"], cfg["material"])
+    assert rel_err(rgb.cpu().numpy()[keep], ref).max() <= 1e-4
+
+
+# ---- support: hits and the frame -------------------------------------------------------
+def test_find_hits_and_render_frame(ctx, w1, gpu1):
+    cfg = w1["cfg"]
+    cam = cfg["camera"]
+    hit, pts, om = ctx.find_hits(gpu1["vol"], cam)
+    o, d = O.camera_rays(cam)
+    rhit, rpts, margin = O.hit_search(w1["levels"][0], 16.0, o, d)
+    sure = margin > 1e-5
+    assert sure.mean() > 0.99
+    h = hit.cpu().numpy().astype(bool)
+    np.testing.assert_array_equal(h[sure], rhit[sure])
+    both = sure & rhit
+    np.testing.assert_allclose(pts.cpu().numpy()[both], rpts[both], rtol=0, atol=5e-6)
+    img = ctx.render_frame(gpu1["vol"], gpu1["light"], gpu1["weights"], cfg["material"], cam)
+    ctx.sync(timeout_ms=60000)
+    ref_img, _, _ = O.render_frame(w1["vol"], 16.0, cfg["light"], cam, w1["weights"],
+                                   cfg["material"], w1["levels"], w1["T"], w1["table"])
+    got = img.cpu().numpy()
+    amb = _ambiguous(w1, rpts.reshape(-1, 3)).reshape(h.shape)
+    ok = sure & ~amb
+    assert np.all(got[~rhit & ok] == 0)
+    e = rel_err(got[ok & rhit], ref_img[ok & rhit])
+    print(f"\n[parity] render 64x64: {int(rhit.sum())} hits, max rel {e.max():.3g}, "
+          f"excluded {int((~ok).sum())} near-threshold pixels")
+    assert e.max() <= 1e-4
+
+
+# ---- error paths (host-side) -------------------------------------------------------------
+def test_error_paths(nis, ctx, w1, gpu1):
+    bad = bytearray(w1["blob"])
+    bad[100] ^= 0xFF
+    with pytest.raises(nis.NisError) as e:
+        ctx.load_weights(bytes(bad))
+    assert e.value.status == -8
+    with pytest.raises(nis.NisError) as e:
+        ctx.load_weights(w1["blob"][:-4])
+    assert e.value.status == -8
+    vol = np.ones((4, 4, 4), np.float32)
+    vol[1, 2, 3] = np.nan
+    h = ctx.upload_volume(vol)
+    with pytest.raises(nis.NisError) as e:
+        ctx.sync(timeout_ms=30000)
+    assert e.value.status == -9
+    ctx.release(h)
+    with pytest.raises(nis.NisError) as e:
+        ctx.build_pyramid(h)
+    assert e.value.status == -2
+    with pytest.raises(nis.NisError) as e:
+        ctx.upload_volume(np.ones((4, 4, 5), np.float32))
+    assert e.value.status == -1
+    mat = dict(w1["cfg"]["material"], g=1.5)
+    dev = torch.device("cuda:0")
+    x = torch.zeros((1, 3), device=dev)
+    with pytest.raises(nis.NisError) as e:
+        ctx.shade_points(gpu1["vol"], gpu1["light"], gpu1["weights"], mat, x, x)
+    assert e.value.status == -1
+    small = nis.Context(0, budget_bytes=1 << 20)
+    with pytest.raises(nis.NisError) as e:
+        small.upload_volume(np.ones((128, 128, 128), np.float32))
+    assert e.value.status == -3
+    small.close()
