@@ -167,6 +167,32 @@ nis_status nis_render_frame(nis_ctx *ctx, nis_volume vol, nis_light light, nis_w
 nis_status nis_update_volume(nis_ctx *ctx, nis_volume vol, const void *density, int dtype,
                              int src_is_device, float sigma_scale, nis_stream stream);
 
+/* ---- allocation-free shading (no counterpart in the paper) ---------------------------
+ * Some callers cannot allocate device memory while they shade: a renderer plug-in whose
+ * host engine owns and budgets every byte of GPU memory, or a frame loop that must not call
+ * cudaMalloc (it can synchronise the device and stall the frame).  This entry point gives
+ * them the result of nis_shade_points for up to NIS_STATIC_MAX_POINTS points per call
+ * without allocating anything: its scratch is one fixed array in the library's device
+ * memory of NIS_STATIC_SCRATCH_BYTES (about 25 MB), which every GPU that loads the library
+ * holds until the process exits.  Callers still pass their own inputs and output.
+ *
+ * - n above NIS_STATIC_MAX_POINTS returns NIS_ERR_INVALID_ARG (split larger batches).
+ * - Nothing is built here: the pyramid, the light's transmittance and the phase table for
+ *   m->g must exist (nis_build_pyramid / nis_build_transmittance / nis_build_phase_table),
+ *   otherwise NIS_ERR_NOT_READY.
+ * - The first call on a device looks up the array's device address; make that first call
+ *   before any stream capture.
+ * - All calls in the process share the one array and leave their intermediates in it; the
+ *   path writes every scratch value before reading it, so nothing needs clearing, but two
+ *   calls whose work overlaps on the GPU (different streams, no ordering) race on it and
+ *   give wrong results.  Serialise them (one stream, or events). */
+#define NIS_STATIC_MAX_POINTS 512
+#define NIS_STATIC_SCRATCH_BYTES 24979456
+nis_status nis_shade_points_static(nis_ctx *ctx, nis_volume vol, nis_light light,
+                                   nis_weights w, const nis_material *m,
+                                   const float *d_points, const float *d_omega, int n,
+                                   float *d_rgb_out, nis_stream stream);
+
 /* Frees a volume (and its lights), a light or a weight set. */
 nis_status nis_release(nis_ctx *ctx, nis_handle h);
 

@@ -435,6 +435,29 @@ struct DeviceGuard {
 namespace nis {
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+nis_status record_error(nis_ctx *ctx, nis_status s, const char *msg) { return fail(ctx, s, msg); }
+
+nis_status resolve_built_inputs(nis_ctx *ctx, nis_volume vol, nis_light light, nis_weights w,
+                                float g, ResolvedInputs *out) {
+    Volume *pv; Light *pl; Weights *pw;
+    nis_status st = resolve(ctx, vol, light, w, &pv, &pl, &pw);
+    if (st) return st;
+    uint32_t key;
+    std::memcpy(&key, &g, 4);
+    auto it = ctx->phase.find(key);
+    if (it == ctx->phase.end())
+        return fail(ctx, NIS_ERR_NOT_READY, "phase table for this g not built "
+                                            "(call nis_build_phase_table first)");
+    out->rho = view_of(*pv, pv->data);
+    out->T = view_of(*pv, pl->data);
+    out->table = it->second;
+    out->W = pw->f32;
+    out->off = pw->off;
+    for (int c = 0; c < 3; ++c) out->dir[c] = pl->dir[c];
+    out->device = ctx->device;
+    return NIS_OK;
+}
+
 void weight_offsets(WeightOffsets *o) {
     size_t p = 0;
     for (int k = 0; k < kLayers; ++k) {

@@ -178,4 +178,19 @@ void launch_find_hits(const float *rho0, int n, const float *sigma_max, const Ca
 void launch_scatter_rgb(const float *rgb, const int *pix_index, int count, float *image,
                         cudaStream_t s);
 
+// Device pointers of a resolved (volume, light, weights, phase table) set, for entry points
+// that must not build or allocate anything.  Fails with NIS_ERR_NOT_READY if the pyramid or
+// the phase table of g is missing.
+struct ResolvedInputs {
+    PyramidView rho, T;
+    const float *table;
+    const float *W;
+    WeightOffsets off;
+    float dir[3];
+    int device;
+};
+nis_status resolve_built_inputs(nis_ctx *ctx, nis_volume vol, nis_light light, nis_weights w,
+                                float g, ResolvedInputs *out);
+nis_status record_error(nis_ctx *ctx, nis_status s, const char *msg);
+
 }  // namespace nis

@@ -91,7 +91,12 @@ _SIGS = {
     "nis_profile_read": (C.c_int, [C.c_void_p, C.c_char_p, C.POINTER(C.c_double),
                                    C.POINTER(C.c_int)]),
     "nis_kernel_launches": (C.c_uint64, []),
+    "nis_shade_points_static": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint64,
+                                          C.POINTER(Material), C.c_void_p, C.c_void_p, C.c_int,
+                                          C.c_void_p, C.c_void_p]),
 }
+
+STATIC_MAX_POINTS = 512
 
 FAMILIES = ("pyramid", "march", "phase", "hits", "gather", "cnn", "mlp", "other")
 
@@ -255,6 +260,16 @@ class Context:
         self._check(self.lib.nis_shade_points(self.h, vol, light, weights, C.byref(m),
                                               _ptr(points), _ptr(omega), n, _ptr(out),
                                               _stream(stream)))
+        return out
+
+    def shade_points_static(self, vol, light, weights, mat: dict, points, omega, out,
+                            stream=None):
+        """nis_shade_points_static: no device allocation inside the call; `out` must be
+        preallocated [n, 3] float32 on the device, n <= STATIC_MAX_POINTS."""
+        m = material(mat)
+        self._check(self.lib.nis_shade_points_static(self.h, vol, light, weights, C.byref(m),
+                                                     _ptr(points), _ptr(omega), points.shape[0],
+                                                     _ptr(out), _stream(stream)))
         return out
 
     def shade_points_debug(self, vol, light, weights, mat: dict, points, omega, stream=None):
