@@ -247,6 +247,12 @@ nis_status nis_profile(nis_ctx *ctx, int enable);
 nis_status nis_profile_read(nis_ctx *ctx, const char *family, double *total_ms,
                             int *launches);
 
+/* Plain GEMM on the tensor-core dense-layer kernel, for tests: C[m][n] = sum_k A[m][k] B[n][k]
+ * with A (m x k, leading dimension lda) and B (n x k, leading dimension ldb) BF16 row-major
+ * device arrays and C FP32 (m x n, dense).  n <= 208; lda and ldb multiples of 8. */
+nis_status nis_debug_tc_gemm(nis_ctx *ctx, const void *d_a, int lda, const void *d_b, int ldb,
+                             int m, int n, int k, float *d_c, nis_stream stream);
+
 /* Number of kernels this library has launched in the process (all contexts). */
 uint64_t nis_kernel_launches(void);
 

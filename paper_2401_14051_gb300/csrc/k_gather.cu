@@ -9,7 +9,7 @@ namespace {
 __device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }
 }
 
-__global__ void __launch_bounds__(256) gather_kernel(const GatherArgs a) {
+__global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ GatherArgs a) {
     const int p = blockIdx.x;
     const int t = threadIdx.x;
     const int lane = t & 31, warp = t >> 5;

@@ -9,7 +9,8 @@ namespace nis {
 // sigma_max is the shading point.  Compacted output (pix_index != null): slot from an
 // atomic counter; otherwise one entry per pixel.
 __global__ void find_hits_kernel(const float *__restrict__ rho0, int n,
-                                 const float *__restrict__ sigma_max, const CameraArgs c,
+                                 const float *__restrict__ sigma_max,
+                                 const __grid_constant__ CameraArgs c,
                                  int *hit_flag, float *points, float *omega, int *pix_index,
                                  int *counter) {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;

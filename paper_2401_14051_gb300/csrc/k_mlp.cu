@@ -30,7 +30,7 @@ __device__ __forceinline__ float load_a(const FcArgs &a, int r, int kk) {
 }  // namespace
 
 template <int MODE>
-__global__ void __launch_bounds__(256) fc_f32_kernel(const FcArgs a) {
+__global__ void __launch_bounds__(256) fc_f32_kernel(const __grid_constant__ FcArgs a) {
     __shared__ float As[BK][BM + 4];
     __shared__ float Bs[BK][BN + 4];
     const int row0 = blockIdx.x * BM, col0 = blockIdx.y * BN;
@@ -82,8 +82,98 @@ __global__ void __launch_bounds__(256) fc_f32_kernel(const FcArgs a) {
     }
 }
 
+// Wide layers (N <= 208): 128 x 208 output tile per CTA, 256 threads as 16 x 16, each
+// thread owns rows ty + 16 i (i < 8) and columns tx + 16 j (j < 13): per k step it reads 8 A
+// and 13 B values from shared memory for 104 FMAs.  The next K slice is fetched into
+// registers while the current one is consumed (two shared-memory buffers).
+namespace {
+constexpr int WM = 128, WN = 208, WK = 16, WI = 8, WJ = 13;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256, 1) fc_f32_wide_kernel(const __grid_constant__ FcArgs a) {
+    __shared__ __align__(16) float As[2][WK][WM];
+    __shared__ __align__(16) float Bs[2][WK][WN];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int row0 = blockIdx.x * WM;
+    float acc[WI][WJ];
+#pragma unroll
+    for (int i = 0; i < WI; ++i)
+#pragma unroll
+        for (int j = 0; j < WJ; ++j) acc[i][j] = 0.f;
+    float ra[WM * WK / 256], rb[WN * WK / 256];
+    auto fetch = [&](int k0) {
+#pragma unroll
+        for (int u = 0; u < WM * WK / 256; ++u) {
+            int e = tid + 256 * u, r = e / WK, kk = e % WK;
+            ra[u] = load_a<MODE>(a, row0 + r, k0 + kk);
+        }
+#pragma unroll
+        for (int u = 0; u < WN * WK / 256; ++u) {
+            int e = tid + 256 * u, c = e / WK, kk = e % WK, gk = k0 + kk;
+            rb[u] = (c < a.N && gk < a.K) ? __ldg(a.W + (size_t)c * a.K + gk) : 0.f;
+        }
+    };
+    auto stash = [&](int buf) {
+#pragma unroll
+        for (int u = 0; u < WM * WK / 256; ++u) {
+            int e = tid + 256 * u;
+            As[buf][e % WK][e / WK] = ra[u];
+        }
+#pragma unroll
+        for (int u = 0; u < WN * WK / 256; ++u) {
+            int e = tid + 256 * u;
+            Bs[buf][e % WK][e / WK] = rb[u];
+        }
+    };
+    const int nk = (a.K + WK - 1) / WK;
+    fetch(0);
+    stash(0);
+    __syncthreads();
+    for (int s = 0; s < nk; ++s) {
+        const int buf = s & 1;
+        if (s + 1 < nk) fetch((s + 1) * WK);
+#pragma unroll
+        for (int kk = 0; kk < WK; ++kk) {
+            float av[WI], bv[WJ];
+#pragma unroll
+            for (int i = 0; i < WI; ++i) av[i] = As[buf][kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < WJ; ++j) bv[j] = Bs[buf][kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < WI; ++i)
+#pragma unroll
+                for (int j = 0; j < WJ; ++j) acc[i][j] += av[i] * bv[j];
+        }
+        if (s + 1 < nk) stash(buf ^ 1);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < WI; ++i) {
+        const int r = row0 + ty + 16 * i;
+        if (r >= a.count) continue;
+#pragma unroll
+        for (int j = 0; j < WJ; ++j) {
+            const int c = tx + 16 * j;
+            if (c >= a.N) continue;
+            float v = acc[i][j] + a.b[c];
+            if (a.relu) v = fmaxf(v, 0.f);
+            if (a.resid) v += a.resid[(size_t)r * a.ldo + c];
+            a.out[(size_t)r * a.ldo + c] = v;
+        }
+    }
+}
+
 void launch_fc_f32(const FcArgs &a, cudaStream_t s) {
     if (a.count <= 0) return;
+    if (!a.decode && a.N > 64 && a.N <= WN) {
+        dim3 grid((a.count + WM - 1) / WM);
+        if (a.mode == kFcFeat) { note_launch(); fc_f32_wide_kernel<kFcFeat><<<grid, 256, 0, s>>>(a); }
+        else if (a.mode == kFcSum) { note_launch(); fc_f32_wide_kernel<kFcSum><<<grid, 256, 0, s>>>(a); }
+        else { note_launch(); fc_f32_wide_kernel<kFcCat><<<grid, 256, 0, s>>>(a); }
+        return;
+    }
     dim3 grid((a.count + BM - 1) / BM, (a.N + BN - 1) / BN);
     if (a.mode == kFcFeat) { note_launch(); fc_f32_kernel<kFcFeat><<<grid, 256, 0, s>>>(a); }
     else if (a.mode == kFcSum) { note_launch(); fc_f32_kernel<kFcSum><<<grid, 256, 0, s>>>(a); }

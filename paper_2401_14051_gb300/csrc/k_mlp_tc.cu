@@ -1,0 +1,267 @@
+// Dense layers of the backbone (Sec. III.C.2, Fig. 6) on the 5th-generation tensor cores:
+// out = epilogue(A B^T) with A = activations [rows][K] and B = weights [N][K], both BF16
+// K-major, FP32 accumulation in tensor memory.
+//
+// Persistent kernel, one CTA per SM, 6 warps:
+//   warp 0     TMA producer: 128x64 A box + N_mma x 64 B box per K step into a 4-stage ring
+//   warp 1     TMEM owner and MMA issuer: 128 x N_mma x 16 tcgen05.mma per 32-byte K slice,
+//              two accumulator buffers (columns 0 and 256) so the epilogue of one tile
+//              overlaps the MMAs of the next
+//   warps 2-5  epilogue: each thread owns one TMEM lane = one row of the tile; reads 32
+//              columns at a time and applies the layer's fused epilogue
+// Every mbarrier wait is bounded: on a time-out the kernel records kErrTimeout in the
+// context's error word and winds down (draining its MMAs before releasing TMEM).
+#include <cuda_bf16.h>
+
+#include "nis_internal.h"
+#include "tc_common.h"
+
+namespace nis {
+
+namespace {
+constexpr int TM = 128, TK = 64, TN_MAX = 208, STAGES = 4;
+constexpr uint32_t A_STAGE = TM * TK * 2;                 // 16 KB
+constexpr uint32_t B_STAGE = TN_MAX * TK * 2;             // 26 KB (208 rows)
+constexpr uint32_t SMEM_TILES = STAGES * (A_STAGE + B_STAGE);
+constexpr uint32_t SMEM_BYTES = SMEM_TILES + 256 + 1024;  // barriers + alignment slack
+constexpr int kEpiWarps = 4;
+
+__device__ __forceinline__ void record_timeout(unsigned *err, int *abort_flag) {
+    *abort_flag = 1;
+    if (err) atomicOr(err, kErrTimeout);
+}
+
+__device__ __forceinline__ void store_bf16x8(__nv_bfloat16 *dst, const float *v) {
+    __align__(16) __nv_bfloat162 p[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) p[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(p);
+}
+__device__ __forceinline__ void load_bf16x8(const __nv_bfloat16 *src, float *v) {
+    uint4 raw = *reinterpret_cast<const uint4 *>(src);
+    const __nv_bfloat162 *p = reinterpret_cast<const __nv_bfloat162 *>(&raw);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float2 f = __bfloat1622float2(p[i]);
+        v[2 * i] = f.x;
+        v[2 * i + 1] = f.y;
+    }
+}
+
+// Fused epilogue of 32 consecutive columns [c0, c0 + 32) of row r (FP32 accumulators in v).
+__device__ __forceinline__ void epilogue_chunk(const TcGemmArgs &a, int r, int c0, float (&v)[32]) {
+    const int N = a.N;
+    switch (a.epi) {
+    case kEpiPlain: {
+        float *o = a.out_f32 + (size_t)r * a.ldo;
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (c0 + j < N) o[c0 + j] = v[j];
+        break;
+    }
+    case kEpiFc1: {
+        // e = ReLU(w_se * acc + W_cfg c + b); s = h_prev + e
+        const float sc = a.row_scale[(size_t)r * a.row_scale_ld];
+        float cf[kCfg];
+#pragma unroll
+        for (int q = 0; q < kCfg; ++q) cf[q] = a.cfg[(size_t)r * kCfg + q];
+        float hv[32];
+        if (a.h_prev) {
+#pragma unroll
+            for (int g = 0; g < 4; ++g)
+                if (c0 + 8 * g < N) load_bf16x8(a.h_prev + (size_t)r * a.ld_h + c0 + 8 * g, hv + 8 * g);
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const int c = c0 + j;
+            if (c < N) {
+                const float *wc = a.w_cfg + (size_t)c * kCfg;
+                float e = v[j] * sc + a.bias[c];
+#pragma unroll
+                for (int q = 0; q < kCfg; ++q) e += wc[q] * cf[q];
+                e = fmaxf(e, 0.f);
+                v[j] = e;
+                hv[j] = a.h_prev ? hv[j] + e : e;
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < 4; ++g)
+            if (c0 + 8 * g < N) {
+                store_bf16x8(a.out_e + (size_t)r * a.ldo + c0 + 8 * g, v + 8 * g);
+                store_bf16x8(a.out_s + (size_t)r * a.ldo + c0 + 8 * g, hv + 8 * g);
+            }
+        break;
+    }
+    case kEpiFc2: {
+        // h = ReLU(acc + b) + e
+        float ev[32];
+#pragma unroll
+        for (int g = 0; g < 4; ++g)
+            if (c0 + 8 * g < N) load_bf16x8(a.resid + (size_t)r * a.ld_resid + c0 + 8 * g, ev + 8 * g);
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (c0 + j < N) v[j] = fmaxf(v[j] + a.bias[c0 + j], 0.f) + ev[j];
+#pragma unroll
+        for (int g = 0; g < 4; ++g)
+            if (c0 + 8 * g < N) store_bf16x8(a.out_bf + (size_t)r * a.ldo + c0 + 8 * g, v + 8 * g);
+        break;
+    }
+    case kEpiRelu: {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (c0 + j < N) v[j] = fmaxf(v[j] + a.bias[c0 + j], 0.f);
+#pragma unroll
+        for (int g = 0; g < 4; ++g)
+            if (c0 + 8 * g < N) store_bf16x8(a.out_bf + (size_t)r * a.ldo + c0 + 8 * g, v + 8 * g);
+        break;
+    }
+    default: {  // kEpiDecode: rgb = I albedo^4 expm1(acc + b), N = 3
+        if (c0 == 0) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                float y = v[j] + a.bias[j];
+                if (a.y_out) a.y_out[(size_t)r * 3 + j] = y;
+                a.out_f32[(size_t)r * 3 + j] = a.dec_scale[j] * expm1f(y);
+            }
+        }
+        break;
+    }
+    }
+}
+}  // namespace
+
+__global__ void __launch_bounds__(192, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+                   const __grid_constant__ TcGemmArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + STAGES * A_STAGE;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + SMEM_TILES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *acc_full = empty + STAGES;
+    uint64_t *acc_empty = acc_full + 2;
+    uint64_t *drain = acc_empty + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_tiles = (a.M + TM - 1) / TM;
+    const int n_mma = a.n_mma;
+    const uint32_t b_bytes = (uint32_t)n_mma * TK * 2;
+    const uint32_t idesc = tc::idesc_bf16_f32(TM, n_mma);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
+        for (int b = 0; b < 2; ++b) { tc::mbar_init(&acc_full[b], 1); tc::mbar_init(&acc_empty[b], kEpiWarps); }
+        tc::mbar_init(drain, 1);
+        *abort_flag = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == 0 && lane == 0) { tc::prefetch_tmap(&map_a); tc::prefetch_tmap(&map_b); }
+    if (warp == 1) {
+        tc::tmem_alloc(tmem_slot, 512);
+        tc::tmem_relinquish();
+        tc::fence_before_sync();
+    }
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int it = 0;
+            for (int tile = blockIdx.x; tile < n_tiles && !*(volatile int *)abort_flag; tile += gridDim.x) {
+                for (int kt = 0; kt < a.k_tiles; ++kt, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (it / STAGES) & 1;
+                    if (!tc::mbar_wait(&empty[s], ph ^ 1)) { record_timeout(a.err, abort_flag); break; }
+                    tc::mbar_expect_tx(&full[s], A_STAGE + b_bytes);
+                    tc::tma_load_2d(sA + s * A_STAGE, &map_a, a.a_col0 + kt * TK, tile * TM, &full[s]);
+                    tc::tma_load_2d(sB + s * B_STAGE, &map_b, kt * TK, 0, &full[s]);
+                }
+            }
+            // wait until every stage issued has landed (the consumer may have stopped early)
+            for (int j = 0; j < STAGES && j < it; ++j) {
+                const int i2 = it - 1 - j;
+                tc::mbar_wait(&full[i2 % STAGES], (i2 / STAGES) & 1, 1u << 16);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int it = 0, t = 0;
+            for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++t) {
+                if (*(volatile int *)abort_flag) break;
+                const int buf = t & 1;
+                if (!tc::mbar_wait(&acc_empty[buf], ((t >> 1) & 1) ^ 1)) { record_timeout(a.err, abort_flag); break; }
+                tc::fence_after_sync();
+                const uint32_t d_tmem = tmem_base + buf * 256;
+                bool ok = true;
+                for (int kt = 0; kt < a.k_tiles; ++kt, ++it) {
+                    const int s = it % STAGES;
+                    if (!tc::mbar_wait(&full[s], (it / STAGES) & 1)) { ok = false; break; }
+                    tc::fence_after_sync();
+                    const uint32_t a_addr = tc::smem_u32(sA + s * A_STAGE);
+                    const uint32_t b_addr = tc::smem_u32(sB + s * B_STAGE);
+                    const int k_left = a.K - kt * TK;
+                    const int n_k16 = k_left >= TK ? TK / 16 : (k_left + 15) / 16;
+                    for (int k = 0; k < n_k16; ++k)
+                        tc::mma_f16(d_tmem, tc::smem_desc_sw128(a_addr + k * 32),
+                                    tc::smem_desc_sw128(b_addr + k * 32), idesc, (kt | k) != 0);
+                    tc::mma_commit(&empty[s]);
+                }
+                if (!ok) { record_timeout(a.err, abort_flag); break; }
+                tc::mma_commit(&acc_full[buf]);
+            }
+            // all MMAs issued by this thread complete before TMEM is released
+            tc::mma_commit(drain);
+            tc::mbar_wait(drain, 0, 1u << 20);
+        }
+    } else {
+        const int q = warp & 3;                        // TMEM lane quarter of this warp
+        int t = 0;
+        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++t) {
+            const int buf = t & 1;
+            bool ok = tc::mbar_wait(&acc_full[buf], (t >> 1) & 1);
+            if (!ok || *(volatile int *)abort_flag) {
+                if (!ok && lane == 0) record_timeout(a.err, abort_flag);
+                break;
+            }
+            tc::fence_after_sync();
+            const int r = tile * TM + q * 32 + lane;
+            const uint32_t lane_addr = tmem_base + buf * 256 + ((uint32_t)(q * 32) << 16);
+            for (int c0 = 0; c0 < a.N; c0 += 32) {
+                float v[32];
+                tc::tmem_ld32(lane_addr + c0, v);
+                tc::tmem_ld_wait();
+                if (r < a.M) epilogue_chunk(a, r, c0, v);
+            }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&acc_empty[buf]);
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem_base, 512);
+    }
+}
+
+uint32_t tc_gemm_smem_bytes() { return SMEM_BYTES; }
+
+void launch_tc_gemm(const TcGemmArgs &a, const CUtensorMap &map_a, const CUtensorMap &map_b,
+                    int num_sms, cudaStream_t s) {
+    if (a.M <= 0) return;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+        attr_set = true;
+    }
+    int tiles = (a.M + TM - 1) / TM;
+    int grid = tiles < num_sms ? tiles : num_sms;
+    note_launch();
+    tc_gemm_kernel<<<grid, 192, SMEM_BYTES, s>>>(map_a, map_b, a);
+}
+
+}  // namespace nis

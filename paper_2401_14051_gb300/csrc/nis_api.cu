@@ -435,6 +435,40 @@ struct DeviceGuard {
 namespace nis {
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+namespace {
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+}  // namespace
+
+bool make_tmap_bf16(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer,
+                    uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer) {
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn || (reinterpret_cast<uintptr_t>(base) & 15) || (row_bytes & 15)) return false;
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {row_bytes};
+    cuuint32_t box[2] = {box_inner, box_outer};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 nis_status record_error(nis_ctx *ctx, nis_status s, const char *msg) { return fail(ctx, s, msg); }
 
 nis_status resolve_built_inputs(nis_ctx *ctx, nis_volume vol, nis_light light, nis_weights w,
@@ -851,6 +885,8 @@ nis_status nis_sync(nis_ctx *ctx, nis_stream stream, int timeout_ms) {
     NIS_CUDA(cudaMemcpy(&err, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
     if (err) {
         NIS_CUDA(cudaMemset(ctx->d_err, 0, sizeof(unsigned)));
+        if (err & kErrTimeout)
+            return fail(ctx, NIS_ERR_TIMEOUT, "a tensor-core kernel's bounded wait gave up");
         if (err & kErrBadDensity)
             return fail(ctx, NIS_ERR_BAD_DATA, "density contained NaN, infinite or negative values");
         return fail(ctx, NIS_ERR_BAD_DATA, "a kernel bounds check failed");
@@ -992,5 +1028,33 @@ nis_status nis_profile_read(nis_ctx *ctx, const char *family, double *total_ms, 
 }
 
 uint64_t nis_kernel_launches(void) { return g_launches.load(); }
+
+nis_status nis_debug_tc_gemm(nis_ctx *ctx, const void *d_a, int lda, const void *d_b, int ldb,
+                             int m, int n, int k, float *d_c, nis_stream stream) {
+    if (!ctx) return NIS_ERR_INVALID_ARG;
+    if (!d_a || !d_b || !d_c || m < 1 || n < 1 || n > 208 || k < 1 || lda < k || ldb < k ||
+        (lda % 8) || (ldb % 8))
+        return fail(ctx, NIS_ERR_INVALID_ARG, "bad GEMM arguments (n <= 208, lda/ldb >= k and % 8)");
+    DeviceGuard g(ctx->device);
+    TcGemmArgs a{};
+    a.M = m; a.N = n; a.K = k;
+    a.n_mma = (n + 15) / 16 * 16;
+    a.k_tiles = (k + 63) / 64;
+    a.epi = kEpiPlain;
+    a.err = ctx->d_err;
+    a.out_f32 = d_c; a.ldo = n;
+    CUtensorMap ma, mb;
+    if (!make_tmap_bf16(&ma, d_a, (uint64_t)k, (uint64_t)m, (uint64_t)lda * 2, 64, 128) ||
+        !make_tmap_bf16(&mb, d_b, (uint64_t)k, (uint64_t)n, (uint64_t)ldb * 2, 64, (uint32_t)a.n_mma))
+        return fail(ctx, NIS_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    {
+        ProfScope ps(ctx, "mlp", reinterpret_cast<cudaStream_t>(stream));
+        launch_tc_gemm(a, ma, mb, sms, reinterpret_cast<cudaStream_t>(stream));
+    }
+    NIS_CUDA(cudaGetLastError());
+    return NIS_OK;
+}
 
 }  // extern "C"

@@ -2,6 +2,8 @@
 // (voxel lookups, geometry), the constants of the method, and the kernel launchers.
 #pragma once
 
+#include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
@@ -110,6 +112,7 @@ __device__ __forceinline__ float exit_distance(float x, float y, float z, float 
 // ---- device-side error word bits (read back by nis_sync) ----------------------------------
 constexpr unsigned kErrBadDensity = 1u;
 constexpr unsigned kErrBadIndex = 2u;
+constexpr unsigned kErrTimeout = 4u;     // a bounded wait in a tensor-core kernel gave up
 
 // ---- launchers (all enqueue on `s`) ----------------------------------------------------------
 void note_launch();                  // counts every kernel launch of the library
@@ -177,6 +180,34 @@ void launch_find_hits(const float *rho0, int n, const float *sigma_max, const Ca
                       int *counter, cudaStream_t s);
 void launch_scatter_rgb(const float *rgb, const int *pix_index, int count, float *image,
                         cudaStream_t s);
+
+// ---- tensor-core dense layer (k_mlp_tc.cu) ------------------------------------------------
+constexpr int kEpiPlain = 0, kEpiFc1 = 1, kEpiFc2 = 2, kEpiRelu = 3, kEpiDecode = 4;
+struct TcGemmArgs {
+    int M, N, K;                      // rows, output columns, reduction length
+    int n_mma;                        // N rounded up to a multiple of 16 (<= 208)
+    int k_tiles;                      // ceil(K / 64)
+    int a_col0;                       // first column of A inside its tensor map
+    int epi;
+    unsigned *err;                    // context error word (kErrTimeout)
+    float *out_f32;                   // kEpiPlain [M][ldo], kEpiDecode rgb [M][3]
+    __nv_bfloat16 *out_bf;            // kEpiFc2, kEpiRelu
+    __nv_bfloat16 *out_e, *out_s;     // kEpiFc1: e and h_prev + e
+    int ldo;
+    const float *bias;                // [N]
+    const float *row_scale; int row_scale_ld;   // kEpiFc1: SE weight per row
+    const float *cfg;                 // kEpiFc1: [M][5] configuration vector
+    const float *w_cfg;               // kEpiFc1: [N][5] weight columns of c
+    const __nv_bfloat16 *h_prev; int ld_h;      // kEpiFc1 running state (may be null)
+    const __nv_bfloat16 *resid; int ld_resid;   // kEpiFc2: e
+    float dec_scale[3];               // kEpiDecode: I * albedo^4
+    float *y_out;                     // kEpiDecode: network output before decode (may be null)
+};
+void launch_tc_gemm(const TcGemmArgs &a, const CUtensorMap &map_a, const CUtensorMap &map_b,
+                    int num_sms, cudaStream_t s);
+// 2-D BF16 tensor map, inner dimension contiguous, box = box_inner x box_outer, 128-byte swizzle.
+bool make_tmap_bf16(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer,
+                    uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer);
 
 // Device pointers of a resolved (volume, light, weights, phase table) set, for entry points
 // that must not build or allocate anything.  Fails with NIS_ERR_NOT_READY if the pyramid or

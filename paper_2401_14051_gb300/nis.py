@@ -91,6 +91,8 @@ _SIGS = {
     "nis_profile_read": (C.c_int, [C.c_void_p, C.c_char_p, C.POINTER(C.c_double),
                                    C.POINTER(C.c_int)]),
     "nis_kernel_launches": (C.c_uint64, []),
+    "nis_debug_tc_gemm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int,
+                                    C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "nis_shade_points_static": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint64,
                                           C.POINTER(Material), C.c_void_p, C.c_void_p, C.c_int,
                                           C.c_void_p, C.c_void_p]),
@@ -270,6 +272,18 @@ class Context:
         self._check(self.lib.nis_shade_points_static(self.h, vol, light, weights, C.byref(m),
                                                      _ptr(points), _ptr(omega), points.shape[0],
                                                      _ptr(out), _stream(stream)))
+        return out
+
+    def debug_tc_gemm(self, a, b, out=None, stream=None):
+        """C = A B^T on the tensor-core dense-layer kernel (A [m][k], B [n][k] BF16 CUDA
+        tensors, row-major with leading dimensions a.stride(0), b.stride(0))."""
+        m, k = a.shape
+        n = b.shape[0]
+        if out is None:
+            out = torch.empty((m, n), dtype=torch.float32, device=a.device)
+        self._check(self.lib.nis_debug_tc_gemm(self.h, a.data_ptr(), a.stride(0), b.data_ptr(),
+                                               b.stride(0), m, n, k, out.data_ptr(),
+                                               _stream(stream)))
         return out
 
     def shade_points_debug(self, vol, light, weights, mat: dict, points, omega, stream=None):
