@@ -258,15 +258,16 @@ def run_nis(args):
     density = torch.from_numpy(vol_np).to(dev)
     v = ctx.upload_volume(density)
     w = ctx.load_weights(blob)
+    w_bf16 = ctx.load_weights(blob, nis.PREC_BF16)
     img = torch.empty((cam["height"], cam["width"], 3), dtype=torch.float32, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
     stream = torch.cuda.current_stream()
 
-    def step():
+    def step(weights_handle=w, out=img):
         ctx.build_pyramid(v)
         lt = ctx.build_transmittance(v, light, 0.6)
         ctx.build_phase_table(mat["g"])
-        ctx.render_frame(v, lt, w, mat, cam, out=img)
+        ctx.render_frame(v, lt, weights_handle, mat, cam, out=out)
         return lt
 
     for _ in range(args.warmup):
@@ -300,6 +301,42 @@ def run_nis(args):
     total_ms = max_over_ranks(sum(times), world)
     ms_per_step = total_ms / args.steps
     value = n_points * args.steps * world / (total_ms / 1e3)
+
+    # ---- the same frames with the dense layers in BF16 on the tensor cores
+    img_bf = torch.empty_like(img)
+    for _ in range(args.warmup):
+        step(w_bf16, img_bf)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    times_bf = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(w_bf16, img_bf)
+        e1.record(stream)
+        e1.synchronize()
+        times_bf.append(e0.elapsed_time(e1))
+    ctx.profile(False)
+    fam_bf = {f: ctx.profile_read(f) for f in nis.FAMILIES}
+    total_bf = max_over_ranks(sum(times_bf), world)
+    hitmask = hit.bool()
+    a_bf, a_32 = img_bf[hitmask].double(), img[hitmask].double()
+    floor = 1e-2 * a_32.abs().amax(dim=0, keepdim=True)
+    e_bf = ((a_bf - a_32).abs() / torch.maximum(a_32.abs(), floor))
+    peaks_bf = measured_peaks()
+    mlp_ms, mlp_n = fam_bf["mlp"]
+    mlp_tf = MLP_FLOP_PER_POINT * n_points * args.steps / (mlp_ms / 1e3) / 1e12
+    bf16 = {"value": n_points * args.steps * world / (total_bf / 1e3), "unit": UNIT,
+            "frame_ms": total_bf / args.steps,
+            "mean_rel_err_vs_fp32": float(e_bf.mean()), "max_rel_err_vs_fp32": float(e_bf.max()),
+            "step_breakdown_ms": {f: round(fam_bf[f][0] / args.steps, 4) for f in nis.FAMILIES},
+            "roofline": {"bound": "tensor", "unit": "TFLOP/s", "kernel": "tc_gemm_kernel (tcgen05, BF16)",
+                         "achieved": mlp_tf, "peak": peaks_bf["bf16_tflops_sustained"],
+                         "frac": mlp_tf / peaks_bf["bf16_tflops_sustained"],
+                         "peak_source": f"{peaks_bf['source']} cuBLAS BF16, sustained",
+                         "launches": mlp_n, "avg_launch_ms": mlp_ms / max(mlp_n, 1),
+                         "traffic": (recorded_traffic("mlp_bf16") or {}).get("bytes_per_launch")}}
 
     # ---- end to end through the C ABI from page-locked host memory
     host_vol = torch.from_numpy(vol_np).pin_memory()
@@ -371,6 +408,7 @@ def run_nis(args):
             "gpu_launches": int(launches),
             "step_breakdown_ms": {f: round(fam[f][0] / args.steps, 4) for f in nis.FAMILIES},
             "roofline": roof,
+            "bf16": bf16,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(vol_np.nbytes),
                     "d2h_bytes_per_step": int(img.numel() * 4),

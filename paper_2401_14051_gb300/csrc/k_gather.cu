@@ -85,9 +85,19 @@ __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ Gat
             float f0 = __ldg(row0 + set * kLat + t), f1 = __ldg(row1 + set * kLat + t);
             f = f0 + wa * (f1 - f0);
             size_t o = ((size_t)p * kLayers + k) * kLat + t;
-            a.H_rho[o] = rho;
             a.H_T[o] = T;
-            a.H_f[o] = f;
+            if (a.Hb_rho) {
+                size_t ob = ((size_t)p * kLayers + k) * kLatPad + t;
+                a.Hb_rho[ob] = __float2bfloat16_rn(rho);
+                a.Hb_f[ob] = __float2bfloat16_rn(f);
+            } else {
+                a.H_rho[o] = rho;
+                a.H_f[o] = f;
+            }
+        } else if (a.Hb_rho && t < kLatPad) {     // zero the BF16 row padding
+            size_t ob = ((size_t)p * kLayers + k) * kLatPad + t;
+            a.Hb_rho[ob] = __float2bfloat16_rn(0.f);
+            a.Hb_f[ob] = __float2bfloat16_rn(0.f);
         }
         // squeeze statistics (mean and max pooling over the layer's points)
         float s0 = rho, s1 = f, s2 = T;

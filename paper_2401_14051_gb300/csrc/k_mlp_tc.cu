@@ -23,8 +23,10 @@ constexpr int TM = 128, TK = 64, TN_MAX = 208, STAGES = 4;
 constexpr uint32_t A_STAGE = TM * TK * 2;                 // 16 KB
 constexpr uint32_t B_STAGE = TN_MAX * TK * 2;             // 26 KB (208 rows)
 constexpr uint32_t SMEM_TILES = STAGES * (A_STAGE + B_STAGE);
-constexpr uint32_t SMEM_BYTES = SMEM_TILES + 256 + 1024;  // barriers + alignment slack
-constexpr int kEpiWarps = 4;
+constexpr uint32_t SMEM_CONST = 2 * TN_MAX * 4;          // per-column epilogue constants
+constexpr uint32_t SMEM_BYTES = SMEM_TILES + 256 + SMEM_CONST + 1024;  // + alignment slack
+constexpr int kEpiWarps = 8;                              // two per TMEM lane quarter
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 
 __device__ __forceinline__ void record_timeout(unsigned *err, int *abort_flag) {
     *abort_flag = 1;
@@ -49,7 +51,12 @@ __device__ __forceinline__ void load_bf16x8(const __nv_bfloat16 *src, float *v) 
 }
 
 // Fused epilogue of 32 consecutive columns [c0, c0 + 32) of row r (FP32 accumulators in v).
-__device__ __forceinline__ void epilogue_chunk(const TcGemmArgs &a, int r, int c0, float (&v)[32]) {
+// s_bias / s_wa: per-column constants in shared memory (bias with the material's part of the
+// configuration vector folded in; weight of alpha).  sc, alpha: this row's SE weight and
+// view angle.  pre: the residual / running-state values of this chunk, already loaded.
+__device__ __forceinline__ void epilogue_chunk(const TcGemmArgs &a, int r, int c0, float (&v)[32],
+                                               const float *s_bias, const float *s_wa, float sc,
+                                               float alpha, const float (&pre)[32]) {
     const int N = a.N;
     switch (a.epi) {
     case kEpiPlain: {
@@ -61,46 +68,25 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs &a, int r, int c
     }
     case kEpiFc1: {
         // e = ReLU(w_se * acc + W_cfg c + b); s = h_prev + e
-        const float sc = a.row_scale[(size_t)r * a.row_scale_ld];
-        float cf[kCfg];
-#pragma unroll
-        for (int q = 0; q < kCfg; ++q) cf[q] = a.cfg[(size_t)r * kCfg + q];
-        float hv[32];
-        if (a.h_prev) {
-#pragma unroll
-            for (int g = 0; g < 4; ++g)
-                if (c0 + 8 * g < N) load_bf16x8(a.h_prev + (size_t)r * a.ld_h + c0 + 8 * g, hv + 8 * g);
-        }
+        float sv[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-            const int c = c0 + j;
-            if (c < N) {
-                const float *wc = a.w_cfg + (size_t)c * kCfg;
-                float e = v[j] * sc + a.bias[c];
-#pragma unroll
-                for (int q = 0; q < kCfg; ++q) e += wc[q] * cf[q];
-                e = fmaxf(e, 0.f);
-                v[j] = e;
-                hv[j] = a.h_prev ? hv[j] + e : e;
-            }
+            float e = fmaxf(fmaf(v[j], sc, fmaf(s_wa[c0 + j], alpha, s_bias[c0 + j])), 0.f);
+            v[j] = e;
+            sv[j] = a.h_prev ? pre[j] + e : e;
         }
 #pragma unroll
         for (int g = 0; g < 4; ++g)
             if (c0 + 8 * g < N) {
                 store_bf16x8(a.out_e + (size_t)r * a.ldo + c0 + 8 * g, v + 8 * g);
-                store_bf16x8(a.out_s + (size_t)r * a.ldo + c0 + 8 * g, hv + 8 * g);
+                store_bf16x8(a.out_s + (size_t)r * a.ldo + c0 + 8 * g, sv + 8 * g);
             }
         break;
     }
     case kEpiFc2: {
         // h = ReLU(acc + b) + e
-        float ev[32];
 #pragma unroll
-        for (int g = 0; g < 4; ++g)
-            if (c0 + 8 * g < N) load_bf16x8(a.resid + (size_t)r * a.ld_resid + c0 + 8 * g, ev + 8 * g);
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-            if (c0 + j < N) v[j] = fmaxf(v[j] + a.bias[c0 + j], 0.f) + ev[j];
+        for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + s_bias[c0 + j], 0.f) + pre[j];
 #pragma unroll
         for (int g = 0; g < 4; ++g)
             if (c0 + 8 * g < N) store_bf16x8(a.out_bf + (size_t)r * a.ldo + c0 + 8 * g, v + 8 * g);
@@ -108,8 +94,7 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs &a, int r, int c
     }
     case kEpiRelu: {
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-            if (c0 + j < N) v[j] = fmaxf(v[j] + a.bias[c0 + j], 0.f);
+        for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + s_bias[c0 + j], 0.f);
 #pragma unroll
         for (int g = 0; g < 4; ++g)
             if (c0 + 8 * g < N) store_bf16x8(a.out_bf + (size_t)r * a.ldo + c0 + 8 * g, v + 8 * g);
@@ -119,7 +104,7 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs &a, int r, int c
         if (c0 == 0) {
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
-                float y = v[j] + a.bias[j];
+                float y = v[j] + s_bias[j];
                 if (a.y_out) a.y_out[(size_t)r * 3 + j] = y;
                 a.out_f32[(size_t)r * 3 + j] = a.dec_scale[j] * expm1f(y);
             }
@@ -128,9 +113,23 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs &a, int r, int c
     }
     }
 }
+
+// Residual (FC-2) or running state (FC-1) of one chunk, BF16 -> FP32; zeros if absent.
+__device__ __forceinline__ void load_pre(const TcGemmArgs &a, int r, int c0, float (&pre)[32]) {
+    const __nv_bfloat16 *src = a.epi == kEpiFc1 ? a.h_prev : (a.epi == kEpiFc2 ? a.resid : nullptr);
+    const int ld = a.epi == kEpiFc1 ? a.ld_h : a.ld_resid;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        if (src && c0 + 8 * g < a.N) load_bf16x8(src + (size_t)r * ld + c0 + 8 * g, pre + 8 * g);
+        else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) pre[8 * g + i] = 0.f;
+        }
+    }
+}
 }  // namespace
 
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                    const __grid_constant__ TcGemmArgs a) {
     extern __shared__ uint8_t smem_raw[];
@@ -144,6 +143,8 @@ __global__ void __launch_bounds__(192, 1)
     uint64_t *drain = acc_empty + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
     int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
+    float *s_bias = reinterpret_cast<float *>(smem + SMEM_TILES + 256);
+    float *s_wa = s_bias + TN_MAX;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_tiles = (a.M + TM - 1) / TM;
@@ -159,6 +160,21 @@ __global__ void __launch_bounds__(192, 1)
         tc::fence_mbar_init();
     }
     if (warp == 0 && lane == 0) { tc::prefetch_tmap(&map_a); tc::prefetch_tmap(&map_b); }
+    // per-column epilogue constants (columns >= N read as zero)
+    for (int c = threadIdx.x; c < TN_MAX; c += blockDim.x) {
+        float b = 0.f, wa = 0.f;
+        if (c < a.N && a.bias) {
+            b = a.bias[c];
+            if (a.epi == kEpiFc1) {
+                const float *wc = a.w_cfg + (size_t)c * a.w_cfg_ld;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) b += wc[q] * a.mat_cfg[q];
+                wa = wc[4];
+            }
+        }
+        s_bias[c] = b;
+        s_wa[c] = wa;
+    }
     if (warp == 1) {
         tc::tmem_alloc(tmem_slot, 512);
         tc::tmem_relinquish();
@@ -219,22 +235,36 @@ __global__ void __launch_bounds__(192, 1)
         }
     } else {
         const int q = warp & 3;                        // TMEM lane quarter of this warp
+        const int half = (warp - 2) >> 2;              // which 32-column chunks this warp takes
         int t = 0;
         for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++t) {
             const int buf = t & 1;
+            const int r = tile * TM + q * 32 + lane;
+            const bool live = r < a.M;
+            float sc = 0.f, alpha = 0.f;
+            if (live && a.epi == kEpiFc1) {
+                sc = a.row_scale[(size_t)r * a.row_scale_ld];
+                alpha = a.cfg[(size_t)r * kCfg + 4];
+            }
+            float pre[32];
+            if (live && half * 32 < a.N) load_pre(a, r, half * 32, pre);
             bool ok = tc::mbar_wait(&acc_full[buf], (t >> 1) & 1);
             if (!ok || *(volatile int *)abort_flag) {
                 if (!ok && lane == 0) record_timeout(a.err, abort_flag);
                 break;
             }
             tc::fence_after_sync();
-            const int r = tile * TM + q * 32 + lane;
             const uint32_t lane_addr = tmem_base + buf * 256 + ((uint32_t)(q * 32) << 16);
-            for (int c0 = 0; c0 < a.N; c0 += 32) {
+            for (int c0 = half * 32; c0 < a.N; c0 += 64) {
                 float v[32];
                 tc::tmem_ld32(lane_addr + c0, v);
+                float cur[32];
+#pragma unroll
+                for (int i = 0; i < 32; ++i) cur[i] = pre[i];
+                // next chunk's residual loads overlap this chunk's TMEM load and math
+                if (live && c0 + 64 < a.N) load_pre(a, r, c0 + 64, pre);
                 tc::tmem_ld_wait();
-                if (r < a.M) epilogue_chunk(a, r, c0, v);
+                if (live) epilogue_chunk(a, r, c0, v, s_bias, s_wa, sc, alpha, cur);
             }
             tc::fence_before_sync();
             __syncwarp();
@@ -248,7 +278,23 @@ __global__ void __launch_bounds__(192, 1)
     }
 }
 
-uint32_t tc_gemm_smem_bytes() { return SMEM_BYTES; }
+__global__ void pack_bf16_kernel(const float *__restrict__ src, int N, int K, int ld_src,
+                                 __nv_bfloat16 *__restrict__ dst, int Np, int Kp) {
+    size_t total = (size_t)Np * Kp;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        int n = (int)(i / Kp), k = (int)(i % Kp);
+        dst[i] = __float2bfloat16_rn(n < N && k < K ? src[(size_t)n * ld_src + k] : 0.f);
+    }
+}
+
+void launch_pack_bf16(const float *src, int N, int K, int ld_src, __nv_bfloat16 *dst, int Np,
+                      int Kp, cudaStream_t s) {
+    size_t total = (size_t)Np * Kp;
+    int blocks = (int)((total + 255) / 256 < 1024 ? (total + 255) / 256 : 1024);
+    note_launch();
+    pack_bf16_kernel<<<blocks, 256, 0, s>>>(src, N, K, ld_src, dst, Np, Kp);
+}
 
 void launch_tc_gemm(const TcGemmArgs &a, const CUtensorMap &map_a, const CUtensorMap &map_b,
                     int num_sms, cudaStream_t s) {
@@ -261,7 +307,7 @@ void launch_tc_gemm(const TcGemmArgs &a, const CUtensorMap &map_a, const CUtenso
     int tiles = (a.M + TM - 1) / TM;
     int grid = tiles < num_sms ? tiles : num_sms;
     note_launch();
-    tc_gemm_kernel<<<grid, 192, SMEM_BYTES, s>>>(map_a, map_b, a);
+    tc_gemm_kernel<<<grid, kThreads, SMEM_BYTES, s>>>(map_a, map_b, a);
 }
 
 }  // namespace nis

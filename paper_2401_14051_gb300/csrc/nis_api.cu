@@ -40,6 +40,18 @@ struct Weights {
     int precision = NIS_PREC_F32;
     float *f32 = nullptr;             // all tensors in blob order
     WeightOffsets off;
+    // BF16 dense layers (precision BF16): zero-padded [n_mma][Kp] matrices and tensor maps
+    __nv_bfloat16 *bf = nullptr;
+    CUtensorMap map_fc1[3][kLayers], map_fc2[3][kLayers], map_mrg[3], map_head[3];
+};
+
+struct WorkspaceBf {                  // scratch of the BF16 path, grow-only
+    int cap = 0;
+    __nv_bfloat16 *Hb_rho = nullptr, *Hb_f = nullptr, *XTb = nullptr, *E = nullptr, *S = nullptr,
+                  *H = nullptr, *mrg_in[3] = {nullptr, nullptr, nullptr}, *head_in = nullptr,
+                  *Z1 = nullptr, *Z2 = nullptr;
+    float *H_T = nullptr, *w_se = nullptr, *cfg = nullptr, *v = nullptr;
+    CUtensorMap map_rho, map_f, map_xt, map_s, map_mrg[3], map_head, map_z1, map_z2;
 };
 
 struct Workspace {                    // scratch of nis_shade_points, grow-only
@@ -70,6 +82,8 @@ struct nis_ctx {
     std::map<nis_handle, Weights> weights;
     std::map<uint32_t, float *> phase;   // by the bit pattern of g
     Workspace ws;
+    WorkspaceBf wsb;
+    int num_sms = 0;
     nis_handle next = 1;
     // kernel timing (nis_profile)
     bool prof_on = false;
@@ -230,6 +244,81 @@ nis_status ensure_workspace(nis_ctx *ctx, int cap, cudaStream_t s) {
     return NIS_OK;
 }
 
+nis_status ensure_workspace_bf16(nis_ctx *ctx, int cap, cudaStream_t s) {
+    WorkspaceBf &w = ctx->wsb;
+    if (w.cap >= cap) return NIS_OK;
+    __nv_bfloat16 **bb[] = {&w.Hb_rho, &w.Hb_f, &w.XTb, &w.E, &w.S, &w.H, &w.mrg_in[0], &w.mrg_in[1],
+                            &w.mrg_in[2], &w.head_in, &w.Z1, &w.Z2};
+    for (auto **b : bb) { dev_free(ctx, *b); *b = nullptr; }
+    float **ff[] = {&w.H_T, &w.w_se, &w.cfg, &w.v};
+    for (float **f : ff) { dev_free(ctx, *f); *f = nullptr; }
+    w.cap = 0;
+    const size_t n = (size_t)cap;
+    nis_status st;
+    if ((st = dev_alloc_t(ctx, n * kLayers * kLatPad, &w.Hb_rho, s))) return st;
+    if ((st = dev_alloc_t(ctx, n * kLayers * kLatPad, &w.Hb_f, s))) return st;
+    if ((st = dev_alloc_t(ctx, n * kLayers * kDT, &w.XTb, s))) return st;
+    for (auto **b : {&w.E, &w.S, &w.H, &w.Z1, &w.Z2})
+        if ((st = dev_alloc_t(ctx, n * kWidth, b, s))) return st;
+    for (int t = 0; t < 3; ++t)
+        if ((st = dev_alloc_t(ctx, n * 2 * kWidth, &w.mrg_in[t], s))) return st;
+    if ((st = dev_alloc_t(ctx, n * 3 * kWidth, &w.head_in, s))) return st;
+    if ((st = dev_alloc_t(ctx, n * kLayers * kLat, &w.H_T, s))) return st;
+    if ((st = dev_alloc_t(ctx, n * kLayers * 3, &w.w_se, s))) return st;
+    if ((st = dev_alloc_t(ctx, n * kCfg, &w.cfg, s))) return st;
+    if ((st = dev_alloc_t(ctx, n * kLayers * 8, &w.v, s))) return st;
+    bool ok = make_tmap_bf16(&w.map_rho, w.Hb_rho, kLayers * kLatPad, n, kLayers * kLatPad * 2, 64, 128) &&
+              make_tmap_bf16(&w.map_f, w.Hb_f, kLayers * kLatPad, n, kLayers * kLatPad * 2, 64, 128) &&
+              make_tmap_bf16(&w.map_xt, w.XTb, kLayers * kDT, n, kLayers * kDT * 2, 64, 128) &&
+              make_tmap_bf16(&w.map_s, w.S, kWidth, n, kWidth * 2, 64, 128) &&
+              make_tmap_bf16(&w.map_head, w.head_in, 3 * kWidth, n, 3 * kWidth * 2, 64, 128) &&
+              make_tmap_bf16(&w.map_z1, w.Z1, kWidth, n, kWidth * 2, 64, 128) &&
+              make_tmap_bf16(&w.map_z2, w.Z2, kWidth, n, kWidth * 2, 64, 128);
+    for (int t = 0; t < 3; ++t)
+        ok = ok && make_tmap_bf16(&w.map_mrg[t], w.mrg_in[t], 2 * kWidth, n, 2 * kWidth * 2, 64, 128);
+    if (!ok) return fail(ctx, NIS_ERR_CUDA, "cuTensorMapEncodeTiled failed for the BF16 workspace");
+    w.cap = cap;
+    return NIS_OK;
+}
+
+int n_mma_of(int n) { return (n + 15) / 16 * 16; }
+int k_pad_of(int k) { return (k + 63) / 64 * 64; }
+
+// BF16 weight pack: one zero-padded [n_mma][Kp] matrix per dense layer plus its tensor map.
+nis_status pack_weights_bf16(nis_ctx *ctx, Weights &w, cudaStream_t s) {
+    struct Mat { const float *src; int N, K, ld; CUtensorMap *map; };
+    std::vector<Mat> mats;
+    const WeightOffsets &o = w.off;
+    for (int t = 0; t < 3; ++t)
+        for (int k = 0; k < kLayers; ++k) {
+            int d = feat_dim(t);
+            mats.push_back({w.f32 + o.blk_w1[t][k], kWidth, d, d + kCfg, &w.map_fc1[t][k]});
+            mats.push_back({w.f32 + o.blk_w2[t][k], kWidth, kWidth, kWidth, &w.map_fc2[t][k]});
+        }
+    for (int t = 0; t < 3; ++t) mats.push_back({w.f32 + o.mrg_w[t], kWidth, 2 * kWidth, 2 * kWidth, &w.map_mrg[t]});
+    mats.push_back({w.f32 + o.head_w[0], kWidth, 3 * kWidth, 3 * kWidth, &w.map_head[0]});
+    mats.push_back({w.f32 + o.head_w[1], kWidth, kWidth, kWidth, &w.map_head[1]});
+    mats.push_back({w.f32 + o.head_w[2], 3, kWidth, kWidth, &w.map_head[2]});
+    size_t total = 0;
+    for (auto &m : mats) total += (size_t)n_mma_of(m.N) * k_pad_of(m.K);
+    nis_status st = dev_alloc_t(ctx, total, &w.bf, s);
+    if (st) return st;
+    size_t off = 0;
+    for (auto &m : mats) {
+        int np = n_mma_of(m.N), kp = k_pad_of(m.K);
+        __nv_bfloat16 *dst = w.bf + off;
+        {
+            ProfScope ps(ctx, "other", s);
+            launch_pack_bf16(m.src, m.N, m.K, m.ld, dst, np, kp, s);
+        }
+        if (!make_tmap_bf16(m.map, dst, (uint64_t)kp, (uint64_t)np, (uint64_t)kp * 2, 64, (uint32_t)np))
+            return fail(ctx, NIS_ERR_CUDA, "cuTensorMapEncodeTiled failed for a weight matrix");
+        off += (size_t)np * kp;
+    }
+    NIS_CUDA(cudaGetLastError());
+    return NIS_OK;
+}
+
 nis_status check_material(nis_ctx *ctx, const nis_material *m) {
     if (!m) return fail(ctx, NIS_ERR_INVALID_ARG, "material is NULL");
     if (!(m->g > -1.f && m->g < 1.f)) return fail(ctx, NIS_ERR_INVALID_ARG, "g must lie in (-1, 1)");
@@ -239,6 +328,11 @@ nis_status check_material(nis_ctx *ctx, const nis_material *m) {
     return NIS_OK;
 }
 
+nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, const Weights &wt,
+                           const nis_material *m, const float *table, const float *pts,
+                           const float *om, int n, float *rgb, const nis_debug_out *dbg,
+                           cudaStream_t s);
+
 // Runs steps 3-6 for `n` points already on the device.
 nis_status shade_impl(nis_ctx *ctx, const Volume &vol, const Light &light, const Weights &wt,
                       const nis_material *m, const float *pts, const float *om, int n,
@@ -246,8 +340,10 @@ nis_status shade_impl(nis_ctx *ctx, const Volume &vol, const Light &light, const
     float *table;
     nis_status st = ensure_phase(ctx, m->g, s, &table);
     if (st) return st;
+    if (n <= 0) return NIS_OK;
+    if (wt.precision == NIS_PREC_BF16)
+        return shade_impl_bf16(ctx, vol, light, wt, m, table, pts, om, n, rgb, dbg, s);
     int chunk = n < kChunk ? n : kChunk;
-    if (chunk <= 0) return NIS_OK;
     if ((st = ensure_workspace(ctx, chunk, s))) return st;
     Workspace &w = ctx->ws;
     const WeightOffsets &o = wt.off;
@@ -282,7 +378,7 @@ nis_status shade_impl(nis_ctx *ctx, const Volume &vol, const Light &light, const
         }
         {
             ProfScope ps(ctx, "cnn", s);
-            launch_cnn_f32(w.H_T, cnt, W, o, w.X_T, s);
+            launch_cnn_f32(w.H_T, cnt, W, o, w.X_T, nullptr, s);
         }
 
         // backbone: 3 types x (diffuse chain of 8, highlight chain of 4)
@@ -353,6 +449,114 @@ nis_status shade_impl(nis_ctx *ctx, const Volume &vol, const Light &light, const
             NIS_CUDA(cp(dbg->H_f, w.H_f, (size_t)kLayers * kLat));
             NIS_CUDA(cp(dbg->v, w.v, (size_t)kLayers * 8));
             NIS_CUDA(cp(dbg->X_T, w.X_T, (size_t)kLayers * kDT));
+            NIS_CUDA(cp(dbg->w_se, w.w_se, (size_t)kLayers * 3));
+        }
+        NIS_CUDA(cudaGetLastError());
+    }
+    return NIS_OK;
+}
+
+// Steps 3-6 with the dense layers on the tensor cores (BF16 operands, FP32 accumulation).
+nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, const Weights &wt,
+                           const nis_material *m, const float *table, const float *pts,
+                           const float *om, int n, float *rgb, const nis_debug_out *dbg,
+                           cudaStream_t s) {
+    int chunk = n < kChunk ? n : kChunk;
+    nis_status st = ensure_workspace_bf16(ctx, chunk, s);
+    if (st) return st;
+    WorkspaceBf &w = ctx->wsb;
+    const WeightOffsets &o = wt.off;
+    const float *W = wt.f32;
+    float dec_scale[3];
+    for (int c = 0; c < 3; ++c) dec_scale[c] = m->intensity[c] * powf(m->albedo[c], 4.0f);
+    auto gemm = [&](const TcGemmArgs &a, const CUtensorMap &ma, const CUtensorMap &mb) {
+        ProfScope ps(ctx, "mlp", s);
+        launch_tc_gemm(a, ma, mb, ctx->num_sms, s);
+    };
+    for (int off = 0; off < n; off += chunk) {
+        int cnt = n - off < chunk ? n - off : chunk;
+        GatherArgs ga{};
+        ga.rho = view_of(vol, vol.data);
+        ga.T = view_of(vol, light.data);
+        ga.table = table;
+        ga.points = pts + 3 * (size_t)off;
+        ga.omega = om + 3 * (size_t)off;
+        ga.count = cnt;
+        ga.lx = light.dir[0]; ga.ly = light.dir[1]; ga.lz = light.dir[2];
+        ga.g = m->g;
+        for (int c = 0; c < 3; ++c) ga.albedo[c] = m->albedo[c];
+        ga.se = W;
+        for (int k = 0; k < kLayers; ++k) {
+            ga.se_w1[k] = o.se_w1[k]; ga.se_b1[k] = o.se_b1[k];
+            ga.se_w2[k] = o.se_w2[k]; ga.se_b2[k] = o.se_b2[k];
+        }
+        ga.H_T = w.H_T; ga.Hb_rho = w.Hb_rho; ga.Hb_f = w.Hb_f;
+        ga.v = dbg ? w.v : nullptr; ga.w_se = w.w_se; ga.cfg = w.cfg;
+        {
+            ProfScope ps(ctx, "gather", s);
+            launch_gather(ga, s);
+        }
+        {
+            ProfScope ps(ctx, "cnn", s);
+            launch_cnn_f32(w.H_T, cnt, W, o, nullptr, w.XTb, s);
+        }
+        for (int t = 0; t < 3; ++t) {
+            const int d = feat_dim(t);
+            const CUtensorMap &fmap = t == 0 ? w.map_rho : (t == 1 ? w.map_f : w.map_xt);
+            const int fstride = t == 2 ? kDT : kLatPad;
+            for (int chain = 0; chain < 2; ++chain) {
+                int k0 = chain == 0 ? 0 : kDiffuse, k1 = chain == 0 ? kDiffuse : kLayers;
+                for (int k = k0; k < k1; ++k) {
+                    TcGemmArgs f1{};
+                    f1.M = cnt; f1.N = kWidth; f1.K = d; f1.n_mma = 208; f1.k_tiles = (d + 63) / 64;
+                    f1.a_col0 = k * fstride; f1.epi = kEpiFc1; f1.err = ctx->d_err;
+                    f1.out_e = w.E; f1.out_s = w.S; f1.ldo = kWidth;
+                    f1.bias = W + o.blk_b1[t][k];
+                    f1.row_scale = w.w_se + k * 3 + t; f1.row_scale_ld = kLayers * 3;
+                    f1.cfg = w.cfg; f1.w_cfg = W + o.blk_w1[t][k] + d; f1.w_cfg_ld = d + kCfg;
+                    f1.mat_cfg[0] = m->g;
+                    for (int c = 0; c < 3; ++c) f1.mat_cfg[1 + c] = m->albedo[c];
+                    f1.h_prev = k == k0 ? nullptr : w.H; f1.ld_h = kWidth;
+                    gemm(f1, fmap, wt.map_fc1[t][k]);
+                    TcGemmArgs f2{};
+                    f2.M = cnt; f2.N = kWidth; f2.K = kWidth; f2.n_mma = 208; f2.k_tiles = 4;
+                    f2.epi = kEpiFc2; f2.err = ctx->d_err;
+                    f2.bias = W + o.blk_b2[t][k];
+                    f2.resid = w.E; f2.ld_resid = kWidth;
+                    if (k == k1 - 1) { f2.out_bf = w.mrg_in[t] + chain * kWidth; f2.ldo = 2 * kWidth; }
+                    else { f2.out_bf = w.H; f2.ldo = kWidth; }
+                    gemm(f2, w.map_s, wt.map_fc2[t][k]);
+                }
+            }
+            TcGemmArgs mg{};
+            mg.M = cnt; mg.N = kWidth; mg.K = 2 * kWidth; mg.n_mma = 208; mg.k_tiles = 7;
+            mg.epi = kEpiRelu; mg.err = ctx->d_err; mg.bias = W + o.mrg_b[t];
+            mg.out_bf = w.head_in + t * kWidth; mg.ldo = 3 * kWidth;
+            gemm(mg, w.map_mrg[t], wt.map_mrg[t]);
+        }
+        TcGemmArgs h1{};
+        h1.M = cnt; h1.N = kWidth; h1.K = 3 * kWidth; h1.n_mma = 208; h1.k_tiles = 10;
+        h1.epi = kEpiRelu; h1.err = ctx->d_err; h1.bias = W + o.head_b[0];
+        h1.out_bf = w.Z1; h1.ldo = kWidth;
+        gemm(h1, w.map_head, wt.map_head[0]);
+        TcGemmArgs h2 = h1;
+        h2.K = kWidth; h2.k_tiles = 4; h2.bias = W + o.head_b[1]; h2.out_bf = w.Z2;
+        gemm(h2, w.map_z1, wt.map_head[1]);
+        TcGemmArgs h3{};
+        h3.M = cnt; h3.N = 3; h3.K = kWidth; h3.n_mma = 16; h3.k_tiles = 4;
+        h3.epi = kEpiDecode; h3.err = ctx->d_err; h3.bias = W + o.head_b[2];
+        for (int c = 0; c < 3; ++c) h3.dec_scale[c] = dec_scale[c];
+        h3.out_f32 = rgb + 3 * (size_t)off;
+        h3.y_out = (dbg && dbg->y) ? dbg->y + 3 * (size_t)off : nullptr;
+        gemm(h3, w.map_z2, wt.map_head[2]);
+        if (dbg) {
+            auto cp = [&](float *dst, const float *src, size_t per) -> cudaError_t {
+                if (!dst) return cudaSuccess;
+                return cudaMemcpyAsync(dst + per * off, src, per * cnt * sizeof(float),
+                                       cudaMemcpyDeviceToDevice, s);
+            };
+            NIS_CUDA(cp(dbg->H_T, w.H_T, (size_t)kLayers * kLat));
+            NIS_CUDA(cp(dbg->v, w.v, (size_t)kLayers * 8));
             NIS_CUDA(cp(dbg->w_se, w.w_se, (size_t)kLayers * 3));
         }
         NIS_CUDA(cudaGetLastError());
@@ -558,6 +762,7 @@ nis_status nis_create(nis_ctx **out, int device, size_t hbm_budget_bytes,
         return NIS_ERR_OOM;
     }
     ctx->d_err = static_cast<unsigned *>(p);
+    cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (cudaMemset(ctx->d_err, 0, sizeof(unsigned)) != cudaSuccess ||
         cudaMallocHost(&ctx->ws.host_count, sizeof(int)) != cudaSuccess) {
         g_create_error = "device set-up failed";
@@ -706,8 +911,8 @@ nis_status nis_load_weights(nis_ctx *ctx, const void *blob, size_t bytes, int pr
                             nis_stream stream, nis_weights *out) {
     if (!ctx) return NIS_ERR_INVALID_ARG;
     if (!blob || !out) return fail(ctx, NIS_ERR_INVALID_ARG, "NULL blob or out");
-    if (precision != NIS_PREC_F32)
-        return fail(ctx, NIS_ERR_UNIMPLEMENTED, "only NIS_PREC_F32 is available");
+    if (precision != NIS_PREC_F32 && precision != NIS_PREC_BF16)
+        return fail(ctx, NIS_ERR_UNIMPLEMENTED, "precision must be NIS_PREC_F32 or NIS_PREC_BF16");
     if (bytes < 80) return fail(ctx, NIS_ERR_BAD_BLOB, "blob shorter than its header");
     uint32_t hd[16];
     uint64_t n_floats, checksum;
@@ -738,6 +943,11 @@ nis_status nis_load_weights(nis_ctx *ctx, const void *blob, size_t bytes, int pr
     cudaError_t e = cudaMemcpyAsync(w.f32, words, o.total * 4, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the caller may free the blob
     if (e != cudaSuccess) { dev_free(ctx, w.f32); return cuda_fail(ctx, e, "weights upload"); }
+    if (precision == NIS_PREC_BF16 && (st = pack_weights_bf16(ctx, w, s))) {
+        dev_free(ctx, w.f32);
+        dev_free(ctx, w.bf);
+        return st;
+    }
     nis_handle h = ctx->next++;
     ctx->weights[h] = w;
     *out = h;
@@ -861,6 +1071,7 @@ nis_status nis_release(nis_ctx *ctx, nis_handle h) {
     if (Weights *w = lookup(ctx->weights, h)) {
         cudaDeviceSynchronize();
         dev_free(ctx, w->f32);
+        dev_free(ctx, w->bf);
         ctx->weights.erase(h);
         return NIS_OK;
     }

@@ -18,6 +18,7 @@ constexpr int kDiffuse = 8;
 constexpr int kHighlight = 4;
 constexpr int kLatA = 5, kLatB = 5, kLatC = 9;
 constexpr int kLat = 225;            // lattice points per layer
+constexpr int kLatPad = 232;         // BF16 feature row per layer, padded to 16 bytes
 constexpr int kPhaseSets = 5;        // all diffuse layers share one set; one per highlight
 constexpr int kAlpha = 1024;         // alpha nodes of the phase table
 constexpr int kRings = 16;           // cap quadrature: rings (angle midpoints) ...
@@ -142,7 +143,8 @@ struct GatherArgs {
     float albedo[3];
     const float *se;                 // FP32 weights base; SE offsets below
     size_t se_w1[kLayers], se_b1[kLayers], se_w2[kLayers], se_b2[kLayers];
-    float *H_rho, *H_T, *H_f;        // [count][12][225]
+    float *H_rho, *H_T, *H_f;        // [count][12][225] (H_rho, H_f may be null when Hb_* set)
+    __nv_bfloat16 *Hb_rho, *Hb_f;    // optional BF16 copies [count][12][kLatPad] (pad zeroed)
     float *v;                        // [count][12][8] (may be null)
     float *w_se;                     // [count][12][3]
     float *cfg;                      // [count][5]
@@ -150,7 +152,10 @@ struct GatherArgs {
 void launch_gather(const GatherArgs &a, cudaStream_t s);
 
 void launch_cnn_f32(const float *H_T, int count, const float *wbase, const WeightOffsets &o,
-                    float *X_T, cudaStream_t s);
+                    float *X_T, __nv_bfloat16 *X_T_bf, cudaStream_t s);
+// dst[n][k] = bf16(src[n * ld_src + k]) for n < N, k < K, zero elsewhere in [Np][Kp]
+void launch_pack_bf16(const float *src, int N, int K, int ld_src, __nv_bfloat16 *dst, int Np,
+                      int Kp, cudaStream_t s);
 
 // One dense layer out[r][j] = epilogue(sum_k A[r][k] W[j][k] + b[j]) over rows r < count.
 struct FcArgs {
@@ -196,8 +201,9 @@ struct TcGemmArgs {
     int ldo;
     const float *bias;                // [N]
     const float *row_scale; int row_scale_ld;   // kEpiFc1: SE weight per row
-    const float *cfg;                 // kEpiFc1: [M][5] configuration vector
-    const float *w_cfg;               // kEpiFc1: [N][5] weight columns of c
+    const float *cfg;                 // kEpiFc1: [M][5] configuration vector (alpha = [4])
+    const float *w_cfg; int w_cfg_ld; // kEpiFc1: weight columns of c, row n at w_cfg + n*ld
+    float mat_cfg[4];                 // kEpiFc1: g, albedo rgb (the same for every row)
     const __nv_bfloat16 *h_prev; int ld_h;      // kEpiFc1 running state (may be null)
     const __nv_bfloat16 *resid; int ld_resid;   // kEpiFc2: e
     float dec_scale[3];               // kEpiDecode: I * albedo^4

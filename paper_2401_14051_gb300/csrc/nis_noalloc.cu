@@ -116,7 +116,7 @@ extern "C" nis_status nis_shade_points_static(nis_ctx *ctx, nis_volume vol, nis_
     }
     ga.H_rho = H_rho; ga.H_T = H_T; ga.H_f = H_f; ga.v = v; ga.w_se = w_se; ga.cfg = cfg;
     launch_gather(ga, s);
-    launch_cnn_f32(H_T, n, W, o, X_T, s);
+    launch_cnn_f32(H_T, n, W, o, X_T, nullptr, s);
     for (int t = 0; t < 3; ++t) {
         const float *X = t == 0 ? H_rho : (t == 1 ? H_f : X_T);
         const int d = feat_dim(t);

@@ -1,0 +1,82 @@
+"""Reduced-precision modes: the dense layers on tensor cores in BF16 (FP32 accumulation),
+the transmittance march and exponentials in FP32.  Radiance error against the FP64 oracle
+on the 64^3 fBm workload, stated as mean and max of the floored relative error; the target
+for BF16 is a mean of at most 2e-2."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def rel_err(a, b):
+    floor = 1e-2 * np.abs(b).max(axis=0, keepdims=True)
+    return np.abs(a - b) / np.maximum(np.abs(b), floor)
+
+
+@pytest.fixture(scope="module")
+def env():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2401_14051_gb300 import build, nis
+    build.build()
+    cfg = synth.config(1)
+    vol = cfg["volume"]()
+    weights = synth.make_weights(cfg["weights_seed"], cfg["sigma_max"])
+    blob = synth.pack_weights(weights)
+    ctx = nis.Context(0)
+    v = ctx.upload_volume(vol)
+    l = ctx.build_transmittance(v, cfg["light"], 0.6)
+    w32 = ctx.load_weights(blob, nis.PREC_F32)
+    wbf = ctx.load_weights(blob, nis.PREC_BF16)
+    ctx.sync(timeout_ms=60000)
+    yield {"nis": nis, "ctx": ctx, "cfg": cfg, "vol": vol, "weights": weights, "v": v, "l": l,
+           "w32": w32, "wbf": wbf}
+    ctx.close()
+
+
+def test_bf16_against_fp64_oracle(env):
+    ctx, cfg = env["ctx"], env["cfg"]
+    p, om = synth.shading_points(2048, 404, 0.05, 0.95)
+    dev = torch.device("cuda:0")
+    rgb = ctx.shade_points(env["v"], env["l"], env["wbf"], cfg["material"],
+                           torch.from_numpy(p).to(dev), torch.from_numpy(om).to(dev))
+    ctx.sync(timeout_ms=60000)
+    levels, tl, table = O.prepare(env["vol"], cfg["light"], cfg["material"]["g"])
+    ref = O.shade_points(p, om, cfg["light"], levels, tl, table, env["weights"], cfg["material"])
+    e = rel_err(rgb.cpu().numpy(), ref)
+    print(f"\n[precision] BF16 vs FP64 oracle, 2048 points: mean rel {e.mean():.3g}, "
+          f"max rel {e.max():.3g}")
+    assert np.isfinite(e).all()
+    assert e.mean() <= 2e-2
+
+
+def test_bf16_against_fp32_path_many_points(env):
+    ctx, cfg = env["ctx"], env["cfg"]
+    n = 70000                                  # more than one 65,536-point pass
+    p, om = synth.shading_points(n, 505, -0.05, 1.05)
+    dev = torch.device("cuda:0")
+    pt, ot = torch.from_numpy(p).to(dev), torch.from_numpy(om).to(dev)
+    r32 = ctx.shade_points(env["v"], env["l"], env["w32"], cfg["material"], pt, ot)
+    rbf = ctx.shade_points(env["v"], env["l"], env["wbf"], cfg["material"], pt, ot)
+    ctx.sync(timeout_ms=60000)
+    e = rel_err(rbf.cpu().numpy(), r32.cpu().numpy())
+    print(f"\n[precision] BF16 vs FP32 path, {n} points: mean rel {e.mean():.3g}, max rel {e.max():.3g}")
+    assert e.mean() <= 2e-2
+
+
+def test_bf16_render_frame(env):
+    ctx, cfg = env["ctx"], env["cfg"]
+    cam = cfg["camera"]
+    i32 = ctx.render_frame(env["v"], env["l"], env["w32"], cfg["material"], cam)
+    ibf = ctx.render_frame(env["v"], env["l"], env["wbf"], cfg["material"], cam)
+    ctx.sync(timeout_ms=60000)
+    a, b = ibf.cpu().numpy(), i32.cpu().numpy()
+    hit = np.abs(b).sum(-1) > 0
+    assert np.array_equal(np.abs(a).sum(-1) > 0, hit)
+    e = rel_err(a[hit], b[hit])
+    print(f"\n[precision] BF16 frame vs FP32 frame: mean rel {e.mean():.3g}, max {e.max():.3g}")
+    assert e.mean() <= 2e-2
