@@ -74,4 +74,30 @@ void launch_downsample(const float *src, int n, float *dst, int m, cudaStream_t 
     downsample_kernel<<<blocks, threads, 0, s>>>(src, n, dst, m);
 }
 
+__global__ void occupancy_kernel(const float *__restrict__ level, int n, unsigned char *occ) {
+    const int nb = bricks_of(n);
+    size_t total = (size_t)nb * nb * nb;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        int bx = (int)(idx % nb), by = (int)((idx / nb) % nb), bz = (int)(idx / ((size_t)nb * nb));
+        int x0 = max(bx * kBrick - 1, 0), x1 = min(bx * kBrick + kBrick, n - 1);
+        int y0 = max(by * kBrick - 1, 0), y1 = min(by * kBrick + kBrick, n - 1);
+        int z0 = max(bz * kBrick - 1, 0), z1 = min(bz * kBrick + kBrick, n - 1);
+        unsigned char any = 0;
+        for (int z = z0; z <= z1 && !any; ++z)
+            for (int y = y0; y <= y1 && !any; ++y)
+                for (int x = x0; x <= x1; ++x)
+                    if (__ldg(level + ((size_t)z * n + y) * n + x) != 0.f) { any = 1; break; }
+        occ[idx] = any;
+    }
+}
+
+void launch_occupancy(const float *level, int n, unsigned char *occ, cudaStream_t s) {
+    const int nb = bricks_of(n);
+    size_t total = (size_t)nb * nb * nb;
+    int blocks = (int)((total + 255) / 256 < 152 * 16 ? (total + 255) / 256 : 152 * 16);
+    note_launch();
+    occupancy_kernel<<<blocks, 256, 0, s>>>(level, n, occ);
+}
+
 }  // namespace nis

@@ -24,6 +24,8 @@ struct Volume {
     size_t total = 0;                 // floats in all levels
     float *data = nullptr;
     float *sigma_max = nullptr;       // device scalar (max of level 0)
+    unsigned char *occ = nullptr;     // brick occupancy of every level (march skipping)
+    size_t occ_off[kMaxLevels] = {};
     void *staging = nullptr;          // pageable-host updates (nis_update_volume)
     size_t staging_bytes = 0;
     bool pyramid = false;
@@ -195,6 +197,20 @@ nis_status build_pyramid_impl(nis_ctx *ctx, Volume &v, cudaStream_t s) {
     for (int m = 1; m < v.levels; ++m) {
         ProfScope ps(ctx, "pyramid", s);
         launch_downsample(v.data + v.off[m - 1], v.sizes[m - 1], v.data + v.off[m], v.sizes[m], s);
+    }
+    if (!v.occ) {
+        size_t total = 0;
+        for (int m = 0; m < v.levels; ++m) {
+            v.occ_off[m] = total;
+            size_t nb = (size_t)bricks_of(v.sizes[m]);
+            total += nb * nb * nb;
+        }
+        nis_status st = dev_alloc_t(ctx, total, &v.occ, s);
+        if (st) return st;
+    }
+    for (int m = 0; m < v.levels; ++m) {
+        ProfScope ps(ctx, "pyramid", s);
+        launch_occupancy(v.data + v.off[m], v.sizes[m], v.occ + v.occ_off[m], s);
     }
     NIS_CUDA(cudaGetLastError());
     v.pyramid = true;
@@ -899,8 +915,8 @@ nis_status nis_build_transmittance(nis_ctx *ctx, nis_volume vol, const float lig
     // u = -l points toward the light
     for (int m = 0; m < v->levels; ++m) {
         ProfScope ps(ctx, "march", s);
-        launch_march(v->data + v->off[m], v->sizes[m], m, -dir[0], -dir[1], -dir[2], lambda,
-                     L.data + v->off[m], s);
+        launch_march(v->data + v->off[m], v->occ + v->occ_off[m], v->sizes[m], m, -dir[0], -dir[1],
+                     -dir[2], lambda, L.data + v->off[m], s);
     }
     NIS_CUDA(cudaGetLastError());
     *out = h;
@@ -1059,6 +1075,7 @@ nis_status nis_release(nis_ctx *ctx, nis_handle h) {
         dev_free(ctx, v->data);
         dev_free(ctx, v->sigma_max);
         dev_free(ctx, v->staging);
+        dev_free(ctx, v->occ);
         ctx->vols.erase(h);
         return NIS_OK;
     }

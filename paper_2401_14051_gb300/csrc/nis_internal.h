@@ -121,9 +121,14 @@ void note_launch();                  // counts every kernel launch of the librar
 void launch_convert_density(const void *src, int dtype, float scale, size_t count,
                             float *dst, unsigned *err, float *sigma_max, cudaStream_t s);
 void launch_downsample(const float *src, int n, float *dst, int m, cudaStream_t s);
+// occupancy of 4^3-voxel bricks of an n^3 level, dilated by one voxel: occ = 0 guarantees
+// that every trilinear cell whose base voxel lies in the brick has eight zero corners
+constexpr int kBrick = 4;
+__host__ __device__ inline int bricks_of(int n) { return (n + kBrick - 1) / kBrick; }
+void launch_occupancy(const float *level, int n, unsigned char *occ, cudaStream_t s);
 // transmittance of one level
-void launch_march(const float *level, int n, int m, float ux, float uy, float uz, float lam,
-                  float *out, cudaStream_t s);
+void launch_march(const float *level, const unsigned char *occ, int n, int m, float ux,
+                  float uy, float uz, float lam, float *out, cudaStream_t s);
 // phase table [kAlpha][kPhaseSets][kLat]
 void launch_phase_table(float g, float *table, cudaStream_t s);
 
