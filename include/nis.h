@@ -193,6 +193,78 @@ nis_status nis_shade_points_static(nis_ctx *ctx, nis_volume vol, nis_light light
                                    const float *d_points, const float *d_omega, int n,
                                    float *d_rgb_out, nis_stream stream);
 
+/* One request's share of a mixed batch: n shading points (device, n x 3) of volume `vol`
+ * lit by `light` with its material; radiance goes to d_rgb_out (device, n x 3). */
+typedef struct nis_segment {
+    nis_volume vol;
+    nis_light light;
+    nis_material material;
+    const float *d_points, *d_omega;
+    int n;
+    float *d_rgb_out;
+} nis_segment;
+
+/* Continuous batching (the paper's "multiple network instances in parallel", Sec. III.C.2,
+ * across requests): shades the points of several requests -- different volumes, lights and
+ * materials -- in the same gather, CNN and MLP launches.  Each point carries its request's
+ * pyramid, transmittance field, phase table, light and material, so every result equals
+ * what nis_shade_points gives for that request alone.  Pyramids must be built. */
+nis_status nis_shade_segments(nis_ctx *ctx, nis_weights w, const nis_segment *segs, int nseg,
+                              nis_stream stream);
+
+/* ---- serving: continuous batching of render requests -----------------------------------
+ * A server owns a context (no other calls on that context while the server lives) and one
+ * host thread.  Requests -- each a density grid in host memory with its light, material and
+ * camera -- are admitted in arrival order while the HBM budget and the in-flight limit
+ * allow; an admitted request's volume upload, pyramid, transmittance march and first-hit
+ * search run on a preparation stream while earlier requests shade on a second stream; the
+ * shading points of all ready requests are shaded together in mixed batches
+ * (nis_shade_segments), so requests that arrive while others run join the next batch.
+ * Pyramids are cached per volume_key and transmittance fields per (volume_key, light,
+ * lambda), kept on the device and evicted least-recently-used (unreferenced only) when the
+ * budget needs room.  Each request's image is written to its rgb_out (host, H x W x 3
+ * float32) before nis_server_wait reports it done. */
+typedef struct nis_server nis_server;
+
+typedef struct nis_server_config {
+    size_t hbm_budget_bytes;      /* device memory the server may hold (0 = no limit) */
+    int max_batch_points;         /* shading points per mixed batch (<= 65536) */
+    int max_inflight;             /* admitted, unfinished requests at most */
+} nis_server_config;
+
+typedef struct nis_request {
+    const void *density;          /* host N^3 grid (NIS_DTYPE_*), kept valid until done */
+    int n;
+    int dtype;
+    uint64_t volume_key;          /* same key = same density: the pyramid is reused */
+    float light_dir[3];
+    float lambda;
+    nis_material material;
+    nis_camera camera;
+    float *rgb_out;               /* host [height][width][3] float32 */
+} nis_request;
+
+typedef struct nis_server_stats {
+    uint64_t submitted, completed, failed;
+    double p50_ms, p99_ms, mean_ms, max_ms;       /* submit -> image in rgb_out */
+    uint64_t points_shaded, batches;
+    double mean_batch_points, mean_batch_requests;
+    uint64_t volume_hits, volume_misses, light_hits, light_misses, evictions;
+    size_t peak_bytes;
+    double span_seconds;          /* first submit -> last completion */
+} nis_server_stats;
+
+nis_status nis_server_create(nis_ctx *ctx, nis_weights w, const nis_server_config *cfg,
+                             nis_server **out);
+/* Queues a request (copies the struct; the buffers it points to stay the caller's). */
+nis_status nis_server_submit(nis_server *srv, const nis_request *req, uint64_t *id);
+/* Waits up to timeout_ms (<= 0: no limit) for request `id`; NIS_ERR_TIMEOUT if not done.
+ * latency_ms (may be NULL) receives submit-to-completion time. */
+nis_status nis_server_wait(nis_server *srv, uint64_t id, int timeout_ms, double *latency_ms);
+nis_status nis_server_get_stats(nis_server *srv, nis_server_stats *out);
+/* Stops the loop after the admitted requests finish and frees the server's buffers. */
+void nis_server_destroy(nis_server *srv);
+
 /* Frees a volume (and its lights), a light or a weight set. */
 nis_status nis_release(nis_ctx *ctx, nis_handle h);
 

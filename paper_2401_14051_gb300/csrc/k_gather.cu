@@ -15,6 +15,13 @@ __global__ void __launch_bounds__(kLayers * 32) gather_kernel(const __grid_const
     const int k = threadIdx.x >> 5;            // one warp per template layer
     const int lane = threadIdx.x & 31;
 
+    // single request, or this point's request in a mixed batch
+    const ReqDesc *d = a.descs ? a.descs + a.req_of_point[p] : nullptr;
+    const PyramidView &RHO = d ? d->rho : a.rho;
+    const PyramidView &TT = d ? d->T : a.T;
+    const float lx = d ? d->l[0] : a.lx, ly = d ? d->l[1] : a.ly, lz = d ? d->l[2] : a.lz;
+    const float gg = d ? d->g : a.g;
+    const float *table = d ? d->table : a.table;
     const float px = a.points[3 * p], py = a.points[3 * p + 1], pz = a.points[3 * p + 2];
     float ox = a.omega[3 * p], oy = a.omega[3 * p + 1], oz = a.omega[3 * p + 2];
     {
@@ -22,7 +29,7 @@ __global__ void __launch_bounds__(kLayers * 32) gather_kernel(const __grid_const
         ox *= inv; oy *= inv; oz *= inv;
     }
     // light frame: e_z toward the light, e_x = omega's part orthogonal to e_z
-    const float ezx = -a.lx, ezy = -a.ly, ezz = -a.lz;
+    const float ezx = -lx, ezy = -ly, ezz = -lz;
     float dz = ox * ezx + oy * ezy + oz * ezz;
     float wx = ox - dz * ezx, wy = oy - dz * ezy, wz = oz - dz * ezz;
     float nw = sqrtf(wx * wx + wy * wy + wz * wz);
@@ -38,17 +45,16 @@ __global__ void __launch_bounds__(kLayers * 32) gather_kernel(const __grid_const
     const float eyx = ezy * exz - ezz * exy, eyy = ezz * exx - ezx * exz,
                 eyz = ezx * exy - ezy * exx;
     // view angle alpha = angle(omega, l), via atan2 for conditioning near 0 and pi
-    float cx_ = oy * a.lz - oz * a.ly, cy_ = oz * a.lx - ox * a.lz, cz_ = ox * a.ly - oy * a.lx;
-    const float alpha = atan2f(sqrtf(cx_ * cx_ + cy_ * cy_ + cz_ * cz_),
-                               ox * a.lx + oy * a.ly + oz * a.lz);
+    float cx_ = oy * lz - oz * ly, cy_ = oz * lx - ox * lz, cz_ = ox * ly - oy * lx;
+    const float alpha = atan2f(sqrtf(cx_ * cx_ + cy_ * cy_ + cz_ * cz_), ox * lx + oy * ly + oz * lz);
     // phase-table interpolation weights
     // (clamped so that a NaN direction cannot index outside the table)
     float tt = fminf(fmaxf(alpha * ((kAlpha - 1) / 3.14159265358979f), 0.f), (float)(kAlpha - 1));
     int ja = min((int)floorf(tt), kAlpha - 2);
     float wa = tt - ja;
 
-    const int N = a.rho.n[0];
-    const int L = a.rho.levels;
+    const int N = RHO.n[0];
+    const int L = RHO.levels;
     // this warp's layer: centre, spacing, mip level and phase point set
     float cxk, cyk, czk, h;
     int m, set;
@@ -68,9 +74,9 @@ __global__ void __launch_bounds__(kLayers * 32) gather_kernel(const __grid_const
         m = (int)fminf(fmaxf(floorf(z), 0.f), (float)(L - 1));
         set = 1 + j;
     }
-    const float *rho_lv = a.rho.lv[m], *T_lv = a.T.lv[m];
-    const int nm = a.rho.n[m];
-    const float *row0 = a.table + ((size_t)ja * kPhaseSets + set) * kLat;
+    const float *rho_lv = RHO.lv[m], *T_lv = TT.lv[m];
+    const int nm = RHO.n[m];
+    const float *row0 = table + ((size_t)ja * kPhaseSets + set) * kLat;
     const float *row1 = row0 + kPhaseSets * kLat;
     const size_t obase = ((size_t)p * kLayers + k) * kLat;
     const size_t obase_b = ((size_t)p * kLayers + k) * kLatPad;
@@ -114,7 +120,7 @@ __global__ void __launch_bounds__(kLayers * 32) gather_kernel(const __grid_const
         m2 = fmaxf(m2, __shfl_xor_sync(~0u, m2, o));
     }
     if (lane == 0) {
-        float v[8] = {s0 * (1.0f / kLat), s1 * (1.0f / kLat), s2 * (1.0f / kLat), m0, m1, m2, a.g, alpha};
+        float v[8] = {s0 * (1.0f / kLat), s1 * (1.0f / kLat), s2 * (1.0f / kLat), m0, m1, m2, gg, alpha};
         if (a.v)
             for (int q = 0; q < 8; ++q) a.v[((size_t)p * kLayers + k) * 8 + q] = v[q];
         // SE excitation: w = sigmoid(W2 ReLU(W1 v + b1) + b2)
@@ -131,7 +137,8 @@ __global__ void __launch_bounds__(kLayers * 32) gather_kernel(const __grid_const
                 sigmoidf_(b2[r] + w2[r * 2] * z[0] + w2[r * 2 + 1] * z[1]);
         if (k == 0) {
             float *c = a.cfg + (size_t)p * kCfg;
-            c[0] = a.g; c[1] = a.albedo[0]; c[2] = a.albedo[1]; c[3] = a.albedo[2]; c[4] = alpha;
+            const float *alb = d ? d->albedo : a.albedo;
+            c[0] = gg; c[1] = alb[0]; c[2] = alb[1]; c[3] = alb[2]; c[4] = alpha;
         }
     }
 }
@@ -140,6 +147,32 @@ void launch_gather(const GatherArgs &a, cudaStream_t s) {
     if (a.count <= 0) return;
     note_launch();
     gather_kernel<<<a.count, kLayers * 32, 0, s>>>(a);
+}
+
+// Mixed batches: row -> request descriptor, and each row's decode scale.
+__global__ void fill_segments_kernel(const int *__restrict__ seg_start,
+                                     const int *__restrict__ seg_desc, int nseg, int count,
+                                     int *__restrict__ req_of_point, float *__restrict__ dec_rows,
+                                     const ReqDesc *__restrict__ descs) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= count) return;
+    int lo = 0, hi = nseg - 1;                // last segment whose start <= r
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (seg_start[mid] <= r) lo = mid; else hi = mid - 1;
+    }
+    int d = seg_desc[lo];
+    req_of_point[r] = d;
+    for (int c = 0; c < 3; ++c) dec_rows[3 * (size_t)r + c] = descs[d].dec[c];
+}
+
+void launch_fill_segments(const int *seg_start, const int *seg_desc, int nseg, int count,
+                          int *req_of_point, float *dec_rows, const ReqDesc *descs,
+                          cudaStream_t s) {
+    if (count <= 0) return;
+    note_launch();
+    fill_segments_kernel<<<(count + 255) / 256, 256, 0, s>>>(seg_start, seg_desc, nseg, count,
+                                                             req_of_point, dec_rows, descs);
 }
 
 }  // namespace nis

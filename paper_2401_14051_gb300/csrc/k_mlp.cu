@@ -74,7 +74,8 @@ __global__ void __launch_bounds__(256) fc_f32_kernel(const __grid_constant__ FcA
             if (a.resid) v += a.resid[(size_t)r * a.ldo + c];
             if (a.decode) {
                 if (a.y_out) a.y_out[(size_t)r * 3 + c] = v;
-                a.out[(size_t)r * 3 + c] = a.dec_scale[c] * expm1f(v);
+                const float ds = a.dec_rows ? a.dec_rows[(size_t)r * 3 + c] : a.dec_scale[c];
+                a.out[(size_t)r * 3 + c] = ds * expm1f(v);
             } else {
                 a.out[(size_t)r * a.ldo + c] = v;
             }

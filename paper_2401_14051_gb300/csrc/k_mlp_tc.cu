@@ -23,7 +23,7 @@ constexpr int TM = 128, TK = 64, TN_MAX = 208, STAGES = 4;
 constexpr uint32_t A_STAGE = TM * TK * 2;                 // 16 KB
 constexpr uint32_t B_STAGE = TN_MAX * TK * 2;             // 26 KB (208 rows)
 constexpr uint32_t SMEM_TILES = STAGES * (A_STAGE + B_STAGE);
-constexpr uint32_t SMEM_CONST = 2 * TN_MAX * 4;          // per-column epilogue constants
+constexpr uint32_t SMEM_CONST = 6 * TN_MAX * 4;          // per-column epilogue constants
 constexpr uint32_t SMEM_BYTES = SMEM_TILES + 256 + SMEM_CONST + 1024;  // + alignment slack
 constexpr int kEpiWarps = 8;                              // two per TMEM lane quarter
 constexpr int kThreads = 64 + 32 * kEpiWarps;
@@ -56,7 +56,8 @@ __device__ __forceinline__ void load_bf16x8(const __nv_bfloat16 *src, float *v) 
 // view angle.  pre: the residual / running-state values of this chunk, already loaded.
 __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs &a, int r, int c0, float (&v)[32],
                                                const float *s_bias, const float *s_wa, float sc,
-                                               float alpha, const float (&pre)[32]) {
+                                               float alpha, const float (&pre)[32],
+                                               const float *s_wm, const float (&rc)[4]) {
     const int N = a.N;
     switch (a.epi) {
     case kEpiPlain: {
@@ -71,7 +72,12 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs &a, int r, int c
         float sv[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-            float e = fmaxf(fmaf(v[j], sc, fmaf(s_wa[c0 + j], alpha, s_bias[c0 + j])), 0.f);
+            float b = fmaf(s_wa[c0 + j], alpha, s_bias[c0 + j]);
+            if (a.cfg_per_row) {                 // mixed batch: this row's g and albedo
+                const float *wm = s_wm + 4 * (c0 + j);
+                b = fmaf(wm[0], rc[0], fmaf(wm[1], rc[1], fmaf(wm[2], rc[2], fmaf(wm[3], rc[3], b))));
+            }
+            float e = fmaxf(fmaf(v[j], sc, b), 0.f);
             v[j] = e;
             sv[j] = a.h_prev ? pre[j] + e : e;
         }
@@ -106,7 +112,8 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs &a, int r, int c
             for (int j = 0; j < 3; ++j) {
                 float y = v[j] + s_bias[j];
                 if (a.y_out) a.y_out[(size_t)r * 3 + j] = y;
-                a.out_f32[(size_t)r * 3 + j] = a.dec_scale[j] * expm1f(y);
+                const float ds = a.dec_rows ? a.dec_rows[(size_t)r * 3 + j] : a.dec_scale[j];
+                a.out_f32[(size_t)r * 3 + j] = ds * expm1f(y);
             }
         }
         break;
@@ -145,6 +152,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
     float *s_bias = reinterpret_cast<float *>(smem + SMEM_TILES + 256);
     float *s_wa = s_bias + TN_MAX;
+    float *s_wm = s_wa + TN_MAX;              // [TN_MAX][4] weights of g and albedo (mixed)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_tiles = (a.M + TM - 1) / TM;
@@ -162,18 +170,23 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 0 && lane == 0) { tc::prefetch_tmap(&map_a); tc::prefetch_tmap(&map_b); }
     // per-column epilogue constants (columns >= N read as zero)
     for (int c = threadIdx.x; c < TN_MAX; c += blockDim.x) {
-        float b = 0.f, wa = 0.f;
+        float b = 0.f, wa = 0.f, wm[4] = {0.f, 0.f, 0.f, 0.f};
         if (c < a.N && a.bias) {
             b = a.bias[c];
             if (a.epi == kEpiFc1) {
                 const float *wc = a.w_cfg + (size_t)c * a.w_cfg_ld;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) b += wc[q] * a.mat_cfg[q];
+                for (int q = 0; q < 4; ++q) {
+                    if (a.cfg_per_row) wm[q] = wc[q];
+                    else b += wc[q] * a.mat_cfg[q];
+                }
                 wa = wc[4];
             }
         }
         s_bias[c] = b;
         s_wa[c] = wa;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) s_wm[4 * c + q] = wm[q];
     }
     if (warp == 1) {
         tc::tmem_alloc(tmem_slot, 512);
@@ -241,10 +254,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int buf = t & 1;
             const int r = tile * TM + q * 32 + lane;
             const bool live = r < a.M;
-            float sc = 0.f, alpha = 0.f;
+            float sc = 0.f, alpha = 0.f, rc[4] = {0.f, 0.f, 0.f, 0.f};
             if (live && a.epi == kEpiFc1) {
                 sc = a.row_scale[(size_t)r * a.row_scale_ld];
                 alpha = a.cfg[(size_t)r * kCfg + 4];
+                if (a.cfg_per_row)
+                    for (int q = 0; q < 4; ++q) rc[q] = a.cfg[(size_t)r * kCfg + q];
             }
             float pre[32];
             if (live && half * 32 < a.N) load_pre(a, r, half * 32, pre);
@@ -264,7 +279,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 // next chunk's residual loads overlap this chunk's TMEM load and math
                 if (live && c0 + 64 < a.N) load_pre(a, r, c0 + 64, pre);
                 tc::tmem_ld_wait();
-                if (live) epilogue_chunk(a, r, c0, v, s_bias, s_wa, sc, alpha, cur);
+                if (live) epilogue_chunk(a, r, c0, v, s_bias, s_wa, sc, alpha, cur, s_wm, rc);
             }
             tc::fence_before_sync();
             __syncwarp();

@@ -85,6 +85,11 @@ struct nis_ctx {
     std::map<uint32_t, float *> phase;   // by the bit pattern of g
     Workspace ws;
     WorkspaceBf wsb;
+    // mixed-batch buffers of nis_shade_segments (grow-only)
+    int mix_cap = 0, mix_desc_cap = 0;
+    float *mix_pts = nullptr, *mix_om = nullptr, *mix_rgb = nullptr, *mix_dec = nullptr;
+    int *mix_req = nullptr, *mix_seg_start = nullptr, *mix_seg_desc = nullptr;
+    ReqDesc *mix_descs = nullptr;
     int num_sms = 0;
     nis_handle next = 1;
     // kernel timing (nis_profile)
@@ -344,21 +349,28 @@ nis_status check_material(nis_ctx *ctx, const nis_material *m) {
     return NIS_OK;
 }
 
+struct Mixed {                        // per-point request descriptors of a mixed batch
+    const ReqDesc *descs;
+    const int *req_of_point;
+    const float *dec_rows;
+};
+
 nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, const Weights &wt,
                            const nis_material *m, const float *table, const float *pts,
                            const float *om, int n, float *rgb, const nis_debug_out *dbg,
-                           cudaStream_t s);
+                           cudaStream_t s, const Mixed *mx);
 
 // Runs steps 3-6 for `n` points already on the device.
 nis_status shade_impl(nis_ctx *ctx, const Volume &vol, const Light &light, const Weights &wt,
                       const nis_material *m, const float *pts, const float *om, int n,
-                      float *rgb, const nis_debug_out *dbg, cudaStream_t s) {
-    float *table;
-    nis_status st = ensure_phase(ctx, m->g, s, &table);
-    if (st) return st;
+                      float *rgb, const nis_debug_out *dbg, cudaStream_t s,
+                      const Mixed *mx = nullptr) {
+    float *table = nullptr;
+    nis_status st;
+    if (!mx && (st = ensure_phase(ctx, m->g, s, &table))) return st;
     if (n <= 0) return NIS_OK;
     if (wt.precision == NIS_PREC_BF16)
-        return shade_impl_bf16(ctx, vol, light, wt, m, table, pts, om, n, rgb, dbg, s);
+        return shade_impl_bf16(ctx, vol, light, wt, m, table, pts, om, n, rgb, dbg, s, mx);
     int chunk = n < kChunk ? n : kChunk;
     if ((st = ensure_workspace(ctx, chunk, s))) return st;
     Workspace &w = ctx->ws;
@@ -388,6 +400,7 @@ nis_status shade_impl(nis_ctx *ctx, const Volume &vol, const Light &light, const
         }
         ga.H_rho = w.H_rho; ga.H_T = w.H_T; ga.H_f = w.H_f;
         ga.v = w.v; ga.w_se = w.w_se; ga.cfg = w.cfg;
+        if (mx) { ga.descs = mx->descs; ga.req_of_point = mx->req_of_point + off; }
         {
             ProfScope ps(ctx, "gather", s);
             launch_gather(ga, s);
@@ -452,6 +465,7 @@ nis_status shade_impl(nis_ctx *ctx, const Volume &vol, const Light &light, const
         for (int c = 0; c < 3; ++c) h3.dec_scale[c] = dec_scale[c];
         h3.y_out = (dbg && dbg->y) ? dbg->y + 3 * (size_t)off : nullptr;
         h3.out = rgb + 3 * (size_t)off; h3.ldo = 3;
+        if (mx) h3.dec_rows = mx->dec_rows + 3 * (size_t)off;
         { ProfScope ps(ctx, "mlp", s); launch_fc_f32(h3, s); }
 
         if (dbg) {
@@ -476,7 +490,7 @@ nis_status shade_impl(nis_ctx *ctx, const Volume &vol, const Light &light, const
 nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, const Weights &wt,
                            const nis_material *m, const float *table, const float *pts,
                            const float *om, int n, float *rgb, const nis_debug_out *dbg,
-                           cudaStream_t s) {
+                           cudaStream_t s, const Mixed *mx) {
     int chunk = n < kChunk ? n : kChunk;
     nis_status st = ensure_workspace_bf16(ctx, chunk, s);
     if (st) return st;
@@ -508,6 +522,7 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
         }
         ga.H_T = w.H_T; ga.Hb_rho = w.Hb_rho; ga.Hb_f = w.Hb_f;
         ga.v = dbg ? w.v : nullptr; ga.w_se = w.w_se; ga.cfg = w.cfg;
+        if (mx) { ga.descs = mx->descs; ga.req_of_point = mx->req_of_point + off; }
         {
             ProfScope ps(ctx, "gather", s);
             launch_gather(ga, s);
@@ -532,6 +547,9 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
                     f1.cfg = w.cfg; f1.w_cfg = W + o.blk_w1[t][k] + d; f1.w_cfg_ld = d + kCfg;
                     f1.mat_cfg[0] = m->g;
                     for (int c = 0; c < 3; ++c) f1.mat_cfg[1 + c] = m->albedo[c];
+                    // per-row configuration even for one request: a request's result is then
+                    // bit-identical alone and inside a mixed batch
+                    f1.cfg_per_row = 1;
                     f1.h_prev = k == k0 ? nullptr : w.H; f1.ld_h = kWidth;
                     gemm(f1, fmap, wt.map_fc1[t][k]);
                     TcGemmArgs f2{};
@@ -564,6 +582,7 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
         for (int c = 0; c < 3; ++c) h3.dec_scale[c] = dec_scale[c];
         h3.out_f32 = rgb + 3 * (size_t)off;
         h3.y_out = (dbg && dbg->y) ? dbg->y + 3 * (size_t)off : nullptr;
+        if (mx) h3.dec_rows = mx->dec_rows + 3 * (size_t)off;
         gemm(h3, w.map_z2, wt.map_head[2]);
         if (dbg) {
             auto cp = [&](float *dst, const float *src, size_t per) -> cudaError_t {
@@ -690,6 +709,23 @@ bool make_tmap_bf16(CUtensorMap *map, const void *base, uint64_t inner, uint64_t
 }
 
 nis_status record_error(nis_ctx *ctx, nis_status s, const char *msg) { return fail(ctx, s, msg); }
+int ctx_device(const nis_ctx *ctx) { return ctx->device; }
+
+nis_status hits_compact(nis_ctx *ctx, nis_volume vol, const nis_camera *cam, float *pts,
+                        float *om, int *pix, int *d_count, cudaStream_t s) {
+    Volume *v = lookup(ctx->vols, vol);
+    if (!v) return fail(ctx, NIS_ERR_NOT_READY, "unknown or released volume handle");
+    CameraArgs c;
+    nis_status st = camera_args(ctx, cam, &c);
+    if (st) return st;
+    NIS_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int), s));
+    {
+        ProfScope ps(ctx, "hits", s);
+        launch_find_hits(v->data, v->n, v->sigma_max, c, nullptr, pts, om, pix, d_count, s);
+    }
+    NIS_CUDA(cudaGetLastError());
+    return NIS_OK;
+}
 
 nis_status resolve_built_inputs(nis_ctx *ctx, nis_volume vol, nis_light light, nis_weights w,
                                 float g, ResolvedInputs *out) {
@@ -1280,6 +1316,115 @@ nis_status nis_debug_tc_gemm(nis_ctx *ctx, const void *d_a, int lda, const void 
     {
         ProfScope ps(ctx, "mlp", reinterpret_cast<cudaStream_t>(stream));
         launch_tc_gemm(a, ma, mb, sms, reinterpret_cast<cudaStream_t>(stream));
+    }
+    NIS_CUDA(cudaGetLastError());
+    return NIS_OK;
+}
+
+
+nis_status nis_shade_segments(nis_ctx *ctx, nis_weights w, const nis_segment *segs, int nseg,
+                              nis_stream stream) {
+    if (!ctx) return NIS_ERR_INVALID_ARG;
+    if (nseg < 0 || (nseg > 0 && !segs)) return fail(ctx, NIS_ERR_INVALID_ARG, "bad segment list");
+    Weights *pw = lookup(ctx->weights, w);
+    if (!pw) return fail(ctx, NIS_ERR_NOT_READY, "unknown or released weights handle");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<ReqDesc> descs(nseg);
+    long long total = 0;
+    Volume *v0 = nullptr;
+    Light *l0 = nullptr;
+    for (int i = 0; i < nseg; ++i) {
+        const nis_segment &sg = segs[i];
+        nis_status st = check_material(ctx, &sg.material);
+        if (st) return st;
+        if (sg.n < 0 || (sg.n > 0 && (!sg.d_points || !sg.d_omega || !sg.d_rgb_out)))
+            return fail(ctx, NIS_ERR_INVALID_ARG, "bad segment buffers");
+        Volume *pv = lookup(ctx->vols, sg.vol);
+        Light *pl = lookup(ctx->lights, sg.light);
+        if (!pv || !pl) return fail(ctx, NIS_ERR_NOT_READY, "unknown or released volume or light handle");
+        if (pl->vol != sg.vol) return fail(ctx, NIS_ERR_INVALID_ARG, "light belongs to another volume");
+        if (!pv->pyramid) return fail(ctx, NIS_ERR_NOT_READY, "pyramid not built");
+        float *table;
+        if ((st = ensure_phase(ctx, sg.material.g, s, &table))) return st;
+        ReqDesc &d = descs[i];
+        d.rho = view_of(*pv, pv->data);
+        d.T = view_of(*pv, pl->data);
+        d.table = table;
+        for (int c = 0; c < 3; ++c) {
+            d.l[c] = pl->dir[c];
+            d.albedo[c] = sg.material.albedo[c];
+            d.dec[c] = sg.material.intensity[c] * powf(sg.material.albedo[c], 4.0f);
+        }
+        d.g = sg.material.g;
+        total += sg.n;
+        if (!v0) { v0 = pv; l0 = pl; }
+    }
+    if (total == 0) return NIS_OK;
+    // batch buffers (grow-only)
+    nis_status st;
+    if (ctx->mix_cap < kChunk) {
+        if ((st = dev_alloc_t(ctx, 3 * (size_t)kChunk, &ctx->mix_pts, s))) return st;
+        if ((st = dev_alloc_t(ctx, 3 * (size_t)kChunk, &ctx->mix_om, s))) return st;
+        if ((st = dev_alloc_t(ctx, 3 * (size_t)kChunk, &ctx->mix_rgb, s))) return st;
+        if ((st = dev_alloc_t(ctx, 3 * (size_t)kChunk, &ctx->mix_dec, s))) return st;
+        if ((st = dev_alloc_t(ctx, (size_t)kChunk, &ctx->mix_req, s))) return st;
+        ctx->mix_cap = kChunk;
+    }
+    if (ctx->mix_desc_cap < nseg) {
+        dev_free(ctx, ctx->mix_descs); dev_free(ctx, ctx->mix_seg_start); dev_free(ctx, ctx->mix_seg_desc);
+        ctx->mix_descs = nullptr; ctx->mix_seg_start = ctx->mix_seg_desc = nullptr;
+        ctx->mix_desc_cap = 0;
+        if ((st = dev_alloc_t(ctx, (size_t)nseg, &ctx->mix_descs, s))) return st;
+        if ((st = dev_alloc_t(ctx, (size_t)nseg, &ctx->mix_seg_start, s))) return st;
+        if ((st = dev_alloc_t(ctx, (size_t)nseg, &ctx->mix_seg_desc, s))) return st;
+        ctx->mix_desc_cap = nseg;
+    }
+    // pageable-source copies are staged by the driver before the call returns
+    NIS_CUDA(cudaMemcpyAsync(ctx->mix_descs, descs.data(), sizeof(ReqDesc) * nseg,
+                             cudaMemcpyHostToDevice, s));
+    int seg = 0, seg_off = 0;
+    while (seg < nseg) {
+        std::vector<int> starts, dids;
+        struct Piece { int seg, off, row, n; };
+        std::vector<Piece> pieces;
+        int rows = 0;
+        while (seg < nseg && rows < kChunk) {
+            int take = std::min(segs[seg].n - seg_off, kChunk - rows);
+            if (take > 0) {
+                pieces.push_back({seg, seg_off, rows, take});
+                starts.push_back(rows);
+                dids.push_back(seg);
+                rows += take;
+                seg_off += take;
+            }
+            if (seg_off >= segs[seg].n) { ++seg; seg_off = 0; }
+        }
+        if (rows == 0) break;
+        for (const Piece &pc : pieces) {
+            const nis_segment &sg = segs[pc.seg];
+            NIS_CUDA(cudaMemcpyAsync(ctx->mix_pts + 3 * (size_t)pc.row, sg.d_points + 3 * (size_t)pc.off,
+                                     12 * (size_t)pc.n, cudaMemcpyDeviceToDevice, s));
+            NIS_CUDA(cudaMemcpyAsync(ctx->mix_om + 3 * (size_t)pc.row, sg.d_omega + 3 * (size_t)pc.off,
+                                     12 * (size_t)pc.n, cudaMemcpyDeviceToDevice, s));
+        }
+        NIS_CUDA(cudaMemcpyAsync(ctx->mix_seg_start, starts.data(), sizeof(int) * starts.size(),
+                                 cudaMemcpyHostToDevice, s));
+        NIS_CUDA(cudaMemcpyAsync(ctx->mix_seg_desc, dids.data(), sizeof(int) * dids.size(),
+                                 cudaMemcpyHostToDevice, s));
+        {
+            ProfScope ps(ctx, "other", s);
+            launch_fill_segments(ctx->mix_seg_start, ctx->mix_seg_desc, (int)starts.size(), rows,
+                                 ctx->mix_req, ctx->mix_dec, ctx->mix_descs, s);
+        }
+        Mixed mx{ctx->mix_descs, ctx->mix_req, ctx->mix_dec};
+        if ((st = shade_impl(ctx, *v0, *l0, *pw, &segs[pieces[0].seg].material, ctx->mix_pts,
+                             ctx->mix_om, rows, ctx->mix_rgb, nullptr, s, &mx)))
+            return st;
+        for (const Piece &pc : pieces)
+            NIS_CUDA(cudaMemcpyAsync(segs[pc.seg].d_rgb_out + 3 * (size_t)pc.off,
+                                     ctx->mix_rgb + 3 * (size_t)pc.row, 12 * (size_t)pc.n,
+                                     cudaMemcpyDeviceToDevice, s));
     }
     NIS_CUDA(cudaGetLastError());
     return NIS_OK;

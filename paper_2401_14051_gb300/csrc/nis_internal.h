@@ -138,7 +138,20 @@ struct PyramidView {                 // device pointers of all levels of a pyram
     int levels;
 };
 
+// Per-request inputs of a mixed batch (continuous batching): point p uses
+// descs[req_of_point[p]] instead of the single-request fields of GatherArgs.
+struct ReqDesc {
+    PyramidView rho, T;
+    const float *table;
+    float l[3];
+    float g;
+    float albedo[3];
+    float dec[3];                    // I * albedo^4 (decode scale)
+};
+
 struct GatherArgs {
+    const ReqDesc *descs;            // mixed batch (may be null)
+    const int *req_of_point;
     PyramidView rho, T;
     const float *table;              // phase table of the material's g
     const float *points, *omega;     // [n][3]
@@ -176,6 +189,7 @@ struct FcArgs {
     float *out; int ldo;
     // decode epilogue (last layer): rgb = intensity * albedo^4 * expm1(acc + b)
     int decode; float dec_scale[3]; float *y_out;
+    const float *dec_rows;           // optional per-row decode scales [count][3]
 };
 constexpr int kFcFeat = 0, kFcSum = 1, kFcCat = 2;
 void launch_fc_f32(const FcArgs &a, cudaStream_t s);
@@ -213,7 +227,13 @@ struct TcGemmArgs {
     const __nv_bfloat16 *resid; int ld_resid;   // kEpiFc2: e
     float dec_scale[3];               // kEpiDecode: I * albedo^4
     float *y_out;                     // kEpiDecode: network output before decode (may be null)
+    const float *dec_rows;            // kEpiDecode: optional per-row scales [M][3]
+    int cfg_per_row;                  // kEpiFc1: use every row's g and albedo from cfg (mixed
+                                      // batches) instead of the folded mat_cfg
 };
+void launch_fill_segments(const int *seg_start, const int *seg_desc, int nseg, int count,
+                          int *req_of_point, float *dec_rows, const ReqDesc *descs,
+                          cudaStream_t s);
 void launch_tc_gemm(const TcGemmArgs &a, const CUtensorMap &map_a, const CUtensorMap &map_b,
                     int num_sms, cudaStream_t s);
 // 2-D BF16 tensor map, inner dimension contiguous, box = box_inner x box_outer, 128-byte swizzle.
@@ -234,5 +254,10 @@ struct ResolvedInputs {
 nis_status resolve_built_inputs(nis_ctx *ctx, nis_volume vol, nis_light light, nis_weights w,
                                 float g, ResolvedInputs *out);
 nis_status record_error(nis_ctx *ctx, nis_status s, const char *msg);
+int ctx_device(const nis_ctx *ctx);
+// First hits of a camera, compacted: points, omegas and pixel indices of the hits, and their
+// number in *d_count (device).  Buffers hold width * height entries.
+nis_status hits_compact(nis_ctx *ctx, nis_volume vol, const nis_camera *cam, float *pts,
+                        float *om, int *pix, int *d_count, cudaStream_t s);
 
 }  // namespace nis

@@ -41,6 +41,34 @@ class Camera(C.Structure):
                 ("fov_y", C.c_float), ("ortho_height", C.c_float)]
 
 
+class Segment(C.Structure):
+    _fields_ = [("vol", C.c_uint64), ("light", C.c_uint64), ("material", Material),
+                ("d_points", C.c_void_p), ("d_omega", C.c_void_p), ("n", C.c_int),
+                ("d_rgb_out", C.c_void_p)]
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_batch_points", C.c_int),
+                ("max_inflight", C.c_int)]
+
+
+class Request(C.Structure):
+    _fields_ = [("density", C.c_void_p), ("n", C.c_int), ("dtype", C.c_int),
+                ("volume_key", C.c_uint64), ("light_dir", C.c_float * 3), ("lam", C.c_float),
+                ("material", Material), ("camera", Camera), ("rgb_out", C.c_void_p)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double),
+                ("max_ms", C.c_double), ("points_shaded", C.c_uint64), ("batches", C.c_uint64),
+                ("mean_batch_points", C.c_double), ("mean_batch_requests", C.c_double),
+                ("volume_hits", C.c_uint64), ("volume_misses", C.c_uint64),
+                ("light_hits", C.c_uint64), ("light_misses", C.c_uint64),
+                ("evictions", C.c_uint64), ("peak_bytes", C.c_size_t),
+                ("span_seconds", C.c_double)]
+
+
 class DebugOut(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in ("H_rho", "H_T", "H_f", "v", "X_T", "w_se", "y")]
 
@@ -93,6 +121,14 @@ _SIGS = {
     "nis_kernel_launches": (C.c_uint64, []),
     "nis_debug_tc_gemm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int,
                                     C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "nis_shade_segments": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(Segment), C.c_int,
+                                     C.c_void_p]),
+    "nis_server_create": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(ServerConfig),
+                                    C.POINTER(C.c_void_p)]),
+    "nis_server_submit": (C.c_int, [C.c_void_p, C.POINTER(Request), C.POINTER(C.c_uint64)]),
+    "nis_server_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int, C.POINTER(C.c_double)]),
+    "nis_server_get_stats": (C.c_int, [C.c_void_p, C.POINTER(ServerStats)]),
+    "nis_server_destroy": (None, [C.c_void_p]),
     "nis_shade_points_static": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint64,
                                           C.POINTER(Material), C.c_void_p, C.c_void_p, C.c_int,
                                           C.c_void_p, C.c_void_p]),
@@ -286,6 +322,14 @@ class Context:
                                                _stream(stream)))
         return out
 
+    def shade_segments(self, weights, segments, stream=None):
+        """segments: list of (vol, light, material dict, points, omega, out) with CUDA tensors."""
+        arr = (Segment * len(segments))()
+        for i, (v, l, m, p, o, out) in enumerate(segments):
+            arr[i] = Segment(v, l, material(m), _ptr(p), _ptr(o), p.shape[0], _ptr(out))
+        self._check(self.lib.nis_shade_segments(self.h, weights, arr, len(segments),
+                                                _stream(stream)))
+
     def shade_points_debug(self, vol, light, weights, mat: dict, points, omega, stream=None):
         n = points.shape[0]
         dev = points.device
@@ -353,3 +397,54 @@ class Context:
                           device=f"cuda:{self.device}")
         self._check(self.lib.nis_build_phase_table(self.h, g, _ptr(out), _stream(stream)))
         return out
+
+
+class Server:
+    """Continuous-batching render server on its own context (nis_server_*)."""
+
+    def __init__(self, ctx: Context, weights: int, budget_bytes: int = 0,
+                 max_batch_points: int = 65536, max_inflight: int = 16):
+        self.ctx = ctx
+        self.lib = ctx.lib
+        cfg = ServerConfig(budget_bytes, max_batch_points, max_inflight)
+        h = C.c_void_p()
+        ctx._check(self.lib.nis_server_create(ctx.h, weights, C.byref(cfg), C.byref(h)))
+        self.h = h
+        self._keep = {}
+
+    def submit(self, density: np.ndarray, key: int, light_dir, lam: float, mat: dict,
+               cam: dict) -> int:
+        """Queues a render request; density is a host [N, N, N] float32/float16 array kept
+        alive until the request completes.  Returns the request id."""
+        density = np.ascontiguousarray(density)
+        dt = DTYPE_F16 if density.dtype == np.float16 else DTYPE_F32
+        c = camera(cam)
+        out = np.zeros((c.height, c.width, 3), dtype=np.float32)
+        req = Request(density.ctypes.data, density.shape[0], dt, key,
+                      (C.c_float * 3)(*[float(x) for x in light_dir]), lam, material(mat), c,
+                      out.ctypes.data)
+        rid = C.c_uint64()
+        st = self.lib.nis_server_submit(self.h, C.byref(req), C.byref(rid))
+        if st != NIS_OK:
+            raise NisError(st, "submit rejected")
+        self._keep[rid.value] = (density, out)
+        return rid.value
+
+    def wait(self, rid: int, timeout_ms: int = 0):
+        """Blocks until request rid is done; returns (image, latency ms)."""
+        lat = C.c_double()
+        st = self.lib.nis_server_wait(self.h, rid, timeout_ms, C.byref(lat))
+        if st != NIS_OK:
+            raise NisError(st, f"request {rid} failed")
+        _, out = self._keep.pop(rid)
+        return out, lat.value
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        self.lib.nis_server_get_stats(self.h, C.byref(s))
+        return {name: getattr(s, name) for name, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.nis_server_destroy(self.h)
+            self.h = None
