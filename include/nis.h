@@ -113,8 +113,9 @@ size_t nis_bytes_in_use(const nis_ctx *ctx);
  * from host or device memory (src_is_device) into a new volume, multiplied by
  * sigma_scale.  The grid must be cubic (nx = ny = nz, 1..2048).  Values are checked on the
  * device: NaN, infinite or negative densities make the next nis_sync return
- * NIS_ERR_BAD_DATA.  The caller keeps ownership of `density`.  Host sources are copied
- * before the call returns. */
+ * NIS_ERR_BAD_DATA.  The caller keeps ownership of `density`.  A page-locked host source
+ * is read in place by the conversion kernel (keep it valid until the stream passes the
+ * call); a pageable host source has been copied when the call returns. */
 nis_status nis_upload_volume(nis_ctx *ctx, const void *density, int nx, int ny, int nz,
                              int dtype, int src_is_device, float sigma_scale,
                              nis_stream stream, nis_volume *out);

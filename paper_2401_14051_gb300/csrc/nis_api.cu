@@ -881,26 +881,33 @@ nis_status nis_upload_volume(nis_ctx *ctx, const void *density, int nx, int ny, 
     const void *src = density;
     void *staging = nullptr;
     if (!src_is_device) {
-        if ((st = dev_alloc(ctx, count * elem, &staging, s))) {
-            dev_free(ctx, v.data); dev_free(ctx, v.sigma_max);
-            return st;
+        cudaPointerAttributes attr{};
+        void *mapped = nullptr;
+        if (cudaPointerGetAttributes(&attr, density) == cudaSuccess &&
+            attr.type == cudaMemoryTypeHost &&
+            cudaHostGetDevicePointer(&mapped, const_cast<void *>(density), 0) == cudaSuccess) {
+            src = mapped;                   // page-locked: the conversion kernel reads it in place
+        } else {
+            cudaGetLastError();
+            // pageable: stream-ordered staging (no device-wide synchronisation); the copy
+            // has consumed the caller's buffer when cudaMemcpyAsync returns
+            cudaError_t e = cudaMallocAsync(&staging, count * elem, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(staging, density, count * elem, cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) {
+                if (staging) cudaFreeAsync(staging, s);
+                dev_free(ctx, v.data); dev_free(ctx, v.sigma_max);
+                return cuda_fail(ctx, e, "density upload");
+            }
+            src = staging;
         }
-        cudaError_t e = cudaMemcpyAsync(staging, density, count * elem, cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) {
-            dev_free(ctx, staging); dev_free(ctx, v.data); dev_free(ctx, v.sigma_max);
-            return cuda_fail(ctx, e, "cudaMemcpyAsync(density)");
-        }
-        src = staging;
     }
     {
         ProfScope ps(ctx, "other", s);
         launch_convert_density(src, dtype, sigma_scale, count, v.data, ctx->d_err, v.sigma_max, s);
     }
     cudaError_t e = cudaGetLastError();
-    if (staging) {
-        cudaStreamSynchronize(s);     // the staging copy is freed before returning
-        dev_free(ctx, staging);
-    }
+    if (staging) cudaFreeAsync(staging, s);
     if (e != cudaSuccess) {
         dev_free(ctx, v.data); dev_free(ctx, v.sigma_max);
         return cuda_fail(ctx, e, "convert_density");

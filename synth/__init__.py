@@ -70,6 +70,47 @@ def fbm(n: int, seed: int, octaves: int = 4, base_cells: int = 4) -> np.ndarray:
     return out
 
 
+def fbm_torch(n: int, seed: int, octaves: int = 4, base_cells: int = 4, device="cuda"):
+    """fbm() evaluated with torch on `device` (same seeded lattices, same smoothstep
+    weights; float32), for the many large volumes of the serving workload."""
+    import torch
+    rng = np.random.default_rng(seed)
+    out = torch.zeros((n, n, n), dtype=torch.float32, device=device)
+    for o in range(octaves):
+        cells = base_cells * 2 ** o
+        lat = torch.from_numpy(rng.uniform(-1.0, 1.0, size=(cells + 1,) * 3)).float().to(device)
+        w = torch.from_numpy(_smooth_weights(n, cells)).float().to(device)
+        out += 0.5 ** o * torch.einsum("kji,zk,yj,xi->zyx", lat, w, w, w)
+    return out
+
+
+def serving_volume(n: int, seed: int, sigma_max: float, device="cuda") -> np.ndarray:
+    """Serving workload volume: fBm clipped at 0, scaled to sigma_max, FP16, host array."""
+    import torch
+    v = torch.clamp(fbm_torch(n, seed, device=device), min=0.0)
+    v = v * (sigma_max / torch.clamp(v.max(), min=1e-30))
+    return v.to(torch.float16).cpu().numpy()
+
+
+def serving_requests(count: int, seed: int = 2024):
+    """The serving workload's request list: grid N uniform in {128, 144, ..., 512}, FP16
+    density, g in U[0.3, 0.9], albedo in U[0.95, 0.999], random light and view, image size
+    from 256^2 to 1920x1080.  Volumes are generated by the caller (serving_volume)."""
+    rng = np.random.default_rng(seed)
+    sizes = [(256, 256), (512, 512), (640, 480), (960, 540), (1280, 720), (1920, 1080)]
+    out = []
+    for i in range(count):
+        n = int(rng.choice(np.arange(128, 513, 16)))
+        w, h = sizes[int(rng.integers(len(sizes)))]
+        g = float(rng.uniform(0.3, 0.9))
+        alb = float(rng.uniform(0.95, 0.999))
+        out.append({"n": n, "seed": 10_000 + i, "g": g, "albedo": alb,
+                    "light": unit_vector(20_000 + i),
+                    "camera": persp_camera(unit_vector(30_000 + i), w, h),
+                    "material": material(g, (alb, alb, alb))})
+    return out
+
+
 def _centres(n: int) -> np.ndarray:
     return (np.arange(n, dtype=np.float64) + 0.5) / n
 
