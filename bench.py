@@ -432,10 +432,13 @@ def run_nis(args):
     if dom == "mlp":
         work = MLP_FLOP_PER_POINT * n_points * args.steps / max(dom_n, 1)
         achieved = work / per_launch_s / 1e12
-        peak = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
-        roof = {"bound": "alu", "unit": "TFLOP/s", "kernel": "fc_f32_kernel (backbone, merges, head)",
-                "peak_source": "FP32 FFMA: 152 SMs x 128 lanes x 2 FLOP x max SM clock "
-                               f"{peaks['sm_max_mhz']:.0f} MHz (derived)"}
+        # FP32-accurate dense layers: each FP32 product is six BF16 tcgen05 products of the
+        # operands' three-way splits, so the ceiling is the BF16 peak / 6
+        peak = peaks["bf16_tflops_sustained"] / 6.0
+        roof = {"bound": "tensor", "unit": "TFLOP/s",
+                "kernel": "tc_gemm_kernel (tcgen05, FP32 via 3-way BF16 split, 6 products)",
+                "peak_source": f"{peaks['source']} cuBLAS BF16 sustained "
+                               f"{peaks['bf16_tflops_sustained']:.0f} TFLOP/s / 6"}
     elif dom == "cnn":
         work = CNN_FLOP_PER_POINT * n_points * args.steps / max(dom_n, 1)
         achieved = work / per_launch_s / 1e12

@@ -61,9 +61,13 @@ typedef int nis_status;
 #define NIS_DTYPE_F32 0
 #define NIS_DTYPE_F16 1
 
-#define NIS_PREC_F32 0           /* FP32 everywhere */
-#define NIS_PREC_BF16 1          /* CNN, SE and MLP in BF16 with FP32 accumulation */
+#define NIS_PREC_F32 0           /* FP32-accurate: dense layers on the tensor cores with every
+                                    operand split into three BF16 parts (x = x0 + x1 + x2,
+                                    residual < 2^-24 |x|) and the six products that matter
+                                    accumulated in FP32; everything else in FP32 */
+#define NIS_PREC_BF16 1          /* CNN output, features and dense layers in BF16, FP32 accumulation */
 #define NIS_PREC_FP8 2           /* as BF16 with e4m3 operands and per-channel scales */
+#define NIS_PREC_F32_SIMT 3      /* FP32 everywhere on the FP32 FFMA pipes (reference path) */
 
 #define NIS_CAMERA_ORTHO 0
 #define NIS_CAMERA_PERSP 1

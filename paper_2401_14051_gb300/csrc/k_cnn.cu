@@ -29,7 +29,8 @@ __global__ void __launch_bounds__(kThreads) cnn_f32_kernel(const float *__restri
                                                            const float *__restrict__ wbase,
                                                            const __grid_constant__ WeightOffsets o,
                                                            float *__restrict__ X_T,
-                                                           __nv_bfloat16 *__restrict__ X_T_bf) {
+                                                           __nv_bfloat16 *__restrict__ X_T_bf,
+                                                           size_t split_part) {
     extern __shared__ __align__(16) float sm[];
     float *w1t = sm + kOffW1, *b1 = sm + kOffB1, *w2t = sm + kOffW2, *b2 = sm + kOffB2;
     float *xin = sm + kOffX, *y1 = sm + kOffY1;
@@ -123,8 +124,17 @@ __global__ void __launch_bounds__(kThreads) cnn_f32_kernel(const float *__restri
                 const size_t o = ((size_t)(p0 + q) * kLayers + k) * kDT + w * kCnnCh + half * 8;
                 if (X_T_bf) {
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) X_T_bf[o + c] = __float2bfloat16_rn(fmaxf(acc[c], 0.f));
-                } else {
+                    for (int c = 0; c < 8; ++c) {
+                        float r = fmaxf(acc[c], 0.f);
+                        const int parts = split_part ? 3 : 1;
+                        for (int q = 0; q < parts; ++q) {
+                            __nv_bfloat16 b = __float2bfloat16_rn(r);
+                            X_T_bf[o + c + q * split_part] = b;
+                            r -= __bfloat162float(b);
+                        }
+                    }
+                }
+                if (X_T) {
 #pragma unroll
                     for (int c = 0; c < 8; ++c) X_T[o + c] = fmaxf(acc[c], 0.f);
                 }
@@ -134,7 +144,7 @@ __global__ void __launch_bounds__(kThreads) cnn_f32_kernel(const float *__restri
 }
 
 void launch_cnn_f32(const float *H_T, int count, const float *wbase, const WeightOffsets &o,
-                    float *X_T, __nv_bfloat16 *X_T_bf, cudaStream_t s) {
+                    float *X_T, __nv_bfloat16 *X_T_bf, cudaStream_t s, size_t split_part) {
     if (count <= 0) return;
     size_t smem = kSmemFloats * sizeof(float);
     static bool attr_set = false;   // per process; the attribute is per function
@@ -145,7 +155,7 @@ void launch_cnn_f32(const float *H_T, int count, const float *wbase, const Weigh
     int n_groups = (count + kPts - 1) / kPts;
     dim3 grid((n_groups + kGroupsPerCta - 1) / kGroupsPerCta, kLayers);
     note_launch();
-    cnn_f32_kernel<<<grid, kThreads, smem, s>>>(H_T, count, wbase, o, X_T, X_T_bf);
+    cnn_f32_kernel<<<grid, kThreads, smem, s>>>(H_T, count, wbase, o, X_T, X_T_bf, split_part);
 }
 
 }  // namespace nis

@@ -96,18 +96,32 @@ __global__ void __launch_bounds__(kLayers * 32) gather_kernel(const __grid_const
             const float f0 = __ldg(row0 + t), f1 = __ldg(row1 + t);
             const float f = f0 + wa * (f1 - f0);
             a.H_T[obase + t] = T;
-            if (a.Hb_rho) {
-                a.Hb_rho[obase_b + t] = __float2bfloat16_rn(rho);
-                a.Hb_f[obase_b + t] = __float2bfloat16_rn(f);
-            } else {
+            if (a.H_rho) {                        // FP32 copies (FP32 SIMT path, or debug)
                 a.H_rho[obase + t] = rho;
                 a.H_f[obase + t] = f;
+            }
+            if (a.Hb_rho) {
+                if (a.split) {                    // three-way BF16 split (FP32-accurate mode)
+                    float r0 = rho, r1 = f;
+                    for (int q = 0; q < 3; ++q) {
+                        __nv_bfloat16 b0 = __float2bfloat16_rn(r0), b1 = __float2bfloat16_rn(r1);
+                        a.Hb_rho[obase_b + t + q * a.part] = b0;
+                        a.Hb_f[obase_b + t + q * a.part] = b1;
+                        r0 -= __bfloat162float(b0);
+                        r1 -= __bfloat162float(b1);
+                    }
+                } else {
+                    a.Hb_rho[obase_b + t] = __float2bfloat16_rn(rho);
+                    a.Hb_f[obase_b + t] = __float2bfloat16_rn(f);
+                }
             }
             s0 += rho; s1 += f; s2 += T;
             m0 = fmaxf(m0, rho); m1 = fmaxf(m1, f); m2 = fmaxf(m2, T);
         } else if (a.Hb_rho && t < kLatPad) {     // zero the BF16 row padding
-            a.Hb_rho[obase_b + t] = __float2bfloat16_rn(0.f);
-            a.Hb_f[obase_b + t] = __float2bfloat16_rn(0.f);
+            for (int q = 0; q < (a.split ? 3 : 1); ++q) {
+                a.Hb_rho[obase_b + t + q * a.part] = __float2bfloat16_rn(0.f);
+                a.Hb_f[obase_b + t + q * a.part] = __float2bfloat16_rn(0.f);
+            }
         }
     }
     // squeeze statistics (mean and max pooling over the layer's points)

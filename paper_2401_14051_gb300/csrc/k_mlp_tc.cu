@@ -33,12 +33,34 @@ __device__ __forceinline__ void record_timeout(unsigned *err, int *abort_flag) {
     if (err) atomicOr(err, kErrTimeout);
 }
 
+// Six products of the three-way split, small to large: (A part, B part).
+__constant__ int kPassA[6] = {2, 1, 0, 1, 0, 0};
+__constant__ int kPassB[6] = {0, 1, 2, 0, 1, 0};
+
 __device__ __forceinline__ void store_bf16x8(__nv_bfloat16 *dst, const float *v) {
     __align__(16) __nv_bfloat162 p[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) p[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
     *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(p);
 }
+// 8 values as BF16, or as the three BF16 parts of their split (part stride `part`).
+__device__ __forceinline__ void store_out8(__nv_bfloat16 *dst, const float *v, int split, size_t part) {
+    if (!split) { store_bf16x8(dst, v); return; }
+    float r[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) r[i] = v[i];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        store_bf16x8(dst + q * part, r);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) r[i] = r[i] - __bfloat162float(__float2bfloat16_rn(r[i]));
+    }
+}
+__device__ __forceinline__ void store_f32x8(float *dst, const float *v) {
+    reinterpret_cast<float4 *>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
+    reinterpret_cast<float4 *>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
+}
+
 __device__ __forceinline__ void load_bf16x8(const __nv_bfloat16 *src, float *v) {
     uint4 raw = *reinterpret_cast<const uint4 *>(src);
     const __nv_bfloat162 *p = reinterpret_cast<const __nv_bfloat162 *>(&raw);
@@ -79,13 +101,14 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs &a, int r, int c
             }
             float e = fmaxf(fmaf(v[j], sc, b), 0.f);
             v[j] = e;
-            sv[j] = a.h_prev ? pre[j] + e : e;
+            sv[j] = (a.h_prev || a.pre_f32) ? pre[j] + e : e;
         }
 #pragma unroll
         for (int g = 0; g < 4; ++g)
             if (c0 + 8 * g < N) {
-                store_bf16x8(a.out_e + (size_t)r * a.ldo + c0 + 8 * g, v + 8 * g);
-                store_bf16x8(a.out_s + (size_t)r * a.ldo + c0 + 8 * g, sv + 8 * g);
+                if (a.out_e_f32) store_f32x8(a.out_e_f32 + (size_t)r * a.ldo + c0 + 8 * g, v + 8 * g);
+                else store_bf16x8(a.out_e + (size_t)r * a.ldo + c0 + 8 * g, v + 8 * g);
+                store_out8(a.out_s + (size_t)r * a.ldo + c0 + 8 * g, sv + 8 * g, a.out_split, a.out_part);
             }
         break;
     }
@@ -95,7 +118,10 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs &a, int r, int c
         for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + s_bias[c0 + j], 0.f) + pre[j];
 #pragma unroll
         for (int g = 0; g < 4; ++g)
-            if (c0 + 8 * g < N) store_bf16x8(a.out_bf + (size_t)r * a.ldo + c0 + 8 * g, v + 8 * g);
+            if (c0 + 8 * g < N) {
+                if (a.out_h_f32) store_f32x8(a.out_h_f32 + (size_t)r * a.ldo + c0 + 8 * g, v + 8 * g);
+                else store_out8(a.out_bf + (size_t)r * a.ldo + c0 + 8 * g, v + 8 * g, a.out_split, a.out_part);
+            }
         break;
     }
     case kEpiRelu: {
@@ -103,7 +129,7 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs &a, int r, int c
         for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + s_bias[c0 + j], 0.f);
 #pragma unroll
         for (int g = 0; g < 4; ++g)
-            if (c0 + 8 * g < N) store_bf16x8(a.out_bf + (size_t)r * a.ldo + c0 + 8 * g, v + 8 * g);
+            if (c0 + 8 * g < N) store_out8(a.out_bf + (size_t)r * a.ldo + c0 + 8 * g, v + 8 * g, a.out_split, a.out_part);
         break;
     }
     default: {  // kEpiDecode: rgb = I albedo^4 expm1(acc + b), N = 3
@@ -123,6 +149,18 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs &a, int r, int c
 
 // Residual (FC-2) or running state (FC-1) of one chunk, BF16 -> FP32; zeros if absent.
 __device__ __forceinline__ void load_pre(const TcGemmArgs &a, int r, int c0, float (&pre)[32]) {
+    if (a.pre_f32 && (a.epi == kEpiFc1 || a.epi == kEpiFc2)) {
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+            if (c0 + 4 * g < a.N) {
+                float4 f = *reinterpret_cast<const float4 *>(a.pre_f32 + (size_t)r * a.ld_pre + c0 + 4 * g);
+                pre[4 * g] = f.x; pre[4 * g + 1] = f.y; pre[4 * g + 2] = f.z; pre[4 * g + 3] = f.w;
+            } else {
+                pre[4 * g] = pre[4 * g + 1] = pre[4 * g + 2] = pre[4 * g + 3] = 0.f;
+            }
+        }
+        return;
+    }
     const __nv_bfloat16 *src = a.epi == kEpiFc1 ? a.h_prev : (a.epi == kEpiFc2 ? a.resid : nullptr);
     const int ld = a.epi == kEpiFc1 ? a.ld_h : a.ld_resid;
 #pragma unroll
@@ -200,14 +238,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 0) {
         if (lane == 0) {
             int it = 0;
+            const int npass = a.n_pass > 1 ? a.n_pass : 1;
+            const int steps = npass * a.k_tiles;
             for (int tile = blockIdx.x; tile < n_tiles && !*(volatile int *)abort_flag; tile += gridDim.x) {
-                for (int kt = 0; kt < a.k_tiles; ++kt, ++it) {
+                for (int st = 0; st < steps; ++st, ++it) {
+                    const int pass = st / a.k_tiles, kt = st % a.k_tiles;
+                    const int pa = npass > 1 ? kPassA[pass] : 0, pb = npass > 1 ? kPassB[pass] : 0;
                     const int s = it % STAGES;
                     const uint32_t ph = (it / STAGES) & 1;
                     if (!tc::mbar_wait(&empty[s], ph ^ 1)) { record_timeout(a.err, abort_flag); break; }
                     tc::mbar_expect_tx(&full[s], A_STAGE + b_bytes);
-                    tc::tma_load_2d(sA + s * A_STAGE, &map_a, a.a_col0 + kt * TK, tile * TM, &full[s]);
-                    tc::tma_load_2d(sB + s * B_STAGE, &map_b, kt * TK, 0, &full[s]);
+                    tc::tma_load_2d(sA + s * A_STAGE, &map_a, a.a_col0 + kt * TK,
+                                    pa * a.a_part_rows + tile * TM, &full[s]);
+                    tc::tma_load_2d(sB + s * B_STAGE, &map_b, kt * TK, pb * a.b_part_rows, &full[s]);
                 }
             }
             // wait until every stage issued has landed (the consumer may have stopped early)
@@ -226,7 +269,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc::fence_after_sync();
                 const uint32_t d_tmem = tmem_base + buf * 256;
                 bool ok = true;
-                for (int kt = 0; kt < a.k_tiles; ++kt, ++it) {
+                const int steps = (a.n_pass > 1 ? a.n_pass : 1) * a.k_tiles;
+                for (int st = 0; st < steps; ++st, ++it) {
+                    const int kt = st % a.k_tiles;
                     const int s = it % STAGES;
                     if (!tc::mbar_wait(&full[s], (it / STAGES) & 1)) { ok = false; break; }
                     tc::fence_after_sync();
@@ -236,7 +281,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const int n_k16 = k_left >= TK ? TK / 16 : (k_left + 15) / 16;
                     for (int k = 0; k < n_k16; ++k)
                         tc::mma_f16(d_tmem, tc::smem_desc_sw128(a_addr + k * 32),
-                                    tc::smem_desc_sw128(b_addr + k * 32), idesc, (kt | k) != 0);
+                                    tc::smem_desc_sw128(b_addr + k * 32), idesc, (st | k) != 0);
                     tc::mma_commit(&empty[s]);
                 }
                 if (!ok) { record_timeout(a.err, abort_flag); break; }
@@ -294,21 +339,22 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 __global__ void pack_bf16_kernel(const float *__restrict__ src, int N, int K, int ld_src,
-                                 __nv_bfloat16 *__restrict__ dst, int Np, int Kp) {
+                                 __nv_bfloat16 *__restrict__ dst, int Np, int Kp, int part) {
     size_t total = (size_t)Np * Kp;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
          i += (size_t)gridDim.x * blockDim.x) {
         int n = (int)(i / Kp), k = (int)(i % Kp);
-        dst[i] = __float2bfloat16_rn(n < N && k < K ? src[(size_t)n * ld_src + k] : 0.f);
+        float x = n < N && k < K ? src[(size_t)n * ld_src + k] : 0.f;
+        dst[i] = __float2bfloat16_rn(part > 0 ? split_residual(x, part) : x);
     }
 }
 
 void launch_pack_bf16(const float *src, int N, int K, int ld_src, __nv_bfloat16 *dst, int Np,
-                      int Kp, cudaStream_t s) {
+                      int Kp, cudaStream_t s, int split_part) {
     size_t total = (size_t)Np * Kp;
     int blocks = (int)((total + 255) / 256 < 1024 ? (total + 255) / 256 : 1024);
     note_launch();
-    pack_bf16_kernel<<<blocks, 256, 0, s>>>(src, N, K, ld_src, dst, Np, Kp);
+    pack_bf16_kernel<<<blocks, 256, 0, s>>>(src, N, K, ld_src, dst, Np, Kp, split_part);
 }
 
 void launch_tc_gemm(const TcGemmArgs &a, const CUtensorMap &map_a, const CUtensorMap &map_b,

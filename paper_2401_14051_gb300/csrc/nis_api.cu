@@ -47,8 +47,10 @@ struct Weights {
     CUtensorMap map_fc1[3][kLayers], map_fc2[3][kLayers], map_mrg[3], map_head[3];
 };
 
-struct WorkspaceBf {                  // scratch of the BF16 path, grow-only
+struct WorkspaceBf {                  // scratch of the tensor-core paths, grow-only
     int cap = 0;
+    int parts = 1;                    // 1: BF16; 3: three-way split (FP32-accurate)
+    float *E32 = nullptr, *H32 = nullptr;   // split mode: e and the running state in FP32
     __nv_bfloat16 *Hb_rho = nullptr, *Hb_f = nullptr, *XTb = nullptr, *E = nullptr, *S = nullptr,
                   *H = nullptr, *mrg_in[3] = {nullptr, nullptr, nullptr}, *head_in = nullptr,
                   *Z1 = nullptr, *Z2 = nullptr;
@@ -84,7 +86,7 @@ struct nis_ctx {
     std::map<nis_handle, Weights> weights;
     std::map<uint32_t, float *> phase;   // by the bit pattern of g
     Workspace ws;
-    WorkspaceBf wsb;
+    WorkspaceBf wsb, wsx;                 // BF16 and split (FP32-accurate) tensor paths
     // mixed-batch buffers of nis_shade_segments (grow-only)
     int mix_cap = 0, mix_desc_cap = 0;
     float *mix_pts = nullptr, *mix_om = nullptr, *mix_rgb = nullptr, *mix_dec = nullptr;
@@ -265,39 +267,47 @@ nis_status ensure_workspace(nis_ctx *ctx, int cap, cudaStream_t s) {
     return NIS_OK;
 }
 
-nis_status ensure_workspace_bf16(nis_ctx *ctx, int cap, cudaStream_t s) {
-    WorkspaceBf &w = ctx->wsb;
+nis_status ensure_workspace_tc(nis_ctx *ctx, WorkspaceBf &w, int parts, int cap, cudaStream_t s) {
     if (w.cap >= cap) return NIS_OK;
     __nv_bfloat16 **bb[] = {&w.Hb_rho, &w.Hb_f, &w.XTb, &w.E, &w.S, &w.H, &w.mrg_in[0], &w.mrg_in[1],
                             &w.mrg_in[2], &w.head_in, &w.Z1, &w.Z2};
     for (auto **b : bb) { dev_free(ctx, *b); *b = nullptr; }
-    float **ff[] = {&w.H_T, &w.w_se, &w.cfg, &w.v};
+    float **ff[] = {&w.H_T, &w.w_se, &w.cfg, &w.v, &w.E32, &w.H32};
     for (float **f : ff) { dev_free(ctx, *f); *f = nullptr; }
     w.cap = 0;
-    const size_t n = (size_t)cap;
+    w.parts = parts;
+    const size_t n = (size_t)cap, P = (size_t)parts;
     nis_status st;
-    if ((st = dev_alloc_t(ctx, n * kLayers * kLatPad, &w.Hb_rho, s))) return st;
-    if ((st = dev_alloc_t(ctx, n * kLayers * kLatPad, &w.Hb_f, s))) return st;
-    if ((st = dev_alloc_t(ctx, n * kLayers * kDT, &w.XTb, s))) return st;
-    for (auto **b : {&w.E, &w.S, &w.H, &w.Z1, &w.Z2})
-        if ((st = dev_alloc_t(ctx, n * kWidth, b, s))) return st;
+    if ((st = dev_alloc_t(ctx, P * n * kLayers * kLatPad, &w.Hb_rho, s))) return st;
+    if ((st = dev_alloc_t(ctx, P * n * kLayers * kLatPad, &w.Hb_f, s))) return st;
+    if ((st = dev_alloc_t(ctx, P * n * kLayers * kDT, &w.XTb, s))) return st;
+    for (auto **b : {&w.S, &w.Z1, &w.Z2})
+        if ((st = dev_alloc_t(ctx, P * n * kWidth, b, s))) return st;
+    if (parts == 1) {
+        for (auto **b : {&w.E, &w.H})
+            if ((st = dev_alloc_t(ctx, n * kWidth, b, s))) return st;
+    } else {
+        for (float **f : {&w.E32, &w.H32})
+            if ((st = dev_alloc_t(ctx, n * kWidth, f, s))) return st;
+    }
     for (int t = 0; t < 3; ++t)
-        if ((st = dev_alloc_t(ctx, n * 2 * kWidth, &w.mrg_in[t], s))) return st;
-    if ((st = dev_alloc_t(ctx, n * 3 * kWidth, &w.head_in, s))) return st;
+        if ((st = dev_alloc_t(ctx, P * n * 2 * kWidth, &w.mrg_in[t], s))) return st;
+    if ((st = dev_alloc_t(ctx, P * n * 3 * kWidth, &w.head_in, s))) return st;
     if ((st = dev_alloc_t(ctx, n * kLayers * kLat, &w.H_T, s))) return st;
     if ((st = dev_alloc_t(ctx, n * kLayers * 3, &w.w_se, s))) return st;
     if ((st = dev_alloc_t(ctx, n * kCfg, &w.cfg, s))) return st;
     if ((st = dev_alloc_t(ctx, n * kLayers * 8, &w.v, s))) return st;
-    bool ok = make_tmap_bf16(&w.map_rho, w.Hb_rho, kLayers * kLatPad, n, kLayers * kLatPad * 2, 64, 128) &&
-              make_tmap_bf16(&w.map_f, w.Hb_f, kLayers * kLatPad, n, kLayers * kLatPad * 2, 64, 128) &&
-              make_tmap_bf16(&w.map_xt, w.XTb, kLayers * kDT, n, kLayers * kDT * 2, 64, 128) &&
-              make_tmap_bf16(&w.map_s, w.S, kWidth, n, kWidth * 2, 64, 128) &&
-              make_tmap_bf16(&w.map_head, w.head_in, 3 * kWidth, n, 3 * kWidth * 2, 64, 128) &&
-              make_tmap_bf16(&w.map_z1, w.Z1, kWidth, n, kWidth * 2, 64, 128) &&
-              make_tmap_bf16(&w.map_z2, w.Z2, kWidth, n, kWidth * 2, 64, 128);
+    const uint64_t rows = P * n;      // the parts of a tensor stack along the row dimension
+    bool ok = make_tmap_bf16(&w.map_rho, w.Hb_rho, kLayers * kLatPad, rows, kLayers * kLatPad * 2, 64, 128) &&
+              make_tmap_bf16(&w.map_f, w.Hb_f, kLayers * kLatPad, rows, kLayers * kLatPad * 2, 64, 128) &&
+              make_tmap_bf16(&w.map_xt, w.XTb, kLayers * kDT, rows, kLayers * kDT * 2, 64, 128) &&
+              make_tmap_bf16(&w.map_s, w.S, kWidth, rows, kWidth * 2, 64, 128) &&
+              make_tmap_bf16(&w.map_head, w.head_in, 3 * kWidth, rows, 3 * kWidth * 2, 64, 128) &&
+              make_tmap_bf16(&w.map_z1, w.Z1, kWidth, rows, kWidth * 2, 64, 128) &&
+              make_tmap_bf16(&w.map_z2, w.Z2, kWidth, rows, kWidth * 2, 64, 128);
     for (int t = 0; t < 3; ++t)
-        ok = ok && make_tmap_bf16(&w.map_mrg[t], w.mrg_in[t], 2 * kWidth, n, 2 * kWidth * 2, 64, 128);
-    if (!ok) return fail(ctx, NIS_ERR_CUDA, "cuTensorMapEncodeTiled failed for the BF16 workspace");
+        ok = ok && make_tmap_bf16(&w.map_mrg[t], w.mrg_in[t], 2 * kWidth, rows, 2 * kWidth * 2, 64, 128);
+    if (!ok) return fail(ctx, NIS_ERR_CUDA, "cuTensorMapEncodeTiled failed for the tensor-core workspace");
     w.cap = cap;
     return NIS_OK;
 }
@@ -305,8 +315,9 @@ nis_status ensure_workspace_bf16(nis_ctx *ctx, int cap, cudaStream_t s) {
 int n_mma_of(int n) { return (n + 15) / 16 * 16; }
 int k_pad_of(int k) { return (k + 63) / 64 * 64; }
 
-// BF16 weight pack: one zero-padded [n_mma][Kp] matrix per dense layer plus its tensor map.
-nis_status pack_weights_bf16(nis_ctx *ctx, Weights &w, cudaStream_t s) {
+// Tensor-core weight pack: per dense layer `parts` zero-padded [n_mma][Kp] BF16 matrices
+// stacked along the rows (1 part: BF16; 3 parts: the three-way split), one tensor map each.
+nis_status pack_weights_tc(nis_ctx *ctx, Weights &w, int parts, cudaStream_t s) {
     struct Mat { const float *src; int N, K, ld; CUtensorMap *map; };
     std::vector<Mat> mats;
     const WeightOffsets &o = w.off;
@@ -321,20 +332,22 @@ nis_status pack_weights_bf16(nis_ctx *ctx, Weights &w, cudaStream_t s) {
     mats.push_back({w.f32 + o.head_w[1], kWidth, kWidth, kWidth, &w.map_head[1]});
     mats.push_back({w.f32 + o.head_w[2], 3, kWidth, kWidth, &w.map_head[2]});
     size_t total = 0;
-    for (auto &m : mats) total += (size_t)n_mma_of(m.N) * k_pad_of(m.K);
+    for (auto &m : mats) total += (size_t)parts * n_mma_of(m.N) * k_pad_of(m.K);
     nis_status st = dev_alloc_t(ctx, total, &w.bf, s);
     if (st) return st;
     size_t off = 0;
     for (auto &m : mats) {
         int np = n_mma_of(m.N), kp = k_pad_of(m.K);
         __nv_bfloat16 *dst = w.bf + off;
-        {
+        for (int q = 0; q < parts; ++q) {
             ProfScope ps(ctx, "other", s);
-            launch_pack_bf16(m.src, m.N, m.K, m.ld, dst, np, kp, s);
+            launch_pack_bf16(m.src, m.N, m.K, m.ld, dst + (size_t)q * np * kp, np, kp, s,
+                             parts > 1 ? q : -1);
         }
-        if (!make_tmap_bf16(m.map, dst, (uint64_t)kp, (uint64_t)np, (uint64_t)kp * 2, 64, (uint32_t)np))
+        if (!make_tmap_bf16(m.map, dst, (uint64_t)kp, (uint64_t)parts * np, (uint64_t)kp * 2, 64,
+                            (uint32_t)np))
             return fail(ctx, NIS_ERR_CUDA, "cuTensorMapEncodeTiled failed for a weight matrix");
-        off += (size_t)np * kp;
+        off += (size_t)parts * np * kp;
     }
     NIS_CUDA(cudaGetLastError());
     return NIS_OK;
@@ -369,7 +382,7 @@ nis_status shade_impl(nis_ctx *ctx, const Volume &vol, const Light &light, const
     nis_status st;
     if (!mx && (st = ensure_phase(ctx, m->g, s, &table))) return st;
     if (n <= 0) return NIS_OK;
-    if (wt.precision == NIS_PREC_BF16)
+    if (wt.precision != NIS_PREC_F32_SIMT)
         return shade_impl_bf16(ctx, vol, light, wt, m, table, pts, om, n, rgb, dbg, s, mx);
     int chunk = n < kChunk ? n : kChunk;
     if ((st = ensure_workspace(ctx, chunk, s))) return st;
@@ -492,14 +505,21 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
                            const float *om, int n, float *rgb, const nis_debug_out *dbg,
                            cudaStream_t s, const Mixed *mx) {
     int chunk = n < kChunk ? n : kChunk;
-    nis_status st = ensure_workspace_bf16(ctx, chunk, s);
+    const bool split = wt.precision == NIS_PREC_F32;
+    WorkspaceBf &w = split ? ctx->wsx : ctx->wsb;
+    const int P = split ? 3 : 1;
+    nis_status st = ensure_workspace_tc(ctx, w, P, chunk, s);
     if (st) return st;
-    WorkspaceBf &w = ctx->wsb;
+    const size_t cap = (size_t)w.cap;
     const WeightOffsets &o = wt.off;
     const float *W = wt.f32;
     float dec_scale[3];
     for (int c = 0; c < 3; ++c) dec_scale[c] = m->intensity[c] * powf(m->albedo[c], 4.0f);
-    auto gemm = [&](const TcGemmArgs &a, const CUtensorMap &ma, const CUtensorMap &mb) {
+    auto gemm = [&](TcGemmArgs a, const CUtensorMap &ma, const CUtensorMap &mb) {
+        a.n_pass = split ? 6 : 1;
+        a.a_part_rows = (int)cap;
+        a.b_part_rows = a.n_mma;
+        a.out_split = split ? 1 : 0;
         ProfScope ps(ctx, "mlp", s);
         launch_tc_gemm(a, ma, mb, ctx->num_sms, s);
     };
@@ -521,6 +541,11 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
             ga.se_w2[k] = o.se_w2[k]; ga.se_b2[k] = o.se_b2[k];
         }
         ga.H_T = w.H_T; ga.Hb_rho = w.Hb_rho; ga.Hb_f = w.Hb_f;
+        ga.split = split; ga.part = cap * kLayers * kLatPad;
+        if (dbg && dbg->H_rho && dbg->H_f) {      // FP32 features straight into the debug buffers
+            ga.H_rho = dbg->H_rho + (size_t)off * kLayers * kLat;
+            ga.H_f = dbg->H_f + (size_t)off * kLayers * kLat;
+        }
         ga.v = dbg ? w.v : nullptr; ga.w_se = w.w_se; ga.cfg = w.cfg;
         if (mx) { ga.descs = mx->descs; ga.req_of_point = mx->req_of_point + off; }
         {
@@ -529,7 +554,8 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
         }
         {
             ProfScope ps(ctx, "cnn", s);
-            launch_cnn_f32(w.H_T, cnt, W, o, nullptr, w.XTb, s);
+            launch_cnn_f32(w.H_T, cnt, W, o, (dbg && dbg->X_T) ? dbg->X_T + (size_t)off * kLayers * kDT : nullptr,
+                           w.XTb, s, split ? cap * kLayers * kDT : 0);
         }
         for (int t = 0; t < 3; ++t) {
             const int d = feat_dim(t);
@@ -542,6 +568,8 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
                     f1.M = cnt; f1.N = kWidth; f1.K = d; f1.n_mma = 208; f1.k_tiles = (d + 63) / 64;
                     f1.a_col0 = k * fstride; f1.epi = kEpiFc1; f1.err = ctx->d_err;
                     f1.out_e = w.E; f1.out_s = w.S; f1.ldo = kWidth;
+                    f1.out_e_f32 = split ? w.E32 : nullptr;
+                    f1.out_part = cap * kWidth;
                     f1.bias = W + o.blk_b1[t][k];
                     f1.row_scale = w.w_se + k * 3 + t; f1.row_scale_ld = kLayers * 3;
                     f1.cfg = w.cfg; f1.w_cfg = W + o.blk_w1[t][k] + d; f1.w_cfg_ld = d + kCfg;
@@ -550,15 +578,23 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
                     // per-row configuration even for one request: a request's result is then
                     // bit-identical alone and inside a mixed batch
                     f1.cfg_per_row = 1;
-                    f1.h_prev = k == k0 ? nullptr : w.H; f1.ld_h = kWidth;
+                    f1.h_prev = (k == k0 || split) ? nullptr : w.H; f1.ld_h = kWidth;
+                    f1.pre_f32 = (k == k0 || !split) ? nullptr : w.H32; f1.ld_pre = kWidth;
                     gemm(f1, fmap, wt.map_fc1[t][k]);
                     TcGemmArgs f2{};
                     f2.M = cnt; f2.N = kWidth; f2.K = kWidth; f2.n_mma = 208; f2.k_tiles = 4;
                     f2.epi = kEpiFc2; f2.err = ctx->d_err;
                     f2.bias = W + o.blk_b2[t][k];
                     f2.resid = w.E; f2.ld_resid = kWidth;
-                    if (k == k1 - 1) { f2.out_bf = w.mrg_in[t] + chain * kWidth; f2.ldo = 2 * kWidth; }
-                    else { f2.out_bf = w.H; f2.ldo = kWidth; }
+                    if (split) { f2.pre_f32 = w.E32; f2.ld_pre = kWidth; }
+                    if (k == k1 - 1) {
+                        f2.out_bf = w.mrg_in[t] + chain * kWidth; f2.ldo = 2 * kWidth;
+                        f2.out_part = cap * 2 * kWidth;
+                    } else if (split) {
+                        f2.out_h_f32 = w.H32; f2.ldo = kWidth;
+                    } else {
+                        f2.out_bf = w.H; f2.ldo = kWidth;
+                    }
                     gemm(f2, w.map_s, wt.map_fc2[t][k]);
                 }
             }
@@ -566,12 +602,14 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
             mg.M = cnt; mg.N = kWidth; mg.K = 2 * kWidth; mg.n_mma = 208; mg.k_tiles = 7;
             mg.epi = kEpiRelu; mg.err = ctx->d_err; mg.bias = W + o.mrg_b[t];
             mg.out_bf = w.head_in + t * kWidth; mg.ldo = 3 * kWidth;
+            mg.out_part = cap * 3 * kWidth;
             gemm(mg, w.map_mrg[t], wt.map_mrg[t]);
         }
         TcGemmArgs h1{};
         h1.M = cnt; h1.N = kWidth; h1.K = 3 * kWidth; h1.n_mma = 208; h1.k_tiles = 10;
         h1.epi = kEpiRelu; h1.err = ctx->d_err; h1.bias = W + o.head_b[0];
         h1.out_bf = w.Z1; h1.ldo = kWidth;
+        h1.out_part = cap * kWidth;
         gemm(h1, w.map_head, wt.map_head[0]);
         TcGemmArgs h2 = h1;
         h2.K = kWidth; h2.k_tiles = 4; h2.bias = W + o.head_b[1]; h2.out_bf = w.Z2;
@@ -970,8 +1008,8 @@ nis_status nis_load_weights(nis_ctx *ctx, const void *blob, size_t bytes, int pr
                             nis_stream stream, nis_weights *out) {
     if (!ctx) return NIS_ERR_INVALID_ARG;
     if (!blob || !out) return fail(ctx, NIS_ERR_INVALID_ARG, "NULL blob or out");
-    if (precision != NIS_PREC_F32 && precision != NIS_PREC_BF16)
-        return fail(ctx, NIS_ERR_UNIMPLEMENTED, "precision must be NIS_PREC_F32 or NIS_PREC_BF16");
+    if (precision != NIS_PREC_F32 && precision != NIS_PREC_BF16 && precision != NIS_PREC_F32_SIMT)
+        return fail(ctx, NIS_ERR_UNIMPLEMENTED, "precision must be F32, BF16 or F32_SIMT");
     if (bytes < 80) return fail(ctx, NIS_ERR_BAD_BLOB, "blob shorter than its header");
     uint32_t hd[16];
     uint64_t n_floats, checksum;
@@ -1002,7 +1040,8 @@ nis_status nis_load_weights(nis_ctx *ctx, const void *blob, size_t bytes, int pr
     cudaError_t e = cudaMemcpyAsync(w.f32, words, o.total * 4, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the caller may free the blob
     if (e != cudaSuccess) { dev_free(ctx, w.f32); return cuda_fail(ctx, e, "weights upload"); }
-    if (precision == NIS_PREC_BF16 && (st = pack_weights_bf16(ctx, w, s))) {
+    if (precision != NIS_PREC_F32_SIMT &&
+        (st = pack_weights_tc(ctx, w, precision == NIS_PREC_F32 ? 3 : 1, s))) {
         dev_free(ctx, w.f32);
         dev_free(ctx, w.bf);
         return st;

@@ -163,6 +163,7 @@ struct GatherArgs {
     size_t se_w1[kLayers], se_b1[kLayers], se_w2[kLayers], se_b2[kLayers];
     float *H_rho, *H_T, *H_f;        // [count][12][225] (H_rho, H_f may be null when Hb_* set)
     __nv_bfloat16 *Hb_rho, *Hb_f;    // optional BF16 copies [count][12][kLatPad] (pad zeroed)
+    int split; size_t part;          // BF16 copies as 3 split parts, part stride in elements
     float *v;                        // [count][12][8] (may be null)
     float *w_se;                     // [count][12][3]
     float *cfg;                      // [count][5]
@@ -170,10 +171,17 @@ struct GatherArgs {
 void launch_gather(const GatherArgs &a, cudaStream_t s);
 
 void launch_cnn_f32(const float *H_T, int count, const float *wbase, const WeightOffsets &o,
-                    float *X_T, __nv_bfloat16 *X_T_bf, cudaStream_t s);
+                    float *X_T, __nv_bfloat16 *X_T_bf, cudaStream_t s, size_t split_part = 0);
 // dst[n][k] = bf16(src[n * ld_src + k]) for n < N, k < K, zero elsewhere in [Np][Kp]
 void launch_pack_bf16(const float *src, int N, int K, int ld_src, __nv_bfloat16 *dst, int Np,
-                      int Kp, cudaStream_t s);
+                      int Kp, cudaStream_t s, int split_part = -1);
+// Part `part` (0, 1, 2) of the three-way BF16 split x = x0 + x1 + x2 (x0 = bf16(x),
+// x1 = bf16(x - x0), x2 = bf16(x - x0 - x1)); part -1 is plain bf16(x).
+__host__ __device__ inline float split_residual(float x, int part) {
+    float r = x;
+    for (int i = 0; i < part; ++i) r = r - __bfloat162float(__float2bfloat16_rn(r));
+    return r;
+}
 
 // One dense layer out[r][j] = epilogue(sum_k A[r][k] W[j][k] + b[j]) over rows r < count.
 struct FcArgs {
@@ -230,6 +238,13 @@ struct TcGemmArgs {
     const float *dec_rows;            // kEpiDecode: optional per-row scales [M][3]
     int cfg_per_row;                  // kEpiFc1: use every row's g and albedo from cfg (mixed
                                       // batches) instead of the folded mat_cfg
+    // FP32-accurate mode: operands split into three BF16 parts, six products per K slice
+    int n_pass;                       // 1 (plain BF16) or 6 (split)
+    int a_part_rows, b_part_rows;     // row offset of part i of A / B inside its tensor map
+    int out_split; size_t out_part;   // BF16 outputs (out_bf, out_s) as 3 parts, part stride
+    float *out_e_f32;                 // kEpiFc1: e in FP32 (else BF16 out_e)
+    float *out_h_f32;                 // kEpiFc2: h in FP32 (else out_bf)
+    const float *pre_f32; int ld_pre; // kEpiFc1 h_prev / kEpiFc2 e in FP32 (else BF16)
 };
 void launch_fill_segments(const int *seg_start, const int *seg_desc, int nseg, int count,
                           int *req_of_point, float *dec_rows, const ReqDesc *descs,

@@ -20,7 +20,7 @@ NIS_OK = 0
 STATUS = {0: "OK", -1: "INVALID_ARG", -2: "NOT_READY", -3: "BUDGET", -4: "OOM", -5: "CUDA",
           -6: "TIMEOUT", -7: "UNIMPLEMENTED", -8: "BAD_BLOB", -9: "BAD_DATA"}
 DTYPE_F32, DTYPE_F16 = 0, 1
-PREC_F32, PREC_BF16, PREC_FP8 = 0, 1, 2
+PREC_F32, PREC_BF16, PREC_FP8, PREC_F32_SIMT = 0, 1, 2, 3
 CAMERA_ORTHO, CAMERA_PERSP = 0, 1
 N_LAYERS, N_LAT, N_ALPHA, N_SETS = 12, 225, 1024, 5
 

@@ -343,3 +343,19 @@ def test_error_paths(nis, ctx, w1, gpu1):
         small.upload_volume(np.ones((128, 128, 128), np.float32))
     assert e.value.status == -3
     small.close()
+
+
+def test_fp32_tensor_path_matches_fp32_ffma_path(nis, ctx, w1, gpu1):
+    # NIS_PREC_F32 runs the dense layers on tcgen05 with three-way BF16 operand splits;
+    # NIS_PREC_F32_SIMT is plain FP32 FFMA.  Both must agree at the FP32 tolerance.
+    simt = ctx.load_weights(w1["blob"], nis.PREC_F32_SIMT)
+    p, om = _points(3000, 909)
+    dev = torch.device("cuda:0")
+    pt, ot = torch.from_numpy(p).to(dev), torch.from_numpy(om).to(dev)
+    mat = w1["cfg"]["material"]
+    a = ctx.shade_points(gpu1["vol"], gpu1["light"], gpu1["weights"], mat, pt, ot).cpu().numpy()
+    b = ctx.shade_points(gpu1["vol"], gpu1["light"], simt, mat, pt, ot).cpu().numpy()
+    ctx.release(simt)
+    e = rel_err(a, b)
+    print(f"\n[parity] FP32 tensor (3-way BF16 split) vs FP32 FFMA: max rel {e.max():.3g}")
+    assert e.max() <= 1e-4
