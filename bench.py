@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=256)
+    ap.add_argument("--ncu-case", choices=("f32", "bf16", "simt"),
+                    help="small case for ncu captures: shade 32,768 points of the 64^3 fBm "
+                         "volume twice at this precision, print nothing else")
     return ap.parse_args()
 
 
@@ -488,8 +491,30 @@ def run_nis(args):
     print(json.dumps(line), flush=True)
 
 
+def run_ncu_case(args):
+    import torch
+    from paper_2401_14051_gb300 import nis
+    prec = {"f32": nis.PREC_F32, "bf16": nis.PREC_BF16, "simt": nis.PREC_F32_SIMT}[args.ncu_case]
+    cfg = synth.config(1)
+    ctx = nis.Context(0)
+    v = ctx.upload_volume(cfg["volume"]())
+    l = ctx.build_transmittance(v, cfg["light"], 0.6)
+    w = ctx.load_weights(synth.pack_weights(synth.make_weights(4, 16.0)), prec)
+    p, om = synth.shading_points(32768, 3)
+    dev = torch.device("cuda:0")
+    pt, ot = torch.from_numpy(p).to(dev), torch.from_numpy(om).to(dev)
+    for _ in range(2):
+        ctx.shade_points(v, l, w, cfg["material"], pt, ot)
+    ctx.sync(timeout_ms=60000)
+    ctx.close()
+    print("ok")
+
+
 def main():
     args = parse()
+    if args.ncu_case:
+        run_ncu_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
