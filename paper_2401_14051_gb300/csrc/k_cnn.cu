@@ -1,24 +1,29 @@
-// Per-layer 3D-CNN over the transmittance stencil (Sec. III.B.1, Fig. 3), FP32 SIMT path:
+// Per-layer 3D-CNN over the transmittance stencil (Sec. III.B.1, Fig. 3), FP32 math:
 // conv 3x3x3 1->16 + ReLU (5x5x9 -> 3x3x7), conv 3x3x3 16->16 + ReLU (-> 1x1x5), output
 // flattened position-major [5][16].
 //
-// One CTA of 160 threads per (layer, run of groups of kPts points).  The layer's weights are
-// staged once in shared memory transposed to channel-fastest order, so a thread that owns
-// one output position keeps its input window in registers and reads the weights of 8 or 16
-// output channels with warp-broadcast float4 loads (several FMAs per shared-memory load).
+// One CTA of 288 threads per (layer, run of groups of kPts points); the layer's weights are
+// staged once in shared memory, channel-fastest.  Both convolutions use sliding-window
+// register tiles along the 9-long c axis:
+//   conv1: a thread owns (point, d, h, half of the 16 output channels): for each (kd, kh) it
+//          loads one 9-value input row and updates 7 outputs x 8 channels (168 FMAs for 9
+//          input loads and 6 broadcast float4 weight loads);
+//   conv2: a thread owns (point, half of the output channels, quarter of the input
+//          channels) and all 5 outputs: for each (ci, kd, kh) one 7-value row of conv1
+//          output and 6 float4 weight loads feed 120 FMAs; the four partial sums (adjacent
+//          lanes) are added with warp shuffles.
 #include "nis_internal.h"
 
 namespace nis {
 
 namespace {
 constexpr int kPts = 16;                         // points per group
-constexpr int kThreads = 160;
+constexpr int kThreads = 288;
 constexpr int kGroupsPerCta = 4;
-constexpr int kPos1 = 63;                        // conv1 output positions (3 x 3 x 7)
-constexpr int kY1 = 1016;                        // per-point stride of y1 (16 x 63 = 1008,
-                                                 // padded so conv2's 4 points hit distinct banks)
-// shared memory (floats): w1t [27][16], b1 [16], w2t [16 ci][27 tap][16 co], b2 [16],
-// x [kPts][225], y1 [kPts][16][63]
+constexpr int kCiGroups = 4;                     // conv2: input-channel quarters
+constexpr int kY1 = 1016;                        // per-point stride of y1 (16 x 63 = 1008, padded)
+// shared memory (floats): w1t [27 taps][16 co], b1 [16], w2t [16 ci][27 taps][16 co], b2 [16],
+// x [kPts][225], y1 [kPts][16 ci][63]
 constexpr int kOffW1 = 0, kOffB1 = kOffW1 + 27 * kCnnCh, kOffW2 = kOffB1 + kCnnCh,
               kOffB2 = kOffW2 + kCnnCh * 27 * kCnnCh, kOffX = kOffB2 + kCnnCh,
               kOffY1 = kOffX + kPts * kLat, kSmemFloats = kOffY1 + kPts * kY1;
@@ -63,80 +68,105 @@ __global__ void __launch_bounds__(kThreads) cnn_f32_kernel(const float *__restri
             xin[i] = q < np ? H_T[((size_t)(p0 + q) * kLayers + k) * kLat + t] : 0.f;
         }
         __syncthreads();
-        // conv1: task = (point, position); 16 output channels per task
-        for (int task = tid; task < kPts * kPos1; task += kThreads) {
-            int q = task / kPos1, pos = task % kPos1;
-            int d = pos / 21, h = (pos / 7) % 3, w = pos % 7;
-            const float *x = xin + q * kLat + (d * 5 + h) * 9 + w;
-            float win[27];
+        // conv1: thread = (point q, row d, row h, channel half); 7 outputs x 8 channels
+        {
+            const int half = tid & 1, r = tid >> 1;            // 144 (q, d, h) rows
+            const int q = r / 9, dh = r % 9, d = dh / 3, h = dh % 3;
+            float acc[7][8];
+#pragma unroll
+            for (int w = 0; w < 7; ++w)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) acc[w][c] = b1[half * 8 + c];
 #pragma unroll
             for (int kd = 0; kd < 3; ++kd)
 #pragma unroll
-                for (int kh = 0; kh < 3; ++kh)
+                for (int kh = 0; kh < 3; ++kh) {
+                    const float *xr = xin + q * kLat + ((d + kd) * 5 + (h + kh)) * 9;
+                    float row[9];
 #pragma unroll
-                    for (int kw = 0; kw < 3; ++kw) win[(kd * 3 + kh) * 3 + kw] = x[(kd * 5 + kh) * 9 + kw];
-            float acc[kCnnCh];
+                    for (int i = 0; i < 9; ++i) row[i] = xr[i];
 #pragma unroll
-            for (int c = 0; c < kCnnCh; ++c) acc[c] = b1[c];
-            // keep the weight loads inside the task loop: hoisted, all 432 would spill
-            int zero = 0;
-            asm volatile("" : "+r"(zero));
-            const float *w1p = w1t + zero;
+                    for (int kw = 0; kw < 3; ++kw) {
+                        const float4 *wv =
+                            reinterpret_cast<const float4 *>(w1t + ((kd * 3 + kh) * 3 + kw) * kCnnCh + half * 8);
+                        const float4 wa = wv[0], wb = wv[1];
 #pragma unroll
-            for (int tap = 0; tap < 27; ++tap) {
-                const float4 *wv = reinterpret_cast<const float4 *>(w1p + tap * kCnnCh);
-#pragma unroll
-                for (int c4 = 0; c4 < 4; ++c4) {
-                    float4 ww = wv[c4];
-                    acc[4 * c4 + 0] += ww.x * win[tap];
-                    acc[4 * c4 + 1] += ww.y * win[tap];
-                    acc[4 * c4 + 2] += ww.z * win[tap];
-                    acc[4 * c4 + 3] += ww.w * win[tap];
-                }
-            }
-            float *yo = y1 + q * kY1 + pos;
-#pragma unroll
-            for (int c = 0; c < kCnnCh; ++c) yo[c * kPos1] = fmaxf(acc[c], 0.f);
-        }
-        __syncthreads();
-        // conv2: thread = (point, output position w, half of the output channels)
-        {
-            const int half = tid & 1, pw = tid >> 1;          // 80 (point, w) pairs
-            const int q = pw / 5, w = pw % 5;
-            const float *y = y1 + q * kY1 + w;
-            float acc[8];
-#pragma unroll
-            for (int c = 0; c < 8; ++c) acc[c] = b2[half * 8 + c];
-            for (int ci = 0; ci < kCnnCh; ++ci) {
-                const float *yc = y + ci * kPos1;
-#pragma unroll
-                for (int tap = 0; tap < 27; ++tap) {
-                    const int kd = tap / 9, kh = (tap / 3) % 3, kw = tap % 3;
-                    float v = yc[(kd * 3 + kh) * 7 + kw];
-                    const float4 *wv =
-                        reinterpret_cast<const float4 *>(w2t + (ci * 27 + tap) * kCnnCh + half * 8);
-                    float4 wa = wv[0], wb = wv[1];
-                    acc[0] += wa.x * v; acc[1] += wa.y * v; acc[2] += wa.z * v; acc[3] += wa.w * v;
-                    acc[4] += wb.x * v; acc[5] += wb.y * v; acc[6] += wb.z * v; acc[7] += wb.w * v;
-                }
-            }
-            if (q < np) {
-                const size_t o = ((size_t)(p0 + q) * kLayers + k) * kDT + w * kCnnCh + half * 8;
-                if (X_T_bf) {
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        float r = fmaxf(acc[c], 0.f);
-                        const int parts = split_part ? 3 : 1;
-                        for (int q = 0; q < parts; ++q) {
-                            __nv_bfloat16 b = __float2bfloat16_rn(r);
-                            X_T_bf[o + c + q * split_part] = b;
-                            r -= __bfloat162float(b);
+                        for (int w = 0; w < 7; ++w) {
+                            const float v = row[w + kw];
+                            acc[w][0] += wa.x * v; acc[w][1] += wa.y * v; acc[w][2] += wa.z * v;
+                            acc[w][3] += wa.w * v; acc[w][4] += wb.x * v; acc[w][5] += wb.y * v;
+                            acc[w][6] += wb.z * v; acc[w][7] += wb.w * v;
                         }
                     }
                 }
-                if (X_T) {
+            float *yo = y1 + q * kY1 + (d * 3 + h) * 7;        // y1[q][ci][d][h][w]
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) X_T[o + c] = fmaxf(acc[c], 0.f);
+            for (int c = 0; c < 8; ++c)
+#pragma unroll
+                for (int w = 0; w < 7; ++w) yo[(half * 8 + c) * 63 + w] = fmaxf(acc[w][c], 0.f);
+        }
+        __syncthreads();
+        // conv2: thread = (point q, channel half, input-channel quarter g); 5 outputs x 8
+        // channels, partial sums over 4 input channels
+        if (tid < kPts * 2 * kCiGroups) {
+            const int g = tid % kCiGroups, half = (tid / kCiGroups) & 1, q = tid / (2 * kCiGroups);
+            float acc[5][8];
+#pragma unroll
+            for (int w = 0; w < 5; ++w)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) acc[w][c] = 0.f;
+            for (int cc = 0; cc < kCnnCh / kCiGroups; ++cc) {
+                const int ci = g * (kCnnCh / kCiGroups) + cc;
+#pragma unroll
+                for (int kd = 0; kd < 3; ++kd)
+#pragma unroll
+                    for (int kh = 0; kh < 3; ++kh) {
+                        const float *yr = y1 + q * kY1 + ci * 63 + (kd * 3 + kh) * 7;
+                        float row[7];
+#pragma unroll
+                        for (int i = 0; i < 7; ++i) row[i] = yr[i];
+#pragma unroll
+                        for (int kw = 0; kw < 3; ++kw) {
+                            const float4 *wv = reinterpret_cast<const float4 *>(
+                                w2t + (ci * 27 + (kd * 3 + kh) * 3 + kw) * kCnnCh + half * 8);
+                            const float4 wa = wv[0], wb = wv[1];
+#pragma unroll
+                            for (int w = 0; w < 5; ++w) {
+                                const float v = row[w + kw];
+                                acc[w][0] += wa.x * v; acc[w][1] += wa.y * v; acc[w][2] += wa.z * v;
+                                acc[w][3] += wa.w * v; acc[w][4] += wb.x * v; acc[w][5] += wb.y * v;
+                                acc[w][6] += wb.z * v; acc[w][7] += wb.w * v;
+                            }
+                        }
+                    }
+            }
+            // add the four input-channel quarters (lanes g = 0..3 of this group)
+#pragma unroll
+            for (int w = 0; w < 5; ++w)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    acc[w][c] += __shfl_xor_sync(~0u, acc[w][c], 1);
+                    acc[w][c] += __shfl_xor_sync(~0u, acc[w][c], 2);
+                }
+            // lane g finalises entries e = 10 g .. 10 g + 9 of the 40 (position, channel) pairs
+            if (q < np) {
+#pragma unroll
+                for (int e = 0; e < 40; ++e) {
+                    if (e / 10 != g) continue;
+                    const int w = e / 8, c = e % 8;
+                    const int r = w * kCnnCh + half * 8 + c;
+                    const float v = fmaxf(acc[w][c] + b2[half * 8 + c], 0.f);
+                    const size_t o = ((size_t)(p0 + q) * kLayers + k) * kDT + r;
+                    if (X_T_bf) {
+                        float rr = v;
+                        const int parts = split_part ? 3 : 1;
+                        for (int s2 = 0; s2 < parts; ++s2) {
+                            __nv_bfloat16 b = __float2bfloat16_rn(rr);
+                            X_T_bf[o + s2 * split_part] = b;
+                            rr -= __bfloat162float(b);
+                        }
+                    }
+                    if (X_T) X_T[o] = v;
                 }
             }
         }
