@@ -325,6 +325,7 @@ def run_nis(args):
     v = ctx.upload_volume(density)
     w = ctx.load_weights(blob)
     w_bf16 = ctx.load_weights(blob, nis.PREC_BF16)
+    w_fp8 = ctx.load_weights(blob, nis.PREC_FP8)
     img = torch.empty((cam["height"], cam["width"], 3), dtype=torch.float32, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
     stream = torch.cuda.current_stream()
@@ -404,6 +405,37 @@ def run_nis(args):
                          "launches": mlp_n, "avg_launch_ms": mlp_ms / max(mlp_n, 1),
                          "traffic": (recorded_traffic("mlp_bf16") or {}).get("bytes_per_launch")}}
 
+    # ---- the same frames in FP8 e4m3 (dense layers)
+    img_f8 = torch.empty_like(img)
+    for _ in range(args.warmup):
+        step(w_fp8, img_f8)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    times_f8 = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(w_fp8, img_f8)
+        e1.record(stream)
+        e1.synchronize()
+        times_f8.append(e0.elapsed_time(e1))
+    ctx.profile(False)
+    fam_f8 = {f: ctx.profile_read(f) for f in nis.FAMILIES}
+    total_f8 = max_over_ranks(sum(times_f8), world)
+    a_f8 = img_f8[hitmask].double()
+    e_f8 = ((a_f8 - a_32).abs() / torch.maximum(a_32.abs(), floor))
+    mlp8_ms = fam_f8["mlp"][0]
+    mlp8_tf = MLP_FLOP_PER_POINT * n_points * args.steps / (mlp8_ms / 1e3) / 1e12
+    fp8 = {"value": n_points * args.steps * world / (total_f8 / 1e3), "unit": UNIT,
+           "frame_ms": total_f8 / args.steps,
+           "mean_rel_err_vs_fp32": float(e_f8.mean()), "max_rel_err_vs_fp32": float(e_f8.max()),
+           "step_breakdown_ms": {f: round(fam_f8[f][0] / args.steps, 4) for f in nis.FAMILIES},
+           "roofline": {"bound": "tensor", "unit": "TFLOP/s", "kernel": "tc_gemm_kernel (tcgen05 kind::f8f6f4, e4m3)",
+                        "achieved": mlp8_tf, "peak": 2 * peaks_bf["bf16_tflops_sustained"],
+                        "frac": mlp8_tf / (2 * peaks_bf["bf16_tflops_sustained"]),
+                        "peak_source": f"{peaks_bf['source']} cuBLAS BF16 sustained x 2 (nominal FP8/BF16 ratio)"}}
+
     # ---- end to end through the C ABI from page-locked host memory
     host_vol = torch.from_numpy(vol_np).pin_memory()
     host_img = torch.empty(img.shape, dtype=torch.float32).pin_memory()
@@ -478,6 +510,7 @@ def run_nis(args):
             "step_breakdown_ms": {f: round(fam[f][0] / args.steps, 4) for f in nis.FAMILIES},
             "roofline": roof,
             "bf16": bf16,
+            "fp8": fp8,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(vol_np.nbytes),
                     "d2h_bytes_per_step": int(img.numel() * 4),

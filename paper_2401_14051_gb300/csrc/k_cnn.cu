@@ -12,6 +12,8 @@
 //          channels) and all 5 outputs: for each (ci, kd, kh) one 7-value row of conv1
 //          output and 6 float4 weight loads feed 120 FMAs; the four partial sums (adjacent
 //          lanes) are added with warp shuffles.
+#include <cuda_fp8.h>
+
 #include "nis_internal.h"
 
 namespace nis {
@@ -29,13 +31,14 @@ constexpr int kOffW1 = 0, kOffB1 = kOffW1 + 27 * kCnnCh, kOffW2 = kOffB1 + kCnnC
               kOffY1 = kOffX + kPts * kLat, kSmemFloats = kOffY1 + kPts * kY1;
 }  // namespace
 
-__global__ void __launch_bounds__(kThreads) cnn_f32_kernel(const float *__restrict__ H_T,
+__global__ void __launch_bounds__(kThreads, 2) cnn_f32_kernel(const float *__restrict__ H_T,
                                                            int count,
                                                            const float *__restrict__ wbase,
                                                            const __grid_constant__ WeightOffsets o,
                                                            float *__restrict__ X_T,
                                                            __nv_bfloat16 *__restrict__ X_T_bf,
-                                                           size_t split_part) {
+                                                           size_t split_part,
+                                                           uint8_t *__restrict__ X_T_f8) {
     extern __shared__ __align__(16) float sm[];
     float *w1t = sm + kOffW1, *b1 = sm + kOffB1, *w2t = sm + kOffW2, *b2 = sm + kOffB2;
     float *xin = sm + kOffX, *y1 = sm + kOffY1;
@@ -167,6 +170,7 @@ __global__ void __launch_bounds__(kThreads) cnn_f32_kernel(const float *__restri
                         }
                     }
                     if (X_T) X_T[o] = v;
+                    if (X_T_f8) X_T_f8[o] = __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
                 }
             }
         }
@@ -174,7 +178,8 @@ __global__ void __launch_bounds__(kThreads) cnn_f32_kernel(const float *__restri
 }
 
 void launch_cnn_f32(const float *H_T, int count, const float *wbase, const WeightOffsets &o,
-                    float *X_T, __nv_bfloat16 *X_T_bf, cudaStream_t s, size_t split_part) {
+                    float *X_T, __nv_bfloat16 *X_T_bf, cudaStream_t s, size_t split_part,
+                    uint8_t *X_T_f8) {
     if (count <= 0) return;
     size_t smem = kSmemFloats * sizeof(float);
     static bool attr_set = false;   // per process; the attribute is per function
@@ -185,7 +190,7 @@ void launch_cnn_f32(const float *H_T, int count, const float *wbase, const Weigh
     int n_groups = (count + kPts - 1) / kPts;
     dim3 grid((n_groups + kGroupsPerCta - 1) / kGroupsPerCta, kLayers);
     note_launch();
-    cnn_f32_kernel<<<grid, kThreads, smem, s>>>(H_T, count, wbase, o, X_T, X_T_bf, split_part);
+    cnn_f32_kernel<<<grid, kThreads, smem, s>>>(H_T, count, wbase, o, X_T, X_T_bf, split_part, X_T_f8);
 }
 
 }  // namespace nis

@@ -2,6 +2,8 @@
 // excitation weights (Eq. 24-26) fused in: one CTA per shading point, one warp per template
 // layer; lane l owns lattice points l, l + 32, ... and the squeeze statistics are reduced
 // with warp shuffles, so the layers proceed independently without block barriers.
+#include <cuda_fp8.h>
+
 #include "nis_internal.h"
 
 namespace nis {
@@ -83,9 +85,11 @@ __global__ void __launch_bounds__(kLayers * 32) gather_kernel(const __grid_const
 
     float s0 = 0.f, s1 = 0.f, s2 = 0.f;
     float m0 = -3.0e38f, m1 = -3.0e38f, m2 = -3.0e38f;
-#pragma unroll 2
-    for (int i = 0; i < (kLatPad + 31) / 32; ++i) {
+    float keep_rho[8], keep_f[8];               // this lane's samples (FP8 needs the max first)
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
         const int t = lane + 32 * i;
+        keep_rho[i] = keep_f[i] = 0.f;
         if (t < kLat) {
             const float qa = (float)(t / 45 - 2), qb = (float)((t / 9) % 5 - 2), qc = (float)(t % 9 - 4);
             const float sx = cxk + h * (qa * exx + qb * eyx + qc * ezx);
@@ -117,6 +121,8 @@ __global__ void __launch_bounds__(kLayers * 32) gather_kernel(const __grid_const
             }
             s0 += rho; s1 += f; s2 += T;
             m0 = fmaxf(m0, rho); m1 = fmaxf(m1, f); m2 = fmaxf(m2, T);
+            keep_rho[i] = rho;
+            keep_f[i] = f;
         } else if (a.Hb_rho && t < kLatPad) {     // zero the BF16 row padding
             for (int q = 0; q < (a.split ? 3 : 1); ++q) {
                 a.Hb_rho[obase_b + t + q * a.part] = __float2bfloat16_rn(0.f);
@@ -132,6 +138,23 @@ __global__ void __launch_bounds__(kLayers * 32) gather_kernel(const __grid_const
         m0 = fmaxf(m0, __shfl_xor_sync(~0u, m0, o));
         m1 = fmaxf(m1, __shfl_xor_sync(~0u, m1, o));
         m2 = fmaxf(m2, __shfl_xor_sync(~0u, m2, o));
+    }
+    if (a.H8_rho) {
+        // e4m3 features scaled per (point, layer, type) by max / 448
+        const float sr = m0 > 0.f ? m0 / 448.f : 1.f, sf = m1 > 0.f ? m1 / 448.f : 1.f;
+        const size_t ob8 = ((size_t)p * kLayers + k) * kLatPad8;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int t = lane + 32 * i;
+            if (t < kLatPad8) {
+                a.H8_rho[ob8 + t] = __nv_cvt_float_to_fp8(keep_rho[i] / sr, __NV_SATFINITE, __NV_E4M3);
+                a.H8_f[ob8 + t] = __nv_cvt_float_to_fp8(keep_f[i] / sf, __NV_SATFINITE, __NV_E4M3);
+            }
+        }
+        if (lane == 0) {
+            a.f8_scale[((size_t)p * kLayers + k) * 2] = sr;
+            a.f8_scale[((size_t)p * kLayers + k) * 2 + 1] = sf;
+        }
     }
     if (lane == 0) {
         float v[8] = {s0 * (1.0f / kLat), s1 * (1.0f / kLat), s2 * (1.0f / kLat), m0, m1, m2, gg, alpha};

@@ -12,6 +12,7 @@
 // Every mbarrier wait is bounded: on a time-out the kernel records kErrTimeout in the
 // context's error word and winds down (draining its MMAs before releasing TMEM).
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "nis_internal.h"
 #include "tc_common.h"
@@ -23,7 +24,7 @@ constexpr int TM = 128, TK = 64, TN_MAX = 208, STAGES = 4;
 constexpr uint32_t A_STAGE = TM * TK * 2;                 // 16 KB
 constexpr uint32_t B_STAGE = TN_MAX * TK * 2;             // 26 KB (208 rows)
 constexpr uint32_t SMEM_TILES = STAGES * (A_STAGE + B_STAGE);
-constexpr uint32_t SMEM_CONST = 6 * TN_MAX * 4;          // per-column epilogue constants
+constexpr uint32_t SMEM_CONST = 7 * TN_MAX * 4;          // per-column epilogue constants
 constexpr uint32_t SMEM_BYTES = SMEM_TILES + 256 + SMEM_CONST + 1024;  // + alignment slack
 constexpr int kEpiWarps = 8;                              // two per TMEM lane quarter
 constexpr int kThreads = 64 + 32 * kEpiWarps;
@@ -56,6 +57,16 @@ __device__ __forceinline__ void store_out8(__nv_bfloat16 *dst, const float *v, i
         for (int i = 0; i < 8; ++i) r[i] = r[i] - __bfloat162float(__float2bfloat16_rn(r[i]));
     }
 }
+// 8 values as e4m3 (saturating), one 8-byte store.
+__device__ __forceinline__ void store_f8x8(uint8_t *dst, const float *v) {
+    uint32_t lo = 0, hi = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        lo |= (uint32_t)__nv_cvt_float_to_fp8(v[i], __NV_SATFINITE, __NV_E4M3) << (8 * i);
+        hi |= (uint32_t)__nv_cvt_float_to_fp8(v[4 + i], __NV_SATFINITE, __NV_E4M3) << (8 * i);
+    }
+    *reinterpret_cast<uint2 *>(dst) = make_uint2(lo, hi);
+}
 __device__ __forceinline__ void store_f32x8(float *dst, const float *v) {
     reinterpret_cast<float4 *>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
     reinterpret_cast<float4 *>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
@@ -79,8 +90,13 @@ __device__ __forceinline__ void load_bf16x8(const __nv_bfloat16 *src, float *v) 
 __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs &a, int r, int c0, float (&v)[32],
                                                const float *s_bias, const float *s_wa, float sc,
                                                float alpha, const float (&pre)[32],
-                                               const float *s_wm, const float (&rc)[4]) {
+                                               const float *s_wm, const float (&rc)[4],
+                                               const float *s_ws) {
     const int N = a.N;
+    if (a.col_scale) {                                   // FP8: per-output-channel weight scale
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] *= s_ws[c0 + j];
+    }
     switch (a.epi) {
     case kEpiPlain: {
         float *o = a.out_f32 + (size_t)r * a.ldo;
@@ -108,7 +124,8 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs &a, int r, int c
             if (c0 + 8 * g < N) {
                 if (a.out_e_f32) store_f32x8(a.out_e_f32 + (size_t)r * a.ldo + c0 + 8 * g, v + 8 * g);
                 else store_bf16x8(a.out_e + (size_t)r * a.ldo + c0 + 8 * g, v + 8 * g);
-                store_out8(a.out_s + (size_t)r * a.ldo + c0 + 8 * g, sv + 8 * g, a.out_split, a.out_part);
+                if (a.out_s8) store_f8x8(a.out_s8 + (size_t)r * kWidth8 + c0 + 8 * g, sv + 8 * g);
+                else store_out8(a.out_s + (size_t)r * a.ldo + c0 + 8 * g, sv + 8 * g, a.out_split, a.out_part);
             }
         break;
     }
@@ -120,6 +137,7 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs &a, int r, int c
         for (int g = 0; g < 4; ++g)
             if (c0 + 8 * g < N) {
                 if (a.out_h_f32) store_f32x8(a.out_h_f32 + (size_t)r * a.ldo + c0 + 8 * g, v + 8 * g);
+                else if (a.out_f8) store_f8x8(a.out_f8 + (size_t)r * a.ldo + c0 + 8 * g, v + 8 * g);
                 else store_out8(a.out_bf + (size_t)r * a.ldo + c0 + 8 * g, v + 8 * g, a.out_split, a.out_part);
             }
         break;
@@ -129,7 +147,10 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs &a, int r, int c
         for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + s_bias[c0 + j], 0.f);
 #pragma unroll
         for (int g = 0; g < 4; ++g)
-            if (c0 + 8 * g < N) store_out8(a.out_bf + (size_t)r * a.ldo + c0 + 8 * g, v + 8 * g, a.out_split, a.out_part);
+            if (c0 + 8 * g < N) {
+                if (a.out_f8) store_f8x8(a.out_f8 + (size_t)r * a.ldo + c0 + 8 * g, v + 8 * g);
+                else store_out8(a.out_bf + (size_t)r * a.ldo + c0 + 8 * g, v + 8 * g, a.out_split, a.out_part);
+            }
         break;
     }
     default: {  // kEpiDecode: rgb = I albedo^4 expm1(acc + b), N = 3
@@ -191,12 +212,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     float *s_bias = reinterpret_cast<float *>(smem + SMEM_TILES + 256);
     float *s_wa = s_bias + TN_MAX;
     float *s_wm = s_wa + TN_MAX;              // [TN_MAX][4] weights of g and albedo (mixed)
+    float *s_ws = s_wm + 4 * TN_MAX;          // FP8 weight scales
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_tiles = (a.M + TM - 1) / TM;
     const int n_mma = a.n_mma;
     const uint32_t b_bytes = (uint32_t)n_mma * TK * 2;
-    const uint32_t idesc = tc::idesc_bf16_f32(TM, n_mma);
+    const uint32_t idesc = a.fp8 ? tc::idesc_e4m3_f32(TM, n_mma) : tc::idesc_bf16_f32(TM, n_mma);
+    const int tk = a.fp8 ? 128 : TK;               // K elements per 128-byte stage row
+    const int kslice = a.fp8 ? 32 : 16;            // K elements per MMA (32 bytes)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
@@ -223,6 +247,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         s_bias[c] = b;
         s_wa[c] = wa;
+        s_ws[c] = (a.col_scale && c < a.N) ? a.col_scale[c] : 1.f;
 #pragma unroll
         for (int q = 0; q < 4; ++q) s_wm[4 * c + q] = wm[q];
     }
@@ -248,9 +273,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint32_t ph = (it / STAGES) & 1;
                     if (!tc::mbar_wait(&empty[s], ph ^ 1)) { record_timeout(a.err, abort_flag); break; }
                     tc::mbar_expect_tx(&full[s], A_STAGE + b_bytes);
-                    tc::tma_load_2d(sA + s * A_STAGE, &map_a, a.a_col0 + kt * TK,
+                    tc::tma_load_2d(sA + s * A_STAGE, &map_a, a.a_col0 + kt * tk,
                                     pa * a.a_part_rows + tile * TM, &full[s]);
-                    tc::tma_load_2d(sB + s * B_STAGE, &map_b, kt * TK, pb * a.b_part_rows, &full[s]);
+                    tc::tma_load_2d(sB + s * B_STAGE, &map_b, kt * tk, pb * a.b_part_rows, &full[s]);
                 }
             }
             // wait until every stage issued has landed (the consumer may have stopped early)
@@ -277,11 +302,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tc::fence_after_sync();
                     const uint32_t a_addr = tc::smem_u32(sA + s * A_STAGE);
                     const uint32_t b_addr = tc::smem_u32(sB + s * B_STAGE);
-                    const int k_left = a.K - kt * TK;
-                    const int n_k16 = k_left >= TK ? TK / 16 : (k_left + 15) / 16;
-                    for (int k = 0; k < n_k16; ++k)
-                        tc::mma_f16(d_tmem, tc::smem_desc_sw128(a_addr + k * 32),
-                                    tc::smem_desc_sw128(b_addr + k * 32), idesc, (st | k) != 0);
+                    const int k_left = a.K - kt * tk;
+                    const int n_sl = k_left >= tk ? 4 : (k_left + kslice - 1) / kslice;
+                    for (int k = 0; k < n_sl; ++k) {
+                        const uint64_t ad = tc::smem_desc_sw128(a_addr + k * 32);
+                        const uint64_t bd = tc::smem_desc_sw128(b_addr + k * 32);
+                        if (a.fp8) tc::mma_f8(d_tmem, ad, bd, idesc, (st | k) != 0);
+                        else tc::mma_f16(d_tmem, ad, bd, idesc, (st | k) != 0);
+                    }
                     tc::mma_commit(&empty[s]);
                 }
                 if (!ok) { record_timeout(a.err, abort_flag); break; }
@@ -302,6 +330,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             float sc = 0.f, alpha = 0.f, rc[4] = {0.f, 0.f, 0.f, 0.f};
             if (live && a.epi == kEpiFc1) {
                 sc = a.row_scale[(size_t)r * a.row_scale_ld];
+                if (a.row_scale2) sc *= a.row_scale2[(size_t)r * a.row_scale2_ld];
                 alpha = a.cfg[(size_t)r * kCfg + 4];
                 if (a.cfg_per_row)
                     for (int q = 0; q < 4; ++q) rc[q] = a.cfg[(size_t)r * kCfg + q];
@@ -324,7 +353,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 // next chunk's residual loads overlap this chunk's TMEM load and math
                 if (live && c0 + 64 < a.N) load_pre(a, r, c0 + 64, pre);
                 tc::tmem_ld_wait();
-                if (live) epilogue_chunk(a, r, c0, v, s_bias, s_wa, sc, alpha, cur, s_wm, rc);
+                if (live) epilogue_chunk(a, r, c0, v, s_bias, s_wa, sc, alpha, cur, s_wm, rc, s_ws);
             }
             tc::fence_before_sync();
             __syncwarp();
@@ -355,6 +384,31 @@ void launch_pack_bf16(const float *src, int N, int K, int ld_src, __nv_bfloat16 
     int blocks = (int)((total + 255) / 256 < 1024 ? (total + 255) / 256 : 1024);
     note_launch();
     pack_bf16_kernel<<<blocks, 256, 0, s>>>(src, N, K, ld_src, dst, Np, Kp, split_part);
+}
+
+// FP8 weights: one warp per output row n finds max |W[n][:K]| and writes the row scale and
+// the e4m3 values W / scale (zero padding beyond N and K).
+__global__ void pack_fp8_kernel(const float *__restrict__ src, int N, int K, int ld_src,
+                                uint8_t *__restrict__ dst, float *__restrict__ scale, int Np, int Kp) {
+    const int n = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (n >= Np) return;
+    float mx = 0.f;
+    if (n < N)
+        for (int k = lane; k < K; k += 32) mx = fmaxf(mx, fabsf(src[(size_t)n * ld_src + k]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(~0u, mx, o));
+    const float sc = mx > 0.f ? mx / 448.f : 1.f;
+    if (lane == 0) scale[n] = sc;
+    for (int k = lane; k < Kp; k += 32) {
+        float x = (n < N && k < K) ? src[(size_t)n * ld_src + k] / sc : 0.f;
+        dst[(size_t)n * Kp + k] = __nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
+    }
+}
+
+void launch_pack_fp8(const float *src, int N, int K, int ld_src, uint8_t *dst, float *scale,
+                     int Np, int Kp, cudaStream_t s) {
+    note_launch();
+    pack_fp8_kernel<<<(Np + 7) / 8, 256, 0, s>>>(src, N, K, ld_src, dst, scale, Np, Kp);
 }
 
 void launch_tc_gemm(const TcGemmArgs &a, const CUtensorMap &map_a, const CUtensorMap &map_b,

@@ -45,6 +45,19 @@ struct Weights {
     // BF16 dense layers (precision BF16): zero-padded [n_mma][Kp] matrices and tensor maps
     __nv_bfloat16 *bf = nullptr;
     CUtensorMap map_fc1[3][kLayers], map_fc2[3][kLayers], map_mrg[3], map_head[3];
+    // FP8 dense layers: e4m3 [n_mma][Kp] matrices and per-output-channel scales
+    uint8_t *f8 = nullptr;
+    float *f8_scales = nullptr;
+    const float *sc_fc1[3][kLayers] = {}, *sc_fc2[3][kLayers] = {}, *sc_mrg[3] = {}, *sc_head[3] = {};
+};
+
+struct WorkspaceF8 {                  // scratch of the FP8 path, grow-only
+    int cap = 0;
+    uint8_t *H8_rho = nullptr, *H8_f = nullptr, *XT8 = nullptr, *S8 = nullptr,
+            *mrg8[3] = {nullptr, nullptr, nullptr}, *head8 = nullptr, *Z1 = nullptr, *Z2 = nullptr;
+    __nv_bfloat16 *E = nullptr, *H = nullptr;
+    float *H_T = nullptr, *w_se = nullptr, *cfg = nullptr, *v = nullptr, *fscale = nullptr;
+    CUtensorMap map_rho, map_f, map_xt, map_s, map_mrg[3], map_head, map_z1, map_z2;
 };
 
 struct WorkspaceBf {                  // scratch of the tensor-core paths, grow-only
@@ -87,6 +100,7 @@ struct nis_ctx {
     std::map<uint32_t, float *> phase;   // by the bit pattern of g
     Workspace ws;
     WorkspaceBf wsb, wsx;                 // BF16 and split (FP32-accurate) tensor paths
+    WorkspaceF8 ws8;
     // mixed-batch buffers of nis_shade_segments (grow-only)
     int mix_cap = 0, mix_desc_cap = 0;
     float *mix_pts = nullptr, *mix_om = nullptr, *mix_rgb = nullptr, *mix_dec = nullptr;
@@ -353,6 +367,88 @@ nis_status pack_weights_tc(nis_ctx *ctx, Weights &w, int parts, cudaStream_t s) 
     return NIS_OK;
 }
 
+// FP8 weight pack: per dense layer an e4m3 [n_mma][Kp] matrix (Kp a multiple of 128) with
+// per-output-channel scales, and a UINT8 tensor map.
+nis_status pack_weights_fp8(nis_ctx *ctx, Weights &w, cudaStream_t s) {
+    struct Mat { const float *src; int N, K, ld; CUtensorMap *map; const float **sc; };
+    std::vector<Mat> mats;
+    const WeightOffsets &o = w.off;
+    for (int t = 0; t < 3; ++t)
+        for (int k = 0; k < kLayers; ++k) {
+            int d = feat_dim(t);
+            mats.push_back({w.f32 + o.blk_w1[t][k], kWidth, d, d + kCfg, &w.map_fc1[t][k], &w.sc_fc1[t][k]});
+            mats.push_back({w.f32 + o.blk_w2[t][k], kWidth, kWidth, kWidth, &w.map_fc2[t][k], &w.sc_fc2[t][k]});
+        }
+    for (int t = 0; t < 3; ++t)
+        mats.push_back({w.f32 + o.mrg_w[t], kWidth, 2 * kWidth, 2 * kWidth, &w.map_mrg[t], &w.sc_mrg[t]});
+    mats.push_back({w.f32 + o.head_w[0], kWidth, 3 * kWidth, 3 * kWidth, &w.map_head[0], &w.sc_head[0]});
+    mats.push_back({w.f32 + o.head_w[1], kWidth, kWidth, kWidth, &w.map_head[1], &w.sc_head[1]});
+    mats.push_back({w.f32 + o.head_w[2], 3, kWidth, kWidth, &w.map_head[2], &w.sc_head[2]});
+    auto kp8 = [](int k) { return (k + 127) / 128 * 128; };
+    size_t total = 0, nsc = 0;
+    for (auto &m : mats) { total += (size_t)n_mma_of(m.N) * kp8(m.K); nsc += n_mma_of(m.N); }
+    nis_status st = dev_alloc_t(ctx, total, &w.f8, s);
+    if (st) return st;
+    if ((st = dev_alloc_t(ctx, nsc, &w.f8_scales, s))) return st;
+    size_t off = 0, soff = 0;
+    for (auto &m : mats) {
+        int np = n_mma_of(m.N), kp = kp8(m.K);
+        {
+            ProfScope ps(ctx, "other", s);
+            launch_pack_fp8(m.src, m.N, m.K, m.ld, w.f8 + off, w.f8_scales + soff, np, kp, s);
+        }
+        if (!make_tmap_u8(m.map, w.f8 + off, (uint64_t)kp, (uint64_t)np, (uint64_t)kp, 128, (uint32_t)np))
+            return fail(ctx, NIS_ERR_CUDA, "cuTensorMapEncodeTiled failed for an FP8 weight matrix");
+        *m.sc = w.f8_scales + soff;
+        off += (size_t)np * kp;
+        soff += np;
+    }
+    NIS_CUDA(cudaGetLastError());
+    return NIS_OK;
+}
+
+nis_status ensure_workspace_fp8(nis_ctx *ctx, int cap, cudaStream_t s) {
+    WorkspaceF8 &w = ctx->ws8;
+    if (w.cap >= cap) return NIS_OK;
+    uint8_t **bb[] = {&w.H8_rho, &w.H8_f, &w.XT8, &w.S8, &w.mrg8[0], &w.mrg8[1], &w.mrg8[2],
+                      &w.head8, &w.Z1, &w.Z2};
+    for (auto **b : bb) { dev_free(ctx, *b); *b = nullptr; }
+    dev_free(ctx, w.E); dev_free(ctx, w.H); w.E = w.H = nullptr;
+    float **ff[] = {&w.H_T, &w.w_se, &w.cfg, &w.v, &w.fscale};
+    for (float **f : ff) { dev_free(ctx, *f); *f = nullptr; }
+    w.cap = 0;
+    const size_t n = (size_t)cap;
+    nis_status st;
+    struct B8 { uint8_t **p; size_t bytes; };
+    B8 list[] = {{&w.H8_rho, n * kLayers * kLatPad8}, {&w.H8_f, n * kLayers * kLatPad8},
+                 {&w.XT8, n * kLayers * kDT}, {&w.S8, n * kWidth8}, {&w.mrg8[0], n * 2 * kWidth},
+                 {&w.mrg8[1], n * 2 * kWidth}, {&w.mrg8[2], n * 2 * kWidth}, {&w.head8, n * kHead8},
+                 {&w.Z1, n * kWidth8}, {&w.Z2, n * kWidth8}};
+    for (auto &b : list) {
+        if ((st = dev_alloc_t(ctx, b.bytes, b.p, s))) return st;
+        NIS_CUDA(cudaMemsetAsync(*b.p, 0, b.bytes, s));   // row padding stays zero
+    }
+    if ((st = dev_alloc_t(ctx, n * kWidth, &w.E, s))) return st;
+    if ((st = dev_alloc_t(ctx, n * kWidth, &w.H, s))) return st;
+    if ((st = dev_alloc_t(ctx, n * kLayers * kLat, &w.H_T, s))) return st;
+    if ((st = dev_alloc_t(ctx, n * kLayers * 3, &w.w_se, s))) return st;
+    if ((st = dev_alloc_t(ctx, n * kCfg, &w.cfg, s))) return st;
+    if ((st = dev_alloc_t(ctx, n * kLayers * 8, &w.v, s))) return st;
+    if ((st = dev_alloc_t(ctx, n * kLayers * 2, &w.fscale, s))) return st;
+    bool ok = make_tmap_u8(&w.map_rho, w.H8_rho, kLayers * kLatPad8, n, kLayers * kLatPad8, 128, 128) &&
+              make_tmap_u8(&w.map_f, w.H8_f, kLayers * kLatPad8, n, kLayers * kLatPad8, 128, 128) &&
+              make_tmap_u8(&w.map_xt, w.XT8, kLayers * kDT, n, kLayers * kDT, 128, 128) &&
+              make_tmap_u8(&w.map_s, w.S8, kWidth8, n, kWidth8, 128, 128) &&
+              make_tmap_u8(&w.map_head, w.head8, kHead8, n, kHead8, 128, 128) &&
+              make_tmap_u8(&w.map_z1, w.Z1, kWidth8, n, kWidth8, 128, 128) &&
+              make_tmap_u8(&w.map_z2, w.Z2, kWidth8, n, kWidth8, 128, 128);
+    for (int t = 0; t < 3; ++t)
+        ok = ok && make_tmap_u8(&w.map_mrg[t], w.mrg8[t], 2 * kWidth, n, 2 * kWidth, 128, 128);
+    if (!ok) return fail(ctx, NIS_ERR_CUDA, "cuTensorMapEncodeTiled failed for the FP8 workspace");
+    w.cap = cap;
+    return NIS_OK;
+}
+
 nis_status check_material(nis_ctx *ctx, const nis_material *m) {
     if (!m) return fail(ctx, NIS_ERR_INVALID_ARG, "material is NULL");
     if (!(m->g > -1.f && m->g < 1.f)) return fail(ctx, NIS_ERR_INVALID_ARG, "g must lie in (-1, 1)");
@@ -372,6 +468,10 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
                            const nis_material *m, const float *table, const float *pts,
                            const float *om, int n, float *rgb, const nis_debug_out *dbg,
                            cudaStream_t s, const Mixed *mx);
+nis_status shade_impl_fp8(nis_ctx *ctx, const Volume &vol, const Light &light, const Weights &wt,
+                          const nis_material *m, const float *table, const float *pts,
+                          const float *om, int n, float *rgb, const nis_debug_out *dbg,
+                          cudaStream_t s, const Mixed *mx);
 
 // Runs steps 3-6 for `n` points already on the device.
 nis_status shade_impl(nis_ctx *ctx, const Volume &vol, const Light &light, const Weights &wt,
@@ -382,6 +482,8 @@ nis_status shade_impl(nis_ctx *ctx, const Volume &vol, const Light &light, const
     nis_status st;
     if (!mx && (st = ensure_phase(ctx, m->g, s, &table))) return st;
     if (n <= 0) return NIS_OK;
+    if (wt.precision == NIS_PREC_FP8)
+        return shade_impl_fp8(ctx, vol, light, wt, m, table, pts, om, n, rgb, dbg, s, mx);
     if (wt.precision != NIS_PREC_F32_SIMT)
         return shade_impl_bf16(ctx, vol, light, wt, m, table, pts, om, n, rgb, dbg, s, mx);
     int chunk = n < kChunk ? n : kChunk;
@@ -637,6 +739,130 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
     return NIS_OK;
 }
 
+// Steps 3-6 with the dense layers in FP8 e4m3 on the tensor cores (FP32 accumulation):
+// weights scaled per output channel, density/phase features per (point, layer), the other
+// activations unscaled.
+nis_status shade_impl_fp8(nis_ctx *ctx, const Volume &vol, const Light &light, const Weights &wt,
+                          const nis_material *m, const float *table, const float *pts,
+                          const float *om, int n, float *rgb, const nis_debug_out *dbg,
+                          cudaStream_t s, const Mixed *mx) {
+    int chunk = n < kChunk ? n : kChunk;
+    nis_status st = ensure_workspace_fp8(ctx, chunk, s);
+    if (st) return st;
+    WorkspaceF8 &w = ctx->ws8;
+    const WeightOffsets &o = wt.off;
+    const float *W = wt.f32;
+    float dec_scale[3];
+    for (int c = 0; c < 3; ++c) dec_scale[c] = m->intensity[c] * powf(m->albedo[c], 4.0f);
+    auto gemm = [&](TcGemmArgs a, const CUtensorMap &ma, const CUtensorMap &mb) {
+        a.fp8 = 1;
+        a.k_tiles = (a.K + 127) / 128;
+        ProfScope ps(ctx, "mlp", s);
+        launch_tc_gemm(a, ma, mb, ctx->num_sms, s);
+    };
+    for (int off = 0; off < n; off += chunk) {
+        int cnt = n - off < chunk ? n - off : chunk;
+        GatherArgs ga{};
+        ga.rho = view_of(vol, vol.data);
+        ga.T = view_of(vol, light.data);
+        ga.table = table;
+        ga.points = pts + 3 * (size_t)off;
+        ga.omega = om + 3 * (size_t)off;
+        ga.count = cnt;
+        ga.lx = light.dir[0]; ga.ly = light.dir[1]; ga.lz = light.dir[2];
+        ga.g = m->g;
+        for (int c = 0; c < 3; ++c) ga.albedo[c] = m->albedo[c];
+        ga.se = W;
+        for (int k = 0; k < kLayers; ++k) {
+            ga.se_w1[k] = o.se_w1[k]; ga.se_b1[k] = o.se_b1[k];
+            ga.se_w2[k] = o.se_w2[k]; ga.se_b2[k] = o.se_b2[k];
+        }
+        ga.H_T = w.H_T; ga.H8_rho = w.H8_rho; ga.H8_f = w.H8_f; ga.f8_scale = w.fscale;
+        if (dbg && dbg->H_rho && dbg->H_f) {
+            ga.H_rho = dbg->H_rho + (size_t)off * kLayers * kLat;
+            ga.H_f = dbg->H_f + (size_t)off * kLayers * kLat;
+        }
+        ga.v = dbg ? w.v : nullptr; ga.w_se = w.w_se; ga.cfg = w.cfg;
+        if (mx) { ga.descs = mx->descs; ga.req_of_point = mx->req_of_point + off; }
+        {
+            ProfScope ps(ctx, "gather", s);
+            launch_gather(ga, s);
+        }
+        {
+            ProfScope ps(ctx, "cnn", s);
+            launch_cnn_f32(w.H_T, cnt, W, o, (dbg && dbg->X_T) ? dbg->X_T + (size_t)off * kLayers * kDT : nullptr,
+                           nullptr, s, 0, w.XT8);
+        }
+        for (int t = 0; t < 3; ++t) {
+            const int d = feat_dim(t);
+            const CUtensorMap &fmap = t == 0 ? w.map_rho : (t == 1 ? w.map_f : w.map_xt);
+            const int fstride = t == 2 ? kDT : kLatPad8;
+            for (int chain = 0; chain < 2; ++chain) {
+                int k0 = chain == 0 ? 0 : kDiffuse, k1 = chain == 0 ? kDiffuse : kLayers;
+                for (int k = k0; k < k1; ++k) {
+                    TcGemmArgs f1{};
+                    f1.M = cnt; f1.N = kWidth; f1.K = d; f1.n_mma = 208;
+                    f1.a_col0 = k * fstride; f1.epi = kEpiFc1; f1.err = ctx->d_err;
+                    f1.out_e = w.E; f1.out_s8 = w.S8; f1.ldo = kWidth;
+                    f1.bias = W + o.blk_b1[t][k];
+                    f1.row_scale = w.w_se + k * 3 + t; f1.row_scale_ld = kLayers * 3;
+                    if (t < 2) { f1.row_scale2 = w.fscale + k * 2 + t; f1.row_scale2_ld = kLayers * 2; }
+                    f1.col_scale = wt.sc_fc1[t][k];
+                    f1.cfg = w.cfg; f1.w_cfg = W + o.blk_w1[t][k] + d; f1.w_cfg_ld = d + kCfg;
+                    f1.cfg_per_row = 1;
+                    f1.h_prev = k == k0 ? nullptr : w.H; f1.ld_h = kWidth;
+                    gemm(f1, fmap, wt.map_fc1[t][k]);
+                    TcGemmArgs f2{};
+                    f2.M = cnt; f2.N = kWidth; f2.K = kWidth; f2.n_mma = 208;
+                    f2.epi = kEpiFc2; f2.err = ctx->d_err;
+                    f2.bias = W + o.blk_b2[t][k];
+                    f2.col_scale = wt.sc_fc2[t][k];
+                    f2.resid = w.E; f2.ld_resid = kWidth;
+                    if (k == k1 - 1) { f2.out_f8 = w.mrg8[t] + chain * kWidth; f2.ldo = 2 * kWidth; }
+                    else { f2.out_bf = w.H; f2.ldo = kWidth; }
+                    gemm(f2, w.map_s, wt.map_fc2[t][k]);
+                }
+            }
+            TcGemmArgs mg{};
+            mg.M = cnt; mg.N = kWidth; mg.K = 2 * kWidth; mg.n_mma = 208;
+            mg.epi = kEpiRelu; mg.err = ctx->d_err; mg.bias = W + o.mrg_b[t];
+            mg.col_scale = wt.sc_mrg[t];
+            mg.out_f8 = w.head8 + t * kWidth; mg.ldo = kHead8;
+            gemm(mg, w.map_mrg[t], wt.map_mrg[t]);
+        }
+        TcGemmArgs h1{};
+        h1.M = cnt; h1.N = kWidth; h1.K = 3 * kWidth; h1.n_mma = 208;
+        h1.epi = kEpiRelu; h1.err = ctx->d_err; h1.bias = W + o.head_b[0];
+        h1.col_scale = wt.sc_head[0];
+        h1.out_f8 = w.Z1; h1.ldo = kWidth8;
+        gemm(h1, w.map_head, wt.map_head[0]);
+        TcGemmArgs h2 = h1;
+        h2.K = kWidth; h2.bias = W + o.head_b[1]; h2.col_scale = wt.sc_head[1]; h2.out_f8 = w.Z2;
+        gemm(h2, w.map_z1, wt.map_head[1]);
+        TcGemmArgs h3{};
+        h3.M = cnt; h3.N = 3; h3.K = kWidth; h3.n_mma = 16;
+        h3.epi = kEpiDecode; h3.err = ctx->d_err; h3.bias = W + o.head_b[2];
+        h3.col_scale = wt.sc_head[2];
+        for (int c = 0; c < 3; ++c) h3.dec_scale[c] = dec_scale[c];
+        h3.out_f32 = rgb + 3 * (size_t)off;
+        h3.y_out = (dbg && dbg->y) ? dbg->y + 3 * (size_t)off : nullptr;
+        if (mx) h3.dec_rows = mx->dec_rows + 3 * (size_t)off;
+        gemm(h3, w.map_z2, wt.map_head[2]);
+        if (dbg) {
+            auto cp = [&](float *dst, const float *src, size_t per) -> cudaError_t {
+                if (!dst) return cudaSuccess;
+                return cudaMemcpyAsync(dst + per * off, src, per * cnt * sizeof(float),
+                                       cudaMemcpyDeviceToDevice, s);
+            };
+            NIS_CUDA(cp(dbg->H_T, w.H_T, (size_t)kLayers * kLat));
+            NIS_CUDA(cp(dbg->v, w.v, (size_t)kLayers * 8));
+            NIS_CUDA(cp(dbg->w_se, w.w_se, (size_t)kLayers * 3));
+        }
+        NIS_CUDA(cudaGetLastError());
+    }
+    return NIS_OK;
+}
+
 template <typename T>
 T *lookup(std::map<nis_handle, T> &m, nis_handle h) {
     auto it = m.find(h);
@@ -732,6 +958,19 @@ EncodeTiledFn encode_tiled() {
     return fn;
 }
 }  // namespace
+
+bool make_tmap_u8(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer,
+                  uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer) {
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn || (reinterpret_cast<uintptr_t>(base) & 15) || (row_bytes & 15)) return false;
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {row_bytes};
+    cuuint32_t box[2] = {box_inner, box_outer};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(base), dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 bool make_tmap_bf16(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer,
                     uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer) {
@@ -1008,8 +1247,9 @@ nis_status nis_load_weights(nis_ctx *ctx, const void *blob, size_t bytes, int pr
                             nis_stream stream, nis_weights *out) {
     if (!ctx) return NIS_ERR_INVALID_ARG;
     if (!blob || !out) return fail(ctx, NIS_ERR_INVALID_ARG, "NULL blob or out");
-    if (precision != NIS_PREC_F32 && precision != NIS_PREC_BF16 && precision != NIS_PREC_F32_SIMT)
-        return fail(ctx, NIS_ERR_UNIMPLEMENTED, "precision must be F32, BF16 or F32_SIMT");
+    if (precision != NIS_PREC_F32 && precision != NIS_PREC_BF16 && precision != NIS_PREC_F32_SIMT &&
+        precision != NIS_PREC_FP8)
+        return fail(ctx, NIS_ERR_INVALID_ARG, "precision must be F32, BF16, FP8 or F32_SIMT");
     if (bytes < 80) return fail(ctx, NIS_ERR_BAD_BLOB, "blob shorter than its header");
     uint32_t hd[16];
     uint64_t n_floats, checksum;
@@ -1040,10 +1280,13 @@ nis_status nis_load_weights(nis_ctx *ctx, const void *blob, size_t bytes, int pr
     cudaError_t e = cudaMemcpyAsync(w.f32, words, o.total * 4, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the caller may free the blob
     if (e != cudaSuccess) { dev_free(ctx, w.f32); return cuda_fail(ctx, e, "weights upload"); }
-    if (precision != NIS_PREC_F32_SIMT &&
-        (st = pack_weights_tc(ctx, w, precision == NIS_PREC_F32 ? 3 : 1, s))) {
+    if (precision == NIS_PREC_FP8) st = pack_weights_fp8(ctx, w, s);
+    else if (precision != NIS_PREC_F32_SIMT) st = pack_weights_tc(ctx, w, precision == NIS_PREC_F32 ? 3 : 1, s);
+    if (st) {
         dev_free(ctx, w.f32);
         dev_free(ctx, w.bf);
+        dev_free(ctx, w.f8);
+        dev_free(ctx, w.f8_scales);
         return st;
     }
     nis_handle h = ctx->next++;
@@ -1171,6 +1414,8 @@ nis_status nis_release(nis_ctx *ctx, nis_handle h) {
         cudaDeviceSynchronize();
         dev_free(ctx, w->f32);
         dev_free(ctx, w->bf);
+        dev_free(ctx, w->f8);
+        dev_free(ctx, w->f8_scales);
         ctx->weights.erase(h);
         return NIS_OK;
     }

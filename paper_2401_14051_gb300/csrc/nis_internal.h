@@ -163,6 +163,8 @@ struct GatherArgs {
     size_t se_w1[kLayers], se_b1[kLayers], se_w2[kLayers], se_b2[kLayers];
     float *H_rho, *H_T, *H_f;        // [count][12][225] (H_rho, H_f may be null when Hb_* set)
     __nv_bfloat16 *Hb_rho, *Hb_f;    // optional BF16 copies [count][12][kLatPad] (pad zeroed)
+    uint8_t *H8_rho, *H8_f;          // optional e4m3 copies [count][12][kLatPad8], each layer's
+    float *f8_scale;                 // row scaled by f8_scale[count][12][2] = max / 448
     int split; size_t part;          // BF16 copies as 3 split parts, part stride in elements
     float *v;                        // [count][12][8] (may be null)
     float *w_se;                     // [count][12][3]
@@ -171,7 +173,13 @@ struct GatherArgs {
 void launch_gather(const GatherArgs &a, cudaStream_t s);
 
 void launch_cnn_f32(const float *H_T, int count, const float *wbase, const WeightOffsets &o,
-                    float *X_T, __nv_bfloat16 *X_T_bf, cudaStream_t s, size_t split_part = 0);
+                    float *X_T, __nv_bfloat16 *X_T_bf, cudaStream_t s, size_t split_part = 0,
+                    uint8_t *X_T_f8 = nullptr);
+// FP8 weights: scale[n] = max_k |W[n][k]| / 448 (1 for empty rows), dst = e4m3(W / scale)
+void launch_pack_fp8(const float *src, int N, int K, int ld_src, uint8_t *dst, float *scale,
+                     int Np, int Kp, cudaStream_t s);
+bool make_tmap_u8(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer,
+                  uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer);
 // dst[n][k] = bf16(src[n * ld_src + k]) for n < N, k < K, zero elsewhere in [Np][Kp]
 void launch_pack_bf16(const float *src, int N, int K, int ld_src, __nv_bfloat16 *dst, int Np,
                       int Kp, cudaStream_t s, int split_part = -1);
@@ -245,7 +253,15 @@ struct TcGemmArgs {
     float *out_e_f32;                 // kEpiFc1: e in FP32 (else BF16 out_e)
     float *out_h_f32;                 // kEpiFc2: h in FP32 (else out_bf)
     const float *pre_f32; int ld_pre; // kEpiFc1 h_prev / kEpiFc2 e in FP32 (else BF16)
+    // FP8 mode: e4m3 operands (kind::f8f6f4, 128 elements per 128-byte K tile)
+    int fp8;
+    const float *col_scale;           // per-output-channel weight scales [N]
+    const float *row_scale2; int row_scale2_ld;  // kEpiFc1: per-row feature scales
+    uint8_t *out_f8, *out_s8;         // e4m3 outputs (FC-2 chain end / ReLU layers; FC-1 s)
 };
+constexpr int kLatPad8 = 240;        // FP8 feature row per layer, padded to 16 bytes
+constexpr int kWidth8 = 208;         // FP8 activation rows padded to 16 bytes
+constexpr int kHead8 = 608;
 void launch_fill_segments(const int *seg_start, const int *seg_desc, int nseg, int count,
                           int *req_of_point, float *dec_rows, const ReqDesc *descs,
                           cudaStream_t s);

@@ -32,9 +32,10 @@ def env():
     l = ctx.build_transmittance(v, cfg["light"], 0.6)
     w32 = ctx.load_weights(blob, nis.PREC_F32)
     wbf = ctx.load_weights(blob, nis.PREC_BF16)
+    wf8 = ctx.load_weights(blob, nis.PREC_FP8)
     ctx.sync(timeout_ms=60000)
     yield {"nis": nis, "ctx": ctx, "cfg": cfg, "vol": vol, "weights": weights, "v": v, "l": l,
-           "w32": w32, "wbf": wbf}
+           "w32": w32, "wbf": wbf, "wf8": wf8}
     ctx.close()
 
 
@@ -80,3 +81,25 @@ def test_bf16_render_frame(env):
     e = rel_err(a[hit], b[hit])
     print(f"\n[precision] BF16 frame vs FP32 frame: mean rel {e.mean():.3g}, max {e.max():.3g}")
     assert e.mean() <= 2e-2
+
+
+def test_fp8_against_fp64_oracle_and_fp32(env):
+    # FP8 e4m3 operands with per-output-channel weight scales and per-(point, layer) feature
+    # scales, FP32 accumulation.  The error is stated (printed) with a loose sanity bound:
+    # e4m3 keeps 3 mantissa bits, and the residual chains carry the rounding of ~60
+    # dependent layers.
+    ctx, cfg = env["ctx"], env["cfg"]
+    p, om = synth.shading_points(2048, 404, 0.05, 0.95)
+    dev = torch.device("cuda:0")
+    pt, ot = torch.from_numpy(p).to(dev), torch.from_numpy(om).to(dev)
+    rf8 = ctx.shade_points(env["v"], env["l"], env["wf8"], cfg["material"], pt, ot)
+    r32 = ctx.shade_points(env["v"], env["l"], env["w32"], cfg["material"], pt, ot)
+    ctx.sync(timeout_ms=60000)
+    levels, tl, table = O.prepare(env["vol"], cfg["light"], cfg["material"]["g"])
+    ref = O.shade_points(p, om, cfg["light"], levels, tl, table, env["weights"], cfg["material"])
+    e = rel_err(rf8.cpu().numpy(), ref)
+    e32 = rel_err(rf8.cpu().numpy(), r32.cpu().numpy())
+    print(f"\n[precision] FP8 vs FP64 oracle, 2048 points: mean rel {e.mean():.3g}, max {e.max():.3g}; "
+          f"vs FP32 path mean {e32.mean():.3g}")
+    assert np.isfinite(rf8.cpu().numpy()).all()
+    assert e.mean() <= 0.3
