@@ -389,7 +389,7 @@ def run_nis(args):
     total_bf = max_over_ranks(sum(times_bf), world)
     hitmask = hit.bool()
     a_bf, a_32 = img_bf[hitmask].double(), img[hitmask].double()
-    floor = 1e-2 * a_32.abs().amax(dim=0, keepdim=True)
+    floor = 5e-2 * a_32.abs().amax(dim=0, keepdim=True)
     e_bf = ((a_bf - a_32).abs() / torch.maximum(a_32.abs(), floor))
     peaks_bf = measured_peaks()
     mlp_ms, mlp_n = fam_bf["mlp"]

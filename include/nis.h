@@ -81,11 +81,18 @@ typedef struct nis_allocator {
 } nis_allocator;
 
 /* Material: HG asymmetry g in (-1, 1) (Eq. 5), RGB albedo in (0, 1] (Sec. III.C.2) and
- * RGB light intensity I (Eq. 16). */
+ * RGB light intensity I (Eq. 16).  g is the network's configuration input and, with
+ * n_lobes <= 1, the phase function of the phase features.  With n_lobes = 2 or 3 the phase
+ * features use the multi-lobe mixture sum_i lobe_w[i] HG(lobe_g[i]) (Eq. 6; weights >= 0
+ * summing to 1), while g stays the network input (for example the mixture's mean cosine).
+ * g = 0 with n_lobes <= 1 is the isotropic phase function (Eq. 7). */
 typedef struct nis_material {
     float g;
     float albedo[3];
     float intensity[3];
+    int n_lobes;
+    float lobe_g[3];
+    float lobe_w[3];
 } nis_material;
 
 /* Pinhole (PERSP, vertical field of view fov_y in radians) or orthographic (ORTHO, view

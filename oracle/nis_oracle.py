@@ -256,7 +256,18 @@ def hg(cos_theta, g: float):
     return (1.0 - g * g) / (4.0 * math.pi * (1.0 + g * g - 2.0 * g * cos_theta) ** 1.5)
 
 
-def cap_mean(cos_gamma, beta: float, g: float, n_rings: int = N_RINGS, n_az: int = N_AZ):
+def phase_fn(cos_theta, g):
+    """HG (Eq. 5) for a scalar g, or the multi-lobe mixture sum_i w_i HG(g_i) (Eq. 6) for a
+    list of (g_i, w_i) lobes whose weights sum to 1; g = 0 is the isotropic case (Eq. 7)."""
+    if isinstance(g, (list, tuple)):
+        out = 0.0
+        for gi, wi in g:
+            out = out + wi * hg(cos_theta, gi)
+        return out
+    return hg(cos_theta, g)
+
+
+def cap_mean(cos_gamma, beta: float, g, n_rings: int = N_RINGS, n_az: int = N_AZ):
     """Mean of HG(phi . b) over the cap of directions phi within beta of an axis a, where
     cos_gamma = a . b (Eq. 9 taken as a mean over the cap, R9).
 
@@ -274,7 +285,7 @@ def cap_mean(cos_gamma, beta: float, g: float, n_rings: int = N_RINGS, n_az: int
         ring = np.zeros(cos_gamma.shape)
         for j in range(n_az):
             phi = 2.0 * math.pi * (j + 0.5) / n_az
-            ring = ring + hg(mu * cos_gamma + s * sin_gamma * math.cos(phi), g)
+            ring = ring + phase_fn(mu * cos_gamma + s * sin_gamma * math.cos(phi), g)
         acc = acc + w * ring
         wsum += w * n_az
     return acc / wsum
@@ -297,7 +308,7 @@ def phase_set_offsets(phase_set: int) -> np.ndarray:
     return q
 
 
-def phase_feature(q: np.ndarray, alpha, g: float) -> np.ndarray:
+def phase_feature(q: np.ndarray, alpha, g) -> np.ndarray:
     """f = f*(n, against l) * f*(n, against omega) for template offsets q (Eq. 8-9, R9).
 
     In the light frame l = (0, 0, -1) and omega = (sin alpha, 0, -cos alpha); n is the
@@ -332,10 +343,11 @@ def alpha_nodes(n_alpha: int = N_ALPHA) -> np.ndarray:
     return np.arange(n_alpha) * (math.pi / (n_alpha - 1))
 
 
-def phase_table(g: float, n_alpha: int = N_ALPHA, columns=None) -> np.ndarray:
+def phase_table(g, n_alpha: int = N_ALPHA, columns=None) -> np.ndarray:
     """Precomputed phase features over all light-view angles (Sec. III.B.5, R10):
-    table[set, point, alpha node].  With ``columns`` only those alpha nodes are filled
-    (the rest NaN), for callers that look up a few angles."""
+    table[set, point, alpha node].  g is a scalar (HG) or a list of (g_i, w_i) lobes (MHG).
+    With ``columns`` only those alpha nodes are filled (the rest NaN), for callers that
+    look up a few angles."""
     a = alpha_nodes(n_alpha)
     cols = np.arange(n_alpha) if columns is None else np.unique(np.asarray(columns))
     out = np.full((N_PHASE_SETS, N_LAT, n_alpha), np.nan)
@@ -559,6 +571,12 @@ def decode(y: np.ndarray, albedo, intensity) -> np.ndarray:
 # ----------------------------------------------------------------------------------------
 # Whole path
 # ----------------------------------------------------------------------------------------
+def material_phase(mat: dict):
+    """The phase function of a material: its lobes (MHG) if it has two or more, else g."""
+    lobes = mat.get("lobes")
+    return [tuple(x) for x in lobes] if lobes and len(lobes) >= 2 else mat["g"]
+
+
 def prepare(rho0, light_dir, g, lam=LAMBDA, lazy_T=False):
     levels = build_pyramid(rho0)
     tl = (LazyTransmittance(levels, light_dir, lam) if lazy_T

@@ -3,26 +3,39 @@
 
 namespace nis {
 
-__device__ __forceinline__ float hg(float c, float g, float k_g) {
-    float base = 1.0f + g * g - 2.0f * g * c;         // >= (1 - |g|)^2 > 0
+// HG (Eq. 5) from omc = 1 - cos(theta) and opc = 1 + cos(theta), both computed without
+// cancellation: 1 + g^2 - 2 g cos = (1 - g)^2 + 2 g omc for g >= 0, (1 + g)^2 - 2 g opc for
+// g < 0, so sharp lobes keep full FP32 precision near their peak.
+__device__ __forceinline__ float hg2(float omc, float opc, float g, float k_g) {
+    float base = g >= 0.f ? (1.f - g) * (1.f - g) + 2.f * g * omc
+                          : (1.f + g) * (1.f + g) - 2.f * g * opc;
     return k_g / (base * sqrtf(base));
 }
 
-// Mean of HG(phi . b) over the cap of half-angle beta around an axis a with
-// a . b = cos_g: rings at psi_i = beta (i + 1/2) / kRings weighted by sin(psi_i), kAzim
-// azimuths measured from b (the cap stands for the solid angle the template point's
-// ball subtends from p, Eq. 9).
-__device__ float cap_mean(float cos_g, float beta, float g, float k_g,
-                          const float *__restrict__ az_cos) {
-    float sin_g = sqrtf(fmaxf(0.f, 1.f - cos_g * cos_g));
+// Mean of the phase function (Eq. 5/6) of the angle theta between b and the directions phi
+// of the cap of half-angle beta around an axis a, where gamma = angle(a, b): rings at
+// psi_i = beta (i + 1/2) / kRings weighted by sin(psi_i), kAzim azimuths phi_j measured
+// from b (the cap stands for the solid angle the template point's ball subtends from p,
+// Eq. 9).  1 -/+ cos(theta) come from the haversine form of the spherical law of cosines,
+//   1 - cos(theta) = 2 [sin^2((psi - gamma)/2) + sin(psi) sin(gamma) sin^2(phi/2)],
+//   1 + cos(theta) = 2 [sin^2((psi + gamma - pi)/2) + sin(psi) sin(gamma) cos^2(phi/2)].
+__device__ float cap_mean(float gamma, float beta, const PhaseSpec &ph, const float *k_g,
+                          const float *__restrict__ az_s2, const float *__restrict__ az_c2) {
+    const float sg = sinf(gamma);
     float acc = 0.f, wsum = 0.f;
     for (int i = 0; i < kRings; ++i) {
-        float psi = beta * ((i + 0.5f) / kRings);
-        float s, mu;
-        sincosf(psi, &s, &mu);
+        const float psi = beta * ((i + 0.5f) / kRings);
+        const float s = sinf(psi);
+        const float hm = sinf(0.5f * (psi - gamma)), hp = sinf(0.5f * (psi + gamma) - 1.5707963267949f);
+        const float hm2 = hm * hm, hp2 = hp * hp, ss = s * sg;
         float ring = 0.f;
-#pragma unroll 8
-        for (int j = 0; j < kAzim; ++j) ring += hg(mu * cos_g + s * sin_g * az_cos[j], g, k_g);
+        for (int j = 0; j < kAzim; ++j) {
+            const float omc = 2.f * (hm2 + ss * az_s2[j]);
+            const float opc = 2.f * (hp2 + ss * az_c2[j]);
+            float v = ph.w[0] * hg2(omc, opc, ph.g[0], k_g[0]);
+            for (int l = 1; l < ph.n; ++l) v += ph.w[l] * hg2(omc, opc, ph.g[l], k_g[l]);
+            ring += v;
+        }
         acc += s * ring;
         wsum += s * kAzim;
     }
@@ -33,10 +46,16 @@ __device__ float cap_mean(float cos_g, float beta, float g, float k_g,
 // Offsets q = (a, b, c) spacings from p in the light frame (e_z toward the light); the
 // highlight set j is shifted 9 (j + 1/2) spacings toward the light.  In that frame
 // l = (0, 0, -1) and omega = (sin alpha, 0, -cos alpha); the direction from the template
-// point toward p is n = -q/|q|, and f = capmean(n . l) * capmean(n . omega) (Eq. 8).
-__global__ void phase_table_kernel(float g, float *__restrict__ table) {
-    __shared__ float az_cos[kAzim];
-    if (threadIdx.x < kAzim) az_cos[threadIdx.x] = cospif((2.0f * threadIdx.x + 1.0f) / kAzim);
+// point toward p is n = -q/|q|, and f = capmean(n, l) * capmean(n, omega) (Eq. 8).  The
+// angles between n and l or omega come from atan2 of exact cross and dot products of q.
+__global__ void phase_table_kernel(const PhaseSpec ph, float *__restrict__ table) {
+    __shared__ float az_s2[kAzim], az_c2[kAzim];
+    if (threadIdx.x < kAzim) {
+        float h = sinpif((2.0f * threadIdx.x + 1.0f) / (2.0f * kAzim));   // sin(phi_j / 2)
+        float c = cospif((2.0f * threadIdx.x + 1.0f) / (2.0f * kAzim));
+        az_s2[threadIdx.x] = h * h;
+        az_c2[threadIdx.x] = c * c;
+    }
     __syncthreads();
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= kAlpha * kPhaseSets * kLat) return;
@@ -49,24 +68,29 @@ __global__ void phase_table_kernel(float g, float *__restrict__ table) {
         val = 1.0f / (16.0f * 3.14159265358979f * 3.14159265358979f);
     } else {
         float r = sqrtf(r2);
-        float nx = -qa / r, nz = -qc / r;
         float beta = atanf(0.5f / r);
         float alpha = (float)a * (3.14159265358979f / (kAlpha - 1));
         float sa, ca;
         sincosf(alpha, &sa, &ca);
-        float k_g = (1.0f - g * g) / (4.0f * 3.14159265358979f);
-        float f_l = cap_mean(-nz, beta, g, k_g, az_cos);
-        float f_w = cap_mean(nx * sa - nz * ca, beta, g, k_g, az_cos);
+        float k_g[3];
+        for (int i = 0; i < 3; ++i) k_g[i] = (1.0f - ph.g[i] * ph.g[i]) / (4.0f * 3.14159265358979f);
+        // n . l = qc / r, |n x l| = sqrt(qa^2 + qb^2) / r
+        float gam_l = atan2f(sqrtf(qa * qa + qb * qb), qc);
+        // n . omega = (qc cos a - qa sin a) / r, |n x omega|^2 = qb^2 + (qc sin a + qa cos a)^2
+        float cr = qc * sa + qa * ca;
+        float gam_w = atan2f(sqrtf(qb * qb + cr * cr), qc * ca - qa * sa);
+        float f_l = cap_mean(gam_l, beta, ph, k_g, az_s2, az_c2);
+        float f_w = cap_mean(gam_w, beta, ph, k_g, az_s2, az_c2);
         val = f_l * f_w;
     }
     table[idx] = val;
 }
 
-void launch_phase_table(float g, float *table, cudaStream_t s) {
+void launch_phase_table(const PhaseSpec &ph, float *table, cudaStream_t s) {
     const int threads = 256;
     int total = kAlpha * kPhaseSets * kLat;
     note_launch();
-    phase_table_kernel<<<(total + threads - 1) / threads, threads, 0, s>>>(g, table);
+    phase_table_kernel<<<(total + threads - 1) / threads, threads, 0, s>>>(ph, table);
 }
 
 }  // namespace nis

@@ -97,7 +97,7 @@ struct nis_ctx {
     std::map<nis_handle, Volume> vols;
     std::map<nis_handle, Light> lights;
     std::map<nis_handle, Weights> weights;
-    std::map<uint32_t, float *> phase;   // by the bit pattern of g
+    std::map<std::vector<uint32_t>, float *> phase;   // by the bit patterns of the phase spec
     Workspace ws;
     WorkspaceBf wsb, wsx;                 // BF16 and split (FP32-accurate) tensor paths
     WorkspaceF8 ws8;
@@ -238,9 +238,36 @@ nis_status build_pyramid_impl(nis_ctx *ctx, Volume &v, cudaStream_t s) {
     return NIS_OK;
 }
 
-nis_status ensure_phase(nis_ctx *ctx, float g, cudaStream_t s, float **out, bool rebuild = false) {
-    uint32_t key;
-    std::memcpy(&key, &g, 4);
+PhaseSpec phase_spec(const nis_material *m) {
+    PhaseSpec ph{};
+    if (m->n_lobes >= 2) {
+        ph.n = m->n_lobes;
+        for (int i = 0; i < 3; ++i) {
+            ph.g[i] = i < ph.n ? m->lobe_g[i] : 0.f;
+            ph.w[i] = i < ph.n ? m->lobe_w[i] : 0.f;
+        }
+    } else {
+        ph.n = 1;
+        ph.g[0] = m->g;
+        ph.w[0] = 1.f;
+    }
+    return ph;
+}
+
+PhaseSpec phase_spec_g(float g) {
+    nis_material m{};
+    m.g = g;
+    return phase_spec(&m);
+}
+
+nis_status ensure_phase(nis_ctx *ctx, const PhaseSpec &ph, cudaStream_t s, float **out,
+                        bool rebuild = false) {
+    std::vector<uint32_t> key(1 + 2 * ph.n);
+    key[0] = (uint32_t)ph.n;
+    for (int i = 0; i < ph.n; ++i) {
+        std::memcpy(&key[1 + 2 * i], &ph.g[i], 4);
+        std::memcpy(&key[2 + 2 * i], &ph.w[i], 4);
+    }
     auto it = ctx->phase.find(key);
     float *t;
     if (it != ctx->phase.end()) {
@@ -253,7 +280,7 @@ nis_status ensure_phase(nis_ctx *ctx, float g, cudaStream_t s, float **out, bool
     }
     {
         ProfScope ps(ctx, "phase", s);
-        launch_phase_table(g, t, s);
+        launch_phase_table(ph, t, s);
     }
     NIS_CUDA(cudaGetLastError());
     ctx->phase[key] = t;
@@ -327,6 +354,7 @@ nis_status ensure_workspace_tc(nis_ctx *ctx, WorkspaceBf &w, int parts, int cap,
 }
 
 int n_mma_of(int n) { return (n + 15) / 16 * 16; }
+
 int k_pad_of(int k) { return (k + 63) / 64 * 64; }
 
 // Tensor-core weight pack: per dense layer `parts` zero-padded [n_mma][Kp] BF16 matrices
@@ -452,6 +480,18 @@ nis_status ensure_workspace_fp8(nis_ctx *ctx, int cap, cudaStream_t s) {
 nis_status check_material(nis_ctx *ctx, const nis_material *m) {
     if (!m) return fail(ctx, NIS_ERR_INVALID_ARG, "material is NULL");
     if (!(m->g > -1.f && m->g < 1.f)) return fail(ctx, NIS_ERR_INVALID_ARG, "g must lie in (-1, 1)");
+    if (m->n_lobes < 0 || m->n_lobes > 3)
+        return fail(ctx, NIS_ERR_INVALID_ARG, "n_lobes must be 0..3");
+    if (m->n_lobes >= 2) {
+        float sum = 0.f;
+        for (int i = 0; i < m->n_lobes; ++i) {
+            if (!(m->lobe_g[i] > -1.f && m->lobe_g[i] < 1.f) || !(m->lobe_w[i] >= 0.f))
+                return fail(ctx, NIS_ERR_INVALID_ARG, "lobe g must lie in (-1, 1), weights >= 0");
+            sum += m->lobe_w[i];
+        }
+        if (std::fabs(sum - 1.f) > 1e-4f)
+            return fail(ctx, NIS_ERR_INVALID_ARG, "lobe weights must sum to 1");
+    }
     for (int c = 0; c < 3; ++c)
         if (!(m->albedo[c] > 0.f && m->albedo[c] <= 1.f) || !std::isfinite(m->intensity[c]))
             return fail(ctx, NIS_ERR_INVALID_ARG, "albedo must lie in (0, 1], intensity finite");
@@ -480,7 +520,7 @@ nis_status shade_impl(nis_ctx *ctx, const Volume &vol, const Light &light, const
                       const Mixed *mx = nullptr) {
     float *table = nullptr;
     nis_status st;
-    if (!mx && (st = ensure_phase(ctx, m->g, s, &table))) return st;
+    if (!mx && (st = ensure_phase(ctx, phase_spec(m), s, &table))) return st;
     if (n <= 0) return NIS_OK;
     if (wt.precision == NIS_PREC_FP8)
         return shade_impl_fp8(ctx, vol, light, wt, m, table, pts, om, n, rgb, dbg, s, mx);
@@ -1005,16 +1045,21 @@ nis_status hits_compact(nis_ctx *ctx, nis_volume vol, const nis_camera *cam, flo
 }
 
 nis_status resolve_built_inputs(nis_ctx *ctx, nis_volume vol, nis_light light, nis_weights w,
-                                float g, ResolvedInputs *out) {
+                                const nis_material *m, ResolvedInputs *out) {
     Volume *pv; Light *pl; Weights *pw;
     nis_status st = resolve(ctx, vol, light, w, &pv, &pl, &pw);
     if (st) return st;
-    uint32_t key;
-    std::memcpy(&key, &g, 4);
+    const PhaseSpec ph = phase_spec(m);
+    std::vector<uint32_t> key(1 + 2 * ph.n);
+    key[0] = (uint32_t)ph.n;
+    for (int i = 0; i < ph.n; ++i) {
+        std::memcpy(&key[1 + 2 * i], &ph.g[i], 4);
+        std::memcpy(&key[2 + 2 * i], &ph.w[i], 4);
+    }
     auto it = ctx->phase.find(key);
     if (it == ctx->phase.end())
-        return fail(ctx, NIS_ERR_NOT_READY, "phase table for this g not built "
-                                            "(call nis_build_phase_table first)");
+        return fail(ctx, NIS_ERR_NOT_READY, "phase table for this material not built "
+                                            "(shade once, or call nis_build_phase_table)");
     out->rho = view_of(*pv, pv->data);
     out->T = view_of(*pv, pl->data);
     out->table = it->second;
@@ -1494,7 +1539,7 @@ nis_status nis_build_phase_table(nis_ctx *ctx, float g, float *d_dst, nis_stream
     DeviceGuard gd(ctx->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     float *t;
-    nis_status st = ensure_phase(ctx, g, s, &t, /*rebuild=*/true);
+    nis_status st = ensure_phase(ctx, phase_spec_g(g), s, &t, /*rebuild=*/true);
     if (st) return st;
     if (d_dst)
         NIS_CUDA(cudaMemcpyAsync(d_dst, t, sizeof(float) * kAlpha * kPhaseSets * kLat,
@@ -1637,7 +1682,7 @@ nis_status nis_shade_segments(nis_ctx *ctx, nis_weights w, const nis_segment *se
         if (pl->vol != sg.vol) return fail(ctx, NIS_ERR_INVALID_ARG, "light belongs to another volume");
         if (!pv->pyramid) return fail(ctx, NIS_ERR_NOT_READY, "pyramid not built");
         float *table;
-        if ((st = ensure_phase(ctx, sg.material.g, s, &table))) return st;
+        if ((st = ensure_phase(ctx, phase_spec(&sg.material), s, &table))) return st;
         ReqDesc &d = descs[i];
         d.rho = view_of(*pv, pv->data);
         d.T = view_of(*pv, pl->data);

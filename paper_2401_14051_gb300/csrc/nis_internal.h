@@ -129,8 +129,13 @@ void launch_occupancy(const float *level, int n, unsigned char *occ, cudaStream_
 // transmittance of one level
 void launch_march(const float *level, const unsigned char *occ, int n, int m, float ux,
                   float uy, float uz, float lam, float *out, cudaStream_t s);
+// phase function of the phase features: one HG lobe, or a mixture of up to 3 (Eq. 6)
+struct PhaseSpec {
+    int n;
+    float g[3], w[3];
+};
 // phase table [kAlpha][kPhaseSets][kLat]
-void launch_phase_table(float g, float *table, cudaStream_t s);
+void launch_phase_table(const PhaseSpec &ph, float *table, cudaStream_t s);
 
 struct PyramidView {                 // device pointers of all levels of a pyramid
     const float *lv[kMaxLevels];
@@ -283,7 +288,7 @@ struct ResolvedInputs {
     int device;
 };
 nis_status resolve_built_inputs(nis_ctx *ctx, nis_volume vol, nis_light light, nis_weights w,
-                                float g, ResolvedInputs *out);
+                                const nis_material *m, ResolvedInputs *out);
 nis_status record_error(nis_ctx *ctx, nis_status s, const char *msg);
 int ctx_device(const nis_ctx *ctx);
 // First hits of a camera, compacted: points, omegas and pixel indices of the hits, and their

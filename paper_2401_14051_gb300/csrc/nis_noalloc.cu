@@ -72,7 +72,7 @@ extern "C" nis_status nis_shade_points_static(nis_ctx *ctx, nis_volume vol, nis_
         if (!(m->albedo[c] > 0.f && m->albedo[c] <= 1.f) || !isfinite(m->intensity[c]))
             return record_error(ctx, NIS_ERR_INVALID_ARG, "albedo must lie in (0, 1], intensity finite");
     ResolvedInputs in;
-    nis_status st = resolve_built_inputs(ctx, vol, light, w, m->g, &in);
+    nis_status st = resolve_built_inputs(ctx, vol, light, w, m, &in);
     if (st) return st;
     if (n == 0) return NIS_OK;
     if (in.device < 0 || in.device >= kMaxDevices)

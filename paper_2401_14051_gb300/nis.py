@@ -32,7 +32,8 @@ class NisError(RuntimeError):
 
 
 class Material(C.Structure):
-    _fields_ = [("g", C.c_float), ("albedo", C.c_float * 3), ("intensity", C.c_float * 3)]
+    _fields_ = [("g", C.c_float), ("albedo", C.c_float * 3), ("intensity", C.c_float * 3),
+                ("n_lobes", C.c_int), ("lobe_g", C.c_float * 3), ("lobe_w", C.c_float * 3)]
 
 
 class Camera(C.Structure):
@@ -161,8 +162,13 @@ def lib():
 
 
 def material(m: dict) -> Material:
+    """dict(g, albedo, intensity[, lobes=[(g_i, w_i), ...]]) -> nis_material."""
+    lobes = list(m.get("lobes") or [])
+    lg = [float(x[0]) for x in lobes] + [0.0] * (3 - len(lobes))
+    lw = [float(x[1]) for x in lobes] + [0.0] * (3 - len(lobes))
     return Material(float(m["g"]), (C.c_float * 3)(*m["albedo"]),
-                    (C.c_float * 3)(*m.get("intensity", (1.0, 1.0, 1.0))))
+                    (C.c_float * 3)(*m.get("intensity", (1.0, 1.0, 1.0))), len(lobes),
+                    (C.c_float * 3)(*lg[:3]), (C.c_float * 3)(*lw[:3]))
 
 
 def camera(cam: dict) -> Camera:

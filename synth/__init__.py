@@ -161,9 +161,14 @@ def unit_vector(seed: int) -> np.ndarray:
             return v / nv
 
 
-def material(g: float, albedo, intensity=(1.0, 1.0, 1.0)) -> dict:
-    return {"g": float(g), "albedo": [float(a) for a in albedo],
-            "intensity": [float(i) for i in intensity]}
+def material(g: float, albedo, intensity=(1.0, 1.0, 1.0), lobes=None) -> dict:
+    """Material: network asymmetry input g, RGB albedo and light intensity; optional MHG
+    lobes [(g_i, w_i), ...] (2 or 3, weights summing to 1) for the phase features."""
+    m = {"g": float(g), "albedo": [float(a) for a in albedo],
+         "intensity": [float(i) for i in intensity]}
+    if lobes:
+        m["lobes"] = [(float(a), float(b)) for a, b in lobes]
+    return m
 
 
 def ortho_camera(view_dir, width: int, height: int, target=(0.5, 0.5, 0.5),

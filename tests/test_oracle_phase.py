@@ -107,3 +107,26 @@ def test_table_nodes_and_interpolation():
         mid = 0.5 * (nodes[5] + nodes[6])
         np.testing.assert_allclose(O.table_lookup(tab, s, np.array([mid]))[0],
                                    0.5 * (tab[s, :, 5] + tab[s, :, 6]), rtol=1e-13)
+
+
+MHG = [[(0.85, 0.7), (-0.3, 0.3)], [(0.9, 0.5), (0.2, 0.3), (-0.5, 0.2)]]
+
+
+@pytest.mark.parametrize("lobes", MHG)
+def test_mhg_is_a_distribution_with_mixed_mean_cosine(lobes):
+    # Eq. 6: a convex mixture of HG lobes integrates to 1 and has mean cosine sum w_i g_i
+    val, _ = integrate.quad(lambda mu: float(O.phase_fn(mu, lobes)), -1, 1, epsabs=1e-13, limit=400)
+    assert 2 * math.pi * val == pytest.approx(1.0, abs=1e-9)
+    mc, _ = integrate.quad(lambda mu: mu * float(O.phase_fn(mu, lobes)), -1, 1, epsabs=1e-13, limit=400)
+    assert 2 * math.pi * mc == pytest.approx(sum(g * w for g, w in lobes), abs=1e-9)
+
+
+def test_mhg_reduces_to_hg_and_mixes_cap_means_linearly():
+    q = O.phase_set_offsets(1)[:30]
+    np.testing.assert_allclose(O.phase_feature(q, 0.8, [(0.6, 1.0)]), O.phase_feature(q, 0.8, 0.6),
+                               rtol=1e-14)
+    # the cap mean is linear in the phase function
+    lobes = MHG[0]
+    mix = O.cap_mean(0.4, 0.3, lobes)
+    parts = sum(w * O.cap_mean(0.4, 0.3, g) for g, w in lobes)
+    assert mix == pytest.approx(float(parts), rel=1e-13)
