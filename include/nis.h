@@ -337,6 +337,14 @@ nis_status nis_profile_read(nis_ctx *ctx, const char *family, double *total_ms,
 nis_status nis_debug_tc_gemm(nis_ctx *ctx, const void *d_a, int lda, const void *d_b, int ldb,
                              int m, int n, int k, float *d_c, nis_stream stream);
 
+/* The FP32 form of the same kernel, as the FP32 precision mode runs it: A (m x k, leading
+ * dimension lda) and B (n x k, leading dimension ldb) are FP32 device arrays; each is split
+ * on the device into three BF16 parts (x = x0 + x1 + x2) and the six products of parts whose
+ * indices sum to at most 2 are accumulated in FP32 tensor memory.  C FP32 (m x n, dense).
+ * n <= 208.  Temporary part buffers are allocated and freed stream-ordered on `stream`. */
+nis_status nis_debug_tc_gemm_f32(nis_ctx *ctx, const float *d_a, int lda, const float *d_b,
+                                 int ldb, int m, int n, int k, float *d_c, nis_stream stream);
+
 /* Number of kernels this library has launched in the process (all contexts). */
 uint64_t nis_kernel_launches(void);
 

@@ -1,14 +1,26 @@
 // Dense layers of the backbone (Sec. III.C.2, Fig. 6) on the 5th-generation tensor cores:
-// out = epilogue(A B^T) with A = activations [rows][K] and B = weights [N][K], both BF16
-// K-major, FP32 accumulation in tensor memory.
+// out = epilogue(A B^T) with A = activations [rows][K] and B = weights [N][K], both K-major,
+// FP32 accumulation in tensor memory.
 //
-// Persistent kernel, one CTA per SM, 6 warps:
-//   warp 0     TMA producer: 128x64 A box + N_mma x 64 B box per K step into a 4-stage ring
-//   warp 1     TMEM owner and MMA issuer: 128 x N_mma x 16 tcgen05.mma per 32-byte K slice,
+// Persistent kernel, one CTA per SM, 10 warps:
+//   warp 0     TMA producer: fills a ring of shared-memory stages, one K slab per stage
+//   warp 1     TMEM owner and MMA issuer: 128 x N_mma tcgen05.mma per 32-byte K slice,
 //              two accumulator buffers (columns 0 and 256) so the epilogue of one tile
 //              overlaps the MMAs of the next
-//   warps 2-5  epilogue: each thread owns one TMEM lane = one row of the tile; reads 32
-//              columns at a time and applies the layer's fused epilogue
+//   warps 2-9  epilogue: two warps per TMEM lane quarter, each thread one row of the tile;
+//              reads 32 columns at a time, applies the layer's fused epilogue and stages
+//              the 32 x 32 result in shared memory, from where one lane writes it with a
+//              TMA store (rows of 128 contiguous bytes instead of one row per lane)
+// Stage layouts:
+//   one part (BF16, FP8)   4 stages of {A 128 x 128 B, B N_mma x 128 B}, 128-byte swizzle
+//   three parts (FP32 as   2 stages of {A0 A1 A2 128 x 64 B, B0 B1 B2 N_mma x 64 B}, 64-byte
+//   three BF16 parts)      swizzle.  A first sweep over K brings each 32-wide slab with all
+//                          its parts and sums the five smaller products of the split; a
+//                          second sweep brings A0 B0 (three slabs per stage) and adds the
+//                          leading product, so the small terms are summed while the
+//                          accumulator is still small (all six products per slab in one
+//                          sweep measured about 7x the end-to-end error of this order).  A0
+//                          and B0 are the only operands fetched twice.
 // Every mbarrier wait is bounded: on a time-out the kernel records kErrTimeout in the
 // context's error word and winds down (draining its MMAs before releasing TMEM).
 #include <cuda_bf16.h>
@@ -23,11 +35,25 @@ namespace {
 constexpr int TM = 128, TK = 64, TN_MAX = 208, STAGES = 4;
 constexpr uint32_t A_STAGE = TM * TK * 2;                 // 16 KB
 constexpr uint32_t B_STAGE = TN_MAX * TK * 2;             // 26 KB (208 rows)
-constexpr uint32_t SMEM_TILES = STAGES * (A_STAGE + B_STAGE);
-constexpr uint32_t SMEM_CONST = 7 * TN_MAX * 4;          // per-column epilogue constants
-constexpr uint32_t SMEM_BYTES = SMEM_TILES + 256 + SMEM_CONST + 1024;  // + alignment slack
+// three-part stages: 64-byte rows (32 BF16 of K)
+constexpr int STAGES3 = 2;
+constexpr uint32_t A_PART3 = TM * 64;                     // 8 KB
+constexpr uint32_t B_PART3 = TN_MAX * 64;                 // 13 KB
+constexpr uint32_t STAGE3 = 3 * A_PART3 + 3 * B_PART3;    // 63 KB
 constexpr int kEpiWarps = 8;                              // two per TMEM lane quarter
 constexpr int kThreads = 64 + 32 * kEpiWarps;
+// per epilogue warp, a staging buffer for the TMA stores of one 32 x 32 chunk: FP32 o1
+// (4 KB) + three BF16 parts of o2 (6 KB) with the split, o1 + o2 as BF16 (2 + 2 KB) without
+constexpr uint32_t STG_SPLIT = 10240, STG_ONE = 4096;
+constexpr uint32_t RING_STG_SPLIT = STAGES3 * STAGE3 + kEpiWarps * STG_SPLIT;
+constexpr uint32_t RING_STG_ONE = STAGES * (A_STAGE + B_STAGE) + kEpiWarps * STG_ONE;
+constexpr uint32_t SMEM_TILES = RING_STG_SPLIT > RING_STG_ONE ? RING_STG_SPLIT : RING_STG_ONE;
+constexpr uint32_t SMEM_CONST = 7 * TN_MAX * 4;          // per-column epilogue constants
+constexpr uint32_t SMEM_BYTES = SMEM_TILES + 256 + SMEM_CONST + 1024;  // + alignment slack
+static_assert(SMEM_BYTES <= 227 * 1024, "shared memory of tc_gemm_kernel");
+static_assert((A_STAGE + B_STAGE) % 1024 == 0 && STAGE3 % 1024 == 0 && B_PART3 % 1024 == 0 &&
+                  STG_SPLIT % 1024 == 0 && STG_ONE % 1024 == 0,
+              "stages, parts and staging buffers must keep the 1024-byte swizzle-atom alignment");
 
 __device__ __forceinline__ void record_timeout(unsigned *err, int *abort_flag) {
     *abort_flag = 1;
@@ -35,8 +61,8 @@ __device__ __forceinline__ void record_timeout(unsigned *err, int *abort_flag) {
 }
 
 // Six products of the three-way split, small to large: (A part, B part).
-__constant__ int kPassA[6] = {2, 1, 0, 1, 0, 0};
-__constant__ int kPassB[6] = {0, 1, 2, 0, 1, 0};
+__device__ constexpr int kPassA[6] = {2, 1, 0, 1, 0, 0};
+__device__ constexpr int kPassB[6] = {0, 1, 2, 0, 1, 0};
 
 __device__ __forceinline__ void store_bf16x8(__nv_bfloat16 *dst, const float *v) {
     __align__(16) __nv_bfloat162 p[4];
@@ -72,6 +98,41 @@ __device__ __forceinline__ void store_f32x8(float *dst, const float *v) {
     reinterpret_cast<float4 *>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
 }
 
+// Staging of one 32 x 32 chunk for a TMA store, thread `lane` holding row `lane`, in the
+// layouts the tensor maps' swizzle modes read: FP32 rows of 128 bytes with 128-byte swizzle
+// (16-byte unit j of row r at unit j ^ (r mod 8)); BF16 rows of 64 bytes with 64-byte swizzle
+// (unit j at j ^ ((r / 2) mod 4)), one 2 KB block per part of a split.  Both write eight
+// different 16-byte bank groups per eight lanes, so the stores are free of bank conflicts.
+__device__ __forceinline__ void stage_f32(uint8_t *buf, int lane, const float (&v)[32]) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        *reinterpret_cast<float4 *>(buf + lane * 128 + ((j ^ (lane & 7)) << 4)) =
+            make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+}
+__device__ __forceinline__ void stage_bf16(uint8_t *buf, int lane, const float (&v)[32], int parts) {
+    float r[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) r[i] = v[i];
+    for (int q = 0; q < parts; ++q) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            __align__(16) __nv_bfloat162 p[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) p[i] = __floats2bfloat162_rn(r[8 * j + 2 * i], r[8 * j + 2 * i + 1]);
+            *reinterpret_cast<uint4 *>(buf + q * 2048 + lane * 64 + ((j ^ ((lane >> 1) & 3)) << 4)) =
+                *reinterpret_cast<const uint4 *>(p);
+        }
+        if (q + 1 < parts) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) r[i] = r[i] - __bfloat162float(__float2bfloat16_rn(r[i]));
+        }
+    }
+}
+__device__ __forceinline__ void stage_out(uint8_t *buf, int lane, const float (&v)[32], int kind, int parts) {
+    if (kind == kOutF32) stage_f32(buf, lane, v);
+    else stage_bf16(buf, lane, v, parts);
+}
+
 __device__ __forceinline__ void load_bf16x8(const __nv_bfloat16 *src, float *v) {
     uint4 raw = *reinterpret_cast<const uint4 *>(src);
     const __nv_bfloat162 *p = reinterpret_cast<const __nv_bfloat162 *>(&raw);
@@ -87,18 +148,24 @@ __device__ __forceinline__ void load_bf16x8(const __nv_bfloat16 *src, float *v) 
 // s_bias / s_wa: per-column constants in shared memory (bias with the material's part of the
 // configuration vector folded in; weight of alpha).  sc, alpha: this row's SE weight and
 // view angle.  pre: the residual / running-state values of this chunk, already loaded.
+// With TMA outputs (a.o1_kind != kOutDirect) every lane stages its row into `stg` (o1 at 0,
+// o2 at o2_off) and the caller issues the stores; otherwise live rows store directly.
 __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs &a, int r, int c0, float (&v)[32],
                                                const float *s_bias, const float *s_wa, float sc,
                                                float alpha, const float (&pre)[32],
                                                const float *s_wm, const float (&rc)[4],
-                                               const float *s_ws) {
+                                               const float *s_ws, uint8_t *stg, uint32_t o2_off,
+                                               int lane, bool live) {
     const int N = a.N;
+    const bool staged = a.o1_kind != kOutDirect;
     if (a.col_scale) {                                   // FP8: per-output-channel weight scale
 #pragma unroll
         for (int j = 0; j < 32; ++j) v[j] *= s_ws[c0 + j];
     }
     switch (a.epi) {
     case kEpiPlain: {
+        if (staged) { stage_out(stg, lane, v, a.o1_kind, a.o1_parts); break; }
+        if (!live) break;
         float *o = a.out_f32 + (size_t)r * a.ldo;
 #pragma unroll
         for (int j = 0; j < 32; ++j)
@@ -119,6 +186,12 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs &a, int r, int c
             v[j] = e;
             sv[j] = (a.h_prev || a.pre_f32) ? pre[j] + e : e;
         }
+        if (staged) {
+            stage_out(stg, lane, v, a.o1_kind, a.o1_parts);
+            stage_out(stg + o2_off, lane, sv, a.o2_kind, a.o2_parts);
+            break;
+        }
+        if (!live) break;
 #pragma unroll
         for (int g = 0; g < 4; ++g)
             if (c0 + 8 * g < N) {
@@ -133,6 +206,8 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs &a, int r, int c
         // h = ReLU(acc + b) + e
 #pragma unroll
         for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + s_bias[c0 + j], 0.f) + pre[j];
+        if (staged) { stage_out(stg, lane, v, a.o1_kind, a.o1_parts); break; }
+        if (!live) break;
 #pragma unroll
         for (int g = 0; g < 4; ++g)
             if (c0 + 8 * g < N) {
@@ -145,6 +220,8 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs &a, int r, int c
     case kEpiRelu: {
 #pragma unroll
         for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + s_bias[c0 + j], 0.f);
+        if (staged) { stage_out(stg, lane, v, a.o1_kind, a.o1_parts); break; }
+        if (!live) break;
 #pragma unroll
         for (int g = 0; g < 4; ++g)
             if (c0 + 8 * g < N) {
@@ -154,7 +231,7 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs &a, int r, int c
         break;
     }
     default: {  // kEpiDecode: rgb = I albedo^4 expm1(acc + b), N = 3
-        if (c0 == 0) {
+        if (c0 == 0 && live) {
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
                 float y = v[j] + s_bias[j];
@@ -197,11 +274,16 @@ __device__ __forceinline__ void load_pre(const TcGemmArgs &a, int r, int c0, flo
 
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+                   const __grid_constant__ CUtensorMap map_o1, const __grid_constant__ CUtensorMap map_o2,
                    const __grid_constant__ TcGemmArgs a) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t *sA = smem;
-    uint8_t *sB = smem + STAGES * A_STAGE;
+    const bool split3 = a.n_pass > 1;              // three-part stages (FP32 split)
+    const int n_stages = split3 ? STAGES3 : STAGES;
+    const uint32_t stage_bytes = split3 ? STAGE3 : A_STAGE + B_STAGE;
+    const uint32_t b_off = split3 ? 3 * A_PART3 : A_STAGE;   // B's offset inside a stage
+    uint8_t *staging = smem + n_stages * stage_bytes;          // epilogue warps' TMA staging
+    const uint32_t stg_stride = split3 ? STG_SPLIT : STG_ONE;
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + SMEM_TILES);
     uint64_t *empty = full + STAGES;
     uint64_t *acc_full = empty + STAGES;
@@ -217,19 +299,28 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_tiles = (a.M + TM - 1) / TM;
     const int n_mma = a.n_mma;
-    const uint32_t b_bytes = (uint32_t)n_mma * TK * 2;
+    const uint32_t slab_tx = A_PART3 + (uint32_t)n_mma * 64;        // one part of A and of B
+    const uint32_t stage_tx = split3 ? 3 * slab_tx : A_STAGE + (uint32_t)n_mma * TK * 2;
+    // stages per tile: one per K slab; the split adds a second sweep of A0 B0, three slabs
+    // per stage
+    const int n_sweep1 = a.k_tiles;
+    const int n_steps = split3 ? n_sweep1 + (a.k_tiles + 2) / 3 : a.k_tiles;
     const uint32_t idesc = a.fp8 ? tc::idesc_e4m3_f32(TM, n_mma) : tc::idesc_bf16_f32(TM, n_mma);
-    const int tk = a.fp8 ? 128 : TK;               // K elements per 128-byte stage row
-    const int kslice = a.fp8 ? 32 : 16;            // K elements per MMA (32 bytes)
+    const int tk = split3 ? 32 : (a.fp8 ? 128 : TK);   // K elements per stage row
+    const int kslice = a.fp8 ? 32 : 16;                // K elements per MMA (32 bytes)
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
+        for (int s = 0; s < n_stages; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
         for (int b = 0; b < 2; ++b) { tc::mbar_init(&acc_full[b], 1); tc::mbar_init(&acc_empty[b], kEpiWarps); }
         tc::mbar_init(drain, 1);
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
     if (warp == 0 && lane == 0) { tc::prefetch_tmap(&map_a); tc::prefetch_tmap(&map_b); }
+    if (warp == 2 && lane == 0 && a.o1_kind != kOutDirect) {
+        tc::prefetch_tmap(&map_o1);
+        if (a.o2_kind != kOutDirect) tc::prefetch_tmap(&map_o2);
+    }
     // per-column epilogue constants (columns >= N read as zero)
     for (int c = threadIdx.x; c < TN_MAX; c += blockDim.x) {
         float b = 0.f, wa = 0.f, wm[4] = {0.f, 0.f, 0.f, 0.f};
@@ -263,25 +354,41 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 0) {
         if (lane == 0) {
             int it = 0;
-            const int npass = a.n_pass > 1 ? a.n_pass : 1;
-            const int steps = npass * a.k_tiles;
             for (int tile = blockIdx.x; tile < n_tiles && !*(volatile int *)abort_flag; tile += gridDim.x) {
-                for (int st = 0; st < steps; ++st, ++it) {
-                    const int pass = st / a.k_tiles, kt = st % a.k_tiles;
-                    const int pa = npass > 1 ? kPassA[pass] : 0, pb = npass > 1 ? kPassB[pass] : 0;
-                    const int s = it % STAGES;
-                    const uint32_t ph = (it / STAGES) & 1;
+                for (int step = 0; step < n_steps; ++step, ++it) {
+                    const int s = it % n_stages;
+                    const uint32_t ph = (it / n_stages) & 1;
                     if (!tc::mbar_wait(&empty[s], ph ^ 1)) { record_timeout(a.err, abort_flag); break; }
-                    tc::mbar_expect_tx(&full[s], A_STAGE + b_bytes);
-                    tc::tma_load_2d(sA + s * A_STAGE, &map_a, a.a_col0 + kt * tk,
-                                    pa * a.a_part_rows + tile * TM, &full[s]);
-                    tc::tma_load_2d(sB + s * B_STAGE, &map_b, kt * tk, pb * a.b_part_rows, &full[s]);
+                    uint8_t *st = smem + s * stage_bytes;
+                    if (!split3) {
+                        tc::mbar_expect_tx(&full[s], stage_tx);
+                        tc::tma_load_2d(st, &map_a, a.a_col0 + step * tk, tile * TM, &full[s]);
+                        tc::tma_load_2d(st + b_off, &map_b, step * tk, 0, &full[s]);
+                    } else if (step < n_sweep1) {              // slab `step`, all three parts
+                        tc::mbar_expect_tx(&full[s], stage_tx);
+                        for (int p = 0; p < 3; ++p) {
+                            tc::tma_load_2d(st + p * A_PART3, &map_a, a.a_col0 + step * tk,
+                                            p * a.a_part_rows + tile * TM, &full[s]);
+                            tc::tma_load_2d(st + b_off + p * B_PART3, &map_b, step * tk,
+                                            p * a.b_part_rows, &full[s]);
+                        }
+                    } else {                                   // up to three slabs of A0 B0
+                        const int j0 = 3 * (step - n_sweep1);
+                        const int nb = a.k_tiles - j0 < 3 ? a.k_tiles - j0 : 3;
+                        tc::mbar_expect_tx(&full[s], nb * slab_tx);
+                        for (int j = 0; j < nb; ++j) {
+                            tc::tma_load_2d(st + j * A_PART3, &map_a, a.a_col0 + (j0 + j) * tk,
+                                            tile * TM, &full[s]);
+                            tc::tma_load_2d(st + b_off + j * B_PART3, &map_b, (j0 + j) * tk, 0,
+                                            &full[s]);
+                        }
+                    }
                 }
             }
             // wait until every stage issued has landed (the consumer may have stopped early)
-            for (int j = 0; j < STAGES && j < it; ++j) {
+            for (int j = 0; j < n_stages && j < it; ++j) {
                 const int i2 = it - 1 - j;
-                tc::mbar_wait(&full[i2 % STAGES], (i2 / STAGES) & 1, 1u << 16);
+                tc::mbar_wait(&full[i2 % n_stages], (i2 / n_stages) & 1, 1u << 16);
             }
         }
     } else if (warp == 1) {
@@ -294,21 +401,46 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc::fence_after_sync();
                 const uint32_t d_tmem = tmem_base + buf * 256;
                 bool ok = true;
-                const int steps = (a.n_pass > 1 ? a.n_pass : 1) * a.k_tiles;
-                for (int st = 0; st < steps; ++st, ++it) {
-                    const int kt = st % a.k_tiles;
-                    const int s = it % STAGES;
-                    if (!tc::mbar_wait(&full[s], (it / STAGES) & 1)) { ok = false; break; }
-                    tc::fence_after_sync();
-                    const uint32_t a_addr = tc::smem_u32(sA + s * A_STAGE);
-                    const uint32_t b_addr = tc::smem_u32(sB + s * B_STAGE);
+                auto slices = [&](int kt) {                    // MMAs of K slab kt
                     const int k_left = a.K - kt * tk;
-                    const int n_sl = k_left >= tk ? 4 : (k_left + kslice - 1) / kslice;
-                    for (int k = 0; k < n_sl; ++k) {
-                        const uint64_t ad = tc::smem_desc_sw128(a_addr + k * 32);
-                        const uint64_t bd = tc::smem_desc_sw128(b_addr + k * 32);
-                        if (a.fp8) tc::mma_f8(d_tmem, ad, bd, idesc, (st | k) != 0);
-                        else tc::mma_f16(d_tmem, ad, bd, idesc, (st | k) != 0);
+                    return k_left >= tk ? tk / kslice : (k_left + kslice - 1) / kslice;
+                };
+                for (int step = 0; step < n_steps; ++step, ++it) {
+                    const int s = it % n_stages;
+                    if (!tc::mbar_wait(&full[s], (it / n_stages) & 1)) { ok = false; break; }
+                    tc::fence_after_sync();
+                    const uint32_t a_addr = tc::smem_u32(smem + s * stage_bytes);
+                    const uint32_t b_addr = a_addr + b_off;
+                    if (!split3) {
+                        const int n_sl = slices(step);
+                        for (int k = 0; k < n_sl; ++k) {
+                            const uint64_t ad = tc::smem_desc_sw128(a_addr + k * 32);
+                            const uint64_t bd = tc::smem_desc_sw128(b_addr + k * 32);
+                            if (a.fp8) tc::mma_f8(d_tmem, ad, bd, idesc, (step | k) != 0);
+                            else tc::mma_f16(d_tmem, ad, bd, idesc, (step | k) != 0);
+                        }
+                    } else if (step < n_sweep1) {
+                        // first sweep: the five products below the leading one, smallest
+                        // first, so that the accumulator holds only small terms while they
+                        // are summed
+                        const int n_sl = slices(step);
+                        for (int p = 0; p < 5; ++p) {
+                            const uint32_t pa = a_addr + kPassA[p] * A_PART3;
+                            const uint32_t pb = b_addr + kPassB[p] * B_PART3;
+                            for (int k = 0; k < n_sl; ++k)
+                                tc::mma_f16(d_tmem, tc::smem_desc_sw64(pa + k * 32),
+                                            tc::smem_desc_sw64(pb + k * 32), idesc, (step | p | k) != 0);
+                        }
+                    } else {
+                        // second sweep: the leading product A0 B0 on top
+                        const int j0 = 3 * (step - n_sweep1);
+                        const int nb = a.k_tiles - j0 < 3 ? a.k_tiles - j0 : 3;
+                        for (int j = 0; j < nb; ++j) {
+                            const int n_sl = slices(j0 + j);
+                            for (int k = 0; k < n_sl; ++k)
+                                tc::mma_f16(d_tmem, tc::smem_desc_sw64(a_addr + j * A_PART3 + k * 32),
+                                            tc::smem_desc_sw64(b_addr + j * B_PART3 + k * 32), idesc, 1);
+                        }
                     }
                     tc::mma_commit(&empty[s]);
                 }
@@ -322,6 +454,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else {
         const int q = warp & 3;                        // TMEM lane quarter of this warp
         const int half = (warp - 2) >> 2;              // which 32-column chunks this warp takes
+        const bool staged = a.o1_kind != kOutDirect;
+        uint8_t *stg = staging + (warp - 2) * stg_stride;
+        const uint32_t o2_off = a.o1_kind == kOutF32 ? 4096u : 2048u * (uint32_t)a.o1_parts;
         int t = 0;
         for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++t) {
             const int buf = t & 1;
@@ -336,6 +471,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int q = 0; q < 4; ++q) rc[q] = a.cfg[(size_t)r * kCfg + q];
             }
             float pre[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) pre[i] = 0.f;
             if (live && half * 32 < a.N) load_pre(a, r, half * 32, pre);
             bool ok = tc::mbar_wait(&acc_full[buf], (t >> 1) & 1);
             if (!ok || *(volatile int *)abort_flag) {
@@ -353,12 +490,28 @@ __global__ void __launch_bounds__(kThreads, 1)
                 // next chunk's residual loads overlap this chunk's TMEM load and math
                 if (live && c0 + 64 < a.N) load_pre(a, r, c0 + 64, pre);
                 tc::tmem_ld_wait();
-                if (live) epilogue_chunk(a, r, c0, v, s_bias, s_wa, sc, alpha, cur, s_wm, rc, s_ws);
+                if (staged) {                          // the previous chunk's stores have read stg
+                    if (lane == 0) tc::bulk_wait_read();
+                    __syncwarp();
+                }
+                epilogue_chunk(a, r, c0, v, s_bias, s_wa, sc, alpha, cur, s_wm, rc, s_ws, stg, o2_off,
+                               lane, live);
+                if (staged) {
+                    tc::fence_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
+                        const int row0 = tile * TM + q * 32;
+                        tc::tma_store_3d(&map_o1, stg, c0, row0, 0);
+                        if (a.o2_kind != kOutDirect) tc::tma_store_3d(&map_o2, stg + o2_off, c0, row0, 0);
+                        tc::bulk_commit();
+                    }
+                }
             }
             tc::fence_before_sync();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&acc_empty[buf]);
         }
+        if (staged && lane == 0) tc::bulk_wait();     // every store of this warp has landed
     }
     __syncthreads();
     if (warp == 1) {
@@ -412,7 +565,8 @@ void launch_pack_fp8(const float *src, int N, int K, int ld_src, uint8_t *dst, f
 }
 
 void launch_tc_gemm(const TcGemmArgs &a, const CUtensorMap &map_a, const CUtensorMap &map_b,
-                    int num_sms, cudaStream_t s) {
+                    int num_sms, cudaStream_t s, const CUtensorMap *map_o1, const CUtensorMap *map_o2) {
+    static const CUtensorMap unused{};            // stands in for outputs written directly
     if (a.M <= 0) return;
     static bool attr_set = false;
     if (!attr_set) {
@@ -422,7 +576,8 @@ void launch_tc_gemm(const TcGemmArgs &a, const CUtensorMap &map_a, const CUtenso
     int tiles = (a.M + TM - 1) / TM;
     int grid = tiles < num_sms ? tiles : num_sms;
     note_launch();
-    tc_gemm_kernel<<<grid, kThreads, SMEM_BYTES, s>>>(map_a, map_b, a);
+    tc_gemm_kernel<<<grid, kThreads, SMEM_BYTES, s>>>(map_a, map_b, map_o1 ? *map_o1 : unused,
+                                                      map_o2 ? *map_o2 : unused, a);
 }
 
 }  // namespace nis

@@ -69,6 +69,9 @@ struct WorkspaceBf {                  // scratch of the tensor-core paths, grow-
                   *Z1 = nullptr, *Z2 = nullptr;
     float *H_T = nullptr, *w_se = nullptr, *cfg = nullptr, *v = nullptr;
     CUtensorMap map_rho, map_f, map_xt, map_s, map_mrg[3], map_head, map_z1, map_z2;
+    // epilogue output maps (TMA stores): e, h (FP32 with the split), s, the chain ends
+    // (per type and chain), the merges (per type) and the head activations
+    CUtensorMap out_e, out_h, out_s, out_mrg[3][2], out_head[3], out_z1, out_z2;
 };
 
 struct Workspace {                    // scratch of nis_shade_points, grow-only
@@ -339,15 +342,31 @@ nis_status ensure_workspace_tc(nis_ctx *ctx, WorkspaceBf &w, int parts, int cap,
     if ((st = dev_alloc_t(ctx, n * kCfg, &w.cfg, s))) return st;
     if ((st = dev_alloc_t(ctx, n * kLayers * 8, &w.v, s))) return st;
     const uint64_t rows = P * n;      // the parts of a tensor stack along the row dimension
-    bool ok = make_tmap_bf16(&w.map_rho, w.Hb_rho, kLayers * kLatPad, rows, kLayers * kLatPad * 2, 64, 128) &&
-              make_tmap_bf16(&w.map_f, w.Hb_f, kLayers * kLatPad, rows, kLayers * kLatPad * 2, 64, 128) &&
-              make_tmap_bf16(&w.map_xt, w.XTb, kLayers * kDT, rows, kLayers * kDT * 2, 64, 128) &&
-              make_tmap_bf16(&w.map_s, w.S, kWidth, rows, kWidth * 2, 64, 128) &&
-              make_tmap_bf16(&w.map_head, w.head_in, 3 * kWidth, rows, 3 * kWidth * 2, 64, 128) &&
-              make_tmap_bf16(&w.map_z1, w.Z1, kWidth, rows, kWidth * 2, 64, 128) &&
-              make_tmap_bf16(&w.map_z2, w.Z2, kWidth, rows, kWidth * 2, 64, 128);
+    const uint32_t bx = tc_box_k(parts);
+    bool ok = make_tmap_bf16(&w.map_rho, w.Hb_rho, kLayers * kLatPad, rows, kLayers * kLatPad * 2, bx, 128) &&
+              make_tmap_bf16(&w.map_f, w.Hb_f, kLayers * kLatPad, rows, kLayers * kLatPad * 2, bx, 128) &&
+              make_tmap_bf16(&w.map_xt, w.XTb, kLayers * kDT, rows, kLayers * kDT * 2, bx, 128) &&
+              make_tmap_bf16(&w.map_s, w.S, kWidth, rows, kWidth * 2, bx, 128) &&
+              make_tmap_bf16(&w.map_head, w.head_in, 3 * kWidth, rows, 3 * kWidth * 2, bx, 128) &&
+              make_tmap_bf16(&w.map_z1, w.Z1, kWidth, rows, kWidth * 2, bx, 128) &&
+              make_tmap_bf16(&w.map_z2, w.Z2, kWidth, rows, kWidth * 2, bx, 128);
     for (int t = 0; t < 3; ++t)
-        ok = ok && make_tmap_bf16(&w.map_mrg[t], w.mrg_in[t], 2 * kWidth, rows, 2 * kWidth * 2, 64, 128);
+        ok = ok && make_tmap_bf16(&w.map_mrg[t], w.mrg_in[t], 2 * kWidth, rows, 2 * kWidth * 2, bx, 128);
+    // outputs: [parts][cap][kWidth] views; FP32 e and h with the split, BF16 otherwise
+    const bool f32 = parts > 1;
+    const uint64_t eb = f32 ? 4 : 2;
+    ok = ok && make_tmap_out(&w.out_e, f32 ? (void *)w.E32 : (void *)w.E, f32, kWidth, n, 1, kWidth * eb, n * kWidth * eb) &&
+         make_tmap_out(&w.out_h, f32 ? (void *)w.H32 : (void *)w.H, f32, kWidth, n, 1, kWidth * eb, n * kWidth * eb) &&
+         make_tmap_out(&w.out_s, w.S, false, kWidth, n, parts, kWidth * 2, n * kWidth * 2) &&
+         make_tmap_out(&w.out_z1, w.Z1, false, kWidth, n, parts, kWidth * 2, n * kWidth * 2) &&
+         make_tmap_out(&w.out_z2, w.Z2, false, kWidth, n, parts, kWidth * 2, n * kWidth * 2);
+    for (int t = 0; t < 3; ++t) {
+        for (int c = 0; c < 2; ++c)
+            ok = ok && make_tmap_out(&w.out_mrg[t][c], w.mrg_in[t] + c * kWidth, false, kWidth, n, parts,
+                                     2 * kWidth * 2, n * 2 * kWidth * 2);
+        ok = ok && make_tmap_out(&w.out_head[t], w.head_in + t * kWidth, false, kWidth, n, parts,
+                                 3 * kWidth * 2, n * 3 * kWidth * 2);
+    }
     if (!ok) return fail(ctx, NIS_ERR_CUDA, "cuTensorMapEncodeTiled failed for the tensor-core workspace");
     w.cap = cap;
     return NIS_OK;
@@ -386,7 +405,7 @@ nis_status pack_weights_tc(nis_ctx *ctx, Weights &w, int parts, cudaStream_t s) 
             launch_pack_bf16(m.src, m.N, m.K, m.ld, dst + (size_t)q * np * kp, np, kp, s,
                              parts > 1 ? q : -1);
         }
-        if (!make_tmap_bf16(m.map, dst, (uint64_t)kp, (uint64_t)parts * np, (uint64_t)kp * 2, 64,
+        if (!make_tmap_bf16(m.map, dst, (uint64_t)kp, (uint64_t)parts * np, (uint64_t)kp * 2, tc_box_k(parts),
                             (uint32_t)np))
             return fail(ctx, NIS_ERR_CUDA, "cuTensorMapEncodeTiled failed for a weight matrix");
         off += (size_t)parts * np * kp;
@@ -657,14 +676,18 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
     const float *W = wt.f32;
     float dec_scale[3];
     for (int c = 0; c < 3; ++c) dec_scale[c] = m->intensity[c] * powf(m->albedo[c], 4.0f);
-    auto gemm = [&](TcGemmArgs a, const CUtensorMap &ma, const CUtensorMap &mb) {
+    // o1 / o2: the epilogue's output maps (TMA stores); null writes through the pointers
+    auto gemm = [&](TcGemmArgs a, const CUtensorMap &ma, const CUtensorMap &mb,
+                    const CUtensorMap *o1 = nullptr, const CUtensorMap *o2 = nullptr) {
         a.n_pass = split ? 6 : 1;
+        a.k_tiles = (a.K + (int)tc_box_k(P) - 1) / (int)tc_box_k(P);
         a.a_part_rows = (int)cap;
         a.b_part_rows = a.n_mma;
         a.out_split = split ? 1 : 0;
         ProfScope ps(ctx, "mlp", s);
-        launch_tc_gemm(a, ma, mb, ctx->num_sms, s);
+        launch_tc_gemm(a, ma, mb, ctx->num_sms, s, o1, o2);
     };
+    const int k_e = split ? kOutF32 : kOutBf16;     // kind of e and h
     for (int off = 0; off < n; off += chunk) {
         int cnt = n - off < chunk ? n - off : chunk;
         GatherArgs ga{};
@@ -722,7 +745,8 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
                     f1.cfg_per_row = 1;
                     f1.h_prev = (k == k0 || split) ? nullptr : w.H; f1.ld_h = kWidth;
                     f1.pre_f32 = (k == k0 || !split) ? nullptr : w.H32; f1.ld_pre = kWidth;
-                    gemm(f1, fmap, wt.map_fc1[t][k]);
+                    f1.o1_kind = k_e; f1.o1_parts = 1; f1.o2_kind = kOutBf16; f1.o2_parts = P;
+                    gemm(f1, fmap, wt.map_fc1[t][k], &w.out_e, &w.out_s);
                     TcGemmArgs f2{};
                     f2.M = cnt; f2.N = kWidth; f2.K = kWidth; f2.n_mma = 208; f2.k_tiles = 4;
                     f2.epi = kEpiFc2; f2.err = ctx->d_err;
@@ -737,7 +761,9 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
                     } else {
                         f2.out_bf = w.H; f2.ldo = kWidth;
                     }
-                    gemm(f2, w.map_s, wt.map_fc2[t][k]);
+                    const bool end = k == k1 - 1;
+                    f2.o1_kind = end ? kOutBf16 : k_e; f2.o1_parts = end ? P : 1;
+                    gemm(f2, w.map_s, wt.map_fc2[t][k], end ? &w.out_mrg[t][chain] : &w.out_h);
                 }
             }
             TcGemmArgs mg{};
@@ -745,17 +771,19 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
             mg.epi = kEpiRelu; mg.err = ctx->d_err; mg.bias = W + o.mrg_b[t];
             mg.out_bf = w.head_in + t * kWidth; mg.ldo = 3 * kWidth;
             mg.out_part = cap * 3 * kWidth;
-            gemm(mg, w.map_mrg[t], wt.map_mrg[t]);
+            mg.o1_kind = kOutBf16; mg.o1_parts = P;
+            gemm(mg, w.map_mrg[t], wt.map_mrg[t], &w.out_head[t]);
         }
         TcGemmArgs h1{};
         h1.M = cnt; h1.N = kWidth; h1.K = 3 * kWidth; h1.n_mma = 208; h1.k_tiles = 10;
         h1.epi = kEpiRelu; h1.err = ctx->d_err; h1.bias = W + o.head_b[0];
         h1.out_bf = w.Z1; h1.ldo = kWidth;
         h1.out_part = cap * kWidth;
-        gemm(h1, w.map_head, wt.map_head[0]);
+        h1.o1_kind = kOutBf16; h1.o1_parts = P;
+        gemm(h1, w.map_head, wt.map_head[0], &w.out_z1);
         TcGemmArgs h2 = h1;
         h2.K = kWidth; h2.k_tiles = 4; h2.bias = W + o.head_b[1]; h2.out_bf = w.Z2;
-        gemm(h2, w.map_z1, wt.map_head[1]);
+        gemm(h2, w.map_z1, wt.map_head[1], &w.out_z2);
         TcGemmArgs h3{};
         h3.M = cnt; h3.N = 3; h3.K = kWidth; h3.n_mma = 16; h3.k_tiles = 4;
         h3.epi = kEpiDecode; h3.err = ctx->d_err; h3.bias = W + o.head_b[2];
@@ -1015,13 +1043,31 @@ bool make_tmap_u8(CUtensorMap *map, const void *base, uint64_t inner, uint64_t o
 bool make_tmap_bf16(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer,
                     uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer) {
     EncodeTiledFn fn = encode_tiled();
+    if (box_inner != 32 && box_inner != 64) return false;   // 64- or 128-byte swizzled rows
     if (!fn || (reinterpret_cast<uintptr_t>(base) & 15) || (row_bytes & 15)) return false;
     cuuint64_t dims[2] = {inner, outer};
     cuuint64_t strides[1] = {row_bytes};
     cuuint32_t box[2] = {box_inner, box_outer};
     cuuint32_t estr[2] = {1, 1};
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box,
-              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              box_inner * 2 == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool make_tmap_out(CUtensorMap *map, const void *base, bool f32, uint64_t cols, uint64_t rows,
+                   uint32_t parts, uint64_t row_bytes, uint64_t part_bytes) {
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn || (reinterpret_cast<uintptr_t>(base) & 15) || (row_bytes & 15) || (part_bytes & 15) ||
+        parts < 1 || parts > 3)
+        return false;
+    cuuint64_t dims[3] = {cols, rows, parts};
+    cuuint64_t strides[2] = {row_bytes, part_bytes};
+    cuuint32_t box[3] = {32, 32, parts};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return fn(map, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+              const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              f32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -1647,16 +1693,65 @@ nis_status nis_debug_tc_gemm(nis_ctx *ctx, const void *d_a, int lda, const void 
     if (!make_tmap_bf16(&ma, d_a, (uint64_t)k, (uint64_t)m, (uint64_t)lda * 2, 64, 128) ||
         !make_tmap_bf16(&mb, d_b, (uint64_t)k, (uint64_t)n, (uint64_t)ldb * 2, 64, (uint32_t)a.n_mma))
         return fail(ctx, NIS_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    // C through the epilogue's TMA stores where its rows are whole 16-byte units
+    CUtensorMap mc;
+    const bool tma_c = n % 4 == 0 && make_tmap_out(&mc, d_c, true, (uint64_t)n, (uint64_t)m, 1,
+                                                   (uint64_t)n * 4, (uint64_t)n * m * 4);
+    if (tma_c) { a.o1_kind = kOutF32; a.o1_parts = 1; }
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
     {
         ProfScope ps(ctx, "mlp", reinterpret_cast<cudaStream_t>(stream));
-        launch_tc_gemm(a, ma, mb, sms, reinterpret_cast<cudaStream_t>(stream));
+        launch_tc_gemm(a, ma, mb, sms, reinterpret_cast<cudaStream_t>(stream), tma_c ? &mc : nullptr);
     }
     NIS_CUDA(cudaGetLastError());
     return NIS_OK;
 }
 
+
+nis_status nis_debug_tc_gemm_f32(nis_ctx *ctx, const float *d_a, int lda, const float *d_b,
+                                 int ldb, int m, int n, int k, float *d_c, nis_stream stream) {
+    if (!ctx) return NIS_ERR_INVALID_ARG;
+    if (!d_a || !d_b || !d_c || m < 1 || n < 1 || n > 208 || k < 1 || lda < k || ldb < k)
+        return fail(ctx, NIS_ERR_INVALID_ARG, "bad GEMM arguments (n <= 208, lda/ldb >= k)");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int n_mma = (n + 15) / 16 * 16, kp = (k + 63) / 64 * 64;
+    const size_t a_elems = (size_t)3 * m * kp, b_elems = (size_t)3 * n_mma * kp;
+    __nv_bfloat16 *parts = nullptr;
+    NIS_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&parts), (a_elems + b_elems) * 2, s));
+    __nv_bfloat16 *ap = parts, *bp = parts + a_elems;
+    for (int q = 0; q < 3; ++q) {
+        launch_pack_bf16(d_a, m, k, lda, ap + (size_t)q * m * kp, m, kp, s, q);
+        launch_pack_bf16(d_b, n, k, ldb, bp + (size_t)q * n_mma * kp, n_mma, kp, s, q);
+    }
+    TcGemmArgs a{};
+    a.M = m; a.N = n; a.K = k;
+    a.n_mma = n_mma;
+    a.n_pass = 6;
+    a.k_tiles = (k + (int)tc_box_k(3) - 1) / (int)tc_box_k(3);
+    a.a_part_rows = m;
+    a.b_part_rows = n_mma;
+    a.epi = kEpiPlain;
+    a.err = ctx->d_err;
+    a.out_f32 = d_c; a.ldo = n;
+    CUtensorMap ma, mb;
+    bool ok = make_tmap_bf16(&ma, ap, (uint64_t)kp, (uint64_t)3 * m, (uint64_t)kp * 2, tc_box_k(3), 128) &&
+              make_tmap_bf16(&mb, bp, (uint64_t)kp, (uint64_t)3 * n_mma, (uint64_t)kp * 2, tc_box_k(3),
+                             (uint32_t)n_mma);
+    CUtensorMap mc;
+    const bool tma_c = n % 4 == 0 && make_tmap_out(&mc, d_c, true, (uint64_t)n, (uint64_t)m, 1,
+                                                   (uint64_t)n * 4, (uint64_t)n * m * 4);
+    if (tma_c) { a.o1_kind = kOutF32; a.o1_parts = 1; }
+    if (ok) {
+        ProfScope ps(ctx, "mlp", s);
+        launch_tc_gemm(a, ma, mb, ctx->num_sms, s, tma_c ? &mc : nullptr);
+    }
+    cudaFreeAsync(parts, s);
+    if (!ok) return fail(ctx, NIS_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    NIS_CUDA(cudaGetLastError());
+    return NIS_OK;
+}
 
 nis_status nis_shade_segments(nis_ctx *ctx, nis_weights w, const nis_segment *segs, int nseg,
                               nis_stream stream) {

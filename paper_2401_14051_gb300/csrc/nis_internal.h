@@ -263,7 +263,12 @@ struct TcGemmArgs {
     const float *col_scale;           // per-output-channel weight scales [N]
     const float *row_scale2; int row_scale2_ld;  // kEpiFc1: per-row feature scales
     uint8_t *out_f8, *out_s8;         // e4m3 outputs (FC-2 chain end / ReLU layers; FC-1 s)
+    // Outputs written through shared memory by TMA stores (kernel arguments map_o1, map_o2)
+    // instead of the pointers above: o1 = the layer's output (FC-1: e), o2 = FC-1's s.
+    // Kind kOutDirect uses the pointers; parts = 3 writes the three BF16 parts of a split.
+    int o1_kind, o1_parts, o2_kind, o2_parts;
 };
+constexpr int kOutDirect = 0, kOutF32 = 1, kOutBf16 = 2;
 constexpr int kLatPad8 = 240;        // FP8 feature row per layer, padded to 16 bytes
 constexpr int kWidth8 = 208;         // FP8 activation rows padded to 16 bytes
 constexpr int kHead8 = 608;
@@ -271,10 +276,19 @@ void launch_fill_segments(const int *seg_start, const int *seg_desc, int nseg, i
                           int *req_of_point, float *dec_rows, const ReqDesc *descs,
                           cudaStream_t s);
 void launch_tc_gemm(const TcGemmArgs &a, const CUtensorMap &map_a, const CUtensorMap &map_b,
-                    int num_sms, cudaStream_t s);
-// 2-D BF16 tensor map, inner dimension contiguous, box = box_inner x box_outer, 128-byte swizzle.
+                    int num_sms, cudaStream_t s, const CUtensorMap *map_o1 = nullptr,
+                    const CUtensorMap *map_o2 = nullptr);
+// K width of a BF16 tensor-core box: 64 elements (128-byte swizzle) for one part, 32 (64-byte
+// swizzle) for the three parts of the FP32 split, whose stage holds every part at once.
+inline uint32_t tc_box_k(int parts) { return parts > 1 ? 32 : 64; }
+// 2-D BF16 tensor map, inner dimension contiguous, box = box_inner x box_outer; box_inner 64
+// gives 128-byte swizzled rows, 32 gives 64-byte swizzled rows (other widths are refused).
 bool make_tmap_bf16(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer,
                     uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer);
+// 3-D output map of the tensor-core epilogue: [parts][rows][cols] FP32 (f32 = true, 128-byte
+// swizzle) or BF16 (64-byte swizzle), box 32 columns x 32 rows x all parts.
+bool make_tmap_out(CUtensorMap *map, const void *base, bool f32, uint64_t cols, uint64_t rows,
+                   uint32_t parts, uint64_t row_bytes, uint64_t part_bytes);
 
 // Device pointers of a resolved (volume, light, weights, phase table) set, for entry points
 // that must not build or allocate anything.  Fails with NIS_ERR_NOT_READY if the pyramid or

@@ -122,6 +122,8 @@ _SIGS = {
     "nis_kernel_launches": (C.c_uint64, []),
     "nis_debug_tc_gemm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int,
                                     C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "nis_debug_tc_gemm_f32": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int,
+                                        C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "nis_shade_segments": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(Segment), C.c_int,
                                      C.c_void_p]),
     "nis_server_create": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(ServerConfig),
@@ -326,6 +328,18 @@ class Context:
         self._check(self.lib.nis_debug_tc_gemm(self.h, a.data_ptr(), a.stride(0), b.data_ptr(),
                                                b.stride(0), m, n, k, out.data_ptr(),
                                                _stream(stream)))
+        return out
+
+    def debug_tc_gemm_f32(self, a, b, out=None, stream=None):
+        """C = A B^T at FP32 accuracy on the tensor-core kernel (three-way BF16 split of the
+        FP32 CUDA tensors A [m][k] and B [n][k], six products accumulated in FP32)."""
+        m, k = a.shape
+        n = b.shape[0]
+        if out is None:
+            out = torch.empty((m, n), dtype=torch.float32, device=a.device)
+        self._check(self.lib.nis_debug_tc_gemm_f32(self.h, a.data_ptr(), a.stride(0),
+                                                   b.data_ptr(), b.stride(0), m, n, k,
+                                                   out.data_ptr(), _stream(stream)))
         return out
 
     def shade_segments(self, weights, segments, stream=None):
