@@ -8,10 +8,13 @@
 //   conv1: a thread owns (point, d, h, half of the 16 output channels): for each (kd, kh) it
 //          loads one 9-value input row and updates 7 outputs x 8 channels (168 FMAs for 9
 //          input loads and 6 broadcast float4 weight loads);
-//   conv2: a thread owns (point, half of the output channels, quarter of the input
-//          channels) and all 5 outputs: for each (ci, kd, kh) one 7-value row of conv1
-//          output and 6 float4 weight loads feed 120 FMAs; the four partial sums (adjacent
-//          lanes) are added with warp shuffles.
+//   conv2: a thread owns (point, half of the output channels, input channels g and g + 8)
+//          and all 5 outputs: for each (ci, kd, kh) one 7-value row of conv1 output and 6
+//          float4 weight loads feed 120 FMAs; the eight partial sums (adjacent lanes) are
+//          added with warp shuffles.  256 of the 288 threads take part.
+// Shared-memory strides are padded so that the eight input channels a quarter-warp reads
+// fall in different banks (weights: 436 floats per input channel; conv1 output: 1040
+// floats per point).
 #include <cuda_fp8.h>
 
 #include "nis_internal.h"
@@ -22,13 +25,15 @@ namespace {
 constexpr int kPts = 16;                         // points per group
 constexpr int kThreads = 288;
 constexpr int kGroupsPerCta = 4;
-constexpr int kCiGroups = 4;                     // conv2: input-channel quarters
-constexpr int kY1 = 1016;                        // per-point stride of y1 (16 x 63 = 1008, padded)
-// shared memory (floats): w1t [27 taps][16 co], b1 [16], w2t [16 ci][27 taps][16 co], b2 [16],
-// x [kPts][225], y1 [kPts][16 ci][63]
+constexpr int kCiGroups = 8;                     // conv2: input channels g and g + 8
+constexpr int kY1 = 1040;                        // per-point stride of y1 (16 x 63 = 1008, padded)
+constexpr int kW2Ci = 436;                       // per-input-channel stride of w2t (27 x 16, padded)
+// shared memory (floats): w1t [27 taps][16 co], b1 [16], w2t [16 ci][kW2Ci: 27 taps x 16 co],
+// b2 [16], x [kPts][225], y1 [kPts][16 ci][63]
 constexpr int kOffW1 = 0, kOffB1 = kOffW1 + 27 * kCnnCh, kOffW2 = kOffB1 + kCnnCh,
-              kOffB2 = kOffW2 + kCnnCh * 27 * kCnnCh, kOffX = kOffB2 + kCnnCh,
+              kOffB2 = kOffW2 + kCnnCh * kW2Ci, kOffX = kOffB2 + kCnnCh,
               kOffY1 = kOffX + kPts * kLat, kSmemFloats = kOffY1 + kPts * kY1;
+static_assert(kOffW2 % 4 == 0 && kW2Ci % 4 == 0, "float4 weight loads need 16-byte alignment");
 }  // namespace
 
 __global__ void __launch_bounds__(kThreads, 2) cnn_f32_kernel(const float *__restrict__ H_T,
@@ -53,7 +58,7 @@ __global__ void __launch_bounds__(kThreads, 2) cnn_f32_kernel(const float *__res
         const float *g2 = wbase + o.cnn_w2[k];          // [co][ci][tap]
         for (int i = tid; i < kCnnCh * kCnnCh * 27; i += kThreads) {
             int co = i / (kCnnCh * 27), r = i % (kCnnCh * 27), ci = r / 27, tap = r % 27;
-            w2t[(ci * 27 + tap) * kCnnCh + co] = g2[i];
+            w2t[ci * kW2Ci + tap * kCnnCh + co] = g2[i];
         }
         if (tid < kCnnCh) {
             b1[tid] = wbase[o.cnn_b1[k] + tid];
@@ -109,8 +114,8 @@ __global__ void __launch_bounds__(kThreads, 2) cnn_f32_kernel(const float *__res
                 for (int w = 0; w < 7; ++w) yo[(half * 8 + c) * 63 + w] = fmaxf(acc[w][c], 0.f);
         }
         __syncthreads();
-        // conv2: thread = (point q, channel half, input-channel quarter g); 5 outputs x 8
-        // channels, partial sums over 4 input channels
+        // conv2: thread = (point q, channel half, input channels g and g + 8); 5 outputs x 8
+        // channels, partial sums over 2 input channels
         if (tid < kPts * 2 * kCiGroups) {
             const int g = tid % kCiGroups, half = (tid / kCiGroups) & 1, q = tid / (2 * kCiGroups);
             float acc[5][8];
@@ -119,7 +124,7 @@ __global__ void __launch_bounds__(kThreads, 2) cnn_f32_kernel(const float *__res
 #pragma unroll
                 for (int c = 0; c < 8; ++c) acc[w][c] = 0.f;
             for (int cc = 0; cc < kCnnCh / kCiGroups; ++cc) {
-                const int ci = g * (kCnnCh / kCiGroups) + cc;
+                const int ci = g + kCiGroups * cc;
 #pragma unroll
                 for (int kd = 0; kd < 3; ++kd)
 #pragma unroll
@@ -131,7 +136,7 @@ __global__ void __launch_bounds__(kThreads, 2) cnn_f32_kernel(const float *__res
 #pragma unroll
                         for (int kw = 0; kw < 3; ++kw) {
                             const float4 *wv = reinterpret_cast<const float4 *>(
-                                w2t + (ci * 27 + (kd * 3 + kh) * 3 + kw) * kCnnCh + half * 8);
+                                w2t + ci * kW2Ci + ((kd * 3 + kh) * 3 + kw) * kCnnCh + half * 8);
                             const float4 wa = wv[0], wb = wv[1];
 #pragma unroll
                             for (int w = 0; w < 5; ++w) {
@@ -143,19 +148,20 @@ __global__ void __launch_bounds__(kThreads, 2) cnn_f32_kernel(const float *__res
                         }
                     }
             }
-            // add the four input-channel quarters (lanes g = 0..3 of this group)
+            // add the eight input-channel groups (lanes g = 0..7 of this group)
 #pragma unroll
             for (int w = 0; w < 5; ++w)
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
                     acc[w][c] += __shfl_xor_sync(~0u, acc[w][c], 1);
                     acc[w][c] += __shfl_xor_sync(~0u, acc[w][c], 2);
+                    acc[w][c] += __shfl_xor_sync(~0u, acc[w][c], 4);
                 }
-            // lane g finalises entries e = 10 g .. 10 g + 9 of the 40 (position, channel) pairs
+            // lane g finalises entries e = 5 g .. 5 g + 4 of the 40 (position, channel) pairs
             if (q < np) {
 #pragma unroll
                 for (int e = 0; e < 40; ++e) {
-                    if (e / 10 != g) continue;
+                    if (e / 5 != g) continue;
                     const int w = e / 8, c = e % 8;
                     const int r = w * kCnnCh + half * 8 + c;
                     const float v = fmaxf(acc[w][c] + b2[half * 8 + c], 0.f);

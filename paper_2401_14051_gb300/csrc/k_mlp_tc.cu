@@ -144,37 +144,23 @@ __device__ __forceinline__ void load_bf16x8(const __nv_bfloat16 *src, float *v) 
     }
 }
 
-// Fused epilogue of 32 consecutive columns [c0, c0 + 32) of row r (FP32 accumulators in v).
-// s_bias / s_wa: per-column constants in shared memory (bias with the material's part of the
-// configuration vector folded in; weight of alpha).  sc, alpha: this row's SE weight and
-// view angle.  pre: the residual / running-state values of this chunk, already loaded.
-// With TMA outputs (a.o1_kind != kOutDirect) every lane stages its row into `stg` (o1 at 0,
-// o2 at o2_off) and the caller issues the stores; otherwise live rows store directly.
-__device__ __forceinline__ void epilogue_chunk(const TcGemmArgs &a, int r, int c0, float (&v)[32],
-                                               const float *s_bias, const float *s_wa, float sc,
-                                               float alpha, const float (&pre)[32],
-                                               const float *s_wm, const float (&rc)[4],
-                                               const float *s_ws, uint8_t *stg, uint32_t o2_off,
-                                               int lane, bool live) {
-    const int N = a.N;
-    const bool staged = a.o1_kind != kOutDirect;
+// Fused epilogue math of 32 consecutive columns [c0, c0 + 32) of one row (FP32 accumulators
+// in v): v becomes the layer's output o1 (FC-1: e), sv FC-1's s = h_prev + e.  s_bias / s_wa:
+// per-column constants in shared memory (bias with the material's part of the configuration
+// vector folded in; weight of alpha).  sc, alpha: this row's SE weight and view angle.
+// pre: the residual / running-state values of this chunk.
+__device__ __forceinline__ void epilogue_math(const TcGemmArgs &a, int c0, float (&v)[32], float (&sv)[32],
+                                              const float *s_bias, const float *s_wa, float sc,
+                                              float alpha, const float (&pre)[32],
+                                              const float *s_wm, const float (&rc)[4],
+                                              const float *s_ws) {
     if (a.col_scale) {                                   // FP8: per-output-channel weight scale
 #pragma unroll
         for (int j = 0; j < 32; ++j) v[j] *= s_ws[c0 + j];
     }
     switch (a.epi) {
-    case kEpiPlain: {
-        if (staged) { stage_out(stg, lane, v, a.o1_kind, a.o1_parts); break; }
-        if (!live) break;
-        float *o = a.out_f32 + (size_t)r * a.ldo;
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-            if (c0 + j < N) o[c0 + j] = v[j];
-        break;
-    }
     case kEpiFc1: {
         // e = ReLU(w_se * acc + W_cfg c + b); s = h_prev + e
-        float sv[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
             float b = fmaf(s_wa[c0 + j], alpha, s_bias[c0 + j]);
@@ -186,12 +172,43 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs &a, int r, int c
             v[j] = e;
             sv[j] = (a.h_prev || a.pre_f32) ? pre[j] + e : e;
         }
-        if (staged) {
-            stage_out(stg, lane, v, a.o1_kind, a.o1_parts);
-            stage_out(stg + o2_off, lane, sv, a.o2_kind, a.o2_parts);
-            break;
-        }
-        if (!live) break;
+        break;
+    }
+    case kEpiFc2:        // h = ReLU(acc + b) + e
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + s_bias[c0 + j], 0.f) + pre[j];
+        break;
+    case kEpiRelu:
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + s_bias[c0 + j], 0.f);
+        break;
+    default:             // kEpiPlain: the accumulators; kEpiDecode: in epilogue_emit
+        break;
+    }
+}
+
+// Output of one chunk.  With TMA outputs (a.o1_kind != kOutDirect) every lane stages its row
+// into `stg` (o1 at 0, o2 at o2_off) and the caller issues the stores; otherwise live rows
+// store through the pointers.
+__device__ __forceinline__ void epilogue_emit(const TcGemmArgs &a, int r, int c0, const float (&v)[32],
+                                              const float (&sv)[32], const float *s_bias,
+                                              uint8_t *stg, uint32_t o2_off, int lane, bool live) {
+    const int N = a.N;
+    if (a.o1_kind != kOutDirect) {
+        stage_out(stg, lane, v, a.o1_kind, a.o1_parts);
+        if (a.o2_kind != kOutDirect) stage_out(stg + o2_off, lane, sv, a.o2_kind, a.o2_parts);
+        return;
+    }
+    if (!live) return;
+    switch (a.epi) {
+    case kEpiPlain: {
+        float *o = a.out_f32 + (size_t)r * a.ldo;
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (c0 + j < N) o[c0 + j] = v[j];
+        break;
+    }
+    case kEpiFc1:
 #pragma unroll
         for (int g = 0; g < 4; ++g)
             if (c0 + 8 * g < N) {
@@ -201,13 +218,7 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs &a, int r, int c
                 else store_out8(a.out_s + (size_t)r * a.ldo + c0 + 8 * g, sv + 8 * g, a.out_split, a.out_part);
             }
         break;
-    }
-    case kEpiFc2: {
-        // h = ReLU(acc + b) + e
-#pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + s_bias[c0 + j], 0.f) + pre[j];
-        if (staged) { stage_out(stg, lane, v, a.o1_kind, a.o1_parts); break; }
-        if (!live) break;
+    case kEpiFc2:
 #pragma unroll
         for (int g = 0; g < 4; ++g)
             if (c0 + 8 * g < N) {
@@ -216,12 +227,7 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs &a, int r, int c
                 else store_out8(a.out_bf + (size_t)r * a.ldo + c0 + 8 * g, v + 8 * g, a.out_split, a.out_part);
             }
         break;
-    }
-    case kEpiRelu: {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + s_bias[c0 + j], 0.f);
-        if (staged) { stage_out(stg, lane, v, a.o1_kind, a.o1_parts); break; }
-        if (!live) break;
+    case kEpiRelu:
 #pragma unroll
         for (int g = 0; g < 4; ++g)
             if (c0 + 8 * g < N) {
@@ -229,9 +235,8 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs &a, int r, int c
                 else store_out8(a.out_bf + (size_t)r * a.ldo + c0 + 8 * g, v + 8 * g, a.out_split, a.out_part);
             }
         break;
-    }
-    default: {  // kEpiDecode: rgb = I albedo^4 expm1(acc + b), N = 3
-        if (c0 == 0 && live) {
+    default:  // kEpiDecode: rgb = I albedo^4 expm1(acc + b), N = 3
+        if (c0 == 0) {
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
                 float y = v[j] + s_bias[j];
@@ -241,7 +246,6 @@ __device__ __forceinline__ void epilogue_chunk(const TcGemmArgs &a, int r, int c
             }
         }
         break;
-    }
     }
 }
 
@@ -490,12 +494,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                 // next chunk's residual loads overlap this chunk's TMEM load and math
                 if (live && c0 + 64 < a.N) load_pre(a, r, c0 + 64, pre);
                 tc::tmem_ld_wait();
+                float sv[32];
+                epilogue_math(a, c0, v, sv, s_bias, s_wa, sc, alpha, cur, s_wm, rc, s_ws);
                 if (staged) {                          // the previous chunk's stores have read stg
                     if (lane == 0) tc::bulk_wait_read();
                     __syncwarp();
                 }
-                epilogue_chunk(a, r, c0, v, s_bias, s_wa, sc, alpha, cur, s_wm, rc, s_ws, stg, o2_off,
-                               lane, live);
+                epilogue_emit(a, r, c0, v, sv, s_bias, stg, o2_off, lane, live);
                 if (staged) {
                     tc::fence_async_smem();
                     __syncwarp();
