@@ -8,13 +8,12 @@
 //   conv1: a thread owns (point, d, h, half of the 16 output channels): for each (kd, kh) it
 //          loads one 9-value input row and updates 7 outputs x 8 channels (168 FMAs for 9
 //          input loads and 6 broadcast float4 weight loads);
-//   conv2: a thread owns (point, half of the output channels, input channels g and g + 8)
-//          and all 5 outputs: for each (ci, kd, kh) one 7-value row of conv1 output and 6
-//          float4 weight loads feed 120 FMAs; the eight partial sums (adjacent lanes) are
-//          added with warp shuffles.  256 of the 288 threads take part.
-// Shared-memory strides are padded so that the eight input channels a quarter-warp reads
-// fall in different banks (weights: 436 floats per input channel; conv1 output: 1040
-// floats per point).
+//   conv2: warp g (of 8) owns input channels g and g + 8, a lane owns (point, half of the
+//          output channels) and all 5 outputs: for each (ci, kd, kh) one 7-value row of
+//          conv1 output and 6 float4 weight loads feed 120 FMAs.  Every lane of a warp reads
+//          the same weights (broadcast) and its own point's row (the per-point stride of the
+//          conv1 output, 1009 floats, puts the 16 points in 16 banks).  The eight partial
+//          sums of each output go through shared memory and are added in a fixed order.
 #include <cuda_fp8.h>
 
 #include "nis_internal.h"
@@ -25,8 +24,10 @@ namespace {
 constexpr int kPts = 16;                         // points per group
 constexpr int kThreads = 288;
 constexpr int kGroupsPerCta = 4;
-constexpr int kCiGroups = 8;                     // conv2: input channels g and g + 8
-constexpr int kY1 = 1040;                        // per-point stride of y1 (16 x 63 = 1008, padded)
+constexpr int kCiGroups = 8;                     // conv2: warps, input channels g and g + 8
+constexpr int kY1 = 1009;                        // per-point stride of y1 (16 x 63 = 1008, padded)
+constexpr int kPartLd = 41;                      // conv2 partial sums: stride per (group, lane)
+static_assert(kCiGroups * 32 * kPartLd <= kPts * kY1, "partial sums alias the conv1 output");
 constexpr int kW2Ci = 436;                       // per-input-channel stride of w2t (27 x 16, padded)
 // shared memory (floats): w1t [27 taps][16 co], b1 [16], w2t [16 ci][kW2Ci: 27 taps x 16 co],
 // b2 [16], x [kPts][225], y1 [kPts][16 ci][63]
@@ -114,17 +115,19 @@ __global__ void __launch_bounds__(kThreads, 2) cnn_f32_kernel(const float *__res
                 for (int w = 0; w < 7; ++w) yo[(half * 8 + c) * 63 + w] = fmaxf(acc[w][c], 0.f);
         }
         __syncthreads();
-        // conv2: thread = (point q, channel half, input channels g and g + 8); 5 outputs x 8
-        // channels, partial sums over 2 input channels
-        if (tid < kPts * 2 * kCiGroups) {
-            const int g = tid % kCiGroups, half = (tid / kCiGroups) & 1, q = tid / (2 * kCiGroups);
+        // conv2: warp g = input channels g and g + 8, lane = (channel half, point q);
+        // 5 outputs x 8 channels, partial sums over 2 input channels
+        const int warp = tid >> 5, lane = tid & 31;
+        float *part = y1;                                 // [g][lane][kPartLd] partial sums
+        if (warp < kCiGroups) {
+            const int half = lane >> 4, q = lane & 15;
             float acc[5][8];
 #pragma unroll
             for (int w = 0; w < 5; ++w)
 #pragma unroll
                 for (int c = 0; c < 8; ++c) acc[w][c] = 0.f;
             for (int cc = 0; cc < kCnnCh / kCiGroups; ++cc) {
-                const int ci = g + kCiGroups * cc;
+                const int ci = warp + kCiGroups * cc;
 #pragma unroll
                 for (int kd = 0; kd < 3; ++kd)
 #pragma unroll
@@ -148,37 +151,38 @@ __global__ void __launch_bounds__(kThreads, 2) cnn_f32_kernel(const float *__res
                         }
                     }
             }
-            // add the eight input-channel groups (lanes g = 0..7 of this group)
+            // the conv2 warps (named barrier 1, 256 threads) are done reading the conv1
+            // output, which the partial sums overwrite
+            asm volatile("bar.sync 1, %0;" ::"r"(kCiGroups * 32) : "memory");
 #pragma unroll
             for (int w = 0; w < 5; ++w)
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    acc[w][c] += __shfl_xor_sync(~0u, acc[w][c], 1);
-                    acc[w][c] += __shfl_xor_sync(~0u, acc[w][c], 2);
-                    acc[w][c] += __shfl_xor_sync(~0u, acc[w][c], 4);
-                }
-            // lane g finalises entries e = 5 g .. 5 g + 4 of the 40 (position, channel) pairs
-            if (q < np) {
+                for (int c = 0; c < 8; ++c) part[(warp * 32 + lane) * kPartLd + w * 8 + c] = acc[w][c];
+        }
+        __syncthreads();
+        // output (point q, entry r = position w x 16 + channel co): the eight groups' partial
+        // sums in order g = 0..7, + bias, ReLU; consecutive threads take consecutive entries
+        for (int e = tid; e < kPts * kDT; e += kThreads) {
+            const int q = e / kDT, r = e % kDT;
+            if (q >= np) continue;
+            const int w = r / kCnnCh, co = r % kCnnCh;
+            const int slot = ((co >> 3) * 16 + q) * kPartLd + w * 8 + (co & 7);
+            float sum = 0.f;
 #pragma unroll
-                for (int e = 0; e < 40; ++e) {
-                    if (e / 5 != g) continue;
-                    const int w = e / 8, c = e % 8;
-                    const int r = w * kCnnCh + half * 8 + c;
-                    const float v = fmaxf(acc[w][c] + b2[half * 8 + c], 0.f);
-                    const size_t o = ((size_t)(p0 + q) * kLayers + k) * kDT + r;
-                    if (X_T_bf) {
-                        float rr = v;
-                        const int parts = split_part ? 3 : 1;
-                        for (int s2 = 0; s2 < parts; ++s2) {
-                            __nv_bfloat16 b = __float2bfloat16_rn(rr);
-                            X_T_bf[o + s2 * split_part] = b;
-                            rr -= __bfloat162float(b);
-                        }
-                    }
-                    if (X_T) X_T[o] = v;
-                    if (X_T_f8) X_T_f8[o] = __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+            for (int g = 0; g < kCiGroups; ++g) sum += part[g * 32 * kPartLd + slot];
+            const float v = fmaxf(sum + b2[co], 0.f);
+            const size_t o = ((size_t)(p0 + q) * kLayers + k) * kDT + r;
+            if (X_T_bf) {
+                float rr = v;
+                const int parts = split_part ? 3 : 1;
+                for (int s2 = 0; s2 < parts; ++s2) {
+                    __nv_bfloat16 b = __float2bfloat16_rn(rr);
+                    X_T_bf[o + s2 * split_part] = b;
+                    rr -= __bfloat162float(b);
                 }
             }
+            if (X_T) X_T[o] = v;
+            if (X_T_f8) X_T_f8[o] = __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
         }
     }
 }
