@@ -141,7 +141,10 @@ nis_status nis_build_pyramid(nis_ctx *ctx, nis_volume vol, nis_stream stream);
  * -light_dir), midpoint rule with step 1/N_m and a partial last step, stopping once the
  * scaled optical depth exceeds 30.  lambda in (0, 1] (the paper uses 0.6).  Builds the
  * pyramid first if needed.  A light with the same volume, direction and lambda is
- * re-marched into its existing buffers and its handle returned again. */
+ * re-marched into its existing buffers and its handle returned again.  The light also keeps
+ * the density and its transmittance interleaved per voxel pair for the template gathers
+ * (about 4x the transmittance pyramid's bytes); shading calls refresh that copy when the
+ * pyramid has been rebuilt since. */
 nis_status nis_build_transmittance(nis_ctx *ctx, nis_volume vol, const float light_dir[3],
                                    float lambda, nis_stream stream, nis_light *out);
 
@@ -191,7 +194,9 @@ nis_status nis_update_volume(nis_ctx *ctx, nis_volume vol, const void *density, 
  * - n above NIS_STATIC_MAX_POINTS returns NIS_ERR_INVALID_ARG (split larger batches).
  * - Nothing is built here: the pyramid, the light's transmittance and the phase table for
  *   m->g must exist (nis_build_pyramid / nis_build_transmittance / nis_build_phase_table),
- *   otherwise NIS_ERR_NOT_READY.
+ *   otherwise NIS_ERR_NOT_READY.  So must the light's copy of the density it shades with:
+ *   after a pyramid rebuild, build the light again or shade once through nis_shade_points
+ *   (which refreshes that copy), else NIS_ERR_NOT_READY.
  * - The first call on a device looks up the array's device address; make that first call
  *   before any stream capture.
  * - All calls in the process share the one array and leave their intermediates in it; the

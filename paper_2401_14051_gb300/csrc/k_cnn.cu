@@ -71,11 +71,19 @@ __global__ void __launch_bounds__(kThreads, 2) cnn_f32_kernel(const float *__res
          grp < n_groups && grp < (blockIdx.x + 1) * kGroupsPerCta; ++grp) {
         const int p0 = grp * kPts;
         const int np = min(kPts, count - p0);
-        __syncthreads();                                  // weights ready / previous group done
-        for (int i = tid; i < kPts * kLat; i += kThreads) {
-            int q = i / kLat, t = i % kLat;
-            xin[i] = q < np ? H_T[((size_t)(p0 + q) * kLayers + k) * kLat + t] : 0.f;
+        // the group's input: all of this thread's loads issued before any store, so that
+        // their latencies overlap (a load-store loop waits for each load in turn)
+        constexpr int kXPer = (kPts * kLat + kThreads - 1) / kThreads;
+        float xr[kXPer];
+#pragma unroll
+        for (int i = 0; i < kXPer; ++i) {
+            const int idx = tid + i * kThreads, q = idx / kLat, t = idx % kLat;
+            xr[i] = (idx < kPts * kLat && q < np) ? H_T[((size_t)(p0 + q) * kLayers + k) * kLat + t] : 0.f;
         }
+        __syncthreads();                                  // weights ready / previous group done
+#pragma unroll
+        for (int i = 0; i < kXPer; ++i)
+            if (tid + i * kThreads < kPts * kLat) xin[tid + i * kThreads] = xr[i];
         __syncthreads();
         // conv1: thread = (point q, row d, row h, channel half); 7 outputs x 8 channels
         {

@@ -19,8 +19,7 @@ __global__ void __launch_bounds__(kLayers * 32) gather_kernel(const __grid_const
 
     // single request, or this point's request in a mixed batch
     const ReqDesc *d = a.descs ? a.descs + a.req_of_point[p] : nullptr;
-    const PyramidView &RHO = d ? d->rho : a.rho;
-    const PyramidView &TT = d ? d->T : a.T;
+    const PairView &RT = d ? d->rt : a.rt;
     const float lx = d ? d->l[0] : a.lx, ly = d ? d->l[1] : a.ly, lz = d ? d->l[2] : a.lz;
     const float gg = d ? d->g : a.g;
     const float *table = d ? d->table : a.table;
@@ -55,8 +54,8 @@ __global__ void __launch_bounds__(kLayers * 32) gather_kernel(const __grid_const
     int ja = min((int)floorf(tt), kAlpha - 2);
     float wa = tt - ja;
 
-    const int N = RHO.n[0];
-    const int L = RHO.levels;
+    const int N = RT.n[0];
+    const int L = RT.levels;
     // this warp's layer: centre, spacing, mip level and phase point set
     float cxk, cyk, czk, h;
     int m, set;
@@ -76,8 +75,8 @@ __global__ void __launch_bounds__(kLayers * 32) gather_kernel(const __grid_const
         m = (int)fminf(fmaxf(floorf(z), 0.f), (float)(L - 1));
         set = 1 + j;
     }
-    const float *rho_lv = RHO.lv[m], *T_lv = TT.lv[m];
-    const int nm = RHO.n[m];
+    const float4 *rt_lv = RT.lv[m];
+    const int nm = RT.n[m];
     const float *row0 = table + ((size_t)ja * kPhaseSets + set) * kLat;
     const float *row1 = row0 + kPhaseSets * kLat;
     const size_t obase = ((size_t)p * kLayers + k) * kLat;
@@ -95,8 +94,8 @@ __global__ void __launch_bounds__(kLayers * 32) gather_kernel(const __grid_const
             const float sx = cxk + h * (qa * exx + qb * eyx + qc * ezx);
             const float sy = cyk + h * (qa * exy + qb * eyy + qc * ezy);
             const float sz = czk + h * (qa * exz + qb * eyz + qc * ezz);
-            const float rho = sample_border(rho_lv, nm, sx, sy, sz, 0.0f);
-            const float T = sample_border(T_lv, nm, sx, sy, sz, 1.0f);
+            const float2 rt = sample_pair(rt_lv, nm, sx, sy, sz);
+            const float rho = rt.x, T = rt.y;
             const float f0 = __ldg(row0 + t), f1 = __ldg(row1 + t);
             const float f = f0 + wa * (f1 - f0);
             a.H_T[obase + t] = T;

@@ -100,4 +100,30 @@ void launch_occupancy(const float *level, int n, unsigned char *occ, cudaStream_
     occupancy_kernel<<<blocks, 256, 0, s>>>(level, n, occ);
 }
 
+// PairView level: entry (z, y, i) = {rho, T} at x = i - 1 and x = i (borders 0 and 1).
+__global__ void pack_pairs_kernel(const float *__restrict__ rho, const float *__restrict__ T, int n,
+                                  float4 *__restrict__ out) {
+    const size_t total = (size_t)n * n * (n + 1);
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % (n + 1));
+        const size_t row = e / (n + 1);                   // z * n + y
+        const float *r = rho + row * n, *t = T + row * n;
+        const int x0 = i - 1, x1 = i;
+        float4 q;
+        q.x = x0 >= 0 ? r[x0] : 0.0f;
+        q.y = x0 >= 0 ? t[x0] : 1.0f;
+        q.z = x1 < n ? r[x1] : 0.0f;
+        q.w = x1 < n ? t[x1] : 1.0f;
+        out[e] = q;
+    }
+}
+
+void launch_pack_pairs(const float *rho, const float *T, int n, float4 *out, cudaStream_t s) {
+    const size_t total = (size_t)n * n * (n + 1);
+    const int blocks = (int)((total + 255) / 256 < 8192 ? (total + 255) / 256 : 8192);
+    note_launch();
+    pack_pairs_kernel<<<blocks, 256, 0, s>>>(rho, T, n, out);
+}
+
 }  // namespace nis

@@ -29,6 +29,7 @@ struct Volume {
     void *staging = nullptr;          // pageable-host updates (nis_update_volume)
     size_t staging_bytes = 0;
     bool pyramid = false;
+    uint64_t version = 0;             // counts pyramid builds (lights pair with one of them)
 };
 
 struct Light {
@@ -36,6 +37,11 @@ struct Light {
     float dir[3] = {0, 0, 0};         // unit propagation direction
     float lambda = 0.6f;
     float *data = nullptr;            // same level layout as the volume
+    // density and transmittance side by side for the gathers (PairView layout), packed
+    // from the volume's pyramid of build `pair_version` (0: not packed)
+    float4 *pairs = nullptr;
+    size_t pair_off[kMaxLevels] = {};
+    uint64_t pair_version = 0;
 };
 
 struct Weights {
@@ -238,7 +244,39 @@ nis_status build_pyramid_impl(nis_ctx *ctx, Volume &v, cudaStream_t s) {
     }
     NIS_CUDA(cudaGetLastError());
     v.pyramid = true;
+    ++v.version;
     return NIS_OK;
+}
+
+// Packs (or re-packs, after a pyramid rebuild) the light's PairView levels.
+nis_status ensure_pairs(nis_ctx *ctx, const Volume &v, Light &L, cudaStream_t s) {
+    if (L.pairs && L.pair_version == v.version) return NIS_OK;
+    if (!L.pairs) {
+        size_t total = 0;
+        for (int m = 0; m < v.levels; ++m) {
+            L.pair_off[m] = total;
+            total += (size_t)v.sizes[m] * v.sizes[m] * (v.sizes[m] + 1);
+        }
+        nis_status st = dev_alloc_t(ctx, total, &L.pairs, s);
+        if (st) return st;
+    }
+    for (int m = 0; m < v.levels; ++m) {
+        ProfScope ps(ctx, "pyramid", s);
+        launch_pack_pairs(v.data + v.off[m], L.data + v.off[m], v.sizes[m], L.pairs + L.pair_off[m], s);
+    }
+    NIS_CUDA(cudaGetLastError());
+    L.pair_version = v.version;
+    return NIS_OK;
+}
+
+PairView pair_view(const Volume &v, const Light &L) {
+    PairView pv{};
+    pv.levels = v.levels;
+    for (int m = 0; m < v.levels; ++m) {
+        pv.lv[m] = L.pairs + L.pair_off[m];
+        pv.n[m] = v.sizes[m];
+    }
+    return pv;
 }
 
 PhaseSpec phase_spec(const nis_material *m) {
@@ -560,6 +598,7 @@ nis_status shade_impl(nis_ctx *ctx, const Volume &vol, const Light &light, const
         GatherArgs ga{};
         ga.rho = view_of(vol, vol.data);
         ga.T = view_of(vol, light.data);
+        ga.rt = pair_view(vol, light);
         ga.table = table;
         ga.points = pts + 3 * (size_t)off;
         ga.omega = om + 3 * (size_t)off;
@@ -693,6 +732,7 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
         GatherArgs ga{};
         ga.rho = view_of(vol, vol.data);
         ga.T = view_of(vol, light.data);
+        ga.rt = pair_view(vol, light);
         ga.table = table;
         ga.points = pts + 3 * (size_t)off;
         ga.omega = om + 3 * (size_t)off;
@@ -833,6 +873,7 @@ nis_status shade_impl_fp8(nis_ctx *ctx, const Volume &vol, const Light &light, c
         GatherArgs ga{};
         ga.rho = view_of(vol, vol.data);
         ga.T = view_of(vol, light.data);
+        ga.rt = pair_view(vol, light);
         ga.table = table;
         ga.points = pts + 3 * (size_t)off;
         ga.omega = om + 3 * (size_t)off;
@@ -1106,8 +1147,12 @@ nis_status resolve_built_inputs(nis_ctx *ctx, nis_volume vol, nis_light light, n
     if (it == ctx->phase.end())
         return fail(ctx, NIS_ERR_NOT_READY, "phase table for this material not built "
                                             "(shade once, or call nis_build_phase_table)");
+    if (!pl->pairs || pl->pair_version != pv->version)
+        return fail(ctx, NIS_ERR_NOT_READY, "light older than the volume's pyramid "
+                                            "(rebuild it, or shade once through nis_shade_points)");
     out->rho = view_of(*pv, pv->data);
     out->T = view_of(*pv, pl->data);
+    out->rt = pair_view(*pv, *pl);
     out->table = it->second;
     out->W = pw->f32;
     out->off = pw->off;
@@ -1330,6 +1375,8 @@ nis_status nis_build_transmittance(nis_ctx *ctx, nis_volume vol, const float lig
                      -dir[2], lambda, L.data + v->off[m], s);
     }
     NIS_CUDA(cudaGetLastError());
+    L.pair_version = 0;                       // new transmittance: re-pack
+    if ((st = ensure_pairs(ctx, *v, L, s))) return st;
     *out = h;
     return NIS_OK;
 }
@@ -1400,6 +1447,7 @@ nis_status nis_shade_points_debug(nis_ctx *ctx, nis_volume vol, nis_light light,
     if ((st = resolve(ctx, vol, light, w, &pv, &pl, &pw))) return st;
     if (n == 0) return NIS_OK;
     DeviceGuard g(ctx->device);
+    if ((st = ensure_pairs(ctx, *pv, *pl, reinterpret_cast<cudaStream_t>(stream)))) return st;
     return shade_impl(ctx, *pv, *pl, *pw, m, d_points, d_omega, n, d_rgb_out, dbg,
                       reinterpret_cast<cudaStream_t>(stream));
 }
@@ -1440,6 +1488,7 @@ nis_status nis_render_frame(nis_ctx *ctx, nis_volume vol, nis_light light, nis_w
     if ((st = resolve(ctx, vol, light, w, &pv, &pl, &pw))) return st;
     DeviceGuard g(ctx->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if ((st = ensure_pairs(ctx, *pv, *pl, s))) return st;
     Workspace &ws = ctx->ws;
     int pixels = c.width * c.height;
     if (ws.hit_cap < pixels) {
@@ -1486,7 +1535,11 @@ nis_status nis_release(nis_ctx *ctx, nis_handle h) {
         cudaDeviceSynchronize();
         std::vector<nis_handle> dead;
         for (auto &kv : ctx->lights)
-            if (kv.second.vol == h) { dev_free(ctx, kv.second.data); dead.push_back(kv.first); }
+            if (kv.second.vol == h) {
+                dev_free(ctx, kv.second.data);
+                dev_free(ctx, kv.second.pairs);
+                dead.push_back(kv.first);
+            }
         for (nis_handle d : dead) ctx->lights.erase(d);
         dev_free(ctx, v->data);
         dev_free(ctx, v->sigma_max);
@@ -1498,6 +1551,7 @@ nis_status nis_release(nis_ctx *ctx, nis_handle h) {
     if (Light *l = lookup(ctx->lights, h)) {
         cudaDeviceSynchronize();
         dev_free(ctx, l->data);
+        dev_free(ctx, l->pairs);
         ctx->lights.erase(h);
         return NIS_OK;
     }
@@ -1778,9 +1832,11 @@ nis_status nis_shade_segments(nis_ctx *ctx, nis_weights w, const nis_segment *se
         if (!pv->pyramid) return fail(ctx, NIS_ERR_NOT_READY, "pyramid not built");
         float *table;
         if ((st = ensure_phase(ctx, phase_spec(&sg.material), s, &table))) return st;
+        if ((st = ensure_pairs(ctx, *pv, *pl, s))) return st;
         ReqDesc &d = descs[i];
         d.rho = view_of(*pv, pv->data);
         d.T = view_of(*pv, pl->data);
+        d.rt = pair_view(*pv, *pl);
         d.table = table;
         for (int c = 0; c < 3; ++c) {
             d.l[c] = pl->dir[c];

@@ -100,6 +100,46 @@ __device__ __forceinline__ float sample_border(const float *__restrict__ g, int 
     return c0 + fz * (c1 - c0);
 }
 
+// sample_border of density and transmittance (borders 0 and 1) at once, from a PairView
+// level: four 16-byte loads instead of sixteen scalar ones, the same arithmetic.
+__device__ __forceinline__ float2 sample_pair(const float4 *__restrict__ g, int n, float x, float y,
+                                              float z) {
+    float gx = x * n - 0.5f, gy = y * n - 0.5f, gz = z * n - 0.5f;
+    float flx = floorf(gx), fly = floorf(gy), flz = floorf(gz);
+    float fx = gx - flx, fy = gy - fly, fz = gz - flz;
+    int ix = (int)fminf(fmaxf(flx, -2.0f), (float)n + 1.0f);
+    int iy = (int)fminf(fmaxf(fly, -2.0f), (float)n + 1.0f);
+    int iz = (int)fminf(fmaxf(flz, -2.0f), (float)n + 1.0f);
+    float4 q[4];                                 // (y, z) corners; .x .y at ix, .z .w at ix + 1
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        int cy = iy + (c & 1), cz = iz + (c >> 1);
+        bool in = (unsigned)cy < (unsigned)n && (unsigned)cz < (unsigned)n && ix >= -1 && ix < n;
+        q[c] = in ? __ldg(g + ((size_t)cz * n + cy) * (n + 1) + (ix + 1))
+                  : make_float4(0.0f, 1.0f, 0.0f, 1.0f);
+    }
+    float2 r;
+    {
+        float c00 = q[0].x + fx * (q[0].z - q[0].x);
+        float c01 = q[1].x + fx * (q[1].z - q[1].x);
+        float c10 = q[2].x + fx * (q[2].z - q[2].x);
+        float c11 = q[3].x + fx * (q[3].z - q[3].x);
+        float c0 = c00 + fy * (c01 - c00);
+        float c1 = c10 + fy * (c11 - c10);
+        r.x = c0 + fz * (c1 - c0);
+    }
+    {
+        float c00 = q[0].y + fx * (q[0].w - q[0].y);
+        float c01 = q[1].y + fx * (q[1].w - q[1].y);
+        float c10 = q[2].y + fx * (q[2].w - q[2].y);
+        float c11 = q[3].y + fx * (q[3].w - q[3].y);
+        float c0 = c00 + fy * (c01 - c00);
+        float c1 = c10 + fy * (c11 - c10);
+        r.y = c0 + fz * (c1 - c0);
+    }
+    return r;
+}
+
 // Distance from (x, y, z) along unit u to the boundary of the unit cube (>= 0).
 __device__ __forceinline__ float exit_distance(float x, float y, float z, float ux, float uy,
                                                float uz) {
@@ -121,6 +161,8 @@ void note_launch();                  // counts every kernel launch of the librar
 void launch_convert_density(const void *src, int dtype, float scale, size_t count,
                             float *dst, unsigned *err, float *sigma_max, cudaStream_t s);
 void launch_downsample(const float *src, int n, float *dst, int m, cudaStream_t s);
+// one PairView level of size n from the density and transmittance levels
+void launch_pack_pairs(const float *rho, const float *T, int n, float4 *out, cudaStream_t s);
 // occupancy of 4^3-voxel bricks of an n^3 level, dilated by one voxel: occ = 0 guarantees
 // that every trilinear cell whose base voxel lies in the brick has eight zero corners
 constexpr int kBrick = 4;
@@ -143,10 +185,21 @@ struct PyramidView {                 // device pointers of all levels of a pyram
     int levels;
 };
 
+// Density and transmittance of a (volume, light) pair side by side for the gathers: entry
+// (z, y, i) of a level of size n, i = 0..n, holds {rho, T} at x = i - 1 and at x = i, each
+// outside the volume as its border value (rho 0, T 1), so that one 16-byte load brings the
+// two x-neighbours of a trilinear cell for both fields.  [z][y][n + 1] float4 per level.
+struct PairView {
+    const float4 *lv[kMaxLevels];
+    int n[kMaxLevels];
+    int levels;
+};
+
 // Per-request inputs of a mixed batch (continuous batching): point p uses
 // descs[req_of_point[p]] instead of the single-request fields of GatherArgs.
 struct ReqDesc {
     PyramidView rho, T;
+    PairView rt;                     // what the gathers read
     const float *table;
     float l[3];
     float g;
@@ -158,6 +211,7 @@ struct GatherArgs {
     const ReqDesc *descs;            // mixed batch (may be null)
     const int *req_of_point;
     PyramidView rho, T;
+    PairView rt;                     // what the gathers read
     const float *table;              // phase table of the material's g
     const float *points, *omega;     // [n][3]
     int count;
@@ -295,6 +349,7 @@ bool make_tmap_out(CUtensorMap *map, const void *base, bool f32, uint64_t cols, 
 // the phase table of g is missing.
 struct ResolvedInputs {
     PyramidView rho, T;
+    PairView rt;
     const float *table;
     const float *W;
     WeightOffsets off;

@@ -102,6 +102,7 @@ extern "C" nis_status nis_shade_points_static(nis_ctx *ctx, nis_volume vol, nis_
     GatherArgs ga{};
     ga.rho = in.rho;
     ga.T = in.T;
+    ga.rt = in.rt;
     ga.table = in.table;
     ga.points = d_points;
     ga.omega = d_omega;

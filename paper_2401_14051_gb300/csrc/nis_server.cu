@@ -88,6 +88,15 @@ size_t level_floats(int n) {
     }
     return total;
 }
+// a light: its transmittance pyramid and the (density, transmittance) pairs of the gathers
+size_t light_bytes(int n) {
+    size_t pairs = 0;
+    for (int sz = n;; sz = (sz + 1) / 2) {
+        pairs += (size_t)sz * sz * (sz + 1);
+        if (sz == 1) break;
+    }
+    return level_floats(n) * 4 + pairs * 16;
+}
 
 }  // namespace
 
@@ -245,7 +254,7 @@ nis_status prepare(nis_server *S, Req *q) {
             if ((rc = nis_build_transmittance(ctx, q->vol, q->r.light_dir, q->r.lambda, st, &q->light)))
                 return rc;
             LightEntry e;
-            e.h = q->light; e.refs = 1; e.last_use = ++S->tick; e.bytes = level_floats(q->r.n) * 4;
+            e.h = q->light; e.refs = 1; e.last_use = ++S->tick; e.bytes = light_bytes(q->r.n);
             S->lights[k] = e;
         }
     } else {

@@ -71,3 +71,23 @@ def test_static_refuses_what_it_cannot_do_without_allocating(setup):
     with pytest.raises(nis.NisError) as e:
         ctx.shade_points_static(v, l, w, other, x[:4], x[:4], x[:4])
     assert e.value.status == -2
+
+
+def test_static_refuses_a_light_older_than_the_pyramid(setup):
+    # a pyramid rebuild leaves the light's (density, transmittance) pairs stale: the static
+    # path refuses to re-pack them, a regular shading call re-packs them, after which the
+    # static path runs again
+    nis, ctx, v, l, w, mat = setup
+    dev = torch.device("cuda:0")
+    p, o = (torch.from_numpy(a).to(dev) for a in synth.shading_points(64, 18))
+    out = torch.empty((64, 3), dtype=torch.float32, device=dev)
+    ctx.build_pyramid(v)
+    ctx.sync(timeout_ms=60000)
+    with pytest.raises(nis.NisError) as e:
+        ctx.shade_points_static(v, l, w, mat, p, o, out)
+    assert e.value.status == -2
+    ref = ctx.shade_points(v, l, w, mat, p, o)
+    ctx.shade_points_static(v, l, w, mat, p, o, out)
+    ctx.sync(timeout_ms=60000)
+    # the static path's dense layers are FP32 FFMA, shade_points' the FP32 tensor split
+    assert _rel(out.cpu().numpy(), ref.cpu().numpy()).max() <= 1e-4
