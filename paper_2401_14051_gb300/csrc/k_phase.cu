@@ -48,49 +48,53 @@ __device__ float cap_mean(float gamma, float beta, const PhaseSpec &ph, const fl
 // l = (0, 0, -1) and omega = (sin alpha, 0, -cos alpha); the direction from the template
 // point toward p is n = -q/|q|, and f = capmean(n, l) * capmean(n, omega) (Eq. 8).  The
 // angles between n and l or omega come from atan2 of exact cross and dot products of q.
+// One CTA per (set, t): the light factor does not depend on alpha and is computed once,
+// the threads then sweep the 1024 view angles.
 __global__ void phase_table_kernel(const PhaseSpec ph, float *__restrict__ table) {
     __shared__ float az_s2[kAzim], az_c2[kAzim];
+    __shared__ float f_light;
     if (threadIdx.x < kAzim) {
         float h = sinpif((2.0f * threadIdx.x + 1.0f) / (2.0f * kAzim));   // sin(phi_j / 2)
         float c = cospif((2.0f * threadIdx.x + 1.0f) / (2.0f * kAzim));
         az_s2[threadIdx.x] = h * h;
         az_c2[threadIdx.x] = c * c;
     }
-    __syncthreads();
-    int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= kAlpha * kPhaseSets * kLat) return;
-    int t = idx % kLat, set = (idx / kLat) % kPhaseSets, a = idx / (kLat * kPhaseSets);
+    const int set = blockIdx.x / kLat, t = blockIdx.x % kLat;
     float qa = (float)(t / 45 - 2), qb = (float)((t / 9) % 5 - 2), qc = (float)(t % 9 - 4);
     if (set > 0) qc += 9.0f * ((set - 1) + 0.5f);
-    float r2 = qa * qa + qb * qb + qc * qc;
-    float val;
-    if (r2 == 0.f) {
-        val = 1.0f / (16.0f * 3.14159265358979f * 3.14159265358979f);
-    } else {
-        float r = sqrtf(r2);
-        float beta = atanf(0.5f / r);
-        float alpha = (float)a * (3.14159265358979f / (kAlpha - 1));
+    const float r2 = qa * qa + qb * qb + qc * qc;
+    float *col = table + (size_t)set * kLat + t;          // entry a at col[a * kPhaseSets * kLat]
+    if (r2 == 0.f) {                                      // the point itself: isotropic value
+        for (int a = threadIdx.x; a < kAlpha; a += blockDim.x)
+            col[(size_t)a * kPhaseSets * kLat] = 1.0f / (16.0f * 3.14159265358979f * 3.14159265358979f);
+        return;
+    }
+    const float r = sqrtf(r2);
+    const float beta = atanf(0.5f / r);
+    float k_g[3];
+    for (int i = 0; i < 3; ++i) k_g[i] = (1.0f - ph.g[i] * ph.g[i]) / (4.0f * 3.14159265358979f);
+    __syncthreads();                                      // azimuth tables ready
+    if (threadIdx.x == 0) {
+        // n . l = qc / r, |n x l| = sqrt(qa^2 + qb^2) / r
+        const float gam_l = atan2f(sqrtf(qa * qa + qb * qb), qc);
+        f_light = cap_mean(gam_l, beta, ph, k_g, az_s2, az_c2);
+    }
+    __syncthreads();
+    const float f_l = f_light;
+    for (int a = threadIdx.x; a < kAlpha; a += blockDim.x) {
+        const float alpha = (float)a * (3.14159265358979f / (kAlpha - 1));
         float sa, ca;
         sincosf(alpha, &sa, &ca);
-        float k_g[3];
-        for (int i = 0; i < 3; ++i) k_g[i] = (1.0f - ph.g[i] * ph.g[i]) / (4.0f * 3.14159265358979f);
-        // n . l = qc / r, |n x l| = sqrt(qa^2 + qb^2) / r
-        float gam_l = atan2f(sqrtf(qa * qa + qb * qb), qc);
         // n . omega = (qc cos a - qa sin a) / r, |n x omega|^2 = qb^2 + (qc sin a + qa cos a)^2
-        float cr = qc * sa + qa * ca;
-        float gam_w = atan2f(sqrtf(qb * qb + cr * cr), qc * ca - qa * sa);
-        float f_l = cap_mean(gam_l, beta, ph, k_g, az_s2, az_c2);
-        float f_w = cap_mean(gam_w, beta, ph, k_g, az_s2, az_c2);
-        val = f_l * f_w;
+        const float cr = qc * sa + qa * ca;
+        const float gam_w = atan2f(sqrtf(qb * qb + cr * cr), qc * ca - qa * sa);
+        col[(size_t)a * kPhaseSets * kLat] = f_l * cap_mean(gam_w, beta, ph, k_g, az_s2, az_c2);
     }
-    table[idx] = val;
 }
 
 void launch_phase_table(const PhaseSpec &ph, float *table, cudaStream_t s) {
-    const int threads = 256;
-    int total = kAlpha * kPhaseSets * kLat;
     note_launch();
-    phase_table_kernel<<<(total + threads - 1) / threads, threads, 0, s>>>(ph, table);
+    phase_table_kernel<<<kPhaseSets * kLat, 256, 0, s>>>(ph, table);
 }
 
 }  // namespace nis
