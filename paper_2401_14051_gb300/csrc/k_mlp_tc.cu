@@ -2,12 +2,13 @@
 // out = epilogue(A B^T) with A = activations [rows][K] and B = weights [N][K], both K-major,
 // FP32 accumulation in tensor memory.
 //
-// Persistent kernel, one CTA per SM, 10 warps:
+// Persistent kernel, one CTA per SM, 6 or 10 warps:
 //   warp 0     TMA producer: fills a ring of shared-memory stages, one K slab per stage
 //   warp 1     TMEM owner and MMA issuer: 128 x N_mma tcgen05.mma per 32-byte K slice,
 //              two accumulator buffers (columns 0 and 256) so the epilogue of one tile
 //              overlaps the MMAs of the next
-//   warps 2-9  epilogue: two warps per TMEM lane quarter, each thread one row of the tile;
+//   warps 2-   epilogue: one (FP32 split) or two (BF16, FP8) warps per TMEM lane quarter,
+//              each thread one row of the tile;
 //              reads 32 columns at a time, applies the layer's fused epilogue and stages
 //              the 32 x 32 result in shared memory, from where one lane writes it with a
 //              TMA store (rows of 128 contiguous bytes instead of one row per lane)
@@ -40,17 +41,25 @@ constexpr int STAGES3 = 2;
 constexpr uint32_t A_PART3 = TM * 64;                     // 8 KB
 constexpr uint32_t B_PART3 = TN_MAX * 64;                 // 13 KB
 constexpr uint32_t STAGE3 = 3 * A_PART3 + 3 * B_PART3;    // 63 KB
-constexpr int kEpiWarps = 8;                              // two per TMEM lane quarter
-constexpr int kThreads = 64 + 32 * kEpiWarps;
+// epilogue warps: 8 (two per TMEM lane quarter, alternate 32-column chunks) for BF16 and
+// FP8, whose epilogue is the bottleneck; 4 (one per quarter) for the FP32 split, where they
+// measured faster (more registers per thread, less L1 contention with the operand loads)
 // per epilogue warp, a staging buffer for the TMA stores of one 32 x 32 chunk: FP32 o1
 // (4 KB) + three BF16 parts of o2 (6 KB) with the split, o1 + o2 as BF16 (2 + 2 KB) without
 constexpr uint32_t STG_SPLIT = 10240, STG_ONE = 4096;
-constexpr uint32_t RING_STG_SPLIT = STAGES3 * STAGE3 + kEpiWarps * STG_SPLIT;
-constexpr uint32_t RING_STG_ONE = STAGES * (A_STAGE + B_STAGE) + kEpiWarps * STG_ONE;
-constexpr uint32_t SMEM_TILES = RING_STG_SPLIT > RING_STG_ONE ? RING_STG_SPLIT : RING_STG_ONE;
 constexpr uint32_t SMEM_CONST = 7 * TN_MAX * 4;          // per-column epilogue constants
-constexpr uint32_t SMEM_BYTES = SMEM_TILES + 256 + SMEM_CONST + 1024;  // + alignment slack
-static_assert(SMEM_BYTES <= 227 * 1024, "shared memory of tc_gemm_kernel");
+constexpr uint32_t PRE_BUF = 2 * 32 * 32 * 4;            // two FP32 32 x 32 residual chunks
+template <int EPI>
+__host__ __device__ constexpr uint32_t smem_tiles() {
+    // the residual buffers are used by the 4-warp (FP32 split) instantiation only
+    const uint32_t split = STAGES3 * STAGE3 + EPI * STG_SPLIT + (EPI == 4 ? EPI * PRE_BUF : 0);
+    const uint32_t one = STAGES * (A_STAGE + B_STAGE) + EPI * STG_ONE;
+    return split > one ? split : one;
+}
+template <int EPI>
+__host__ __device__ constexpr uint32_t smem_bytes() { return smem_tiles<EPI>() + 256 + SMEM_CONST + 1024; }  // + alignment slack
+static_assert(smem_bytes<8>() <= 227 * 1024 && smem_bytes<4>() <= 227 * 1024,
+              "shared memory of tc_gemm_kernel");
 static_assert((A_STAGE + B_STAGE) % 1024 == 0 && STAGE3 % 1024 == 0 && B_PART3 % 1024 == 0 &&
                   STG_SPLIT % 1024 == 0 && STG_ONE % 1024 == 0,
               "stages, parts and staging buffers must keep the 1024-byte swizzle-atom alignment");
@@ -276,10 +285,11 @@ __device__ __forceinline__ void load_pre(const TcGemmArgs &a, int r, int c0, flo
 }
 }  // namespace
 
-__global__ void __launch_bounds__(kThreads, 1)
+template <int EPI>
+__global__ void __launch_bounds__(64 + 32 * EPI, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                    const __grid_constant__ CUtensorMap map_o1, const __grid_constant__ CUtensorMap map_o2,
-                   const __grid_constant__ TcGemmArgs a) {
+                   const __grid_constant__ CUtensorMap map_pre, const __grid_constant__ TcGemmArgs a) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const bool split3 = a.n_pass > 1;              // three-part stages (FP32 split)
@@ -288,14 +298,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t b_off = split3 ? 3 * A_PART3 : A_STAGE;   // B's offset inside a stage
     uint8_t *staging = smem + n_stages * stage_bytes;          // epilogue warps' TMA staging
     const uint32_t stg_stride = split3 ? STG_SPLIT : STG_ONE;
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + SMEM_TILES);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + smem_tiles<EPI>());
     uint64_t *empty = full + STAGES;
     uint64_t *acc_full = empty + STAGES;
     uint64_t *acc_empty = acc_full + 2;
     uint64_t *drain = acc_empty + 2;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    uint64_t *pre_full = drain + 1;           // [EPI][2] residual-chunk barriers
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(pre_full + 2 * EPI);
     int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
-    float *s_bias = reinterpret_cast<float *>(smem + SMEM_TILES + 256);
+    float *s_bias = reinterpret_cast<float *>(smem + smem_tiles<EPI>() + 256);
     float *s_wa = s_bias + TN_MAX;
     float *s_wm = s_wa + TN_MAX;              // [TN_MAX][4] weights of g and albedo (mixed)
     float *s_ws = s_wm + 4 * TN_MAX;          // FP8 weight scales
@@ -315,12 +326,14 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < n_stages; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
-        for (int b = 0; b < 2; ++b) { tc::mbar_init(&acc_full[b], 1); tc::mbar_init(&acc_empty[b], kEpiWarps); }
+        for (int b = 0; b < 2; ++b) { tc::mbar_init(&acc_full[b], 1); tc::mbar_init(&acc_empty[b], EPI); }
         tc::mbar_init(drain, 1);
+        for (int i = 0; i < 2 * EPI; ++i) tc::mbar_init(&pre_full[i], 1);
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
     if (warp == 0 && lane == 0) { tc::prefetch_tmap(&map_a); tc::prefetch_tmap(&map_b); }
+    if (warp == 3 && lane == 0 && EPI == 4 && a.pre_tma) tc::prefetch_tmap(&map_pre);
     if (warp == 2 && lane == 0 && a.o1_kind != kOutDirect) {
         tc::prefetch_tmap(&map_o1);
         if (a.o2_kind != kOutDirect) tc::prefetch_tmap(&map_o2);
@@ -457,10 +470,26 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else {
         const int q = warp & 3;                        // TMEM lane quarter of this warp
-        const int half = (warp - 2) >> 2;              // which 32-column chunks this warp takes
+        // which 32-column chunks this warp takes: every one (EPI 4) or every other (EPI 8)
+        const int half = EPI == 8 ? (warp - 2) >> 2 : 0;
+        constexpr int kStride = EPI == 8 ? 64 : 32;
         const bool staged = a.o1_kind != kOutDirect;
         uint8_t *stg = staging + (warp - 2) * stg_stride;
         const uint32_t o2_off = a.o1_kind == kOutF32 ? 4096u : 2048u * (uint32_t)a.o1_parts;
+        // FP32 split: each 32 x 32 residual chunk arrives by TMA, two chunks ahead, in one of
+        // this warp's two buffers (128-byte swizzle: unit j of row r at unit j ^ (r mod 8))
+        const bool pre_tma = EPI == 4 && a.pre_tma;
+        uint8_t *pbuf = staging + EPI * stg_stride + (warp - 2) * PRE_BUF;
+        uint64_t *pbar = pre_full + 2 * (warp - 2);
+        uint32_t pre_issued = 0, pre_used = 0;
+        auto issue_pre = [&](int c0, int row0) {
+            const int b = pre_issued & 1;
+            if (lane == 0) {
+                tc::mbar_expect_tx(&pbar[b], 32 * 32 * 4);
+                tc::tma_load_3d(pbuf + b * 4096, &map_pre, c0, row0, 0, &pbar[b]);
+            }
+            ++pre_issued;
+        };
         int t = 0;
         for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++t) {
             const int buf = t & 1;
@@ -477,7 +506,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             float pre[32];
 #pragma unroll
             for (int i = 0; i < 32; ++i) pre[i] = 0.f;
-            if (live && half * 32 < a.N) load_pre(a, r, half * 32, pre);
+            const int row0 = tile * TM + q * 32;
+            if (pre_tma) {
+                issue_pre(0, row0);
+                if (32 < a.N) issue_pre(32, row0);
+            } else if (live && half * 32 < a.N) {
+                load_pre(a, r, half * 32, pre);
+            }
             bool ok = tc::mbar_wait(&acc_full[buf], (t >> 1) & 1);
             if (!ok || *(volatile int *)abort_flag) {
                 if (!ok && lane == 0) record_timeout(a.err, abort_flag);
@@ -485,14 +520,33 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             tc::fence_after_sync();
             const uint32_t lane_addr = tmem_base + buf * 256 + ((uint32_t)(q * 32) << 16);
-            for (int c0 = half * 32; c0 < a.N; c0 += 64) {
+            for (int c0 = half * 32; c0 < a.N; c0 += kStride) {
                 float v[32];
                 tc::tmem_ld32(lane_addr + c0, v);
                 float cur[32];
+                if (pre_tma) {
+                    const int b = pre_used & 1;
+                    const uint32_t ph = (pre_used >> 1) & 1;
+                    ++pre_used;
+                    if (!tc::mbar_wait(&pbar[b], ph)) {
+                        if (lane == 0) record_timeout(a.err, abort_flag);
+                        ok = false;
+                        break;
+                    }
+                    const uint8_t *src = pbuf + b * 4096 + lane * 128;
 #pragma unroll
-                for (int i = 0; i < 32; ++i) cur[i] = pre[i];
-                // next chunk's residual loads overlap this chunk's TMEM load and math
-                if (live && c0 + 64 < a.N) load_pre(a, r, c0 + 64, pre);
+                    for (int j = 0; j < 8; ++j) {
+                        const float4 f = *reinterpret_cast<const float4 *>(src + ((j ^ (lane & 7)) << 4));
+                        cur[4 * j] = f.x; cur[4 * j + 1] = f.y; cur[4 * j + 2] = f.z; cur[4 * j + 3] = f.w;
+                    }
+                    __syncwarp();                      // every lane has read buffer b
+                    if (c0 + 64 < a.N) issue_pre(c0 + 64, row0);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) cur[i] = pre[i];
+                    // next chunk's residual loads overlap this chunk's TMEM load and math
+                    if (live && c0 + kStride < a.N) load_pre(a, r, c0 + kStride, pre);
+                }
                 tc::tmem_ld_wait();
                 float sv[32];
                 epilogue_math(a, c0, v, sv, s_bias, s_wa, sc, alpha, cur, s_wm, rc, s_ws);
@@ -505,17 +559,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tc::fence_async_smem();
                     __syncwarp();
                     if (lane == 0) {
-                        const int row0 = tile * TM + q * 32;
                         tc::tma_store_3d(&map_o1, stg, c0, row0, 0);
                         if (a.o2_kind != kOutDirect) tc::tma_store_3d(&map_o2, stg + o2_off, c0, row0, 0);
                         tc::bulk_commit();
                     }
                 }
             }
+            if (!ok) break;
             tc::fence_before_sync();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&acc_empty[buf]);
         }
+        // residual loads still in flight (after a time-out) land before the CTA exits
+        for (; pre_used < pre_issued; ++pre_used)
+            tc::mbar_wait(&pbar[pre_used & 1], (pre_used >> 1) & 1, 1u << 16);
         if (staged && lane == 0) tc::bulk_wait();     // every store of this warp has landed
     }
     __syncthreads();
@@ -570,19 +627,23 @@ void launch_pack_fp8(const float *src, int N, int K, int ld_src, uint8_t *dst, f
 }
 
 void launch_tc_gemm(const TcGemmArgs &a, const CUtensorMap &map_a, const CUtensorMap &map_b,
-                    int num_sms, cudaStream_t s, const CUtensorMap *map_o1, const CUtensorMap *map_o2) {
+                    int num_sms, cudaStream_t s, const CUtensorMap *map_o1, const CUtensorMap *map_o2,
+                    const CUtensorMap *map_pre) {
     static const CUtensorMap unused{};            // stands in for outputs written directly
     if (a.M <= 0) return;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+        cudaFuncSetAttribute(tc_gemm_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<4>());
+        cudaFuncSetAttribute(tc_gemm_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<8>());
         attr_set = true;
     }
     int tiles = (a.M + TM - 1) / TM;
     int grid = tiles < num_sms ? tiles : num_sms;
     note_launch();
-    tc_gemm_kernel<<<grid, kThreads, SMEM_BYTES, s>>>(map_a, map_b, map_o1 ? *map_o1 : unused,
-                                                      map_o2 ? *map_o2 : unused, a);
+    const CUtensorMap &o1 = map_o1 ? *map_o1 : unused, &o2 = map_o2 ? *map_o2 : unused;
+    const CUtensorMap &pr = map_pre ? *map_pre : unused;
+    if (a.n_pass > 1) tc_gemm_kernel<4><<<grid, 64 + 32 * 4, smem_bytes<4>(), s>>>(map_a, map_b, o1, o2, pr, a);
+    else tc_gemm_kernel<8><<<grid, 64 + 32 * 8, smem_bytes<8>(), s>>>(map_a, map_b, o1, o2, pr, a);
 }
 
 }  // namespace nis

@@ -717,14 +717,16 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
     for (int c = 0; c < 3; ++c) dec_scale[c] = m->intensity[c] * powf(m->albedo[c], 4.0f);
     // o1 / o2: the epilogue's output maps (TMA stores); null writes through the pointers
     auto gemm = [&](TcGemmArgs a, const CUtensorMap &ma, const CUtensorMap &mb,
-                    const CUtensorMap *o1 = nullptr, const CUtensorMap *o2 = nullptr) {
+                    const CUtensorMap *o1 = nullptr, const CUtensorMap *o2 = nullptr,
+                    const CUtensorMap *pre = nullptr) {
         a.n_pass = split ? 6 : 1;
         a.k_tiles = (a.K + (int)tc_box_k(P) - 1) / (int)tc_box_k(P);
         a.a_part_rows = (int)cap;
         a.b_part_rows = a.n_mma;
         a.out_split = split ? 1 : 0;
         ProfScope ps(ctx, "mlp", s);
-        launch_tc_gemm(a, ma, mb, ctx->num_sms, s, o1, o2);
+        a.pre_tma = pre != nullptr;
+        launch_tc_gemm(a, ma, mb, ctx->num_sms, s, o1, o2, pre);
     };
     const int k_e = split ? kOutF32 : kOutBf16;     // kind of e and h
     for (int off = 0; off < n; off += chunk) {
@@ -786,7 +788,10 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
                     f1.h_prev = (k == k0 || split) ? nullptr : w.H; f1.ld_h = kWidth;
                     f1.pre_f32 = (k == k0 || !split) ? nullptr : w.H32; f1.ld_pre = kWidth;
                     f1.o1_kind = k_e; f1.o1_parts = 1; f1.o2_kind = kOutBf16; f1.o2_parts = P;
-                    gemm(f1, fmap, wt.map_fc1[t][k], &w.out_e, &w.out_s);
+                    // with the split, the running state h arrives by TMA (the e and h output
+                    // maps read back as 32 x 32 FP32 boxes)
+                    gemm(f1, fmap, wt.map_fc1[t][k], &w.out_e, &w.out_s,
+                         split && f1.pre_f32 ? &w.out_h : nullptr);
                     TcGemmArgs f2{};
                     f2.M = cnt; f2.N = kWidth; f2.K = kWidth; f2.n_mma = 208; f2.k_tiles = 4;
                     f2.epi = kEpiFc2; f2.err = ctx->d_err;
@@ -803,7 +808,8 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
                     }
                     const bool end = k == k1 - 1;
                     f2.o1_kind = end ? kOutBf16 : k_e; f2.o1_parts = end ? P : 1;
-                    gemm(f2, w.map_s, wt.map_fc2[t][k], end ? &w.out_mrg[t][chain] : &w.out_h);
+                    gemm(f2, w.map_s, wt.map_fc2[t][k], end ? &w.out_mrg[t][chain] : &w.out_h, nullptr,
+                         split ? &w.out_e : nullptr);
                 }
             }
             TcGemmArgs mg{};

@@ -321,6 +321,9 @@ struct TcGemmArgs {
     // instead of the pointers above: o1 = the layer's output (FC-1: e), o2 = FC-1's s.
     // Kind kOutDirect uses the pointers; parts = 3 writes the three BF16 parts of a split.
     int o1_kind, o1_parts, o2_kind, o2_parts;
+    // FP32 split: pre_f32 read through TMA (kernel argument map_pre, [1][rows][N] FP32 with
+    // 32 x 32 boxes) instead of one row per lane
+    int pre_tma;
 };
 constexpr int kOutDirect = 0, kOutF32 = 1, kOutBf16 = 2;
 constexpr int kLatPad8 = 240;        // FP8 feature row per layer, padded to 16 bytes
@@ -331,7 +334,7 @@ void launch_fill_segments(const int *seg_start, const int *seg_desc, int nseg, i
                           cudaStream_t s);
 void launch_tc_gemm(const TcGemmArgs &a, const CUtensorMap &map_a, const CUtensorMap &map_b,
                     int num_sms, cudaStream_t s, const CUtensorMap *map_o1 = nullptr,
-                    const CUtensorMap *map_o2 = nullptr);
+                    const CUtensorMap *map_o2 = nullptr, const CUtensorMap *map_pre = nullptr);
 // K width of a BF16 tensor-core box: 64 elements (128-byte swizzle) for one part, 32 (64-byte
 // swizzle) for the three parts of the FP32 split, whose stage holds every part at once.
 inline uint32_t tc_box_k(int parts) { return parts > 1 ? 32 : 64; }
