@@ -36,10 +36,11 @@ namespace {
 constexpr int TM = 128, TK = 64, TN_MAX = 208, STAGES = 4;
 constexpr uint32_t A_STAGE = TM * TK * 2;                 // 16 KB
 constexpr uint32_t B_STAGE = TN_MAX * TK * 2;             // 26 KB (208 rows)
-// three-part stages: 64-byte rows (32 BF16 of K)
-constexpr int STAGES3 = 2;
-constexpr uint32_t A_PART3 = TM * 64;                     // 8 KB
-constexpr uint32_t B_PART3 = TN_MAX * 64;                 // 13 KB
+// three-part stages: rows of kSplitSlabK BF16 of K (64 bytes: 64-byte swizzle)
+constexpr uint32_t ROW3 = kSplitSlabK * 2;
+constexpr int STAGES3 = kSplitSlabK == 16 ? 4 : 2;
+constexpr uint32_t A_PART3 = TM * ROW3;                   // 8 KB
+constexpr uint32_t B_PART3 = TN_MAX * ROW3;               // 13 KB
 constexpr uint32_t STAGE3 = 3 * A_PART3 + 3 * B_PART3;    // 63 KB
 // epilogue warps: 8 (two per TMEM lane quarter, alternate 32-column chunks) for BF16 and
 // FP8, whose epilogue is the bottleneck; 4 (one per quarter) for the FP32 split, where they
@@ -60,13 +61,18 @@ template <int EPI>
 __host__ __device__ constexpr uint32_t smem_bytes() { return smem_tiles<EPI>() + 256 + SMEM_CONST + 1024; }  // + alignment slack
 static_assert(smem_bytes<8>() <= 227 * 1024 && smem_bytes<4>() <= 227 * 1024,
               "shared memory of tc_gemm_kernel");
-static_assert((A_STAGE + B_STAGE) % 1024 == 0 && STAGE3 % 1024 == 0 && B_PART3 % 1024 == 0 &&
-                  STG_SPLIT % 1024 == 0 && STG_ONE % 1024 == 0,
+static_assert((A_STAGE + B_STAGE) % 1024 == 0 && STAGE3 % 256 == 0 && B_PART3 % 256 == 0 &&
+                  (STAGES3 * STAGE3) % 1024 == 0 && STG_SPLIT % 1024 == 0 && STG_ONE % 1024 == 0,
               "stages, parts and staging buffers must keep the 1024-byte swizzle-atom alignment");
 
 __device__ __forceinline__ void record_timeout(unsigned *err, int *abort_flag) {
     *abort_flag = 1;
     if (err) atomicOr(err, kErrTimeout);
+}
+
+// Shared-memory descriptor of a split stage's operand rows.
+__device__ __forceinline__ uint64_t split_desc(uint32_t saddr) {
+    return kSplitSlabK == 16 ? tc::smem_desc_sw32(saddr) : tc::smem_desc_sw64(saddr);
 }
 
 // Six products of the three-way split, small to large: (A part, B part).
@@ -314,14 +320,14 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_tiles = (a.M + TM - 1) / TM;
     const int n_mma = a.n_mma;
-    const uint32_t slab_tx = A_PART3 + (uint32_t)n_mma * 64;        // one part of A and of B
+    const uint32_t slab_tx = A_PART3 + (uint32_t)n_mma * ROW3;      // one part of A and of B
     const uint32_t stage_tx = split3 ? 3 * slab_tx : A_STAGE + (uint32_t)n_mma * TK * 2;
     // stages per tile: one per K slab; the split adds a second sweep of A0 B0, three slabs
     // per stage
     const int n_sweep1 = a.k_tiles;
     const int n_steps = split3 ? n_sweep1 + (a.k_tiles + 2) / 3 : a.k_tiles;
     const uint32_t idesc = a.fp8 ? tc::idesc_e4m3_f32(TM, n_mma) : tc::idesc_bf16_f32(TM, n_mma);
-    const int tk = split3 ? 32 : (a.fp8 ? 128 : TK);   // K elements per stage row
+    const int tk = split3 ? kSplitSlabK : (a.fp8 ? 128 : TK);   // K elements per stage row
     const int kslice = a.fp8 ? 32 : 16;                // K elements per MMA (32 bytes)
 
     if (threadIdx.x == 0) {
@@ -445,8 +451,8 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
                             const uint32_t pa = a_addr + kPassA[p] * A_PART3;
                             const uint32_t pb = b_addr + kPassB[p] * B_PART3;
                             for (int k = 0; k < n_sl; ++k)
-                                tc::mma_f16(d_tmem, tc::smem_desc_sw64(pa + k * 32),
-                                            tc::smem_desc_sw64(pb + k * 32), idesc, (step | p | k) != 0);
+                                tc::mma_f16(d_tmem, split_desc(pa + k * 32), split_desc(pb + k * 32), idesc,
+                                            (step | p | k) != 0);
                         }
                     } else {
                         // second sweep: the leading product A0 B0 on top
@@ -455,8 +461,8 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
                         for (int j = 0; j < nb; ++j) {
                             const int n_sl = slices(j0 + j);
                             for (int k = 0; k < n_sl; ++k)
-                                tc::mma_f16(d_tmem, tc::smem_desc_sw64(a_addr + j * A_PART3 + k * 32),
-                                            tc::smem_desc_sw64(b_addr + j * B_PART3 + k * 32), idesc, 1);
+                                tc::mma_f16(d_tmem, split_desc(a_addr + j * A_PART3 + k * 32),
+                                            split_desc(b_addr + j * B_PART3 + k * 32), idesc, 1);
                         }
                     }
                     tc::mma_commit(&empty[s]);

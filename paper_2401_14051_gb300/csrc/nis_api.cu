@@ -91,7 +91,15 @@ struct Workspace {                    // scratch of nis_shade_points, grow-only
     int *host_count = nullptr;        // pinned
 };
 constexpr int kActBufs = 15;          // e, h0, h1, 6 chain ends, 3 merges, z1, z2, spare
-constexpr int kChunk = 65536;         // shading points per pipeline pass
+constexpr int kChunk = 65536;         // shading points per pipeline pass, at most
+// Points per pass for n points: the passes share n equally (rounded up to whole 128-row
+// tensor-core tiles), so that no pass is a small remainder that leaves most SMs idle.
+int pass_size(int n) {
+    if (n <= kChunk) return n;
+    const int passes = (n + kChunk - 1) / kChunk;
+    const int per = (n + passes - 1) / passes;
+    return (per + 127) / 128 * 128;
+}
 
 }  // namespace
 
@@ -583,7 +591,7 @@ nis_status shade_impl(nis_ctx *ctx, const Volume &vol, const Light &light, const
         return shade_impl_fp8(ctx, vol, light, wt, m, table, pts, om, n, rgb, dbg, s, mx);
     if (wt.precision != NIS_PREC_F32_SIMT)
         return shade_impl_bf16(ctx, vol, light, wt, m, table, pts, om, n, rgb, dbg, s, mx);
-    int chunk = n < kChunk ? n : kChunk;
+    int chunk = pass_size(n);
     if ((st = ensure_workspace(ctx, chunk, s))) return st;
     Workspace &w = ctx->ws;
     const WeightOffsets &o = wt.off;
@@ -704,7 +712,7 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
                            const nis_material *m, const float *table, const float *pts,
                            const float *om, int n, float *rgb, const nis_debug_out *dbg,
                            cudaStream_t s, const Mixed *mx) {
-    int chunk = n < kChunk ? n : kChunk;
+    int chunk = pass_size(n);
     const bool split = wt.precision == NIS_PREC_F32;
     WorkspaceBf &w = split ? ctx->wsx : ctx->wsb;
     const int P = split ? 3 : 1;
@@ -860,7 +868,7 @@ nis_status shade_impl_fp8(nis_ctx *ctx, const Volume &vol, const Light &light, c
                           const nis_material *m, const float *table, const float *pts,
                           const float *om, int n, float *rgb, const nis_debug_out *dbg,
                           cudaStream_t s, const Mixed *mx) {
-    int chunk = n < kChunk ? n : kChunk;
+    int chunk = pass_size(n);
     nis_status st = ensure_workspace_fp8(ctx, chunk, s);
     if (st) return st;
     WorkspaceF8 &w = ctx->ws8;
@@ -1090,7 +1098,7 @@ bool make_tmap_u8(CUtensorMap *map, const void *base, uint64_t inner, uint64_t o
 bool make_tmap_bf16(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer,
                     uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer) {
     EncodeTiledFn fn = encode_tiled();
-    if (box_inner != 32 && box_inner != 64) return false;   // 64- or 128-byte swizzled rows
+    if (box_inner != 16 && box_inner != 32 && box_inner != 64) return false;   // swizzled rows
     if (!fn || (reinterpret_cast<uintptr_t>(base) & 15) || (row_bytes & 15)) return false;
     cuuint64_t dims[2] = {inner, outer};
     cuuint64_t strides[1] = {row_bytes};
@@ -1098,7 +1106,8 @@ bool make_tmap_bf16(CUtensorMap *map, const void *base, uint64_t inner, uint64_t
     cuuint32_t estr[2] = {1, 1};
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box,
               estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-              box_inner * 2 == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+              box_inner == 16 ? CU_TENSOR_MAP_SWIZZLE_32B
+                              : (box_inner == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B),
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 

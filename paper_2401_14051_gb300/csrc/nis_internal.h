@@ -335,11 +335,14 @@ void launch_fill_segments(const int *seg_start, const int *seg_desc, int nseg, i
 void launch_tc_gemm(const TcGemmArgs &a, const CUtensorMap &map_a, const CUtensorMap &map_b,
                     int num_sms, cudaStream_t s, const CUtensorMap *map_o1 = nullptr,
                     const CUtensorMap *map_o2 = nullptr, const CUtensorMap *map_pre = nullptr);
-// K width of a BF16 tensor-core box: 64 elements (128-byte swizzle) for one part, 32 (64-byte
-// swizzle) for the three parts of the FP32 split, whose stage holds every part at once.
-inline uint32_t tc_box_k(int parts) { return parts > 1 ? 32 : 64; }
-// 2-D BF16 tensor map, inner dimension contiguous, box = box_inner x box_outer; box_inner 64
-// gives 128-byte swizzled rows, 32 gives 64-byte swizzled rows (other widths are refused).
+// K width of a BF16 tensor-core box: 64 elements (128-byte swizzle) for one part,
+// kSplitSlabK for the three parts of the FP32 split, whose stage holds every part of a slab
+// at once: 32 (64-byte swizzle, two 63 KB stages); 16 (32-byte swizzle, four 31.5 KB
+// stages) is supported and measured 14% slower.
+constexpr int kSplitSlabK = 32;
+inline uint32_t tc_box_k(int parts) { return parts > 1 ? kSplitSlabK : 64; }
+// 2-D BF16 tensor map, inner dimension contiguous, box = box_inner x box_outer; box_inner 64,
+// 32 or 16 gives 128-, 64- or 32-byte swizzled rows (other widths are refused).
 bool make_tmap_bf16(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer,
                     uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer);
 // 3-D output map of the tensor-core epilogue: [parts][rows][cols] FP32 (f32 = true, 128-byte
