@@ -7,35 +7,35 @@ namespace nis {
 // T_m(x) = exp(-lam^(m+1) * sum of midpoint samples), step 1/n from x to the cube exit,
 // the last step partial; the march stops once the scaled optical depth passes kTauMax.
 // Neighbouring threads own x-neighbouring voxels, so their rays run parallel one voxel
-// apart and their trilinear loads hit the same cache lines.  Samples in empty bricks cost
-// one byte load instead of eight (exact empty-space skipping: the positions, the sums and
-// the stop rule are unchanged).
-// Trilinear clamp-to-edge sample that skips the eight loads when the cell's brick is empty
-// (exact: all eight corners are zero there).
-__device__ __forceinline__ float sample_clamped_occ(const float *__restrict__ g,
-                                                    const unsigned char *__restrict__ occ, int nb,
-                                                    int n, float x, float y, float z) {
-    const float hi = (float)(n - 1);
-    float gx = fminf(fmaxf(x * n - 0.5f, 0.0f), hi);
-    float gy = fminf(fmaxf(y * n - 0.5f, 0.0f), hi);
-    float gz = fminf(fmaxf(z * n - 0.5f, 0.0f), hi);
-    const int top = n > 1 ? n - 2 : 0;
-    int ix = min((int)floorf(gx), top), iy = min((int)floorf(gy), top), iz = min((int)floorf(gz), top);
-    if (!__ldg(occ + ((size_t)(iz / kBrick) * nb + iy / kBrick) * nb + ix / kBrick)) return 0.f;
-    float fx = gx - ix, fy = gy - iy, fz = gz - iz;
-    int dx = (ix + 1 < n) ? 1 : 0;
-    int dy = (iy + 1 < n) ? n : 0;
-    int dz = (iz + 1 < n) ? n * n : 0;
-    const float *p = g + ((size_t)iz * n + iy) * n + ix;
-    float c00 = __ldg(p) + fx * (__ldg(p + dx) - __ldg(p));
-    float c01 = __ldg(p + dy) + fx * (__ldg(p + dy + dx) - __ldg(p + dy));
-    float c10 = __ldg(p + dz) + fx * (__ldg(p + dz + dx) - __ldg(p + dz));
-    float c11 = __ldg(p + dz + dy) + fx * (__ldg(p + dz + dy + dx) - __ldg(p + dz + dy));
-    float c0 = c00 + fy * (c01 - c00);
-    float c1 = c10 + fy * (c11 - c10);
+// apart and their trilinear loads hit the same cache lines.  The march is bound by its
+// instruction count, so a sample is computed in grid units: sample s of the ray from voxel
+// (i, j, k) sits at g = (i, j, k) + u (s + 1/2) (g = x n - 1/2), clamped to the grid; a cell
+// flagged empty in the occupancy (all eight corners zero) costs one byte load instead of
+// eight.  The positions, the sums and the stop rule are those of the midpoint rule.
+template <typename Index>
+__device__ __forceinline__ float sample_cell(const float *__restrict__ g,
+                                             const unsigned char *__restrict__ occ, Index n,
+                                             float hi, float top, Index d1, Index dn, Index dnn,
+                                             float gx, float gy, float gz) {
+    gx = fminf(fmaxf(gx, 0.0f), hi);
+    gy = fminf(fmaxf(gy, 0.0f), hi);
+    gz = fminf(fmaxf(gz, 0.0f), hi);
+    const float flx = fminf(floorf(gx), top), fly = fminf(floorf(gy), top), flz = fminf(floorf(gz), top);
+    const Index idx = ((Index)flz * n + (Index)fly) * n + (Index)flx;
+    if (!__ldg(occ + idx)) return 0.f;
+    const float fx = gx - flx, fy = gy - fly, fz = gz - flz;
+    const float *p = g + idx;
+    const float v0 = __ldg(p), v1 = __ldg(p + d1), v2 = __ldg(p + dn), v3 = __ldg(p + dn + d1);
+    const float v4 = __ldg(p + dnn), v5 = __ldg(p + dnn + d1), v6 = __ldg(p + dnn + dn),
+                v7 = __ldg(p + dnn + dn + d1);
+    const float c00 = v0 + fx * (v1 - v0), c01 = v2 + fx * (v3 - v2);
+    const float c10 = v4 + fx * (v5 - v4), c11 = v6 + fx * (v7 - v6);
+    const float c0 = c00 + fy * (c01 - c00), c1 = c10 + fy * (c11 - c10);
     return c0 + fz * (c1 - c0);
 }
 
+// Index: 32-bit for levels up to 1024^3 (2^30 voxels), 64-bit beyond.
+template <typename Index>
 __global__ void __launch_bounds__(256) march_kernel(const float *__restrict__ level,
                                                     const unsigned char *__restrict__ occ, int n,
                                                     float ux, float uy, float uz, float scale,
@@ -52,17 +52,22 @@ __global__ void __launch_bounds__(256) march_kernel(const float *__restrict__ le
     float sum = 0.f;
     const float limit = kTauMax / scale;     // stop rule on the unscaled sum
     bool stopped = false;
-    const int nb = bricks_of(n);
+    // corner offsets of a cell (a 1^3 level has one voxel: all corners are that voxel)
+    const Index N = (Index)n, d1 = n > 1 ? 1 : 0, dn = n > 1 ? N : 0, dnn = n > 1 ? N * N : 0;
+    const float hi = (float)(n - 1), top = (float)(n > 1 ? n - 2 : 0);
+    const float fi = (float)i, fj = (float)j, fk = (float)k;
     for (int s = 0; s < steps; ++s) {
-        float t = (s + 0.5f) * inv_n;
-        sum += sample_clamped_occ(level, occ, nb, n, x + ux * t, y + uy * t, z + uz * t) * inv_n;
+        const float a = s + 0.5f;
+        sum += sample_cell<Index>(level, occ, N, hi, top, d1, dn, dnn, fmaf(ux, a, fi), fmaf(uy, a, fj),
+                                  fmaf(uz, a, fk)) * inv_n;
         if (sum > limit) { stopped = true; break; }
     }
     if (!stopped) {
         float rest = d - nfull * inv_n;
         if (rest > 0.f) {
-            float t = nfull * inv_n + 0.5f * rest;
-            sum += sample_clamped_occ(level, occ, nb, n, x + ux * t, y + uy * t, z + uz * t) * rest;
+            const float a = nfull + 0.5f * rest * n;
+            sum += sample_cell<Index>(level, occ, N, hi, top, d1, dn, dnn, fmaf(ux, a, fi),
+                                      fmaf(uy, a, fj), fmaf(uz, a, fk)) * rest;
         }
     }
     out[idx] = expf(-scale * sum);
@@ -75,7 +80,10 @@ void launch_march(const float *level, const unsigned char *occ, int n, int m, fl
     const int threads = 256;
     unsigned blocks = (unsigned)((total + threads - 1) / threads);
     note_launch();
-    march_kernel<<<blocks, threads, 0, s>>>(level, occ, n, ux, uy, uz, scale, out);
+    if (n <= 1024)
+        march_kernel<unsigned><<<blocks, threads, 0, s>>>(level, occ, n, ux, uy, uz, scale, out);
+    else
+        march_kernel<size_t><<<blocks, threads, 0, s>>>(level, occ, n, ux, uy, uz, scale, out);
 }
 
 }  // namespace nis

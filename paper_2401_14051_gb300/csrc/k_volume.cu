@@ -75,27 +75,24 @@ void launch_downsample(const float *src, int n, float *dst, int m, cudaStream_t 
 }
 
 __global__ void occupancy_kernel(const float *__restrict__ level, int n, unsigned char *occ) {
-    const int nb = bricks_of(n);
-    size_t total = (size_t)nb * nb * nb;
+    const size_t total = (size_t)n * n * n;
+    const size_t nn = (size_t)n * n;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
-        int bx = (int)(idx % nb), by = (int)((idx / nb) % nb), bz = (int)(idx / ((size_t)nb * nb));
-        int x0 = max(bx * kBrick - 1, 0), x1 = min(bx * kBrick + kBrick, n - 1);
-        int y0 = max(by * kBrick - 1, 0), y1 = min(by * kBrick + kBrick, n - 1);
-        int z0 = max(bz * kBrick - 1, 0), z1 = min(bz * kBrick + kBrick, n - 1);
-        unsigned char any = 0;
-        for (int z = z0; z <= z1 && !any; ++z)
-            for (int y = y0; y <= y1 && !any; ++y)
-                for (int x = x0; x <= x1; ++x)
-                    if (__ldg(level + ((size_t)z * n + y) * n + x) != 0.f) { any = 1; break; }
-        occ[idx] = any;
+        const int i = (int)(idx % n), j = (int)((idx / n) % n), k = (int)(idx / nn);
+        const size_t dx = i + 1 < n ? 1 : 0, dy = j + 1 < n ? (size_t)n : 0, dz = k + 1 < n ? nn : 0;
+        const float *p = level + idx;
+        const bool any = __ldg(p) != 0.f || __ldg(p + dx) != 0.f || __ldg(p + dy) != 0.f ||
+                         __ldg(p + dy + dx) != 0.f || __ldg(p + dz) != 0.f ||
+                         __ldg(p + dz + dx) != 0.f || __ldg(p + dz + dy) != 0.f ||
+                         __ldg(p + dz + dy + dx) != 0.f;
+        occ[idx] = any ? 1 : 0;
     }
 }
 
 void launch_occupancy(const float *level, int n, unsigned char *occ, cudaStream_t s) {
-    const int nb = bricks_of(n);
-    size_t total = (size_t)nb * nb * nb;
-    int blocks = (int)((total + 255) / 256 < 152 * 16 ? (total + 255) / 256 : 152 * 16);
+    const size_t total = (size_t)n * n * n;
+    int blocks = (int)((total + 255) / 256 < 152 * 32 ? (total + 255) / 256 : 152 * 32);
     note_launch();
     occupancy_kernel<<<blocks, 256, 0, s>>>(level, n, occ);
 }

@@ -240,8 +240,8 @@ nis_status build_pyramid_impl(nis_ctx *ctx, Volume &v, cudaStream_t s) {
         size_t total = 0;
         for (int m = 0; m < v.levels; ++m) {
             v.occ_off[m] = total;
-            size_t nb = (size_t)bricks_of(v.sizes[m]);
-            total += nb * nb * nb;
+            const size_t n = (size_t)v.sizes[m];
+            total += n * n * n;
         }
         nis_status st = dev_alloc_t(ctx, total, &v.occ, s);
         if (st) return st;

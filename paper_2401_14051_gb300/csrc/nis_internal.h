@@ -163,10 +163,8 @@ void launch_convert_density(const void *src, int dtype, float scale, size_t coun
 void launch_downsample(const float *src, int n, float *dst, int m, cudaStream_t s);
 // one PairView level of size n from the density and transmittance levels
 void launch_pack_pairs(const float *rho, const float *T, int n, float4 *out, cudaStream_t s);
-// occupancy of 4^3-voxel bricks of an n^3 level, dilated by one voxel: occ = 0 guarantees
-// that every trilinear cell whose base voxel lies in the brick has eight zero corners
-constexpr int kBrick = 4;
-__host__ __device__ inline int bricks_of(int n) { return (n + kBrick - 1) / kBrick; }
+// occupancy of the trilinear cells of an n^3 level, one byte per base voxel (i, j, k):
+// occ = 0 guarantees that the cell's corners (i..min(i+1, n-1), likewise j, k) are all zero
 void launch_occupancy(const float *level, int n, unsigned char *occ, cudaStream_t s);
 // transmittance of one level
 void launch_march(const float *level, const unsigned char *occ, int n, int m, float ux,
