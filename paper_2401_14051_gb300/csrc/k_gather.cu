@@ -16,6 +16,11 @@ __global__ void __launch_bounds__(kLayers * 32) gather_kernel(const __grid_const
     const int p = blockIdx.x;
     const int k = threadIdx.x >> 5;            // one warp per template layer
     const int lane = threadIdx.x & 31;
+    // lattice offsets (a, b, c) of the 225 template points, in spacings
+    __shared__ float4 s_lat[kLat];
+    for (int t = threadIdx.x; t < kLat; t += blockDim.x)
+        s_lat[t] = make_float4((float)(t / 45 - 2), (float)((t / 9) % 5 - 2), (float)(t % 9 - 4), 0.f);
+    __syncthreads();
 
     // single request, or this point's request in a mixed batch
     const ReqDesc *d = a.descs ? a.descs + a.req_of_point[p] : nullptr;
@@ -90,7 +95,8 @@ __global__ void __launch_bounds__(kLayers * 32) gather_kernel(const __grid_const
         const int t = lane + 32 * i;
         keep_rho[i] = keep_f[i] = 0.f;
         if (t < kLat) {
-            const float qa = (float)(t / 45 - 2), qb = (float)((t / 9) % 5 - 2), qc = (float)(t % 9 - 4);
+            const float4 ql = s_lat[t];
+            const float qa = ql.x, qb = ql.y, qc = ql.z;
             const float sx = cxk + h * (qa * exx + qb * eyx + qc * ezx);
             const float sy = cyk + h * (qa * exy + qb * eyy + qc * ezy);
             const float sz = czk + h * (qa * exz + qb * eyz + qc * ezz);
