@@ -12,7 +12,9 @@ namespace {
 __device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }
 }
 
-__global__ void __launch_bounds__(kLayers * 32) gather_kernel(const __grid_constant__ GatherArgs a) {
+// kF8: the FP8 path, which keeps every sample of the layer to scale them by its maximum.
+template <bool kF8>
+__global__ void __launch_bounds__(kLayers * 32, kF8 ? 2 : 3) gather_kernel(const __grid_constant__ GatherArgs a) {
     const int p = blockIdx.x;
     const int k = threadIdx.x >> 5;            // one warp per template layer
     const int lane = threadIdx.x & 31;
@@ -89,11 +91,11 @@ __global__ void __launch_bounds__(kLayers * 32) gather_kernel(const __grid_const
 
     float s0 = 0.f, s1 = 0.f, s2 = 0.f;
     float m0 = -3.0e38f, m1 = -3.0e38f, m2 = -3.0e38f;
-    float keep_rho[8], keep_f[8];               // this lane's samples (FP8 needs the max first)
+    float keep_rho[kF8 ? 8 : 1], keep_f[kF8 ? 8 : 1];   // this lane's samples (FP8 only)
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int t = lane + 32 * i;
-        keep_rho[i] = keep_f[i] = 0.f;
+        if (kF8) keep_rho[i] = keep_f[i] = 0.f;
         if (t < kLat) {
             const float4 ql = s_lat[t];
             const float qa = ql.x, qb = ql.y, qc = ql.z;
@@ -126,8 +128,10 @@ __global__ void __launch_bounds__(kLayers * 32) gather_kernel(const __grid_const
             }
             s0 += rho; s1 += f; s2 += T;
             m0 = fmaxf(m0, rho); m1 = fmaxf(m1, f); m2 = fmaxf(m2, T);
-            keep_rho[i] = rho;
-            keep_f[i] = f;
+            if (kF8) {
+                keep_rho[i] = rho;
+                keep_f[i] = f;
+            }
         } else if (a.Hb_rho && t < kLatPad) {     // zero the BF16 row padding
             for (int q = 0; q < (a.split ? 3 : 1); ++q) {
                 a.Hb_rho[obase_b + t + q * a.part] = __float2bfloat16_rn(0.f);
@@ -144,7 +148,7 @@ __global__ void __launch_bounds__(kLayers * 32) gather_kernel(const __grid_const
         m1 = fmaxf(m1, __shfl_xor_sync(~0u, m1, o));
         m2 = fmaxf(m2, __shfl_xor_sync(~0u, m2, o));
     }
-    if (a.H8_rho) {
+    if (kF8) {
         // e4m3 features scaled per (point, layer, type) by max / 448
         const float sr = m0 > 0.f ? m0 / 448.f : 1.f, sf = m1 > 0.f ? m1 / 448.f : 1.f;
         const size_t ob8 = ((size_t)p * kLayers + k) * kLatPad8;
@@ -188,7 +192,8 @@ __global__ void __launch_bounds__(kLayers * 32) gather_kernel(const __grid_const
 void launch_gather(const GatherArgs &a, cudaStream_t s) {
     if (a.count <= 0) return;
     note_launch();
-    gather_kernel<<<a.count, kLayers * 32, 0, s>>>(a);
+    if (a.H8_rho) gather_kernel<true><<<a.count, kLayers * 32, 0, s>>>(a);
+    else gather_kernel<false><<<a.count, kLayers * 32, 0, s>>>(a);
 }
 
 // Mixed batches: row -> request descriptor, and each row's decode scale.
