@@ -12,7 +12,7 @@
 //          output channels) and all 5 outputs: for each (ci, kd, kh) one 7-value row of
 //          conv1 output and 6 float4 weight loads feed 120 FMAs.  Every lane of a warp reads
 //          the same weights (broadcast) and its own point's row (the per-point stride of the
-//          conv1 output, 1009 floats, puts the 16 points in 16 banks).  The eight partial
+//          conv1 output, 1071 floats, puts the 16 points in 16 banks).  The eight partial
 //          sums of each output go through shared memory and are added in a fixed order.
 #include <cuda_fp8.h>
 
@@ -25,12 +25,16 @@ constexpr int kPts = 16;                         // points per group
 constexpr int kThreads = 288;
 constexpr int kGroupsPerCta = 4;
 constexpr int kCiGroups = 8;                     // conv2: warps, input channels g and g + 8
-constexpr int kY1 = 1009;                        // per-point stride of y1 (16 x 63 = 1008, padded)
+// conv1 output y1[q][ci][d][h][w]: 63 values per channel at a stride of 66, 1071 per point.
+// With these strides the conv1 stores of a warp (16 (point, d, h) rows x 2 channel halves)
+// and the conv2 loads (16 points, one channel) each fall in 32 different banks.
+constexpr int kY1Ci = 66;
+constexpr int kY1 = 1071;
 constexpr int kPartLd = 41;                      // conv2 partial sums: stride per (group, lane)
 static_assert(kCiGroups * 32 * kPartLd <= kPts * kY1, "partial sums alias the conv1 output");
 constexpr int kW2Ci = 436;                       // per-input-channel stride of w2t (27 x 16, padded)
 // shared memory (floats): w1t [27 taps][16 co], b1 [16], w2t [16 ci][kW2Ci: 27 taps x 16 co],
-// b2 [16], x [kPts][225], y1 [kPts][16 ci][63]
+// b2 [16], x [kPts][225], y1 [kPts][16 ci][kY1Ci]
 constexpr int kOffW1 = 0, kOffB1 = kOffW1 + 27 * kCnnCh, kOffW2 = kOffB1 + kCnnCh,
               kOffB2 = kOffW2 + kCnnCh * kW2Ci, kOffX = kOffB2 + kCnnCh,
               kOffY1 = kOffX + kPts * kLat, kSmemFloats = kOffY1 + kPts * kY1;
@@ -120,7 +124,7 @@ __global__ void __launch_bounds__(kThreads, 2) cnn_f32_kernel(const float *__res
 #pragma unroll
             for (int c = 0; c < 8; ++c)
 #pragma unroll
-                for (int w = 0; w < 7; ++w) yo[(half * 8 + c) * 63 + w] = fmaxf(acc[w][c], 0.f);
+                for (int w = 0; w < 7; ++w) yo[(half * 8 + c) * kY1Ci + w] = fmaxf(acc[w][c], 0.f);
         }
         __syncthreads();
         // conv2: warp g = input channels g and g + 8, lane = (channel half, point q);
@@ -140,7 +144,7 @@ __global__ void __launch_bounds__(kThreads, 2) cnn_f32_kernel(const float *__res
                 for (int kd = 0; kd < 3; ++kd)
 #pragma unroll
                     for (int kh = 0; kh < 3; ++kh) {
-                        const float *yr = y1 + q * kY1 + ci * 63 + (kd * 3 + kh) * 7;
+                        const float *yr = y1 + q * kY1 + ci * kY1Ci + (kd * 3 + kh) * 7;
                         float row[7];
 #pragma unroll
                         for (int i = 0; i < 7; ++i) row[i] = yr[i];
