@@ -146,6 +146,20 @@ def plume_volume(n: int, seed: int, sigma_max: float) -> np.ndarray:
     return _scale_to_max((fbm(n, seed) + 0.35) * mask, sigma_max).astype(np.float32)
 
 
+def plume_volume_torch(n: int, seed: int, sigma_max: float, device="cuda") -> np.ndarray:
+    """plume_volume() with the fBm from fbm_torch (float32 on `device`), returned as an FP16
+    host array: the 1024^3 plume without float64 temporaries of 8 GB each."""
+    import torch
+    c = torch.from_numpy(_centres(n)).float().to(device)
+    y = c[None, :, None]
+    rxz = torch.sqrt((c[:, None, None] - 0.5) ** 2 + (c[None, None, :] - 0.5) ** 2)
+    radius = 0.05 + 0.35 * y
+    mask = torch.clamp(1.0 - rxz / radius, min=0.0) * ((y > 0.03) & (y < 0.97)).float()
+    v = torch.clamp((fbm_torch(n, seed, device=device) + 0.35) * mask, min=0.0)
+    v = v * (sigma_max / torch.clamp(v.max(), min=1e-30))
+    return v.to(torch.float16).cpu().numpy()
+
+
 def constant_volume(n: int, sigma: float) -> np.ndarray:
     return np.full((n, n, n), sigma, dtype=np.float32)
 
