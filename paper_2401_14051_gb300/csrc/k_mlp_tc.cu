@@ -49,12 +49,17 @@ constexpr uint32_t STAGE3 = 3 * A_PART3 + 3 * B_PART3;    // 63 KB
 // (4 KB) + three BF16 parts of o2 (6 KB) with the split, o1 + o2 as BF16 (2 + 2 KB) without
 constexpr uint32_t STG_SPLIT = 10240, STG_ONE = 4096;
 constexpr uint32_t SMEM_CONST = 7 * TN_MAX * 4;          // per-column epilogue constants
-constexpr uint32_t PRE_BUF = 2 * 32 * 32 * 4;            // two FP32 32 x 32 residual chunks
+// per epilogue warp, two 32 x 32 residual chunks loaded by TMA: FP32 with the split, BF16
+// otherwise
+constexpr uint32_t PRE_SPLIT = 2 * 32 * 32 * 4, PRE_ONE = 2 * 32 * 32 * 2;
+// one-part stages: four with four epilogue warps, three with eight (shared memory)
+template <int EPI>
+__host__ __device__ constexpr int stages_one() { return EPI == 8 ? 3 : STAGES; }
 template <int EPI>
 __host__ __device__ constexpr uint32_t smem_tiles() {
-    // the residual buffers are used by the 4-warp (FP32 split) instantiation only
-    const uint32_t split = STAGES3 * STAGE3 + EPI * STG_SPLIT + (EPI == 4 ? EPI * PRE_BUF : 0);
-    const uint32_t one = STAGES * (A_STAGE + B_STAGE) + EPI * STG_ONE;
+    // the FP32 split runs with four epilogue warps only
+    const uint32_t split = EPI == 4 ? STAGES3 * STAGE3 + EPI * (STG_SPLIT + PRE_SPLIT) : 0;
+    const uint32_t one = stages_one<EPI>() * (A_STAGE + B_STAGE) + EPI * (STG_ONE + PRE_ONE);
     return split > one ? split : one;
 }
 template <int EPI>
@@ -299,7 +304,7 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const bool split3 = a.n_pass > 1;              // three-part stages (FP32 split)
-    const int n_stages = split3 ? STAGES3 : STAGES;
+    const int n_stages = split3 ? STAGES3 : stages_one<EPI>();
     const uint32_t stage_bytes = split3 ? STAGE3 : A_STAGE + B_STAGE;
     const uint32_t b_off = split3 ? 3 * A_PART3 : A_STAGE;   // B's offset inside a stage
     uint8_t *staging = smem + n_stages * stage_bytes;          // epilogue warps' TMA staging
@@ -339,7 +344,7 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
         tc::fence_mbar_init();
     }
     if (warp == 0 && lane == 0) { tc::prefetch_tmap(&map_a); tc::prefetch_tmap(&map_b); }
-    if (warp == 3 && lane == 0 && EPI == 4 && a.pre_tma) tc::prefetch_tmap(&map_pre);
+    if (warp == 3 && lane == 0 && a.pre_tma) tc::prefetch_tmap(&map_pre);
     if (warp == 2 && lane == 0 && a.o1_kind != kOutDirect) {
         tc::prefetch_tmap(&map_o1);
         if (a.o2_kind != kOutDirect) tc::prefetch_tmap(&map_o2);
@@ -482,17 +487,21 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
         const bool staged = a.o1_kind != kOutDirect;
         uint8_t *stg = staging + (warp - 2) * stg_stride;
         const uint32_t o2_off = a.o1_kind == kOutF32 ? 4096u : 2048u * (uint32_t)a.o1_parts;
-        // FP32 split: each 32 x 32 residual chunk arrives by TMA, two chunks ahead, in one of
-        // this warp's two buffers (128-byte swizzle: unit j of row r at unit j ^ (r mod 8))
-        const bool pre_tma = EPI == 4 && a.pre_tma;
-        uint8_t *pbuf = staging + EPI * stg_stride + (warp - 2) * PRE_BUF;
+        // each 32 x 32 residual chunk of this warp arrives by TMA, two chunks ahead, in one of
+        // its two buffers: FP32 rows of 128 bytes (128-byte swizzle: unit j of row r at
+        // j ^ (r mod 8)) with the split, BF16 rows of 64 bytes (64-byte swizzle: unit j at
+        // j ^ ((r / 2) mod 4)) otherwise
+        const bool pre_tma = a.pre_tma != 0;
+        const bool pre_f32 = a.pre_tma == 1;
+        const uint32_t pre_chunk = pre_f32 ? 4096u : 2048u;
+        uint8_t *pbuf = staging + EPI * stg_stride + (warp - 2) * 2 * pre_chunk;
         uint64_t *pbar = pre_full + 2 * (warp - 2);
         uint32_t pre_issued = 0, pre_used = 0;
         auto issue_pre = [&](int c0, int row0) {
             const int b = pre_issued & 1;
             if (lane == 0) {
-                tc::mbar_expect_tx(&pbar[b], 32 * 32 * 4);
-                tc::tma_load_3d(pbuf + b * 4096, &map_pre, c0, row0, 0, &pbar[b]);
+                tc::mbar_expect_tx(&pbar[b], pre_chunk);
+                tc::tma_load_3d(pbuf + b * pre_chunk, &map_pre, c0, row0, 0, &pbar[b]);
             }
             ++pre_issued;
         };
@@ -514,8 +523,8 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
             for (int i = 0; i < 32; ++i) pre[i] = 0.f;
             const int row0 = tile * TM + q * 32;
             if (pre_tma) {
-                issue_pre(0, row0);
-                if (32 < a.N) issue_pre(32, row0);
+                if (half * 32 < a.N) issue_pre(half * 32, row0);
+                if (half * 32 + kStride < a.N) issue_pre(half * 32 + kStride, row0);
             } else if (live && half * 32 < a.N) {
                 load_pre(a, r, half * 32, pre);
             }
@@ -539,14 +548,22 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
                         ok = false;
                         break;
                     }
-                    const uint8_t *src = pbuf + b * 4096 + lane * 128;
+                    if (pre_f32) {
+                        const uint8_t *src = pbuf + b * pre_chunk + lane * 128;
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const float4 f = *reinterpret_cast<const float4 *>(src + ((j ^ (lane & 7)) << 4));
-                        cur[4 * j] = f.x; cur[4 * j + 1] = f.y; cur[4 * j + 2] = f.z; cur[4 * j + 3] = f.w;
+                        for (int j = 0; j < 8; ++j) {
+                            const float4 f = *reinterpret_cast<const float4 *>(src + ((j ^ (lane & 7)) << 4));
+                            cur[4 * j] = f.x; cur[4 * j + 1] = f.y; cur[4 * j + 2] = f.z; cur[4 * j + 3] = f.w;
+                        }
+                    } else {
+                        const uint8_t *src = pbuf + b * pre_chunk + lane * 64;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            load_bf16x8(reinterpret_cast<const __nv_bfloat16 *>(src + ((j ^ ((lane >> 1) & 3)) << 4)),
+                                        cur + 8 * j);
                     }
                     __syncwarp();                      // every lane has read buffer b
-                    if (c0 + 64 < a.N) issue_pre(c0 + 64, row0);
+                    if (c0 + 2 * kStride < a.N) issue_pre(c0 + 2 * kStride, row0);
                 } else {
 #pragma unroll
                     for (int i = 0; i < 32; ++i) cur[i] = pre[i];

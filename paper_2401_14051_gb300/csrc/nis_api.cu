@@ -733,7 +733,7 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
         a.b_part_rows = a.n_mma;
         a.out_split = split ? 1 : 0;
         ProfScope ps(ctx, "mlp", s);
-        a.pre_tma = pre != nullptr;
+        a.pre_tma = pre ? (split ? 1 : 2) : 0;
         launch_tc_gemm(a, ma, mb, ctx->num_sms, s, o1, o2, pre);
     };
     const int k_e = split ? kOutF32 : kOutBf16;     // kind of e and h
@@ -796,10 +796,10 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
                     f1.h_prev = (k == k0 || split) ? nullptr : w.H; f1.ld_h = kWidth;
                     f1.pre_f32 = (k == k0 || !split) ? nullptr : w.H32; f1.ld_pre = kWidth;
                     f1.o1_kind = k_e; f1.o1_parts = 1; f1.o2_kind = kOutBf16; f1.o2_parts = P;
-                    // with the split, the running state h arrives by TMA (the e and h output
-                    // maps read back as 32 x 32 FP32 boxes)
+                    // the running state h arrives by TMA (the e and h output maps read back
+                    // as 32 x 32 boxes)
                     gemm(f1, fmap, wt.map_fc1[t][k], &w.out_e, &w.out_s,
-                         split && f1.pre_f32 ? &w.out_h : nullptr);
+                         (f1.pre_f32 || f1.h_prev) ? &w.out_h : nullptr);
                     TcGemmArgs f2{};
                     f2.M = cnt; f2.N = kWidth; f2.K = kWidth; f2.n_mma = 208; f2.k_tiles = 4;
                     f2.epi = kEpiFc2; f2.err = ctx->d_err;
@@ -817,7 +817,7 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
                     const bool end = k == k1 - 1;
                     f2.o1_kind = end ? kOutBf16 : k_e; f2.o1_parts = end ? P : 1;
                     gemm(f2, w.map_s, wt.map_fc2[t][k], end ? &w.out_mrg[t][chain] : &w.out_h, nullptr,
-                         split ? &w.out_e : nullptr);
+                         &w.out_e);
                 }
             }
             TcGemmArgs mg{};

@@ -332,8 +332,9 @@ struct TcGemmArgs {
     // instead of the pointers above: o1 = the layer's output (FC-1: e), o2 = FC-1's s.
     // Kind kOutDirect uses the pointers; parts = 3 writes the three BF16 parts of a split.
     int o1_kind, o1_parts, o2_kind, o2_parts;
-    // FP32 split: pre_f32 read through TMA (kernel argument map_pre, [1][rows][N] FP32 with
-    // 32 x 32 boxes) instead of one row per lane
+    // the residual / running state read through TMA (kernel argument map_pre, [1][rows][N]
+    // with 32 x 32 boxes) instead of one row per lane: 1 = FP32 (pre_f32, the split),
+    // 2 = BF16 (h_prev / resid); 0 = per-lane loads
     int pre_tma;
 };
 constexpr int kOutDirect = 0, kOutF32 = 1, kOutBf16 = 2;
