@@ -91,7 +91,11 @@ struct Workspace {                    // scratch of nis_shade_points, grow-only
     int *host_count = nullptr;        // pinned
 };
 constexpr int kActBufs = 15;          // e, h0, h1, 6 chain ends, 3 merges, z1, z2, spare
-constexpr int kChunk = 65536;         // shading points per pipeline pass, at most
+// Shading points per pipeline pass, at most.  Each dense layer is one launch per pass, and
+// a launch costs ~17 us beyond its tiles (prologue, pipeline fill, the last tile's epilogue),
+// so passes are as large as the workspace allows: the 1080p frame (215,053 points) is one
+// pass.  The tensor-core workspace is ~66 KB per point with the FP32 split (17 GB here).
+constexpr int kChunk = 262144;
 // Points per pass for n points: the passes share n equally (rounded up to whole 128-row
 // tensor-core tiles), so that no pass is a small remainder that leaves most SMs idle.
 int pass_size(int n) {
