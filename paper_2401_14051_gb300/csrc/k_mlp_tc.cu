@@ -378,6 +378,12 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem_base = *tmem_slot;
+    // Programmatic dependent launch: everything above reads only the weights, so it overlaps
+    // the previous layer's tail; the activations it wrote are read only after it completes.
+    // This kernel's own dependents may launch now: they wait for its completion the same way,
+    // and every CTA of this grid is already resident.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
     if (warp == 0) {
         if (lane == 0) {
@@ -665,8 +671,25 @@ void launch_tc_gemm(const TcGemmArgs &a, const CUtensorMap &map_a, const CUtenso
     note_launch();
     const CUtensorMap &o1 = map_o1 ? *map_o1 : unused, &o2 = map_o2 ? *map_o2 : unused;
     const CUtensorMap &pr = map_pre ? *map_pre : unused;
-    if (a.n_pass > 1) tc_gemm_kernel<4><<<grid, 64 + 32 * 4, smem_bytes<4>(), s>>>(map_a, map_b, o1, o2, pr, a);
-    else tc_gemm_kernel<8><<<grid, 64 + 32 * 8, smem_bytes<8>(), s>>>(map_a, map_b, o1, o2, pr, a);
+    // launched as a programmatic dependent of the previous kernel in the stream (see the
+    // griddepcontrol instructions in the kernel)
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.gridDim = dim3(grid);
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (a.n_pass > 1) {
+        cfg.blockDim = dim3(64 + 32 * 4);
+        cfg.dynamicSmemBytes = smem_bytes<4>();
+        cudaLaunchKernelEx(&cfg, tc_gemm_kernel<4>, map_a, map_b, o1, o2, pr, a);
+    } else {
+        cfg.blockDim = dim3(64 + 32 * 8);
+        cfg.dynamicSmemBytes = smem_bytes<8>();
+        cudaLaunchKernelEx(&cfg, tc_gemm_kernel<8>, map_a, map_b, o1, o2, pr, a);
+    }
 }
 
 }  // namespace nis

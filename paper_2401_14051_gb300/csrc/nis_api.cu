@@ -131,7 +131,8 @@ struct nis_ctx {
     nis_handle next = 1;
     // kernel timing (nis_profile)
     bool prof_on = false;
-    std::map<std::string, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>> prof;
+    struct ProfRecord { cudaEvent_t e0, e1; int launches; };
+    std::map<std::string, std::vector<ProfRecord>> prof;
     std::vector<cudaEvent_t> event_pool;
 };
 
@@ -166,20 +167,28 @@ cudaEvent_t take_event(nis_ctx *c) {
 }
 
 // Brackets the kernel launches of its scope with events on `s` when profiling is on.
+// Brackets the kernels launched in its scope with two events and counts them (the
+// library's launch counter: profile from one host thread).  The dense layers of a shading
+// pass are one scope, so no event sits between two of their launches (programmatic
+// dependent launch overlaps each with the previous one's tail).
 struct ProfScope {
     nis_ctx *c;
     const char *family;
     cudaStream_t s;
     cudaEvent_t e0 = nullptr;
+    uint64_t l0 = 0;
     ProfScope(nis_ctx *c_, const char *f, cudaStream_t s_) : c(c_), family(f), s(s_) {
-        if (c->prof_on && (e0 = take_event(c))) cudaEventRecord(e0, s);
+        if (c->prof_on && (e0 = take_event(c))) {
+            cudaEventRecord(e0, s);
+            l0 = g_launches.load();
+        }
     }
     ~ProfScope() {
         if (!e0) return;
         cudaEvent_t e1 = take_event(c);
         if (!e1) return;
         cudaEventRecord(e1, s);
-        c->prof[family].push_back({e0, e1});
+        c->prof[family].push_back({e0, e1, (int)(g_launches.load() - l0)});
     }
 };
 
@@ -736,7 +745,6 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
         a.a_part_rows = (int)cap;
         a.b_part_rows = a.n_mma;
         a.out_split = split ? 1 : 0;
-        ProfScope ps(ctx, "mlp", s);
         a.pre_tma = pre ? (split ? 1 : 2) : 0;
         launch_tc_gemm(a, ma, mb, ctx->num_sms, s, o1, o2, pre);
     };
@@ -776,80 +784,83 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
             launch_cnn_f32(w.H_T, cnt, W, o, (dbg && dbg->X_T) ? dbg->X_T + (size_t)off * kLayers * kDT : nullptr,
                            w.XTb, s, split ? cap * kLayers * kDT : 0);
         }
-        for (int t = 0; t < 3; ++t) {
-            const int d = feat_dim(t);
-            const CUtensorMap &fmap = t == 0 ? w.map_rho : (t == 1 ? w.map_f : w.map_xt);
-            const int fstride = t == 2 ? kDT : kLatPad;
-            for (int chain = 0; chain < 2; ++chain) {
-                int k0 = chain == 0 ? 0 : kDiffuse, k1 = chain == 0 ? kDiffuse : kLayers;
-                for (int k = k0; k < k1; ++k) {
-                    TcGemmArgs f1{};
-                    f1.M = cnt; f1.N = kWidth; f1.K = d; f1.n_mma = 208; f1.k_tiles = (d + 63) / 64;
-                    f1.a_col0 = k * fstride; f1.epi = kEpiFc1; f1.err = ctx->d_err;
-                    f1.out_e = w.E; f1.out_s = w.S; f1.ldo = kWidth;
-                    f1.out_e_f32 = split ? w.E32 : nullptr;
-                    f1.out_part = cap * kWidth;
-                    f1.bias = W + o.blk_b1[t][k];
-                    f1.row_scale = w.w_se + k * 3 + t; f1.row_scale_ld = kLayers * 3;
-                    f1.cfg = w.cfg; f1.w_cfg = W + o.blk_w1[t][k] + d; f1.w_cfg_ld = d + kCfg;
-                    f1.mat_cfg[0] = m->g;
-                    for (int c = 0; c < 3; ++c) f1.mat_cfg[1 + c] = m->albedo[c];
-                    // per-row configuration even for one request: a request's result is then
-                    // bit-identical alone and inside a mixed batch
-                    f1.cfg_per_row = 1;
-                    f1.h_prev = (k == k0 || split) ? nullptr : w.H; f1.ld_h = kWidth;
-                    f1.pre_f32 = (k == k0 || !split) ? nullptr : w.H32; f1.ld_pre = kWidth;
-                    f1.o1_kind = k_e; f1.o1_parts = 1; f1.o2_kind = kOutBf16; f1.o2_parts = P;
-                    // the running state h arrives by TMA (the e and h output maps read back
-                    // as 32 x 32 boxes)
-                    gemm(f1, fmap, wt.map_fc1[t][k], &w.out_e, &w.out_s,
-                         (f1.pre_f32 || f1.h_prev) ? &w.out_h : nullptr);
-                    TcGemmArgs f2{};
-                    f2.M = cnt; f2.N = kWidth; f2.K = kWidth; f2.n_mma = 208; f2.k_tiles = 4;
-                    f2.epi = kEpiFc2; f2.err = ctx->d_err;
-                    f2.bias = W + o.blk_b2[t][k];
-                    f2.resid = w.E; f2.ld_resid = kWidth;
-                    if (split) { f2.pre_f32 = w.E32; f2.ld_pre = kWidth; }
-                    if (k == k1 - 1) {
-                        f2.out_bf = w.mrg_in[t] + chain * kWidth; f2.ldo = 2 * kWidth;
-                        f2.out_part = cap * 2 * kWidth;
-                    } else if (split) {
-                        f2.out_h_f32 = w.H32; f2.ldo = kWidth;
-                    } else {
-                        f2.out_bf = w.H; f2.ldo = kWidth;
+        {
+            ProfScope pm(ctx, "mlp", s);   // the pass's dense layers as one timed block
+            for (int t = 0; t < 3; ++t) {
+                const int d = feat_dim(t);
+                const CUtensorMap &fmap = t == 0 ? w.map_rho : (t == 1 ? w.map_f : w.map_xt);
+                const int fstride = t == 2 ? kDT : kLatPad;
+                for (int chain = 0; chain < 2; ++chain) {
+                    int k0 = chain == 0 ? 0 : kDiffuse, k1 = chain == 0 ? kDiffuse : kLayers;
+                    for (int k = k0; k < k1; ++k) {
+                        TcGemmArgs f1{};
+                        f1.M = cnt; f1.N = kWidth; f1.K = d; f1.n_mma = 208; f1.k_tiles = (d + 63) / 64;
+                        f1.a_col0 = k * fstride; f1.epi = kEpiFc1; f1.err = ctx->d_err;
+                        f1.out_e = w.E; f1.out_s = w.S; f1.ldo = kWidth;
+                        f1.out_e_f32 = split ? w.E32 : nullptr;
+                        f1.out_part = cap * kWidth;
+                        f1.bias = W + o.blk_b1[t][k];
+                        f1.row_scale = w.w_se + k * 3 + t; f1.row_scale_ld = kLayers * 3;
+                        f1.cfg = w.cfg; f1.w_cfg = W + o.blk_w1[t][k] + d; f1.w_cfg_ld = d + kCfg;
+                        f1.mat_cfg[0] = m->g;
+                        for (int c = 0; c < 3; ++c) f1.mat_cfg[1 + c] = m->albedo[c];
+                        // per-row configuration even for one request: a request's result is then
+                        // bit-identical alone and inside a mixed batch
+                        f1.cfg_per_row = 1;
+                        f1.h_prev = (k == k0 || split) ? nullptr : w.H; f1.ld_h = kWidth;
+                        f1.pre_f32 = (k == k0 || !split) ? nullptr : w.H32; f1.ld_pre = kWidth;
+                        f1.o1_kind = k_e; f1.o1_parts = 1; f1.o2_kind = kOutBf16; f1.o2_parts = P;
+                        // the running state h arrives by TMA (the e and h output maps read back
+                        // as 32 x 32 boxes)
+                        gemm(f1, fmap, wt.map_fc1[t][k], &w.out_e, &w.out_s,
+                             (f1.pre_f32 || f1.h_prev) ? &w.out_h : nullptr);
+                        TcGemmArgs f2{};
+                        f2.M = cnt; f2.N = kWidth; f2.K = kWidth; f2.n_mma = 208; f2.k_tiles = 4;
+                        f2.epi = kEpiFc2; f2.err = ctx->d_err;
+                        f2.bias = W + o.blk_b2[t][k];
+                        f2.resid = w.E; f2.ld_resid = kWidth;
+                        if (split) { f2.pre_f32 = w.E32; f2.ld_pre = kWidth; }
+                        if (k == k1 - 1) {
+                            f2.out_bf = w.mrg_in[t] + chain * kWidth; f2.ldo = 2 * kWidth;
+                            f2.out_part = cap * 2 * kWidth;
+                        } else if (split) {
+                            f2.out_h_f32 = w.H32; f2.ldo = kWidth;
+                        } else {
+                            f2.out_bf = w.H; f2.ldo = kWidth;
+                        }
+                        const bool end = k == k1 - 1;
+                        f2.o1_kind = end ? kOutBf16 : k_e; f2.o1_parts = end ? P : 1;
+                        gemm(f2, w.map_s, wt.map_fc2[t][k], end ? &w.out_mrg[t][chain] : &w.out_h, nullptr,
+                             &w.out_e);
                     }
-                    const bool end = k == k1 - 1;
-                    f2.o1_kind = end ? kOutBf16 : k_e; f2.o1_parts = end ? P : 1;
-                    gemm(f2, w.map_s, wt.map_fc2[t][k], end ? &w.out_mrg[t][chain] : &w.out_h, nullptr,
-                         &w.out_e);
                 }
+                TcGemmArgs mg{};
+                mg.M = cnt; mg.N = kWidth; mg.K = 2 * kWidth; mg.n_mma = 208; mg.k_tiles = 7;
+                mg.epi = kEpiRelu; mg.err = ctx->d_err; mg.bias = W + o.mrg_b[t];
+                mg.out_bf = w.head_in + t * kWidth; mg.ldo = 3 * kWidth;
+                mg.out_part = cap * 3 * kWidth;
+                mg.o1_kind = kOutBf16; mg.o1_parts = P;
+                gemm(mg, w.map_mrg[t], wt.map_mrg[t], &w.out_head[t]);
             }
-            TcGemmArgs mg{};
-            mg.M = cnt; mg.N = kWidth; mg.K = 2 * kWidth; mg.n_mma = 208; mg.k_tiles = 7;
-            mg.epi = kEpiRelu; mg.err = ctx->d_err; mg.bias = W + o.mrg_b[t];
-            mg.out_bf = w.head_in + t * kWidth; mg.ldo = 3 * kWidth;
-            mg.out_part = cap * 3 * kWidth;
-            mg.o1_kind = kOutBf16; mg.o1_parts = P;
-            gemm(mg, w.map_mrg[t], wt.map_mrg[t], &w.out_head[t]);
+            TcGemmArgs h1{};
+            h1.M = cnt; h1.N = kWidth; h1.K = 3 * kWidth; h1.n_mma = 208; h1.k_tiles = 10;
+            h1.epi = kEpiRelu; h1.err = ctx->d_err; h1.bias = W + o.head_b[0];
+            h1.out_bf = w.Z1; h1.ldo = kWidth;
+            h1.out_part = cap * kWidth;
+            h1.o1_kind = kOutBf16; h1.o1_parts = P;
+            gemm(h1, w.map_head, wt.map_head[0], &w.out_z1);
+            TcGemmArgs h2 = h1;
+            h2.K = kWidth; h2.k_tiles = 4; h2.bias = W + o.head_b[1]; h2.out_bf = w.Z2;
+            gemm(h2, w.map_z1, wt.map_head[1], &w.out_z2);
+            TcGemmArgs h3{};
+            h3.M = cnt; h3.N = 3; h3.K = kWidth; h3.n_mma = 16; h3.k_tiles = 4;
+            h3.epi = kEpiDecode; h3.err = ctx->d_err; h3.bias = W + o.head_b[2];
+            for (int c = 0; c < 3; ++c) h3.dec_scale[c] = dec_scale[c];
+            h3.out_f32 = rgb + 3 * (size_t)off;
+            h3.y_out = (dbg && dbg->y) ? dbg->y + 3 * (size_t)off : nullptr;
+            if (mx) h3.dec_rows = mx->dec_rows + 3 * (size_t)off;
+            gemm(h3, w.map_z2, wt.map_head[2]);
         }
-        TcGemmArgs h1{};
-        h1.M = cnt; h1.N = kWidth; h1.K = 3 * kWidth; h1.n_mma = 208; h1.k_tiles = 10;
-        h1.epi = kEpiRelu; h1.err = ctx->d_err; h1.bias = W + o.head_b[0];
-        h1.out_bf = w.Z1; h1.ldo = kWidth;
-        h1.out_part = cap * kWidth;
-        h1.o1_kind = kOutBf16; h1.o1_parts = P;
-        gemm(h1, w.map_head, wt.map_head[0], &w.out_z1);
-        TcGemmArgs h2 = h1;
-        h2.K = kWidth; h2.k_tiles = 4; h2.bias = W + o.head_b[1]; h2.out_bf = w.Z2;
-        gemm(h2, w.map_z1, wt.map_head[1], &w.out_z2);
-        TcGemmArgs h3{};
-        h3.M = cnt; h3.N = 3; h3.K = kWidth; h3.n_mma = 16; h3.k_tiles = 4;
-        h3.epi = kEpiDecode; h3.err = ctx->d_err; h3.bias = W + o.head_b[2];
-        for (int c = 0; c < 3; ++c) h3.dec_scale[c] = dec_scale[c];
-        h3.out_f32 = rgb + 3 * (size_t)off;
-        h3.y_out = (dbg && dbg->y) ? dbg->y + 3 * (size_t)off : nullptr;
-        if (mx) h3.dec_rows = mx->dec_rows + 3 * (size_t)off;
-        gemm(h3, w.map_z2, wt.map_head[2]);
         if (dbg) {
             auto cp = [&](float *dst, const float *src, size_t per) -> cudaError_t {
                 if (!dst) return cudaSuccess;
@@ -883,7 +894,6 @@ nis_status shade_impl_fp8(nis_ctx *ctx, const Volume &vol, const Light &light, c
     auto gemm = [&](TcGemmArgs a, const CUtensorMap &ma, const CUtensorMap &mb) {
         a.fp8 = 1;
         a.k_tiles = (a.K + 127) / 128;
-        ProfScope ps(ctx, "mlp", s);
         launch_tc_gemm(a, ma, mb, ctx->num_sms, s);
     };
     for (int off = 0; off < n; off += chunk) {
@@ -920,61 +930,64 @@ nis_status shade_impl_fp8(nis_ctx *ctx, const Volume &vol, const Light &light, c
             launch_cnn_f32(w.H_T, cnt, W, o, (dbg && dbg->X_T) ? dbg->X_T + (size_t)off * kLayers * kDT : nullptr,
                            nullptr, s, 0, w.XT8);
         }
-        for (int t = 0; t < 3; ++t) {
-            const int d = feat_dim(t);
-            const CUtensorMap &fmap = t == 0 ? w.map_rho : (t == 1 ? w.map_f : w.map_xt);
-            const int fstride = t == 2 ? kDT : kLatPad8;
-            for (int chain = 0; chain < 2; ++chain) {
-                int k0 = chain == 0 ? 0 : kDiffuse, k1 = chain == 0 ? kDiffuse : kLayers;
-                for (int k = k0; k < k1; ++k) {
-                    TcGemmArgs f1{};
-                    f1.M = cnt; f1.N = kWidth; f1.K = d; f1.n_mma = 208;
-                    f1.a_col0 = k * fstride; f1.epi = kEpiFc1; f1.err = ctx->d_err;
-                    f1.out_e = w.E; f1.out_s8 = w.S8; f1.ldo = kWidth;
-                    f1.bias = W + o.blk_b1[t][k];
-                    f1.row_scale = w.w_se + k * 3 + t; f1.row_scale_ld = kLayers * 3;
-                    if (t < 2) { f1.row_scale2 = w.fscale + k * 2 + t; f1.row_scale2_ld = kLayers * 2; }
-                    f1.col_scale = wt.sc_fc1[t][k];
-                    f1.cfg = w.cfg; f1.w_cfg = W + o.blk_w1[t][k] + d; f1.w_cfg_ld = d + kCfg;
-                    f1.cfg_per_row = 1;
-                    f1.h_prev = k == k0 ? nullptr : w.H; f1.ld_h = kWidth;
-                    gemm(f1, fmap, wt.map_fc1[t][k]);
-                    TcGemmArgs f2{};
-                    f2.M = cnt; f2.N = kWidth; f2.K = kWidth; f2.n_mma = 208;
-                    f2.epi = kEpiFc2; f2.err = ctx->d_err;
-                    f2.bias = W + o.blk_b2[t][k];
-                    f2.col_scale = wt.sc_fc2[t][k];
-                    f2.resid = w.E; f2.ld_resid = kWidth;
-                    if (k == k1 - 1) { f2.out_f8 = w.mrg8[t] + chain * kWidth; f2.ldo = 2 * kWidth; }
-                    else { f2.out_bf = w.H; f2.ldo = kWidth; }
-                    gemm(f2, w.map_s, wt.map_fc2[t][k]);
+        {
+            ProfScope pm(ctx, "mlp", s);   // the pass's dense layers as one timed block
+            for (int t = 0; t < 3; ++t) {
+                const int d = feat_dim(t);
+                const CUtensorMap &fmap = t == 0 ? w.map_rho : (t == 1 ? w.map_f : w.map_xt);
+                const int fstride = t == 2 ? kDT : kLatPad8;
+                for (int chain = 0; chain < 2; ++chain) {
+                    int k0 = chain == 0 ? 0 : kDiffuse, k1 = chain == 0 ? kDiffuse : kLayers;
+                    for (int k = k0; k < k1; ++k) {
+                        TcGemmArgs f1{};
+                        f1.M = cnt; f1.N = kWidth; f1.K = d; f1.n_mma = 208;
+                        f1.a_col0 = k * fstride; f1.epi = kEpiFc1; f1.err = ctx->d_err;
+                        f1.out_e = w.E; f1.out_s8 = w.S8; f1.ldo = kWidth;
+                        f1.bias = W + o.blk_b1[t][k];
+                        f1.row_scale = w.w_se + k * 3 + t; f1.row_scale_ld = kLayers * 3;
+                        if (t < 2) { f1.row_scale2 = w.fscale + k * 2 + t; f1.row_scale2_ld = kLayers * 2; }
+                        f1.col_scale = wt.sc_fc1[t][k];
+                        f1.cfg = w.cfg; f1.w_cfg = W + o.blk_w1[t][k] + d; f1.w_cfg_ld = d + kCfg;
+                        f1.cfg_per_row = 1;
+                        f1.h_prev = k == k0 ? nullptr : w.H; f1.ld_h = kWidth;
+                        gemm(f1, fmap, wt.map_fc1[t][k]);
+                        TcGemmArgs f2{};
+                        f2.M = cnt; f2.N = kWidth; f2.K = kWidth; f2.n_mma = 208;
+                        f2.epi = kEpiFc2; f2.err = ctx->d_err;
+                        f2.bias = W + o.blk_b2[t][k];
+                        f2.col_scale = wt.sc_fc2[t][k];
+                        f2.resid = w.E; f2.ld_resid = kWidth;
+                        if (k == k1 - 1) { f2.out_f8 = w.mrg8[t] + chain * kWidth; f2.ldo = 2 * kWidth; }
+                        else { f2.out_bf = w.H; f2.ldo = kWidth; }
+                        gemm(f2, w.map_s, wt.map_fc2[t][k]);
+                    }
                 }
+                TcGemmArgs mg{};
+                mg.M = cnt; mg.N = kWidth; mg.K = 2 * kWidth; mg.n_mma = 208;
+                mg.epi = kEpiRelu; mg.err = ctx->d_err; mg.bias = W + o.mrg_b[t];
+                mg.col_scale = wt.sc_mrg[t];
+                mg.out_f8 = w.head8 + t * kWidth; mg.ldo = kHead8;
+                gemm(mg, w.map_mrg[t], wt.map_mrg[t]);
             }
-            TcGemmArgs mg{};
-            mg.M = cnt; mg.N = kWidth; mg.K = 2 * kWidth; mg.n_mma = 208;
-            mg.epi = kEpiRelu; mg.err = ctx->d_err; mg.bias = W + o.mrg_b[t];
-            mg.col_scale = wt.sc_mrg[t];
-            mg.out_f8 = w.head8 + t * kWidth; mg.ldo = kHead8;
-            gemm(mg, w.map_mrg[t], wt.map_mrg[t]);
+            TcGemmArgs h1{};
+            h1.M = cnt; h1.N = kWidth; h1.K = 3 * kWidth; h1.n_mma = 208;
+            h1.epi = kEpiRelu; h1.err = ctx->d_err; h1.bias = W + o.head_b[0];
+            h1.col_scale = wt.sc_head[0];
+            h1.out_f8 = w.Z1; h1.ldo = kWidth8;
+            gemm(h1, w.map_head, wt.map_head[0]);
+            TcGemmArgs h2 = h1;
+            h2.K = kWidth; h2.bias = W + o.head_b[1]; h2.col_scale = wt.sc_head[1]; h2.out_f8 = w.Z2;
+            gemm(h2, w.map_z1, wt.map_head[1]);
+            TcGemmArgs h3{};
+            h3.M = cnt; h3.N = 3; h3.K = kWidth; h3.n_mma = 16;
+            h3.epi = kEpiDecode; h3.err = ctx->d_err; h3.bias = W + o.head_b[2];
+            h3.col_scale = wt.sc_head[2];
+            for (int c = 0; c < 3; ++c) h3.dec_scale[c] = dec_scale[c];
+            h3.out_f32 = rgb + 3 * (size_t)off;
+            h3.y_out = (dbg && dbg->y) ? dbg->y + 3 * (size_t)off : nullptr;
+            if (mx) h3.dec_rows = mx->dec_rows + 3 * (size_t)off;
+            gemm(h3, w.map_z2, wt.map_head[2]);
         }
-        TcGemmArgs h1{};
-        h1.M = cnt; h1.N = kWidth; h1.K = 3 * kWidth; h1.n_mma = 208;
-        h1.epi = kEpiRelu; h1.err = ctx->d_err; h1.bias = W + o.head_b[0];
-        h1.col_scale = wt.sc_head[0];
-        h1.out_f8 = w.Z1; h1.ldo = kWidth8;
-        gemm(h1, w.map_head, wt.map_head[0]);
-        TcGemmArgs h2 = h1;
-        h2.K = kWidth; h2.bias = W + o.head_b[1]; h2.col_scale = wt.sc_head[1]; h2.out_f8 = w.Z2;
-        gemm(h2, w.map_z1, wt.map_head[1]);
-        TcGemmArgs h3{};
-        h3.M = cnt; h3.N = 3; h3.K = kWidth; h3.n_mma = 16;
-        h3.epi = kEpiDecode; h3.err = ctx->d_err; h3.bias = W + o.head_b[2];
-        h3.col_scale = wt.sc_head[2];
-        for (int c = 0; c < 3; ++c) h3.dec_scale[c] = dec_scale[c];
-        h3.out_f32 = rgb + 3 * (size_t)off;
-        h3.y_out = (dbg && dbg->y) ? dbg->y + 3 * (size_t)off : nullptr;
-        if (mx) h3.dec_rows = mx->dec_rows + 3 * (size_t)off;
-        gemm(h3, w.map_z2, wt.map_head[2]);
         if (dbg) {
             auto cp = [&](float *dst, const float *src, size_t per) -> cudaError_t {
                 if (!dst) return cudaSuccess;
@@ -1268,7 +1281,7 @@ void nis_destroy(nis_ctx *ctx) {
     for (void *p : ptrs) dev_free(ctx, p);
     if (ctx->ws.host_count) cudaFreeHost(ctx->ws.host_count);
     for (auto &kv : ctx->prof)
-        for (auto &e : kv.second) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+        for (auto &e : kv.second) { cudaEventDestroy(e.e0); cudaEventDestroy(e.e1); }
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
     delete ctx;
 }
@@ -1719,8 +1732,8 @@ nis_status nis_profile(nis_ctx *ctx, int enable) {
         cudaDeviceSynchronize();
         for (auto &kv : ctx->prof)
             for (auto &e : kv.second) {
-                ctx->event_pool.push_back(e.first);
-                ctx->event_pool.push_back(e.second);
+                ctx->event_pool.push_back(e.e0);
+                ctx->event_pool.push_back(e.e1);
             }
         ctx->prof.clear();
     }
@@ -1737,11 +1750,11 @@ nis_status nis_profile_read(nis_ctx *ctx, const char *family, double *total_ms, 
     auto it = ctx->prof.find(family);
     if (it == ctx->prof.end()) return NIS_OK;
     for (auto &e : it->second) {
-        NIS_CUDA(cudaEventSynchronize(e.second));
+        NIS_CUDA(cudaEventSynchronize(e.e1));
         float ms = 0.f;
-        NIS_CUDA(cudaEventElapsedTime(&ms, e.first, e.second));
+        NIS_CUDA(cudaEventElapsedTime(&ms, e.e0, e.e1));
         *total_ms += ms;
-        ++*launches;
+        *launches += e.launches;
     }
     return NIS_OK;
 }
