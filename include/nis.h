@@ -174,6 +174,16 @@ nis_status nis_render_frame(nis_ctx *ctx, nis_volume vol, nis_light light, nis_w
                             const nis_material *m, const nis_camera *cam, float *d_rgb_out,
                             nis_stream stream);
 
+/* The same frame lit by several directional lights (no counterpart in the paper's
+ * experiments, which use one; the in-scattered radiance of independent lights adds): the
+ * shading points are found once, each light's radiance is estimated with its own
+ * transmittance field (nis_build_transmittance per light, all of `vol`) and the per-light
+ * radiances are summed per pixel in the order of `lights`.  1 <= n_lights <= 64; the light
+ * handles are read before the call returns. */
+nis_status nis_render_frame_lights(nis_ctx *ctx, nis_volume vol, const nis_light *lights,
+                                   int n_lights, nis_weights w, const nis_material *m,
+                                   const nis_camera *cam, float *d_rgb_out, nis_stream stream);
+
 /* Overwrites the density of an existing volume with a grid of the same size (same
  * conventions as nis_upload_volume) without allocating: device sources and page-locked
  * host sources are read in place (a GB300 kernel reads pinned host memory over

@@ -693,3 +693,15 @@ def render_frame(rho0, sigma_max, light_dir, cam, weights, mat, levels=None, tle
         rgb = shade_points(pts[hit], -d[hit], light_dir, levels, tlevels, table, weights, mat)
         img[hit] = rgb
     return img, hit, margin
+
+
+def render_frame_lights(rho0, sigma_max, light_dirs, cam, weights, mat, levels, tlevels_list,
+                        table):
+    """Several directional lights: the sum over lights of render_frame, each with its own
+    transmittance levels.  Returns (image, hit, margin); hits do not depend on the light."""
+    img = None
+    for light_dir, tl in zip(light_dirs, tlevels_list):
+        im, hit, margin = render_frame(rho0, sigma_max, light_dir, cam, weights, mat, levels, tl,
+                                       table)
+        img = im if img is None else img + im
+    return img, hit, margin

@@ -79,21 +79,25 @@ void launch_find_hits(const float *rho0, int n, const float *sigma_max, const Ca
                                                          omega, pix_index, counter);
 }
 
+// Writes (or, with accumulate, adds) each shading point's radiance to its pixel; a pixel
+// has at most one shading point, so the additions do not race.
 __global__ void scatter_rgb_kernel(const float *__restrict__ rgb, const int *__restrict__ pix,
-                                   int count, float *image) {
+                                   int count, float *image, int accumulate) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
     int p = pix[i];
-    image[3 * (size_t)p] = rgb[3 * (size_t)i];
-    image[3 * (size_t)p + 1] = rgb[3 * (size_t)i + 1];
-    image[3 * (size_t)p + 2] = rgb[3 * (size_t)i + 2];
+    for (int c = 0; c < 3; ++c) {
+        const float v = rgb[3 * (size_t)i + c];
+        image[3 * (size_t)p + c] = accumulate ? image[3 * (size_t)p + c] + v : v;
+    }
 }
 
 void launch_scatter_rgb(const float *rgb, const int *pix_index, int count, float *image,
-                        cudaStream_t s) {
+                        cudaStream_t s, bool accumulate) {
     if (count <= 0) return;
     note_launch();
-    scatter_rgb_kernel<<<(count + 255) / 256, 256, 0, s>>>(rgb, pix_index, count, image);
+    scatter_rgb_kernel<<<(count + 255) / 256, 256, 0, s>>>(rgb, pix_index, count, image,
+                                                           accumulate ? 1 : 0);
 }
 
 }  // namespace nis

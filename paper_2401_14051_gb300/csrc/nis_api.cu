@@ -1507,20 +1507,28 @@ nis_status nis_find_hits(nis_ctx *ctx, nis_volume vol, const nis_camera *cam, in
     return NIS_OK;
 }
 
-nis_status nis_render_frame(nis_ctx *ctx, nis_volume vol, nis_light light, nis_weights w,
-                            const nis_material *m, const nis_camera *cam, float *d_rgb_out,
-                            nis_stream stream) {
+// Frame for one or more lights: the shading points (first hits) do not depend on the light;
+// each light's radiance is shaded with its own transmittance and added to the pixels.
+nis_status render_impl(nis_ctx *ctx, nis_volume vol, const nis_light *lights, int n_lights,
+                       nis_weights w, const nis_material *m, const nis_camera *cam,
+                       float *d_rgb_out, nis_stream stream) {
     if (!ctx) return NIS_ERR_INVALID_ARG;
     if (!d_rgb_out) return fail(ctx, NIS_ERR_INVALID_ARG, "NULL output");
+    if (!lights || n_lights < 1) return fail(ctx, NIS_ERR_INVALID_ARG, "no light");
     nis_status st = check_material(ctx, m);
     if (st) return st;
     CameraArgs c;
     if ((st = camera_args(ctx, cam, &c))) return st;
     Volume *pv; Light *pl; Weights *pw;
-    if ((st = resolve(ctx, vol, light, w, &pv, &pl, &pw))) return st;
+    std::vector<Light *> ls(n_lights);
+    for (int q = 0; q < n_lights; ++q) {
+        if ((st = resolve(ctx, vol, lights[q], w, &pv, &pl, &pw))) return st;
+        ls[q] = pl;
+    }
     DeviceGuard g(ctx->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    if ((st = ensure_pairs(ctx, *pv, *pl, s))) return st;
+    for (Light *l : ls)
+        if ((st = ensure_pairs(ctx, *pv, *l, s))) return st;
     Workspace &ws = ctx->ws;
     int pixels = c.width * c.height;
     if (ws.hit_cap < pixels) {
@@ -1548,16 +1556,29 @@ nis_status nis_render_frame(nis_ctx *ctx, nis_volume vol, nis_light light, nis_w
     int count = *ws.host_count;
     NIS_CUDA(cudaMemsetAsync(d_rgb_out, 0, sizeof(float) * 3 * (size_t)pixels, s));
     if (count > 0) {
-        if ((st = shade_impl(ctx, *pv, *pl, *pw, m, ws.hit_pts, ws.hit_omega, count, ws.hit_rgb,
-                             nullptr, s)))
-            return st;
-        {
+        for (int q = 0; q < n_lights; ++q) {
+            if ((st = shade_impl(ctx, *pv, *ls[q], *pw, m, ws.hit_pts, ws.hit_omega, count, ws.hit_rgb,
+                                 nullptr, s)))
+                return st;
             ProfScope ps(ctx, "other", s);
-            launch_scatter_rgb(ws.hit_rgb, ws.hit_pix, count, d_rgb_out, s);
+            launch_scatter_rgb(ws.hit_rgb, ws.hit_pix, count, d_rgb_out, s, q > 0);
         }
         NIS_CUDA(cudaGetLastError());
     }
     return NIS_OK;
+}
+
+nis_status nis_render_frame(nis_ctx *ctx, nis_volume vol, nis_light light, nis_weights w,
+                            const nis_material *m, const nis_camera *cam, float *d_rgb_out,
+                            nis_stream stream) {
+    return render_impl(ctx, vol, &light, 1, w, m, cam, d_rgb_out, stream);
+}
+
+nis_status nis_render_frame_lights(nis_ctx *ctx, nis_volume vol, const nis_light *lights,
+                                   int n_lights, nis_weights w, const nis_material *m,
+                                   const nis_camera *cam, float *d_rgb_out, nis_stream stream) {
+    if (ctx && n_lights > 64) return fail(ctx, NIS_ERR_INVALID_ARG, "at most 64 lights");
+    return render_impl(ctx, vol, lights, n_lights, w, m, cam, d_rgb_out, stream);
 }
 
 nis_status nis_release(nis_ctx *ctx, nis_handle h) {

@@ -289,7 +289,7 @@ void launch_find_hits(const float *rho0, int n, const float *sigma_max, const Ca
                       int *hit_flag, float *points, float *omega, int *pix_index,
                       int *counter, cudaStream_t s);
 void launch_scatter_rgb(const float *rgb, const int *pix_index, int count, float *image,
-                        cudaStream_t s);
+                        cudaStream_t s, bool accumulate = false);
 
 // ---- tensor-core dense layer (k_mlp_tc.cu) ------------------------------------------------
 constexpr int kEpiPlain = 0, kEpiFc1 = 1, kEpiFc2 = 2, kEpiRelu = 3, kEpiDecode = 4;

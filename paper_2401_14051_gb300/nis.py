@@ -102,6 +102,9 @@ _SIGS = {
                                    C.c_void_p, C.c_void_p]),
     "nis_render_frame": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint64,
                                    C.POINTER(Material), C.POINTER(Camera), C.c_void_p, C.c_void_p]),
+    "nis_render_frame_lights": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(C.c_uint64), C.c_int,
+                                          C.c_uint64, C.POINTER(Material), C.POINTER(Camera),
+                                          C.c_void_p, C.c_void_p]),
     "nis_release": (C.c_int, [C.c_void_p, C.c_uint64]),
     "nis_sync": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "nis_volume_info": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(C.c_int), C.c_int * 16,
@@ -372,6 +375,20 @@ class Context:
         m = material(mat)
         self._check(self.lib.nis_render_frame(self.h, vol, light, weights, C.byref(m), C.byref(c),
                                               _ptr(out), _stream(stream)))
+        return out
+
+    def render_frame_lights(self, vol, lights, weights, mat: dict, cam: dict, out=None, stream=None):
+        """render_frame lit by several lights (handles of vol's lights): per-light radiance
+        summed per pixel."""
+        c = camera(cam)
+        if out is None:
+            out = torch.empty((c.height, c.width, 3), dtype=torch.float32,
+                              device=f"cuda:{self.device}")
+        m = material(mat)
+        arr = (C.c_uint64 * len(lights))(*lights)
+        self._check(self.lib.nis_render_frame_lights(self.h, vol, arr, len(lights), weights,
+                                                     C.byref(m), C.byref(c), _ptr(out),
+                                                     _stream(stream)))
         return out
 
     def find_hits(self, vol, cam: dict, stream=None):

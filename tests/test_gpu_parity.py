@@ -253,6 +253,38 @@ def test_shade_points_end_to_end(ctx, w1, gpu1):
     assert normwise(rgb.cpu().numpy()[keep], ref) <= NORMWISE
 
 
+def test_render_frame_two_lights(ctx, w1, gpu1):
+    # two directional lights: the GPU frame equals the sum of its single-light frames (same
+    # FP32 additions, in light order) and the oracle's sum over the two lights
+    cfg = w1["cfg"]
+    cam = cfg["camera"]
+    l2 = synth.unit_vector(99)
+    lt2 = ctx.build_transmittance(gpu1["vol"], l2, 0.6)
+    img = ctx.render_frame_lights(gpu1["vol"], [gpu1["light"], lt2], gpu1["weights"], cfg["material"], cam)
+    one = ctx.render_frame(gpu1["vol"], gpu1["light"], gpu1["weights"], cfg["material"], cam)
+    two = ctx.render_frame(gpu1["vol"], lt2, gpu1["weights"], cfg["material"], cam)
+    ctx.sync(timeout_ms=60000)
+    got = img.cpu().numpy()
+    assert np.array_equal(got, one.cpu().numpy() + two.cpu().numpy())
+    _, t2, _ = O.prepare(w1["vol"], l2, cfg["material"]["g"])
+    ref, rhit, margin = O.render_frame_lights(w1["vol"], 16.0, [cfg["light"], l2], cam, w1["weights"],
+                                              cfg["material"], w1["levels"], [w1["T"], t2], w1["table"])
+    o, d = O.camera_rays(cam)
+    _, rpts, _ = O.hit_search(w1["levels"][0], 16.0, o, d)
+    p = rpts.reshape(-1, 3).astype(np.float64)
+    amb = np.zeros(p.shape[0], dtype=bool)
+    for l in (cfg["light"], l2):
+        amb |= O.layer_geometry(p, l, 64)[4].min(axis=1) < 1e-4
+    ok = (margin > 1e-5) & ~amb.reshape(margin.shape) & rhit
+    e = rel_err(got[ok], ref[ok])
+    print(f"\n[parity] render 64x64, two lights: max rel {e.max():.3g}, "
+          f"normwise {normwise(got[ok], ref[ok]):.3g}")
+    assert ok.sum() > 1500
+    assert e.max() <= 1e-4
+    assert normwise(got[ok], ref[ok]) <= 5e-5         # hit points 5e-6 from the oracle's
+    ctx.release(lt2)
+
+
 def test_ragged_and_degenerate_points(ctx, w1, gpu1):
     cfg = w1["cfg"]
     l = np.asarray(cfg["light"])

@@ -60,3 +60,25 @@ def test_blob_header_and_checksum():
     payload = np.frombuffer(blob[80:], dtype="<f4")
     np.testing.assert_array_equal(payload[:16 * 27], w["cnn"][0]["w1"].ravel())
     np.testing.assert_array_equal(payload[-3:], w["head"][2]["b"])
+
+
+def test_render_frame_lights_is_the_sum_over_lights():
+    # several directional lights: the in-scattered radiance of independent sources adds, so
+    # one light reproduces render_frame and the same light twice doubles every pixel
+    vol = synth.fbm_volume(6, 3, 8.0)
+    cam = synth.ortho_camera(synth.unit_vector(5), 4, 4)
+    mat = synth.material(0.5, (0.95, 0.97, 0.99))
+    weights = synth.make_weights(6, 8.0)
+    l1, l2 = synth.unit_vector(7), synth.unit_vector(8)
+    levels, t1, table = O.prepare(vol, l1, mat["g"])
+    _, t2, _ = O.prepare(vol, l2, mat["g"])
+    one, hit, _ = O.render_frame(vol, 8.0, l1, cam, weights, mat, levels, t1, table)
+    assert hit.sum() > 4
+    got, hit1, _ = O.render_frame_lights(vol, 8.0, [l1], cam, weights, mat, levels, [t1], table)
+    assert np.array_equal(got, one) and np.array_equal(hit1, hit)
+    twice, _, _ = O.render_frame_lights(vol, 8.0, [l1, l1], cam, weights, mat, levels, [t1, t1], table)
+    assert np.array_equal(twice, 2.0 * one)
+    two, _, _ = O.render_frame_lights(vol, 8.0, [l1, l2], cam, weights, mat, levels, [t1, t2], table)
+    other, _, _ = O.render_frame(vol, 8.0, l2, cam, weights, mat, levels, t2, table)
+    np.testing.assert_allclose(two, one + other, rtol=1e-15, atol=0)
+    assert np.abs(other - one).max() > 0          # the second light changes the radiance
