@@ -337,11 +337,14 @@ nis_status nis_shade_points_debug(nis_ctx *ctx, nis_volume vol, nis_light light,
 nis_status nis_find_hits(nis_ctx *ctx, nis_volume vol, const nis_camera *cam, int *d_hit,
                          float *d_points, float *d_omega, nis_stream stream);
 
-/* Kernel timing: with profiling on, every kernel the context launches is bracketed by
- * CUDA events on its stream, accumulated per kernel family.  nis_profile(ctx, 1) clears
- * and starts, nis_profile(ctx, 0) stops.  nis_profile_read waits for the recorded events
- * and returns the summed device time and launch count of one family: "pyramid", "march",
- * "phase", "hits", "gather", "cnn", "mlp" or "other". */
+/* Kernel timing: with profiling on, the kernels the context launches are bracketed by CUDA
+ * events on their stream, accumulated per kernel family: each kernel on its own, except the
+ * dense layers of one shading pass, which are one bracketed block (no event between two of
+ * their launches, which overlap as programmatic dependent launches).  nis_profile(ctx, 1)
+ * clears and starts, nis_profile(ctx, 0) stops.  nis_profile_read waits for the recorded
+ * events and returns the summed device time and the number of kernels launched inside the
+ * brackets of one family: "pyramid", "march", "phase", "hits", "gather", "cnn", "mlp" or
+ * "other".  The launch count assumes one host thread launching on the library. */
 nis_status nis_profile(nis_ctx *ctx, int enable);
 nis_status nis_profile_read(nis_ctx *ctx, const char *family, double *total_ms,
                             int *launches);

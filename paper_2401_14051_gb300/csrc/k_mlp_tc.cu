@@ -8,12 +8,13 @@
 //              two accumulator buffers (columns 0 and 256) so the epilogue of one tile
 //              overlaps the MMAs of the next
 //   warps 2-   epilogue: one (FP32 split) or two (BF16, FP8) warps per TMEM lane quarter,
-//              each thread one row of the tile;
-//              reads 32 columns at a time, applies the layer's fused epilogue and stages
-//              the 32 x 32 result in shared memory, from where one lane writes it with a
-//              TMA store (rows of 128 contiguous bytes instead of one row per lane)
+//              each thread one row of the tile.  A warp takes 32 columns at a time: its
+//              32 x 32 residual chunk arrives by TMA two chunks ahead, it applies the
+//              layer's fused epilogue and stages the result in shared memory, from where
+//              one lane writes it with a TMA store (rows of 128 contiguous bytes instead of
+//              one row per lane)
 // Stage layouts:
-//   one part (BF16, FP8)   4 stages of {A 128 x 128 B, B N_mma x 128 B}, 128-byte swizzle
+//   one part (BF16, FP8)   3 stages of {A 128 x 128 B, B N_mma x 128 B}, 128-byte swizzle
 //   three parts (FP32 as   2 stages of {A0 A1 A2 128 x 64 B, B0 B1 B2 N_mma x 64 B}, 64-byte
 //   three BF16 parts)      swizzle.  A first sweep over K brings each 32-wide slab with all
 //                          its parts and sums the five smaller products of the split; a
@@ -22,6 +23,8 @@
 //                          accumulator is still small (all six products per slab in one
 //                          sweep measured about 7x the end-to-end error of this order).  A0
 //                          and B0 are the only operands fetched twice.
+// Consecutive layers are programmatic dependent launches: the prologue (barriers, TMEM,
+// per-column constants) overlaps the previous layer's tail.
 // Every mbarrier wait is bounded: on a time-out the kernel records kErrTimeout in the
 // context's error word and winds down (draining its MMAs before releasing TMEM).
 #include <cuda_bf16.h>
@@ -42,11 +45,12 @@ constexpr int STAGES3 = kSplitSlabK == 16 ? 4 : 2;
 constexpr uint32_t A_PART3 = TM * ROW3;                   // 8 KB
 constexpr uint32_t B_PART3 = TN_MAX * ROW3;               // 13 KB
 constexpr uint32_t STAGE3 = 3 * A_PART3 + 3 * B_PART3;    // 63 KB
-// epilogue warps: 8 (two per TMEM lane quarter, alternate 32-column chunks) for BF16 and
-// FP8, whose epilogue is the bottleneck; 4 (one per quarter) for the FP32 split, where they
-// measured faster (more registers per thread, less L1 contention with the operand loads)
-// per epilogue warp, a staging buffer for the TMA stores of one 32 x 32 chunk: FP32 o1
-// (4 KB) + three BF16 parts of o2 (6 KB) with the split, o1 + o2 as BF16 (2 + 2 KB) without
+// Epilogue warps (the kernel's template argument EPI): 8 (two per TMEM lane quarter,
+// alternate 32-column chunks) for BF16 and FP8, whose epilogue is the bottleneck; 4 (one per
+// quarter) for the FP32 split, where they measured faster (more registers per thread, less
+// L1 contention with the operand loads).
+// Per epilogue warp, a staging buffer for the TMA stores of one 32 x 32 chunk: FP32 o1
+// (4 KB) + three BF16 parts of o2 (6 KB) with the split, o1 + o2 as BF16 (2 + 2 KB) without.
 constexpr uint32_t STG_SPLIT = 10240, STG_ONE = 4096;
 constexpr uint32_t SMEM_CONST = 7 * TN_MAX * 4;          // per-column epilogue constants
 // per epilogue warp, two 32 x 32 residual chunks loaded by TMA: FP32 with the split, BF16
