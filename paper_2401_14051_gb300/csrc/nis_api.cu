@@ -781,8 +781,11 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
         }
         {
             ProfScope ps(ctx, "cnn", s);
-            launch_cnn_f32(w.H_T, cnt, W, o, (dbg && dbg->X_T) ? dbg->X_T + (size_t)off * kLayers * kDT : nullptr,
-                           w.XTb, s, split ? cap * kLayers * kDT : 0);
+            float *xt_dbg = (dbg && dbg->X_T) ? dbg->X_T + (size_t)off * kLayers * kDT : nullptr;
+            if (split)      // FP32: the FP32 CNN, its output split into three BF16 parts
+                launch_cnn_f32(w.H_T, cnt, W, o, xt_dbg, w.XTb, s, cap * kLayers * kDT);
+            else            // BF16: the CNN with BF16 operands on the tensor cores
+                launch_cnn_tc(w.H_T, cnt, W, o, xt_dbg, w.XTb, nullptr, ctx->d_err, ctx->num_sms, s);
         }
         {
             ProfScope pm(ctx, "mlp", s);   // the pass's dense layers as one timed block
@@ -927,8 +930,8 @@ nis_status shade_impl_fp8(nis_ctx *ctx, const Volume &vol, const Light &light, c
         }
         {
             ProfScope ps(ctx, "cnn", s);
-            launch_cnn_f32(w.H_T, cnt, W, o, (dbg && dbg->X_T) ? dbg->X_T + (size_t)off * kLayers * kDT : nullptr,
-                           nullptr, s, 0, w.XT8);
+            launch_cnn_tc(w.H_T, cnt, W, o, (dbg && dbg->X_T) ? dbg->X_T + (size_t)off * kLayers * kDT : nullptr,
+                          nullptr, w.XT8, ctx->d_err, ctx->num_sms, s);
         }
         {
             ProfScope pm(ctx, "mlp", s);   // the pass's dense layers as one timed block

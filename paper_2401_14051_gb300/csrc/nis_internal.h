@@ -245,6 +245,11 @@ void launch_gather(const GatherArgs &a, cudaStream_t s);
 void launch_cnn_f32(const float *H_T, int count, const float *wbase, const WeightOffsets &o,
                     float *X_T, __nv_bfloat16 *X_T_bf, cudaStream_t s, size_t split_part = 0,
                     uint8_t *X_T_f8 = nullptr);
+// The same CNN with BF16 operands on the tensor cores (FP32 accumulation): outputs X_T
+// (FP32, optional), X_T_bf (BF16, optional), X_T_f8 (e4m3, optional), [count][12][80].
+void launch_cnn_tc(const float *H_T, int count, const float *wbase, const WeightOffsets &o,
+                   float *X_T, __nv_bfloat16 *X_T_bf, uint8_t *X_T_f8, unsigned *err, int num_sms,
+                   cudaStream_t s);
 // FP8 weights: scale[n] = max_k |W[n][k]| / 448 (1 for empty rows), dst = e4m3(W / scale)
 void launch_pack_fp8(const float *src, int N, int K, int ld_src, uint8_t *dst, float *scale,
                      int Np, int Kp, cudaStream_t s);

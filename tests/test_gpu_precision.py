@@ -1,5 +1,5 @@
-"""Reduced-precision modes: the dense layers on tensor cores in BF16 (FP32 accumulation),
-the transmittance march and exponentials in FP32.  Radiance error against the FP64 oracle
+"""Reduced-precision modes: the CNN and the dense layers on tensor cores in BF16 (FP32
+accumulation), the transmittance march and exponentials in FP32.  Radiance error against the FP64 oracle
 on the 64^3 fBm workload, stated as mean and max of the floored relative error; the target
 for BF16 is a mean of at most 2e-2."""
 import numpy as np
@@ -57,7 +57,7 @@ def test_bf16_against_fp64_oracle(env):
 
 def test_bf16_against_fp32_path_many_points(env):
     ctx, cfg = env["ctx"], env["cfg"]
-    n = 70000                                  # more than one 65,536-point pass
+    n = 270000                                 # more than one 262,144-point pass
     p, om = synth.shading_points(n, 505, -0.05, 1.05)
     dev = torch.device("cuda:0")
     pt, ot = torch.from_numpy(p).to(dev), torch.from_numpy(om).to(dev)
@@ -103,3 +103,25 @@ def test_fp8_against_fp64_oracle_and_fp32(env):
           f"vs FP32 path mean {e32.mean():.3g}")
     assert np.isfinite(rf8.cpu().numpy()).all()
     assert e.mean() <= 0.3
+
+
+def test_bf16_cnn_against_fp64_on_the_same_inputs(env):
+    # the tensor-core CNN (BF16 operands, BF16 conv1 output, FP32 accumulation) on the GPU's
+    # own transmittance lattices, against the oracle's FP64 convolution of the same values:
+    # each product carries the BF16 rounding of both operands (2^-9 relative each) and
+    # conv2 sums 432 of them, so the error is stated against the output range
+    ctx, cfg = env["ctx"], env["cfg"]
+    p, om = synth.shading_points(1500, 606, 0.05, 0.95)
+    dev = torch.device("cuda:0")
+    r = ctx.shade_points_debug(env["v"], env["l"], env["wbf"], cfg["material"],
+                               torch.from_numpy(p).to(dev), torch.from_numpy(om).to(dev))
+    ctx.sync(timeout_ms=60000)
+    ht = r["H_T"].cpu().numpy().astype(np.float64)
+    xt = r["X_T"].cpu().numpy().astype(np.float64)
+    ref = O.cnn(ht, env["weights"])
+    scale = np.abs(ref).max()
+    err = np.abs(xt - ref)
+    print(f"\n[precision] BF16 tensor-core CNN vs FP64, 1500 points x 12 layers: max |d| "
+          f"{err.max() / scale:.3g}, mean |d| {err.mean() / scale:.3g} of the output range")
+    assert err.max() <= 3e-2 * scale
+    assert err.mean() <= 2e-3 * scale
