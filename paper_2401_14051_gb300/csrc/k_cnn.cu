@@ -47,8 +47,7 @@ __global__ void __launch_bounds__(kThreads, 2) cnn_f32_kernel(const float *__res
                                                            const __grid_constant__ WeightOffsets o,
                                                            float *__restrict__ X_T,
                                                            __nv_bfloat16 *__restrict__ X_T_bf,
-                                                           size_t split_part,
-                                                           uint8_t *__restrict__ X_T_f8) {
+                                                           size_t split_part) {
     extern __shared__ __align__(16) float sm[];
     float *w1t = sm + kOffW1, *b1 = sm + kOffB1, *w2t = sm + kOffW2, *b2 = sm + kOffB2;
     float *xin = sm + kOffX, *y1 = sm + kOffY1;
@@ -194,14 +193,12 @@ __global__ void __launch_bounds__(kThreads, 2) cnn_f32_kernel(const float *__res
                 }
             }
             if (X_T) X_T[o] = v;
-            if (X_T_f8) X_T_f8[o] = __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
         }
     }
 }
 
 void launch_cnn_f32(const float *H_T, int count, const float *wbase, const WeightOffsets &o,
-                    float *X_T, __nv_bfloat16 *X_T_bf, cudaStream_t s, size_t split_part,
-                    uint8_t *X_T_f8) {
+                    float *X_T, __nv_bfloat16 *X_T_bf, cudaStream_t s, size_t split_part) {
     if (count <= 0) return;
     size_t smem = kSmemFloats * sizeof(float);
     static bool attr_set = false;   // per process; the attribute is per function
@@ -212,7 +209,7 @@ void launch_cnn_f32(const float *H_T, int count, const float *wbase, const Weigh
     int n_groups = (count + kPts - 1) / kPts;
     dim3 grid((n_groups + kGroupsPerCta - 1) / kGroupsPerCta, kLayers);
     note_launch();
-    cnn_f32_kernel<<<grid, kThreads, smem, s>>>(H_T, count, wbase, o, X_T, X_T_bf, split_part, X_T_f8);
+    cnn_f32_kernel<<<grid, kThreads, smem, s>>>(H_T, count, wbase, o, X_T, X_T_bf, split_part);
 }
 
 }  // namespace nis

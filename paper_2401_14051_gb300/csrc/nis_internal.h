@@ -242,9 +242,10 @@ struct GatherArgs {
 };
 void launch_gather(const GatherArgs &a, cudaStream_t s);
 
+// FP32 CNN (FP32 FFMA): outputs X_T (FP32, optional) and X_T_bf (BF16, optional; three
+// split parts `split_part` elements apart when split_part != 0), [count][12][80].
 void launch_cnn_f32(const float *H_T, int count, const float *wbase, const WeightOffsets &o,
-                    float *X_T, __nv_bfloat16 *X_T_bf, cudaStream_t s, size_t split_part = 0,
-                    uint8_t *X_T_f8 = nullptr);
+                    float *X_T, __nv_bfloat16 *X_T_bf, cudaStream_t s, size_t split_part = 0);
 // The same CNN with BF16 operands on the tensor cores (FP32 accumulation): outputs X_T
 // (FP32, optional), X_T_bf (BF16, optional), X_T_f8 (e4m3, optional), [count][12][80].
 void launch_cnn_tc(const float *H_T, int count, const float *wbase, const WeightOffsets &o,
