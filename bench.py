@@ -95,6 +95,24 @@ def max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
+def sum_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def whole_job_rate(units: float, seconds: float, world: int):
+    """Weak-scaling throughput: the units every rank processed over the slowest rank's
+    time.  Returns (units per second, slowest rank's seconds)."""
+    slowest = max_over_ranks(seconds, world)
+    return sum_over_ranks(units, world) / slowest, slowest
+
+
 # ---- clocks during the timed region --------------------------------------------------------
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -365,9 +383,9 @@ def run_nis(args):
     barrier(world)
     clk = clocks.stop()
     fam = {f: ctx.profile_read(f) for f in nis.FAMILIES}
-    total_ms = max_over_ranks(sum(times), world)
+    value, total_s = whole_job_rate(n_points * args.steps, sum(times) / 1e3, world)
+    total_ms = 1e3 * total_s
     ms_per_step = total_ms / args.steps
-    value = n_points * args.steps * world / (total_ms / 1e3)
 
     # ---- the same frames with the dense layers in BF16 on the tensor cores
     img_bf = torch.empty_like(img)
@@ -386,7 +404,8 @@ def run_nis(args):
         times_bf.append(e0.elapsed_time(e1))
     ctx.profile(False)
     fam_bf = {f: ctx.profile_read(f) for f in nis.FAMILIES}
-    total_bf = max_over_ranks(sum(times_bf), world)
+    value_bf, total_bf = whole_job_rate(n_points * args.steps, sum(times_bf) / 1e3, world)
+    total_bf *= 1e3
     hitmask = hit.bool()
     a_bf, a_32 = img_bf[hitmask].double(), img[hitmask].double()
     floor = 5e-2 * a_32.abs().amax(dim=0, keepdim=True)
@@ -394,7 +413,7 @@ def run_nis(args):
     peaks_bf = measured_peaks()
     mlp_ms, mlp_n = fam_bf["mlp"]
     mlp_tf = MLP_FLOP_PER_POINT * n_points * args.steps / (mlp_ms / 1e3) / 1e12
-    bf16 = {"value": n_points * args.steps * world / (total_bf / 1e3), "unit": UNIT,
+    bf16 = {"value": value_bf, "unit": UNIT,
             "frame_ms": total_bf / args.steps,
             "mean_rel_err_vs_fp32": float(e_bf.mean()), "max_rel_err_vs_fp32": float(e_bf.max()),
             "step_breakdown_ms": {f: round(fam_bf[f][0] / args.steps, 4) for f in nis.FAMILIES},
@@ -422,12 +441,13 @@ def run_nis(args):
         times_f8.append(e0.elapsed_time(e1))
     ctx.profile(False)
     fam_f8 = {f: ctx.profile_read(f) for f in nis.FAMILIES}
-    total_f8 = max_over_ranks(sum(times_f8), world)
+    value_f8, total_f8 = whole_job_rate(n_points * args.steps, sum(times_f8) / 1e3, world)
+    total_f8 *= 1e3
     a_f8 = img_f8[hitmask].double()
     e_f8 = ((a_f8 - a_32).abs() / torch.maximum(a_32.abs(), floor))
     mlp8_ms = fam_f8["mlp"][0]
     mlp8_tf = MLP_FLOP_PER_POINT * n_points * args.steps / (mlp8_ms / 1e3) / 1e12
-    fp8 = {"value": n_points * args.steps * world / (total_f8 / 1e3), "unit": UNIT,
+    fp8 = {"value": value_f8, "unit": UNIT,
            "frame_ms": total_f8 / args.steps,
            "mean_rel_err_vs_fp32": float(e_f8.mean()), "max_rel_err_vs_fp32": float(e_f8.max()),
            "step_breakdown_ms": {f: round(fam_f8[f][0] / args.steps, 4) for f in nis.FAMILIES},
@@ -450,8 +470,7 @@ def run_nis(args):
         torch.cuda.synchronize()
         if i >= args.warmup:
             e2e_times.append(time.perf_counter() - t0)
-    e2e_total = max_over_ranks(sum(e2e_times), world)
-    e2e_value = n_points * args.steps * world / e2e_total
+    e2e_value, e2e_total = whole_job_rate(n_points * args.steps, sum(e2e_times), world)
     ctx.sync(timeout_ms=120000)
 
     if rank != 0:
