@@ -238,22 +238,25 @@ def shear_warp_level(grid: np.ndarray, level: int, light_dir, lam: float = LAMBD
     light side has a-index c_k (n-1-k if u_a > 0, else k).  Ray (rho_p, rho_q), integers,
     crosses slice k at perpendicular position rho - k r with r = u_perp / |u_a| (|r| <= 1),
     so between slices it moves by -(sign(u_a), r_p, r_q), i.e. along -u, a length
-    t_s = 1/(n |u_a|).  Its optical depth at slice k is the one at slice k-1 plus the part
-    of that step inside the cube, times the density (trilinear, clamp-to-edge) at the
-    midpoint of that part; before slice 0 the ray is outside.  A voxel centre (c_k, j)
-    lies between the rays rho = floor(j + k r) and rho + 1 in each perpendicular axis; the
-    rays whose crossing lies strictly inside the cube carry a mean density M = tau / d_ray
-    (d_ray the exit distance of the crossing toward the light), and
+    t_s = 1/(n |u_a|).  Each ray keeps its optical depth tau and its length ell inside the
+    cube, both from its crossing toward the light: step k adds the part of the move from
+    slice k-1 to slice k that lies inside the cube to ell, and that length times the
+    density (trilinear, clamp-to-edge) at the part's midpoint to tau; before slice 0 the
+    ray is outside.  At slice k a ray's mean density is M = tau / ell, or, for a ray that
+    has not met the cube (ell = 0), the density at its crossing (clamp-to-edge): the limit
+    of tau / ell as the crossing approaches the cube.  A voxel centre (c_k, j) lies between
+    the rays rho = floor(j + k r) and rho + 1 in each perpendicular axis, and
 
-        S(x) = d(x) * sum(w M) / sum(w)
+        S(x) = d(x) * sum(w M)
 
-    over those rays, w the bilinear weights.  T_m = exp(-lambda^(m+1) S), no stop rule.
+    over those four rays, w the bilinear weights and d(x) the exit distance of x toward the
+    light.  T_m = exp(-lambda^(m+1) S), no stop rule.
 
     A light along an axis gives the march's own sums (rays through the voxel centres); a
     homogeneous medium gives sigma d(x) for any light (every ray carries M = sigma).  For a
     smooth density the interpolation error does not accumulate along the rays: it is
     second order in the voxel size on average and first order at the rays through a cube
-    edge, where d has a kink.
+    edge, where d has a kink.  S is continuous in the light direction.
     """
     n = grid.shape[0]
     u = -np.asarray(light_dir, dtype=np.float64)
@@ -283,6 +286,7 @@ def shear_warp_level(grid: np.ndarray, level: int, light_dir, lam: float = LAMBD
 
     jp, jq = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
     tau = np.zeros(rho_p.shape)
+    ell = np.zeros(rho_p.shape)
     depth = np.zeros((n, n, n))                  # S, [coord a][coord perp0][coord perp1]
     for k in range(n):
         g_prev = crossing(k - 1)
@@ -292,27 +296,22 @@ def shear_warp_level(grid: np.ndarray, level: int, light_dir, lam: float = LAMBD
         if np.any(hit):
             mid = g_prev[hit] + (0.5 * (t0[hit] + t1[hit]))[:, None] * step
             tau[hit] += sample_clamped(grid, to_world(mid)) * (seg[hit] * ts)
-        g_k = crossing(k)
-        inside = ((g_k[..., perp[0]] > -0.5) & (g_k[..., perp[0]] < n - 0.5)
-                  & (g_k[..., perp[1]] > -0.5) & (g_k[..., perp[1]] < n - 0.5))
-        d_ray = exit_distance(to_world(g_k), u)
-        mean = np.where(inside, tau / np.where(inside, d_ray, 1.0), 0.0)
+            ell[hit] += seg[hit] * ts
+        met = ell > 0
+        mean = np.where(met, tau / np.where(met, ell, 1.0),
+                        sample_clamped(grid, to_world(crossing(k))))
         # resample slice k: voxel j between rays floor(j + k r) and floor(j + k r) + 1
         fp_, fq_ = jp + k * r[0], jq + k * r[1]
         p0, q0 = np.floor(fp_).astype(np.int64), np.floor(fq_).astype(np.int64)
         wp1, wq1 = fp_ - p0, fq_ - q0
-        num = np.zeros((n, n))
-        den = np.zeros((n, n))
+        m_vox = np.zeros((n, n))
         for dp, wp in ((0, 1.0 - wp1), (1, wp1)):
             for dq, wq in ((0, 1.0 - wq1), (1, wq1)):
-                ip, iq = p0 + dp - lo[0], q0 + dq - lo[1]
-                w = wp * wq * inside[ip, iq]
-                num += w * mean[ip, iq]
-                den += w
+                m_vox += wp * wq * mean[p0 + dp - lo[0], q0 + dq - lo[1]]
         g_vox = np.empty((n, n, 3))
         g_vox[..., a] = (n - 1 - k) if sgn > 0 else k
         g_vox[..., perp[0]], g_vox[..., perp[1]] = jp, jq
-        depth[(n - 1 - k) if sgn > 0 else k] = exit_distance(to_world(g_vox), u) * num / den
+        depth[(n - 1 - k) if sgn > 0 else k] = exit_distance(to_world(g_vox), u) * m_vox
     coords = [a] + perp
     depth = depth.transpose([coords.index(2), coords.index(1), coords.index(0)])  # [z, y, x]
     return np.exp(-(lam ** (level + 1)) * depth)

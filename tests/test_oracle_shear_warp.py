@@ -85,3 +85,19 @@ def test_bounds_and_ray_order():
         assert np.all(t > 0) and np.all(t <= 1)
     t = O.shear_warp_level(v, 0, np.array([0.0, 0.0, -1.0]))   # light travels toward -z
     assert np.all(np.diff(t, axis=0) >= 0)                     # deeper (lower z): darker
+
+
+@pytest.mark.parametrize("light", [(0.6, -0.8, 0.0), (3.0, 4.0, -12.0), (1.0, 1.0, 0.0),
+                                   (-1.0, 0.5, 0.25)])
+def test_continuous_in_the_light_direction(light):
+    # Lights whose shifts r are simple fractions put ray crossings exactly on cube faces;
+    # a nudge of 1e-9 moves them across, and the field must not jump (a ray that has not
+    # met the cube carries the density at its crossing, the limit of its mean).
+    rng = np.random.default_rng(11)
+    v = synth.cloud_volume(24, 5, 64.0).astype(np.float64)
+    l = np.asarray(light, dtype=np.float64)
+    l /= np.linalg.norm(l)
+    base = O.shear_warp_level(v, 0, l)
+    for _ in range(3):
+        nudged = l + 1e-9 * rng.standard_normal(3)
+        np.testing.assert_allclose(O.shear_warp_level(v, 0, nudged), base, rtol=0, atol=1e-6)
