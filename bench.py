@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--workload", type=int, default=2, choices=(1, 2, 5))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-shear-warp", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=256)
     ap.add_argument("--ncu-case", choices=("f32", "bf16", "simt"),
                     help="small case for ncu captures: shade 32,768 points of the 64^3 fBm "
@@ -263,6 +264,84 @@ def run_reference(args):
 
 
 # ---- the CUDA path ------------------------------------------------------------------------
+def _time_builds(ctx, v, light, method, reps, stream):
+    import torch
+    ms = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.build_transmittance(v, light, 0.6, method=method)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return statistics.median(ms)
+
+
+def run_shear_warp(args, nis, ctx, v, w, cfg, img, hitmask, flush, stream, n_points) -> dict:
+    """The frame of the main measurement with the transmittance from shear-warp rays
+    instead of the march: build times of both, frame throughput, and the frame's
+    difference from the marched FP32 frame."""
+    import torch
+    light, mat, cam = cfg["light"], cfg["material"], cfg["camera"]
+    march_ms = _time_builds(ctx, v, light, nis.TRANSMITTANCE_MARCH, 3, stream)
+    _time_builds(ctx, v, light, nis.TRANSMITTANCE_SHEAR_WARP, 1, stream)
+    sw_ms = _time_builds(ctx, v, light, nis.TRANSMITTANCE_SHEAR_WARP, 5, stream)
+    img_sw = torch.empty_like(img)
+
+    def step():
+        ctx.build_pyramid(v)
+        lt = ctx.build_transmittance(v, light, 0.6, method=nis.TRANSMITTANCE_SHEAR_WARP)
+        ctx.build_phase_table(mat["g"])
+        ctx.render_frame(v, lt, w, mat, cam, out=img_sw)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    a_sw, a_32 = img_sw[hitmask].double(), img[hitmask].double()
+    floor = 5e-2 * a_32.abs().amax(dim=0, keepdim=True)
+    e = (a_sw - a_32).abs() / torch.maximum(a_32.abs(), floor)
+    return {"value": n_points * args.steps / (sum(times) / 1e3), "unit": UNIT,
+            "frame_ms": sum(times) / args.steps,
+            "transmittance_build_ms": {"march": round(march_ms, 4), "shear_warp": round(sw_ms, 4)},
+            "mean_rel_err_vs_marched_frame": float(e.mean()),
+            "max_rel_err_vs_marched_frame": float(e.max())}
+
+
+def plume_transmittance(nis, local: int) -> dict:
+    """Transmittance of the 1024^3 FP16 plume toward its light (all 11 levels) by the march
+    and by shear-warp rays: one build each (timed after a warm-up build of the latter) and
+    the level-0 difference."""
+    import torch
+    cfg = synth.config(5)
+    vol = synth.plume_volume_torch(1024, 9, 128.0, device=f"cuda:{local}")
+    ctx = nis.Context(local)
+    stream = torch.cuda.current_stream()
+    v = ctx.upload_volume(vol)
+    ctx.build_pyramid(v)
+    ctx.sync(timeout_ms=120000)
+    march_ms = _time_builds(ctx, v, cfg["light"], nis.TRANSMITTANCE_MARCH, 1, stream)
+    _time_builds(ctx, v, cfg["light"], nis.TRANSMITTANCE_SHEAR_WARP, 1, stream)
+    sw_ms = _time_builds(ctx, v, cfg["light"], nis.TRANSMITTANCE_SHEAR_WARP, 2, stream)
+    a = ctx.build_transmittance(v, cfg["light"], 0.6)
+    b = ctx.build_transmittance(v, cfg["light"], 0.6, method=nis.TRANSMITTANCE_SHEAR_WARP)
+    d = (ctx.copy_transmittance(a, v, 0) - ctx.copy_transmittance(b, v, 0)).abs()
+    out = {"volume": "1024^3 float16 plume, 11 levels",
+           "transmittance_build_ms": {"march": round(march_ms, 3), "shear_warp": round(sw_ms, 3)},
+           "level0_max_abs_dT": float(d.max()), "level0_mean_abs_dT": float(d.mean())}
+    del d
+    ctx.close()
+    return out
+
+
 def run_serving(args, nis, blob, local: int) -> dict:
     """256 Poisson-arriving render requests (grids 128^3-512^3 FP16, images 256^2 to 1080p,
     g and albedo per request) through the continuous-batching server under a 120 GB HBM
@@ -456,6 +535,11 @@ def run_nis(args):
                         "frac": mlp8_tf / (2 * peaks_bf["bf16_tflops_sustained"]),
                         "peak_source": f"{peaks_bf['source']} cuBLAS BF16 sustained x 2 (nominal FP8/BF16 ratio)"}}
 
+    # ---- the same frames with the transmittance from shear-warp rays (O(N^3) per level)
+    sw = None
+    if not args.no_shear_warp:
+        sw = run_shear_warp(args, nis, ctx, v, w, cfg, img, hitmask, flush, stream, n_points)
+
     # ---- end to end through the C ABI from page-locked host memory
     host_vol = torch.from_numpy(vol_np).pin_memory()
     host_img = torch.empty(img.shape, dtype=torch.float32).pin_memory()
@@ -530,6 +614,7 @@ def run_nis(args):
             "roofline": roof,
             "bf16": bf16,
             "fp8": fp8,
+            "shear_warp": sw,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(vol_np.nbytes),
                     "d2h_bytes_per_step": int(img.numel() * 4),
@@ -538,6 +623,8 @@ def run_nis(args):
     ctx.close()
     if not args.no_serving:
         line["serving"] = run_serving(args, nis, blob, local)
+    if not args.no_shear_warp:
+        line["shear_warp"]["plume1024"] = plume_transmittance(nis, local)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, vol_np, weights)
     print(json.dumps(line), flush=True)

@@ -148,6 +148,29 @@ nis_status nis_build_pyramid(nis_ctx *ctx, nis_volume vol, nis_stream stream);
 nis_status nis_build_transmittance(nis_ctx *ctx, nis_volume vol, const float light_dir[3],
                                    float lambda, nis_stream stream, nis_light *out);
 
+/* Transmittance methods of nis_build_transmittance_method. */
+#define NIS_TRANSMITTANCE_MARCH 0       /* the march above, O(N^4) per level */
+#define NIS_TRANSMITTANCE_SHEAR_WARP 1  /* O(N^3) approximation, below */
+
+/* nis_build_transmittance with a choice of method (no counterpart in the paper, which
+ * marches every voxel).  NIS_TRANSMITTANCE_SHEAR_WARP approximates Eq. 1's depth for large
+ * grids: parallel rays toward the light cross the slices normal to the axis a where
+ * |light_dir| is largest at positions that shift by r = u_perp / |u_a| per slice (u =
+ * -light_dir); each ray sums, slice by slice, the density at the midpoint of its part inside
+ * the cube times that part's length; each voxel centre takes the mean density (depth / exit
+ * distance) of the four rays around it, bilinear weights over those whose crossing lies
+ * strictly inside the cube, times its own exit distance.  No stop rule.  A light along an
+ * axis reproduces the march (to rounding), a homogeneous medium gives the exact depth, and
+ * otherwise the error is an interpolation error made once per voxel: second order in the
+ * voxel size on average, first order on rays through a cube edge.  It takes N_0 + 1
+ * launches of one kernel (all levels together) and a ray scratch of about
+ * 2 (1 + |r_p|)(1 + |r_q|) N^2 floats per level, owned by the context (grow-only; calls on
+ * one context that overlap on the GPU race on it).  A light is identified by volume,
+ * direction, lambda and method.  Unknown methods return NIS_ERR_INVALID_ARG. */
+nis_status nis_build_transmittance_method(nis_ctx *ctx, nis_volume vol, const float light_dir[3],
+                                          float lambda, int method, nis_stream stream,
+                                          nis_light *out);
+
 /* Parses a weight blob (80-byte header, float32 tensors in the fixed order below, a
  * position-weighted word checksum) and uploads it at `precision`.  The caller keeps the
  * blob.  Tensor order: CNN[12]{w1 16x1x3x3x3, b1, w2 16x16x3x3x3, b2}, SE[12]{w1 2x8, b1,

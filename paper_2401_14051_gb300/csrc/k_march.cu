@@ -86,4 +86,216 @@ void launch_march(const float *level, const unsigned char *occ, int n, int m, fl
         march_kernel<size_t><<<blocks, threads, 0, s>>>(level, occ, n, ux, uy, uz, scale, out);
 }
 
+// ---- shear-warp transmittance ------------------------------------------------------------
+// An O(N^3) approximation of the march for large grids (not in the paper).  Rays toward
+// the light are parallel, so the slices normal to the dominant axis a of u meet them at
+// positions shifted by the same fraction per slice: ray (rho_p, rho_q) crosses slice k
+// (counted from the light side) at rho - k r, r = u_perp / |u_a|.  Every ray keeps its
+// optical depth and its length inside the cube from its crossing toward the light.  Step
+// k advances every ray from slice k-1 to slice k (the part of that move inside the cube,
+// its density taken at the part's midpoint) and, in the same launch, fills slice k-1: a
+// voxel centre lies between four rays and takes their bilinearly weighted mean density
+// (depth / length; for a ray that has not met the cube, the density at its crossing)
+// times its own exit distance.  The interpolation happens once per voxel, so its error
+// does not build up along the rays; a light along an axis gives the march's sums and a
+// homogeneous medium the exact depth.
+namespace {
+
+constexpr int kSwMaxSeg = 2 * kMaxLevels;
+
+// the work of one step: per level, a ray segment (k < n) and a voxel segment (1 <= k <= n)
+struct SwStep {
+    int k, n_seg;
+    unsigned total;
+    unsigned start[kSwMaxSeg];
+    unsigned char level[kSwMaxSeg], voxels[kSwMaxSeg];
+};
+
+__device__ __forceinline__ void sw_xyz(const ShearWarpArgs &a, float ga, float gp, float gq,
+                                       float &x, float &y, float &z) {
+    x = a.ax_a == 0 ? ga : (a.ax_p == 0 ? gp : gq);
+    y = a.ax_a == 1 ? ga : (a.ax_p == 1 ? gp : gq);
+    z = a.ax_a == 2 ? ga : (a.ax_p == 2 ? gp : gq);
+}
+
+// intersects the parameter range [t0, t1] of g0 + t dg with the closed cube [-1/2, n-1/2]
+// (inv_dg = 1 / dg, or 0 for dg = 0)
+__device__ __forceinline__ void sw_clip(float g0, float inv_dg, float nhi, float &t0, float &t1) {
+    if (inv_dg != 0.f) {
+        const float lo = (-0.5f - g0) * inv_dg, hi = (nhi - g0) * inv_dg;
+        t0 = fmaxf(t0, fminf(lo, hi));
+        t1 = fminf(t1, fmaxf(lo, hi));
+    } else if (g0 < -0.5f || g0 > nhi) {
+        t1 = -1.f;
+    }
+}
+
+// exit distance toward the light of the grid point (gx, gy, gz), in cube units
+__device__ __forceinline__ float sw_exit(const ShearWarpArgs &a, float gx, float gy, float gz,
+                                         float nhi, float inv_n) {
+    float t = 3.0e38f;
+    if (a.ux > 0.f) t = fminf(t, (nhi - gx) * a.iux); else if (a.ux < 0.f) t = fminf(t, (gx + 0.5f) * a.iux);
+    if (a.uy > 0.f) t = fminf(t, (nhi - gy) * a.iuy); else if (a.uy < 0.f) t = fminf(t, (gy + 0.5f) * a.iuy);
+    if (a.uz > 0.f) t = fminf(t, (nhi - gz) * a.iuz); else if (a.uz < 0.f) t = fminf(t, (gz + 0.5f) * a.iuz);
+    return fmaxf(t, 0.f) * inv_n;
+}
+
+template <typename Index>
+__global__ void __launch_bounds__(256) shear_warp_kernel(const __grid_constant__ ShearWarpArgs a,
+                                                         const __grid_constant__ SwStep st) {
+    // programmatic dependent launch: the previous step's rays are read only after it ends
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= st.total) return;
+    int s = 0;
+    while (s + 1 < st.n_seg && t >= st.start[s + 1]) ++s;
+    const ShearWarpLevel &L = a.lv[st.level[s]];
+    const unsigned i = t - st.start[s];
+    const int k = st.k, n = L.n;
+    const Index N = (Index)n, d1 = n > 1 ? 1 : 0, dn = n > 1 ? N : 0, dnn = n > 1 ? N * N : 0;
+    const float hi = (float)(n - 1), top = (float)(n > 1 ? n - 2 : 0);
+    if (!st.voxels[s]) {
+        // ray (lo_p + ip, lo_q + iq): from its crossing of slice k-1 one step along
+        // (-sgn, -r_p, -r_q) to slice k.  Stored: (depth, length) once it has met the cube,
+        // (density at the crossing, 0) before.
+        const int ip = (int)(i % (unsigned)L.P), iq = (int)(i / (unsigned)L.P);
+        const float sg = (float)a.sgn, nhi = (float)n - 0.5f;
+        const float ga = a.sgn > 0 ? (float)(n - k) : (float)(k - 1);
+        const float gp = (float)(L.lo_p + ip) - (float)(k - 1) * L.r_p;
+        const float gq = (float)(L.lo_q + iq) - (float)(k - 1) * L.r_q;
+        float t0 = 0.f, t1 = 1.f;
+        sw_clip(ga, -sg, nhi, t0, t1);
+        sw_clip(gp, -L.inv_rp, nhi, t0, t1);
+        sw_clip(gq, -L.inv_rq, nhi, t0, t1);
+        float tau = 0.f, ell = 0.f;
+        if (k > 0) {
+            const float2 old = L.ray[(k - 1) & 1][i];
+            if (old.y > 0.f) { tau = old.x; ell = old.y; }
+        }
+        if (t1 > t0) {
+            const float tm = 0.5f * (t0 + t1), len = (t1 - t0) * L.ts;
+            float x, y, z;
+            sw_xyz(a, ga - sg * tm, gp - L.r_p * tm, gq - L.r_q * tm, x, y, z);
+            tau += sample_cell<Index>(L.rho, L.occ, N, hi, top, d1, dn, dnn, x, y, z) * len;
+            ell += len;
+        }
+        if (!(ell > 0.f)) {
+            // voxels read rays whose crossing is within one voxel of the cube
+            const float cp = gp - L.r_p, cq = gq - L.r_q;
+            tau = 0.f;
+            if (cp >= -2.f && cp <= (float)n + 1.f && cq >= -2.f && cq <= (float)n + 1.f) {
+                float x, y, z;
+                sw_xyz(a, ga - sg, cp, cq, x, y, z);
+                tau = sample_cell<Index>(L.rho, L.occ, N, hi, top, d1, dn, dnn, x, y, z);
+            }
+            ell = 0.f;
+        }
+        L.ray[k & 1][i] = make_float2(tau, ell);
+    } else {
+        // voxel (jp, jq) of slice k-1 between the rays floor(j + (k-1) r) and the next one
+        const int kk = k - 1;
+        const int jp = (int)(i % (unsigned)n), jq = (int)(i / (unsigned)n);
+        const float fp = (float)jp + (float)kk * L.r_p, fq = (float)jq + (float)kk * L.r_q;
+        const float p0 = floorf(fp), q0 = floorf(fq);
+        const float wp = fp - p0, wq = fq - q0;
+        const float2 *ray = L.ray[kk & 1];
+        float mean = 0.f;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int dp = c & 1, dq = c >> 1;
+            const float w = (dp ? wp : 1.f - wp) * (dq ? wq : 1.f - wq);
+            const int ip = min(max((int)p0 + dp - L.lo_p, 0), L.P - 1);
+            const int iq = min(max((int)q0 + dq - L.lo_q, 0), L.Q - 1);
+            const float2 rv = ray[(size_t)iq * L.P + ip];
+            mean += w * (rv.y > 0.f ? __fdividef(rv.x, rv.y) : rv.x);
+        }
+        const float ga = a.sgn > 0 ? (float)(n - 1 - kk) : (float)kk;
+        float x, y, z;
+        sw_xyz(a, ga, (float)jp, (float)jq, x, y, z);
+        const float d = sw_exit(a, x, y, z, (float)n - 0.5f, 1.0f / (float)n);
+        L.T[((Index)z * N + (Index)y) * N + (Index)x] = expf(-L.scale * d * mean);
+    }
+}
+
+}  // namespace
+
+void shear_warp_setup(ShearWarpArgs &a, const int *sizes, int levels, float ux, float uy,
+                      float uz, float lam, size_t *ray_floats) {
+    const double u[3] = {ux, uy, uz};
+    int ax = 0;
+    for (int c = 1; c < 3; ++c)
+        if (std::fabs(u[c]) > std::fabs(u[ax])) ax = c;
+    a.levels = levels;
+    a.sgn = u[ax] > 0 ? 1 : -1;
+    a.ax_a = ax;
+    a.ax_p = ax == 0 ? 1 : 0;
+    a.ax_q = ax == 2 ? 1 : 2;
+    a.ux = ux;
+    a.uy = uy;
+    a.uz = uz;
+    a.iux = ux != 0.f ? (float)(1.0 / std::fabs(u[0])) : 0.f;
+    a.iuy = uy != 0.f ? (float)(1.0 / std::fabs(u[1])) : 0.f;
+    a.iuz = uz != 0.f ? (float)(1.0 / std::fabs(u[2])) : 0.f;
+    const double ua = std::fabs(u[ax]);
+    const double rp = u[a.ax_p] / ua, rq = u[a.ax_q] / ua;
+    for (int m = 0; m < levels; ++m) {
+        ShearWarpLevel &L = a.lv[m];
+        const int n = sizes[m];
+        L.n = n;
+        L.lo_p = (int)std::floor(-1.0 + std::min(0.0, (n - 1) * rp));
+        L.lo_q = (int)std::floor(-1.0 + std::min(0.0, (n - 1) * rq));
+        L.P = (int)std::ceil(n + std::max(0.0, (n - 1) * rp)) - L.lo_p + 1;
+        L.Q = (int)std::ceil(n + std::max(0.0, (n - 1) * rq)) - L.lo_q + 1;
+        L.r_p = (float)rp;
+        L.r_q = (float)rq;
+        L.inv_rp = rp != 0.0 ? (float)(1.0 / rp) : 0.f;
+        L.inv_rq = rq != 0.0 ? (float)(1.0 / rq) : 0.f;
+        L.ts = (float)(1.0 / (n * ua));
+        L.scale = powf(lam, (float)(m + 1));
+        ray_floats[m] = 4 * (size_t)L.P * L.Q;
+    }
+}
+
+void launch_shear_warp(const ShearWarpArgs &a, cudaStream_t s) {
+    const int n0 = a.lv[0].n;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    for (int k = 0; k <= n0; ++k) {
+        SwStep st{};
+        st.k = k;
+        unsigned total = 0;
+        int ns = 0;
+        for (int m = 0; m < a.levels; ++m) {
+            const ShearWarpLevel &L = a.lv[m];
+            if (k < L.n) {
+                st.start[ns] = total;
+                st.level[ns] = (unsigned char)m;
+                st.voxels[ns++] = 0;
+                total += (unsigned)L.P * (unsigned)L.Q;
+            }
+            if (k >= 1 && k <= L.n) {
+                st.start[ns] = total;
+                st.level[ns] = (unsigned char)m;
+                st.voxels[ns++] = 1;
+                total += (unsigned)L.n * (unsigned)L.n;
+            }
+        }
+        st.n_seg = ns;
+        st.total = total;
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3((total + 255) / 256);
+        cfg.blockDim = dim3(256);
+        cfg.stream = s;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        note_launch();
+        if (n0 <= 1024)
+            cudaLaunchKernelEx(&cfg, shear_warp_kernel<unsigned>, a, st);
+        else
+            cudaLaunchKernelEx(&cfg, shear_warp_kernel<size_t>, a, st);
+    }
+}
+
 }  // namespace nis

@@ -97,6 +97,27 @@ void launch_occupancy(const float *level, int n, unsigned char *occ, cudaStream_
     occupancy_kernel<<<blocks, 256, 0, s>>>(level, n, occ);
 }
 
+// out[c][r] = in[r][c] for an R x C row-major matrix, through 32 x 32 shared-memory tiles
+// (one tile per block, 32 x 8 threads, both sides coalesced)
+__global__ void __launch_bounds__(256) transpose_kernel(const float *__restrict__ in, size_t R,
+                                                        size_t C, size_t tiles_c,
+                                                        float *__restrict__ out) {
+    __shared__ float tile[32][33];
+    const size_t r0 = (blockIdx.x / tiles_c) * 32, c0 = (blockIdx.x % tiles_c) * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int i = ty; i < 32; i += 8)
+        if (r0 + i < R && c0 + tx < C) tile[i][tx] = __ldg(in + (r0 + i) * C + c0 + tx);
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8)
+        if (c0 + i < C && r0 + tx < R) out[(c0 + i) * R + r0 + tx] = tile[tx][i];
+}
+
+void launch_transpose(const float *in, size_t R, size_t C, float *out, cudaStream_t s) {
+    const size_t tiles_r = (R + 31) / 32, tiles_c = (C + 31) / 32;
+    note_launch();
+    transpose_kernel<<<(unsigned)(tiles_r * tiles_c), 256, 0, s>>>(in, R, C, tiles_c, out);
+}
+
 // PairView level: entry (z, y, i) = {rho, T} at x = i - 1 and x = i (borders 0 and 1).
 __global__ void pack_pairs_kernel(const float *__restrict__ rho, const float *__restrict__ T, int n,
                                   float4 *__restrict__ out) {

@@ -30,12 +30,19 @@ struct Volume {
     size_t staging_bytes = 0;
     bool pyramid = false;
     uint64_t version = 0;             // counts pyramid builds (lights pair with one of them)
+    // x-major copy of the pyramid, [x][z][y] per level, and its occupancy: the shear-warp
+    // sweep of a light along x reads its slices contiguously (built on first use, from
+    // pyramid build `xmaj_version`)
+    float *xmaj = nullptr;
+    unsigned char *xmaj_occ = nullptr;
+    uint64_t xmaj_version = 0;
 };
 
 struct Light {
     nis_handle vol = 0;
     float dir[3] = {0, 0, 0};         // unit propagation direction
     float lambda = 0.6f;
+    int method = NIS_TRANSMITTANCE_MARCH;
     float *data = nullptr;            // same level layout as the volume
     // density and transmittance side by side for the gathers (PairView layout), packed
     // from the volume's pyramid of build `pair_version` (0: not packed)
@@ -127,6 +134,10 @@ struct nis_ctx {
     float *mix_pts = nullptr, *mix_om = nullptr, *mix_rgb = nullptr, *mix_dec = nullptr;
     int *mix_req = nullptr, *mix_seg_start = nullptr, *mix_seg_desc = nullptr;
     ReqDesc *mix_descs = nullptr;
+    // ray states of the shear-warp transmittance, and its x-major output before the
+    // transpose (grow-only, floats)
+    float *sw_rays = nullptr, *sw_T = nullptr;
+    size_t sw_cap = 0, sw_T_cap = 0;
     int num_sms = 0;
     nis_handle next = 1;
     // kernel timing (nis_profile)
@@ -266,6 +277,26 @@ nis_status build_pyramid_impl(nis_ctx *ctx, Volume &v, cudaStream_t s) {
     NIS_CUDA(cudaGetLastError());
     v.pyramid = true;
     ++v.version;
+    return NIS_OK;
+}
+
+// The x-major copy of the pyramid and its occupancy, (re)built after each pyramid build.
+nis_status ensure_xmajor(nis_ctx *ctx, Volume &v, cudaStream_t s) {
+    if (v.xmaj && v.xmaj_version == v.version) return NIS_OK;
+    nis_status st;
+    if (!v.xmaj) {
+        size_t occ_total = 0;
+        for (int m = 0; m < v.levels; ++m) occ_total += (size_t)v.sizes[m] * v.sizes[m] * v.sizes[m];
+        if ((st = dev_alloc_t(ctx, v.total, &v.xmaj, s))) return st;
+        if ((st = dev_alloc_t(ctx, occ_total, &v.xmaj_occ, s))) return st;
+    }
+    for (int m = 0; m < v.levels; ++m) {
+        const size_t n = (size_t)v.sizes[m];
+        launch_transpose(v.data + v.off[m], n * n, n, v.xmaj + v.off[m], s);   // [(z,y)][x] -> [x][(z,y)]
+        launch_occupancy(v.xmaj + v.off[m], (int)n, v.xmaj_occ + v.occ_off[m], s);
+    }
+    NIS_CUDA(cudaGetLastError());
+    v.xmaj_version = v.version;
     return NIS_OK;
 }
 
@@ -1376,8 +1407,17 @@ nis_status nis_build_pyramid(nis_ctx *ctx, nis_volume vol, nis_stream stream) {
 
 nis_status nis_build_transmittance(nis_ctx *ctx, nis_volume vol, const float light_dir[3],
                                    float lambda, nis_stream stream, nis_light *out) {
+    return nis_build_transmittance_method(ctx, vol, light_dir, lambda, NIS_TRANSMITTANCE_MARCH,
+                                          stream, out);
+}
+
+nis_status nis_build_transmittance_method(nis_ctx *ctx, nis_volume vol, const float light_dir[3],
+                                          float lambda, int method, nis_stream stream,
+                                          nis_light *out) {
     if (!ctx) return NIS_ERR_INVALID_ARG;
     if (!light_dir || !out) return fail(ctx, NIS_ERR_INVALID_ARG, "NULL light_dir or out");
+    if (method != NIS_TRANSMITTANCE_MARCH && method != NIS_TRANSMITTANCE_SHEAR_WARP)
+        return fail(ctx, NIS_ERR_INVALID_ARG, "unknown transmittance method");
     if (!(lambda > 0.f && lambda <= 1.f)) return fail(ctx, NIS_ERR_INVALID_ARG, "lambda must lie in (0, 1]");
     Volume *v = lookup(ctx->vols, vol);
     if (!v) return fail(ctx, NIS_ERR_NOT_READY, "unknown or released volume handle");
@@ -1391,23 +1431,75 @@ nis_status nis_build_transmittance(nis_ctx *ctx, nis_volume vol, const float lig
     if (!v->pyramid && (st = build_pyramid_impl(ctx, *v, s))) return st;
     nis_handle h = 0;
     for (auto &kv : ctx->lights)
-        if (kv.second.vol == vol && kv.second.lambda == lambda &&
+        if (kv.second.vol == vol && kv.second.lambda == lambda && kv.second.method == method &&
             std::memcmp(kv.second.dir, dir, sizeof(dir)) == 0) { h = kv.first; break; }
     if (!h) {
         Light L;
         L.vol = vol;
         std::memcpy(L.dir, dir, sizeof(dir));
         L.lambda = lambda;
+        L.method = method;
         if ((st = dev_alloc_t(ctx, v->total, &L.data, s))) return st;
         h = ctx->next++;
         ctx->lights[h] = L;
     }
     Light &L = ctx->lights[h];
     // u = -l points toward the light
-    for (int m = 0; m < v->levels; ++m) {
+    if (method == NIS_TRANSMITTANCE_MARCH) {
+        for (int m = 0; m < v->levels; ++m) {
+            ProfScope ps(ctx, "march", s);
+            launch_march(v->data + v->off[m], v->occ + v->occ_off[m], v->sizes[m], m, -dir[0],
+                         -dir[1], -dir[2], lambda, L.data + v->off[m], s);
+        }
+    } else {
+        ShearWarpArgs sw{};
+        size_t rays[kMaxLevels] = {}, total = 0;
+        shear_warp_setup(sw, v->sizes, v->levels, -dir[0], -dir[1], -dir[2], lambda, rays);
+        for (int m = 0; m < v->levels; ++m) total += rays[m];
         ProfScope ps(ctx, "march", s);
-        launch_march(v->data + v->off[m], v->occ + v->occ_off[m], v->sizes[m], m, -dir[0], -dir[1],
-                     -dir[2], lambda, L.data + v->off[m], s);
+        // slices normal to x are strided in [z][y][x]: sweep the x-major copy instead, as a
+        // cube whose (x, y, z) are the volume's (y, z, x), and transpose the result back
+        const bool xmajor = sw.ax_a == 0;
+        if (xmajor) {
+            if ((st = ensure_xmajor(ctx, *v, s))) return st;
+            if (ctx->sw_T_cap < v->total) {
+                dev_free(ctx, ctx->sw_T);
+                ctx->sw_T = nullptr;
+                ctx->sw_T_cap = 0;
+                if ((st = dev_alloc_t(ctx, v->total, &ctx->sw_T, s))) return st;
+                ctx->sw_T_cap = v->total;
+            }
+            sw.ax_a = 2;
+            sw.ax_p = 0;
+            sw.ax_q = 1;
+            const float ux = sw.ux, iux = sw.iux;
+            sw.ux = sw.uy; sw.iux = sw.iuy;
+            sw.uy = sw.uz; sw.iuy = sw.iuz;
+            sw.uz = ux;    sw.iuz = iux;
+        }
+        if (ctx->sw_cap < total) {
+            dev_free(ctx, ctx->sw_rays);
+            ctx->sw_rays = nullptr;
+            ctx->sw_cap = 0;
+            if ((st = dev_alloc_t(ctx, total, &ctx->sw_rays, s))) return st;
+            ctx->sw_cap = total;
+        }
+        float *r = ctx->sw_rays;
+        for (int m = 0; m < v->levels; ++m) {
+            ShearWarpLevel &Lm = sw.lv[m];
+            Lm.rho = (xmajor ? v->xmaj : v->data) + v->off[m];
+            Lm.occ = (xmajor ? v->xmaj_occ : v->occ) + v->occ_off[m];
+            Lm.T = (xmajor ? ctx->sw_T : L.data) + v->off[m];
+            Lm.ray[0] = reinterpret_cast<float2 *>(r);
+            Lm.ray[1] = reinterpret_cast<float2 *>(r + rays[m] / 2);
+            r += rays[m];
+        }
+        launch_shear_warp(sw, s);
+        if (xmajor)
+            for (int m = 0; m < v->levels; ++m) {
+                const size_t n = (size_t)v->sizes[m];
+                launch_transpose(ctx->sw_T + v->off[m], n, n * n, L.data + v->off[m], s);
+            }
     }
     NIS_CUDA(cudaGetLastError());
     L.pair_version = 0;                       // new transmittance: re-pack
@@ -1601,6 +1693,8 @@ nis_status nis_release(nis_ctx *ctx, nis_handle h) {
         dev_free(ctx, v->sigma_max);
         dev_free(ctx, v->staging);
         dev_free(ctx, v->occ);
+        dev_free(ctx, v->xmaj);
+        dev_free(ctx, v->xmaj_occ);
         ctx->vols.erase(h);
         return NIS_OK;
     }

@@ -179,9 +179,40 @@ void launch_pack_pairs(const float *rho, const float *T, int n, float4 *out, cud
 // occupancy of the trilinear cells of an n^3 level, one byte per base voxel (i, j, k):
 // occ = 0 guarantees that the cell's corners (i..min(i+1, n-1), likewise j, k) are all zero
 void launch_occupancy(const float *level, int n, unsigned char *occ, cudaStream_t s);
+// out[c][r] = in[r][c] for an R x C row-major float matrix (R / 32 * C / 32 < 2^31 tiles)
+void launch_transpose(const float *in, size_t R, size_t C, float *out, cudaStream_t s);
 // transmittance of one level
 void launch_march(const float *level, const unsigned char *occ, int n, int m, float ux,
                   float uy, float uz, float lam, float *out, cudaStream_t s);
+// shear-warp transmittance, an O(N^3) approximation of the march (all levels, one light):
+// parallel rays toward the light cross the slices normal to the dominant axis a of u at
+// perpendicular positions rho - k r (rho integer, r = u_perp / |u_a|, k the slice count
+// from the light side); each ray keeps a running optical depth and in-cube length, and
+// each voxel centre takes the mean density of its four nearest rays times its own exit
+// distance
+struct ShearWarpLevel {
+    const float *rho;             // density level, [z][y][x]
+    const unsigned char *occ;     // its cell occupancy
+    float *T;                     // transmittance out, [z][y][x]
+    float2 *ray[2];               // ray (depth, length) [q][p], ping-pong by step parity
+    int n, P, Q, lo_p, lo_q;      // P x Q rays, ray (lo_p + ip, lo_q + iq) at index iq P + ip
+    float r_p, r_q, ts, scale;    // shifts per slice, step length 1/(n |u_a|), lambda^(m+1)
+    float inv_rp, inv_rq;         // 1 / r (0 where r = 0)
+};
+struct ShearWarpArgs {
+    int levels, sgn;              // sgn = sign(u_a): slice a-index of step k is n-1-k or k
+    int ax_a, ax_p, ax_q;         // coordinate (0 x, 1 y, 2 z) of the axes a, p < q in the
+                                  // arrays the kernel reads and writes
+    float ux, uy, uz;             // unit direction toward the light, in those coordinates
+    float iux, iuy, iuz;          // 1 / |u| per coordinate (0 where u = 0)
+    ShearWarpLevel lv[kMaxLevels];
+};
+// fills the geometry of `a` (axes, shifts, ray ranges; not the pointers) for levels of the
+// given sizes and returns the ray-buffer floats each level needs (4 per ray) in ray_floats
+void shear_warp_setup(ShearWarpArgs &a, const int *sizes, int levels, float ux, float uy,
+                      float uz, float lam, size_t *ray_floats);
+// enqueues the n_0 + 1 sweep steps (the ray pointers of `a` set by the caller)
+void launch_shear_warp(const ShearWarpArgs &a, cudaStream_t s);
 // phase function of the phase features: one HG lobe, or a mixture of up to 3 (Eq. 6)
 struct PhaseSpec {
     int n;

@@ -21,6 +21,7 @@ STATUS = {0: "OK", -1: "INVALID_ARG", -2: "NOT_READY", -3: "BUDGET", -4: "OOM", 
           -6: "TIMEOUT", -7: "UNIMPLEMENTED", -8: "BAD_BLOB", -9: "BAD_DATA"}
 DTYPE_F32, DTYPE_F16 = 0, 1
 PREC_F32, PREC_BF16, PREC_FP8, PREC_F32_SIMT = 0, 1, 2, 3
+TRANSMITTANCE_MARCH, TRANSMITTANCE_SHEAR_WARP = 0, 1
 CAMERA_ORTHO, CAMERA_PERSP = 0, 1
 N_LAYERS, N_LAT, N_ALPHA, N_SETS = 12, 225, 1024, 5
 
@@ -95,6 +96,9 @@ _SIGS = {
     "nis_build_pyramid": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p]),
     "nis_build_transmittance": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(C.c_float), C.c_float,
                                           C.c_void_p, C.POINTER(C.c_uint64)]),
+    "nis_build_transmittance_method": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(C.c_float),
+                                                 C.c_float, C.c_int, C.c_void_p,
+                                                 C.POINTER(C.c_uint64)]),
     "nis_load_weights": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int, C.c_void_p,
                                    C.POINTER(C.c_uint64)]),
     "nis_shade_points": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint64,
@@ -287,11 +291,16 @@ class Context:
     def build_pyramid(self, vol: int, stream=None):
         self._check(self.lib.nis_build_pyramid(self.h, vol, _stream(stream)))
 
-    def build_transmittance(self, vol: int, light_dir, lam: float = 0.6, stream=None) -> int:
+    def build_transmittance(self, vol: int, light_dir, lam: float = 0.6, stream=None,
+                            method: int | None = None) -> int:
         out = C.c_uint64()
         d = (C.c_float * 3)(*[float(x) for x in light_dir])
-        self._check(self.lib.nis_build_transmittance(self.h, vol, d, lam, _stream(stream),
-                                                     C.byref(out)))
+        if method is None:
+            self._check(self.lib.nis_build_transmittance(self.h, vol, d, lam, _stream(stream),
+                                                         C.byref(out)))
+        else:
+            self._check(self.lib.nis_build_transmittance_method(self.h, vol, d, lam, method,
+                                                                _stream(stream), C.byref(out)))
         return out.value
 
     def load_weights(self, blob: bytes, precision: int = PREC_F32, stream=None) -> int:
