@@ -58,9 +58,11 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-shear-warp", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=256)
-    ap.add_argument("--ncu-case", choices=("f32", "bf16", "simt"),
+    ap.add_argument("--ncu-case", choices=("f32", "bf16", "simt", "sweep"),
                     help="small case for ncu captures: shade 32,768 points of the 64^3 fBm "
-                         "volume twice at this precision, print nothing else")
+                         "volume twice at this precision (sweep: one shear-warp "
+                         "transmittance of a 512^3 FP16 plume toward a light along x), print "
+                         "nothing else")
     return ap.parse_args()
 
 
@@ -633,6 +635,14 @@ def run_nis(args):
 def run_ncu_case(args):
     import torch
     from paper_2401_14051_gb300 import nis
+    if args.ncu_case == "sweep":
+        ctx = nis.Context(0)
+        v = ctx.upload_volume(synth.plume_volume_torch(512, 9, 128.0))
+        ctx.build_transmittance(v, synth.unit_vector(10), 0.6, method=nis.TRANSMITTANCE_SHEAR_WARP)
+        ctx.sync(timeout_ms=60000)
+        ctx.close()
+        print("ok")
+        return
     prec = {"f32": nis.PREC_F32, "bf16": nis.PREC_BF16, "simt": nis.PREC_F32_SIMT}[args.ncu_case]
     cfg = synth.config(1)
     ctx = nis.Context(0)

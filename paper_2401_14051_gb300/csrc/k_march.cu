@@ -103,13 +103,26 @@ namespace {
 
 constexpr int kSwMaxSeg = 2 * kMaxLevels;
 
-// the work of one step: per level, a ray segment (k < n) and a voxel segment (1 <= k <= n)
+// the work of one step: per level, a ray segment (k < n) and a voxel segment (1 <= k <= n).
+// A ray segment covers the window of rays whose crossing of slice k-1 or k lies within
+// two voxels of the cube; the others keep their state (rays move monotonically across the
+// window: one not yet in it has not met the cube, and one past it is read no more).
 struct SwStep {
     int k, n_seg;
     unsigned total;
     unsigned start[kSwMaxSeg];
+    int width[kSwMaxSeg];             // threads per row: window width (rays) or n (voxels)
+    float inv_width[kSwMaxSeg];
+    int ip0[kSwMaxSeg], iq0[kSwMaxSeg];   // ray index of the window's first row and column
     unsigned char level[kSwMaxSeg], voxels[kSwMaxSeg];
 };
+
+// (i / w, i % w) for i < 2^24 through a float reciprocal, corrected by one step
+__device__ __forceinline__ void sw_divmod(unsigned i, int w, float inv_w, int &q, int &r) {
+    q = (int)((float)i * inv_w);
+    r = (int)i - q * w;
+    if (r >= w) { ++q; r -= w; } else if (r < 0) { --q; r += w; }
+}
 
 __device__ __forceinline__ void sw_xyz(const ShearWarpArgs &a, float ga, float gp, float gq,
                                        float &x, float &y, float &z) {
@@ -159,7 +172,11 @@ __global__ void __launch_bounds__(256) shear_warp_kernel(const __grid_constant__
         // ray (lo_p + ip, lo_q + iq): from its crossing of slice k-1 one step along
         // (-sgn, -r_p, -r_q) to slice k.  Stored: (depth, length) once it has met the cube,
         // (density at the crossing, 0) before.
-        const int ip = (int)(i % (unsigned)L.P), iq = (int)(i / (unsigned)L.P);
+        int ip, iq;
+        sw_divmod(i, st.width[s], st.inv_width[s], iq, ip);
+        ip += st.ip0[s];
+        iq += st.iq0[s];
+        const unsigned ri = (unsigned)iq * (unsigned)L.P + (unsigned)ip;
         const float sg = (float)a.sgn, nhi = (float)n - 0.5f;
         const float ga = a.sgn > 0 ? (float)(n - k) : (float)(k - 1);
         const float gp = (float)(L.lo_p + ip) - (float)(k - 1) * L.r_p;
@@ -170,7 +187,7 @@ __global__ void __launch_bounds__(256) shear_warp_kernel(const __grid_constant__
         sw_clip(gq, -L.inv_rq, nhi, t0, t1);
         float tau = 0.f, ell = 0.f;
         if (k > 0) {
-            const float2 old = L.ray[(k - 1) & 1][i];
+            const float2 old = L.ray[(k - 1) & 1][ri];
             if (old.y > 0.f) { tau = old.x; ell = old.y; }
         }
         if (t1 > t0) {
@@ -191,11 +208,12 @@ __global__ void __launch_bounds__(256) shear_warp_kernel(const __grid_constant__
             }
             ell = 0.f;
         }
-        L.ray[k & 1][i] = make_float2(tau, ell);
+        L.ray[k & 1][ri] = make_float2(tau, ell);
     } else {
         // voxel (jp, jq) of slice k-1 between the rays floor(j + (k-1) r) and the next one
         const int kk = k - 1;
-        const int jp = (int)(i % (unsigned)n), jq = (int)(i / (unsigned)n);
+        int jp, jq;
+        sw_divmod(i, n, st.inv_width[s], jq, jp);
         const float fp = (float)jp + (float)kk * L.r_p, fq = (float)jq + (float)kk * L.r_q;
         const float p0 = floorf(fp), q0 = floorf(fq);
         const float wp = fp - p0, wq = fq - q0;
@@ -270,14 +288,33 @@ void launch_shear_warp(const ShearWarpArgs &a, cudaStream_t s) {
         for (int m = 0; m < a.levels; ++m) {
             const ShearWarpLevel &L = a.lv[m];
             if (k < L.n) {
-                st.start[ns] = total;
-                st.level[ns] = (unsigned char)m;
-                st.voxels[ns++] = 0;
-                total += (unsigned)L.P * (unsigned)L.Q;
+                // rays whose crossing of slice k-1 or k is within [-2, n+1]
+                auto window = [&](double r, int lo, int count, int &first, int &width) {
+                    const double a0 = std::min((k - 1) * r, k * r), a1 = std::max((k - 1) * r, k * r);
+                    const int r0 = std::max(lo, (int)std::floor(-2.0 + a0));
+                    const int r1 = std::min(lo + count - 1, (int)std::ceil(L.n + 1.0 + a1));
+                    first = r0 - lo;
+                    width = std::max(0, r1 - r0 + 1);
+                };
+                int fp, wp, fq, wq;
+                window(L.r_p, L.lo_p, L.P, fp, wp);
+                window(L.r_q, L.lo_q, L.Q, fq, wq);
+                if (wp > 0 && wq > 0) {
+                    st.start[ns] = total;
+                    st.level[ns] = (unsigned char)m;
+                    st.width[ns] = wp;
+                    st.inv_width[ns] = 1.0f / (float)wp;
+                    st.ip0[ns] = fp;
+                    st.iq0[ns] = fq;
+                    st.voxels[ns++] = 0;
+                    total += (unsigned)wp * (unsigned)wq;
+                }
             }
             if (k >= 1 && k <= L.n) {
                 st.start[ns] = total;
                 st.level[ns] = (unsigned char)m;
+                st.width[ns] = L.n;
+                st.inv_width[ns] = 1.0f / (float)L.n;
                 st.voxels[ns++] = 1;
                 total += (unsigned)L.n * (unsigned)L.n;
             }

@@ -1484,6 +1484,8 @@ nis_status nis_build_transmittance_method(nis_ctx *ctx, nis_volume vol, const fl
             if ((st = dev_alloc_t(ctx, total, &ctx->sw_rays, s))) return st;
             ctx->sw_cap = total;
         }
+        // rays outside a step's window keep their state: all start as not having met the cube
+        NIS_CUDA(cudaMemsetAsync(ctx->sw_rays, 0, total * sizeof(float), s));
         float *r = ctx->sw_rays;
         for (int m = 0; m < v->levels; ++m) {
             ShearWarpLevel &Lm = sw.lv[m];
