@@ -344,11 +344,7 @@ def plume_transmittance(nis, local: int) -> dict:
     return out
 
 
-def run_serving(args, nis, blob, local: int) -> dict:
-    """256 Poisson-arriving render requests (grids 128^3-512^3 FP16, images 256^2 to 1080p,
-    g and albedo per request) through the continuous-batching server under a 120 GB HBM
-    budget, BF16 network.  The arrival rate targets ~70 % GPU load from a measured
-    back-to-back service time."""
+def serving_volumes(args, local: int):
     import torch
     reqs = synth.serving_requests(args.serving_requests)
     t0 = time.perf_counter()
@@ -356,14 +352,23 @@ def run_serving(args, nis, blob, local: int) -> dict:
     pinned = [torch.from_numpy(synth.serving_volume(r["n"], r["seed"], 32.0,
                                                      device=f"cuda:{local}")).pin_memory()
               for r in reqs]
-    vols = [t.numpy() for t in pinned]
-    gen_s = time.perf_counter() - t0
     torch.cuda.synchronize()
+    return reqs, pinned, time.perf_counter() - t0
+
+
+def run_serving(args, nis, blob, local: int, workload, method: int = 0) -> dict:
+    """256 Poisson-arriving render requests (grids 128^3-512^3 FP16, images 256^2 to 1080p,
+    g and albedo per request) through the continuous-batching server under a 120 GB HBM
+    budget, BF16 network.  The arrival rate targets ~70 % GPU load from a measured
+    back-to-back service time.  `method`: the server's transmittance method."""
+    reqs, pinned, gen_s = workload
+    vols = [t.numpy() for t in pinned]
     ctx = nis.Context(local, torch_allocator=False)
     w = ctx.load_weights(blob, nis.PREC_BF16)
     budget = 120 * 2 ** 30
     # service time: 8 requests back to back on their own server
-    srv = nis.Server(ctx, w, budget_bytes=budget, max_batch_points=65536, max_inflight=16)
+    srv = nis.Server(ctx, w, budget_bytes=budget, max_batch_points=65536, max_inflight=16,
+                     transmittance_method=method)
     t0 = time.perf_counter()
     ids = [srv.submit(vols[i], 10 ** 6 + i, reqs[i]["light"], 0.6, reqs[i]["material"],
                       reqs[i]["camera"]) for i in range(8)]
@@ -374,7 +379,8 @@ def run_serving(args, nis, blob, local: int) -> dict:
     rate = 0.7 / service_s
     rng = np.random.default_rng(7)
     gaps = rng.exponential(1.0 / rate, size=len(reqs))
-    srv = nis.Server(ctx, w, budget_bytes=budget, max_batch_points=65536, max_inflight=32)
+    srv = nis.Server(ctx, w, budget_bytes=budget, max_batch_points=65536, max_inflight=32,
+                     transmittance_method=method)
     ids = []
     start = time.perf_counter()
     due = start
@@ -391,6 +397,7 @@ def run_serving(args, nis, blob, local: int) -> dict:
     ctx.close()
     pixels = sum(r["camera"]["width"] * r["camera"]["height"] for r in reqs)
     return {"requests": len(reqs), "precision": "bf16", "hbm_budget_gb": 120,
+            "transmittance": "shear-warp" if method else "march",
             "arrival": f"Poisson, {rate:.1f} req/s (0.7 / back-to-back service time "
                        f"{1e3 * service_s:.1f} ms)",
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
@@ -624,7 +631,12 @@ def run_nis(args):
             "clocks": clk}
     ctx.close()
     if not args.no_serving:
-        line["serving"] = run_serving(args, nis, blob, local)
+        workload = serving_volumes(args, local)
+        line["serving"] = run_serving(args, nis, blob, local, workload)
+        if not args.no_shear_warp:
+            line["serving_shear_warp"] = run_serving(args, nis, blob, local, workload,
+                                                     nis.TRANSMITTANCE_SHEAR_WARP)
+        del workload
     if not args.no_shear_warp:
         line["shear_warp"]["plume1024"] = plume_transmittance(nis, local)
     if world == 1 and not args.no_cpu_baseline:

@@ -266,7 +266,7 @@ nis_status nis_shade_segments(nis_ctx *ctx, nis_weights w, const nis_segment *se
  * A server owns a context (no other calls on that context while the server lives) and one
  * host thread.  Requests -- each a density grid in host memory with its light, material and
  * camera -- are admitted in arrival order while the HBM budget and the in-flight limit
- * allow; an admitted request's volume upload, pyramid, transmittance march and first-hit
+ * allow; an admitted request's volume upload, pyramid, transmittance and first-hit
  * search run on a preparation stream while earlier requests shade on a second stream; the
  * shading points of all ready requests are shaded together in mixed batches
  * (nis_shade_segments), so requests that arrive while others run join the next batch.
@@ -280,6 +280,8 @@ typedef struct nis_server_config {
     size_t hbm_budget_bytes;      /* device memory the server may hold (0 = no limit) */
     int max_batch_points;         /* shading points per mixed batch (<= 65536) */
     int max_inflight;             /* admitted, unfinished requests at most */
+    int transmittance_method;     /* NIS_TRANSMITTANCE_* of every light the server builds
+                                     (0, the march, when zero-initialised) */
 } nis_server_config;
 
 typedef struct nis_request {

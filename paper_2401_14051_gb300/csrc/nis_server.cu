@@ -97,6 +97,17 @@ size_t light_bytes(int n) {
     }
     return level_floats(n) * 4 + pairs * 16;
 }
+// what a shear-warp build may add: the volume's x-major pyramid copy and its occupancy
+// (new volumes), the context's x-major output and ray states (grow-only, bounded here by
+// this grid's size)
+size_t sweep_bytes(int n, bool new_volume) {
+    size_t rays = 0;
+    for (int sz = n;; sz = (sz + 1) / 2) {
+        rays += 2 * (size_t)(2 * sz + 3) * (2 * sz + 3) * 8;
+        if (sz == 1) break;
+    }
+    return (new_volume ? level_floats(n) * 5 : 0) + level_floats(n) * 4 + rays;
+}
 
 }  // namespace
 
@@ -251,7 +262,8 @@ nis_status prepare(nis_server *S, Req *q) {
             q->light = lt->second.h;
         } else {
             ++S->lmiss;
-            if ((rc = nis_build_transmittance(ctx, q->vol, q->r.light_dir, q->r.lambda, st, &q->light)))
+            if ((rc = nis_build_transmittance_method(ctx, q->vol, q->r.light_dir, q->r.lambda,
+                                                      S->cfg.transmittance_method, st, &q->light)))
                 return rc;
             LightEntry e;
             e.h = q->light; e.refs = 1; e.last_use = ++S->tick; e.bytes = light_bytes(q->r.n);
@@ -264,7 +276,8 @@ nis_status prepare(nis_server *S, Req *q) {
                                     &q->vol)))
             return rc;
         if ((rc = nis_build_pyramid(ctx, q->vol, st))) return rc;
-        if ((rc = nis_build_transmittance(ctx, q->vol, q->r.light_dir, q->r.lambda, st, &q->light)))
+        if ((rc = nis_build_transmittance_method(ctx, q->vol, q->r.light_dir, q->r.lambda,
+                                                      S->cfg.transmittance_method, st, &q->light)))
             return rc;
     }
     // per-request buffers and first hits
@@ -321,10 +334,11 @@ void loop(nis_server *S) {
                 if (S->queue.empty() || (int)S->active.size() >= S->cfg.max_inflight) break;
                 q = S->queue.front();
             }
-            size_t need = request_bytes(q);
+            size_t need = request_bytes(q) + light_bytes(q->r.n);   // light, if not cached
             bool cached_vol = q->r.volume_key && S->vols.count(q->r.volume_key);
-            if (!cached_vol) need += 2 * level_floats(q->r.n) * 4 + (size_t)q->r.n * q->r.n * q->r.n * 4;
-            else need += level_floats(q->r.n) * 4;      // transmittance if not cached
+            if (!cached_vol) need += level_floats(q->r.n) * 4 + (size_t)q->r.n * q->r.n * q->r.n * 4;
+            if (S->cfg.transmittance_method == NIS_TRANSMITTANCE_SHEAR_WARP)
+                need += sweep_bytes(q->r.n, !cached_vol);
             if (S->cfg.hbm_budget_bytes) {
                 while (held_bytes(S) + need > S->cfg.hbm_budget_bytes && evict_one(S)) {
                 }
@@ -429,6 +443,9 @@ nis_status nis_server_create(nis_ctx *ctx, nis_weights w, const nis_server_confi
     if (!ctx || !cfg || !out) return NIS_ERR_INVALID_ARG;
     if (cfg->max_batch_points < 1 || cfg->max_batch_points > 65536 || cfg->max_inflight < 1)
         return record_error(ctx, NIS_ERR_INVALID_ARG, "max_batch_points in [1, 65536], max_inflight >= 1");
+    if (cfg->transmittance_method != NIS_TRANSMITTANCE_MARCH &&
+        cfg->transmittance_method != NIS_TRANSMITTANCE_SHEAR_WARP)
+        return record_error(ctx, NIS_ERR_INVALID_ARG, "unknown transmittance method");
     nis_server *S = new nis_server();
     S->ctx = ctx;
     cudaSetDevice(ctx_device(ctx));

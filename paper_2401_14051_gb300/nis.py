@@ -51,7 +51,7 @@ class Segment(C.Structure):
 
 class ServerConfig(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_batch_points", C.c_int),
-                ("max_inflight", C.c_int)]
+                ("max_inflight", C.c_int), ("transmittance_method", C.c_int)]
 
 
 class Request(C.Structure):
@@ -449,10 +449,11 @@ class Server:
     """Continuous-batching render server on its own context (nis_server_*)."""
 
     def __init__(self, ctx: Context, weights: int, budget_bytes: int = 0,
-                 max_batch_points: int = 65536, max_inflight: int = 16):
+                 max_batch_points: int = 65536, max_inflight: int = 16,
+                 transmittance_method: int = TRANSMITTANCE_MARCH):
         self.ctx = ctx
         self.lib = ctx.lib
-        cfg = ServerConfig(budget_bytes, max_batch_points, max_inflight)
+        cfg = ServerConfig(budget_bytes, max_batch_points, max_inflight, transmittance_method)
         h = C.c_void_p()
         ctx._check(self.lib.nis_server_create(ctx.h, weights, C.byref(cfg), C.byref(h)))
         self.h = h

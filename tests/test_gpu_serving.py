@@ -59,31 +59,34 @@ def test_mixed_batch_equals_each_request_alone(nis, prec):
     ctx.close()
 
 
-def _render_direct(nis, r, blob):
+def _render_direct(nis, r, blob, method=0):
     ctx = nis.Context(0, torch_allocator=False)
     w = ctx.load_weights(blob)
     v = ctx.upload_volume(r["vol"])
-    l = ctx.build_transmittance(v, r["light"], 0.6)
+    l = ctx.build_transmittance(v, r["light"], 0.6, method=method)
     img = ctx.render_frame(v, l, w, r["mat"], r["cam"]).cpu().numpy()
     ctx.close()
     return img
 
 
-def test_server_same_alone_and_in_mix(nis):
+@pytest.mark.parametrize("method", [0, 1])       # the march; shear-warp transmittance
+def test_server_same_alone_and_in_mix(nis, method):
     blob = synth.pack_weights(synth.make_weights(22, 12.0))
     reqs = _requests()
     target = reqs[1]
-    direct = _render_direct(nis, target, blob)
+    direct = _render_direct(nis, target, blob, method)
     # alone
     ctx = nis.Context(0, torch_allocator=False)
-    srv = nis.Server(ctx, ctx.load_weights(blob), max_batch_points=4096, max_inflight=8)
+    srv = nis.Server(ctx, ctx.load_weights(blob), max_batch_points=4096, max_inflight=8,
+                     transmittance_method=method)
     alone, _ = srv.wait(srv.submit(target["vol"], target["key"], target["light"], 0.6,
                                    target["mat"], target["cam"]), 60000)
     srv.close()
     ctx.close()
     # in a mix: requests arrive while others run; small batches force mixing across requests
     ctx = nis.Context(0, torch_allocator=False)
-    srv = nis.Server(ctx, ctx.load_weights(blob), max_batch_points=1500, max_inflight=8)
+    srv = nis.Server(ctx, ctx.load_weights(blob), max_batch_points=1500, max_inflight=8,
+                     transmittance_method=method)
     ids = {}
     for i, r in enumerate(reqs):
         ids[i] = srv.submit(r["vol"], r["key"], r["light"], 0.6, r["mat"], r["cam"])
@@ -97,7 +100,7 @@ def test_server_same_alone_and_in_mix(nis):
     np.testing.assert_array_equal(imgs[1], alone)
     for i, r in enumerate(reqs):
         if i != 1:
-            np.testing.assert_array_equal(imgs[i], _render_direct(nis, r, blob))
+            np.testing.assert_array_equal(imgs[i], _render_direct(nis, r, blob, method))
     assert st["completed"] == len(reqs) and st["failed"] == 0
     assert st["mean_batch_requests"] > 1.0          # batches did mix requests
     assert 0 < st["p50_ms"] <= st["p99_ms"]
