@@ -47,6 +47,26 @@ CNN_FLOP_PER_POINT = 2 * 12 * (63 * 16 * 27 + 5 * 16 * 16 * 27)
 GATHER_BYTES_PER_POINT = 4 * (3 * 12 * 225 + 12 * 8 + 12 * 3 + 5 + 6)
 
 
+def mlp_bytes_per_point(op: int, st: int) -> int:
+    """Algorithmic HBM bytes per shading point of the dense layers as launched: every layer
+    reads its operand and its epilogue inputs once and writes its outputs once.  op: bytes
+    per operand element (6 for the FP32 split's three BF16 parts, 2 BF16, 1 e4m3); st:
+    bytes per element of e and the running state h (4 FP32 with the split, else 2).  FC-1
+    reads the features (+ 24 B of per-row configuration and SE scale) and h_prev, writes e
+    and s = h_prev + e; FC-2 reads s and e, writes h (the chain's end: the merge input)."""
+    width, total = 200, 0
+    for d in (225, 225, 80):                         # rho, f, T feature widths
+        for first, last in ((0, 7), (8, 11)):        # diffuse and highlight chains
+            for k in range(first, last + 1):
+                total += op * d + 24 + (st * width if k != first else 0) + st * width + op * width
+                total += op * width + st * width + (op * width if k == last else st * width)
+        total += op * 2 * width + op * width         # merge 400 -> 200
+    total += op * 3 * width + op * width             # head 600 -> 200
+    total += 2 * (op * width + op * width)           # head 200 -> 200
+    total += op * width + 12                         # head 200 -> 3, RGB out
+    return total
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -501,14 +521,18 @@ def run_nis(args):
     peaks_bf = measured_peaks()
     mlp_ms, mlp_n = fam_bf["mlp"]
     mlp_tf = MLP_FLOP_PER_POINT * n_points * args.steps / (mlp_ms / 1e3) / 1e12
+    mlp_gbs = mlp_bytes_per_point(2, 2) * n_points * args.steps / (mlp_ms / 1e3) / 1e9
     bf16 = {"value": value_bf, "unit": UNIT,
             "frame_ms": total_bf / args.steps,
             "mean_rel_err_vs_fp32": float(e_bf.mean()), "max_rel_err_vs_fp32": float(e_bf.max()),
             "step_breakdown_ms": {f: round(fam_bf[f][0] / args.steps, 4) for f in nis.FAMILIES},
-            "roofline": {"bound": "tensor", "unit": "TFLOP/s", "kernel": "tc_gemm_kernel (tcgen05, BF16)",
-                         "achieved": mlp_tf, "peak": peaks_bf["bf16_tflops_sustained"],
-                         "frac": mlp_tf / peaks_bf["bf16_tflops_sustained"],
-                         "peak_source": f"{peaks_bf['source']} cuBLAS BF16, sustained",
+            "roofline": {"bound": "hbm", "unit": "GB/s", "kernel": "tc_gemm_kernel (tcgen05, BF16)",
+                         "achieved": mlp_gbs, "peak": peaks_bf["hbm_gbs"],
+                         "frac": mlp_gbs / peaks_bf["hbm_gbs"],
+                         "peak_source": f"{peaks_bf['source']} STREAM copy",
+                         "intensity_flop_per_byte": MLP_FLOP_PER_POINT / mlp_bytes_per_point(2, 2),
+                         "tensor_tflops": mlp_tf,
+                         "tensor_frac": mlp_tf / peaks_bf["bf16_tflops_sustained"],
                          "launches": mlp_n, "avg_launch_ms": mlp_ms / max(mlp_n, 1),
                          "traffic": (recorded_traffic("mlp_bf16") or {}).get("bytes_per_launch")}}
 
@@ -535,14 +559,19 @@ def run_nis(args):
     e_f8 = ((a_f8 - a_32).abs() / torch.maximum(a_32.abs(), floor))
     mlp8_ms = fam_f8["mlp"][0]
     mlp8_tf = MLP_FLOP_PER_POINT * n_points * args.steps / (mlp8_ms / 1e3) / 1e12
+    mlp8_gbs = mlp_bytes_per_point(1, 2) * n_points * args.steps / (mlp8_ms / 1e3) / 1e9
     fp8 = {"value": value_f8, "unit": UNIT,
            "frame_ms": total_f8 / args.steps,
            "mean_rel_err_vs_fp32": float(e_f8.mean()), "max_rel_err_vs_fp32": float(e_f8.max()),
            "step_breakdown_ms": {f: round(fam_f8[f][0] / args.steps, 4) for f in nis.FAMILIES},
-           "roofline": {"bound": "tensor", "unit": "TFLOP/s", "kernel": "tc_gemm_kernel (tcgen05 kind::f8f6f4, e4m3)",
-                        "achieved": mlp8_tf, "peak": 2 * peaks_bf["bf16_tflops_sustained"],
-                        "frac": mlp8_tf / (2 * peaks_bf["bf16_tflops_sustained"]),
-                        "peak_source": f"{peaks_bf['source']} cuBLAS BF16 sustained x 2 (nominal FP8/BF16 ratio)"}}
+           "roofline": {"bound": "hbm", "unit": "GB/s", "kernel": "tc_gemm_kernel (tcgen05 kind::f8f6f4, e4m3)",
+                        "achieved": mlp8_gbs, "peak": peaks_bf["hbm_gbs"],
+                        "frac": mlp8_gbs / peaks_bf["hbm_gbs"],
+                        "peak_source": f"{peaks_bf['source']} STREAM copy",
+                        "intensity_flop_per_byte": MLP_FLOP_PER_POINT / mlp_bytes_per_point(1, 2),
+                        "tensor_tflops": mlp8_tf,
+                        "tensor_frac": mlp8_tf / (2 * peaks_bf["bf16_tflops_sustained"]),
+                        "tensor_peak_source": f"{peaks_bf['source']} cuBLAS BF16 sustained x 2 (nominal FP8/BF16 ratio)"}}
 
     # ---- the same frames with the transmittance from shear-warp rays (O(N^3) per level)
     sw = None
@@ -577,15 +606,24 @@ def run_nis(args):
     per_launch_s = dom_ms / 1e3 / max(dom_n, 1)
     n_levels = len(range(int(math.log2(cfg["n"])) + 1))
     if dom == "mlp":
-        work = MLP_FLOP_PER_POINT * n_points * args.steps / max(dom_n, 1)
-        achieved = work / per_launch_s / 1e12
         # FP32-accurate dense layers: each FP32 product is six BF16 tcgen05 products of the
-        # operands' three-way splits, so the ceiling is the BF16 peak / 6
-        peak = peaks["bf16_tflops_sustained"] / 6.0
-        roof = {"bound": "tensor", "unit": "TFLOP/s",
+        # operands' three-way splits (tensor ceiling: BF16 sustained / 6).  Per launch the
+        # layer's FLOPs over its algorithmic bytes are ~25 FLOP/B, below the ridge of that
+        # ceiling and the HBM copy rate (~41 FLOP/B): the layers are bound by HBM.
+        flops = MLP_FLOP_PER_POINT * n_points * args.steps / max(dom_n, 1)
+        work = mlp_bytes_per_point(6, 4) * n_points * args.steps / max(dom_n, 1)
+        achieved = work / per_launch_s / 1e9
+        peak = peaks["hbm_gbs"]
+        tensor_peak = peaks["bf16_tflops_sustained"] / 6.0
+        roof = {"bound": "hbm", "unit": "GB/s",
                 "kernel": "tc_gemm_kernel (tcgen05, FP32 via 3-way BF16 split, 6 products)",
-                "peak_source": f"{peaks['source']} cuBLAS BF16 sustained "
-                               f"{peaks['bf16_tflops_sustained']:.0f} TFLOP/s / 6"}
+                "peak_source": f"{peaks['source']} STREAM copy",
+                "intensity_flop_per_byte": flops / work,
+                "ridge_flop_per_byte": tensor_peak * 1e12 / (peak * 1e9),
+                "tensor_tflops": flops / per_launch_s / 1e12,
+                "tensor_frac": flops / per_launch_s / 1e12 / tensor_peak,
+                "tensor_peak_source": f"{peaks['source']} cuBLAS BF16 sustained "
+                                      f"{peaks['bf16_tflops_sustained']:.0f} TFLOP/s / 6"}
     elif dom == "cnn":
         work = CNN_FLOP_PER_POINT * n_points * args.steps / max(dom_n, 1)
         achieved = work / per_launch_s / 1e12
