@@ -85,6 +85,10 @@ __device__ __forceinline__ void bulk_commit() {
 __device__ __forceinline__ void bulk_wait_read() {
     asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
+// ... all but the most recent group (double-buffered staging)
+__device__ __forceinline__ void bulk_wait_read1() {
+    asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
 // ... or have completed.
 __device__ __forceinline__ void bulk_wait() {
     asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
