@@ -663,7 +663,8 @@ def config_vector(g: float, albedo, alpha: np.ndarray) -> np.ndarray:
 
 
 def backbone(X_rho, X_f, X_T, c, weights: dict) -> np.ndarray:
-    """y [n, 3] from the SE-scaled features of the three types (Fig. 6)."""
+    """y [n, 3] from the SE-scaled features of the three types (Fig. 6): each an array
+    [n, 12, d] or a list of 12 per-layer arrays [n, d_k]."""
     npts = c.shape[0]
     merged = []
     for t, X in enumerate((X_rho, X_f, X_T)):
@@ -672,7 +673,8 @@ def backbone(X_rho, X_f, X_T, c, weights: dict) -> np.ndarray:
             h = np.zeros((npts, WIDTH))
             for k in range(k0, k1):
                 blk = weights["blocks"][t][k]
-                e = relu(_linear(np.concatenate([X[:, k], c], axis=1), blk["w1"], blk["b1"]))
+                xk = X[k] if isinstance(X, (list, tuple)) else X[:, k]    # per-layer widths
+                e = relu(_linear(np.concatenate([xk, c], axis=1), blk["w1"], blk["b1"]))
                 h = relu(_linear(h + e, blk["w2"], blk["b2"])) + e
             chain_out.append(h)
         mg = weights["merge"][t]
@@ -719,6 +721,182 @@ def shade_points(points, omegas, light_dir, levels, tlevels, table, weights, mat
     if return_all:
         return rgb, {"H_rho": H_rho, "H_T": H_T, "H_f": H_f, "v": v, "X_T": X_T,
                      "w": w, "y": y, "alpha": alpha}
+    return rgb
+
+
+# ----------------------------------------------------------------------------------------
+# The paper's own templates and volume-level transmission feature: a second model beside
+# the lattice one (Sec. III.B.1-2, Eq. 2-4, Fig. 3).  Readings, where the text is silent or
+# inconsistent:
+#   P1  diffuse layer sizes 6, 8, 12, 16, 24, 32, 48, 48 as listed (194 points; the text's
+#       total of 182 disagrees with its own list); highlight layers 32, 16, 16, 8 (72).
+#  P2  "evenly distributed": unit directions by the spherical Fibonacci lattice (layer k's
+#       azimuths turned by k golden angles); layer 0 is the centre plus five such
+#       directions at half radius; highlight layers are sunflower patterns on the unit disc.
+#   P3  Eq. 3: D(S_k) = mean over a layer's unit-radius points of the distance to the
+#       nearest other point of the layer.  Eq. 4 with i = k + 1 and 2^8 read as the finest
+#       resolution N (as R6): layer k lies on the sphere of radius r_k = 2^k xi_(k+1) /
+#       (N D(S_k)), so its point spacing r_k D(S_k) is 2^k xi_(k+1) / N; mip level min(k, L-1).
+#   P4  highlight layer j: centre p + u (j + 1/2) d / 4 (as R7), points on the disc of radius
+#       d / 8 normal to u; spacing (d / 8) D(S_j), mip level clamp(floor(log2(spacing N) +
+#       1/2), 0, L-1).  Points are placed in the per-point light frame (e_x, e_y, e_z = -l).
+#   P5  volume-level transmission feature (Fig. 3: a weight per level, superimposed): at a
+#       template point x, T_f(x) = b + sum_m w_m T_m(x) over the volume's levels (w_0..w_10).
+#   P6  phase feature of a template point: as R9 with the layer's spacing as the ball
+#       diameter, f*(q / spacing); it depends on alpha and g only (a table over alpha).
+#  The SE squeeze (R11, over a layer's points), the backbone, merges, head and decode are
+#  those of the lattice model, with layer k's input width n_k + 5.
+# ----------------------------------------------------------------------------------------
+DIFFUSE_COUNTS = (6, 8, 12, 16, 24, 32, 48, 48)
+HIGHLIGHT_COUNTS = (32, 16, 16, 8)
+TEMPLATE_COUNTS = DIFFUSE_COUNTS + HIGHLIGHT_COUNTS
+N_TEMPLATE = sum(TEMPLATE_COUNTS)                       # 266
+N_LEVEL_WEIGHTS = 11
+GOLDEN_ANGLE = math.pi * (3.0 - math.sqrt(5.0))
+
+
+def fibonacci_sphere(n: int, turn: float = 0.0) -> np.ndarray:
+    """n near-uniform unit vectors: z_i = 1 - (2 i + 1) / n, azimuth i * golden angle + turn."""
+    i = np.arange(n, dtype=np.float64)
+    z = 1.0 - (2.0 * i + 1.0) / n
+    r = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    phi = i * GOLDEN_ANGLE + turn
+    return np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=-1)
+
+
+def sunflower_disc(n: int) -> np.ndarray:
+    """n near-uniform points of the unit disc (z = 0): radius sqrt((i + 1/2) / n), azimuth
+    i * golden angle."""
+    i = np.arange(n, dtype=np.float64)
+    r = np.sqrt((i + 0.5) / n)
+    phi = i * GOLDEN_ANGLE
+    return np.stack([r * np.cos(phi), r * np.sin(phi), np.zeros(n)], axis=-1)
+
+
+def mean_nn_distance(pts: np.ndarray) -> float:
+    """Eq. 3: mean over the points of the distance to the nearest other point."""
+    d = np.linalg.norm(pts[:, None, :] - pts[None, :, :], axis=-1)
+    np.fill_diagonal(d, np.inf)
+    return float(d.min(axis=1).mean())
+
+
+def template_unit_layers():
+    """Unit-radius point sets of the 12 layers (P1-P2) and their D(S_k) (P3)."""
+    layers = []
+    for k, n in enumerate(DIFFUSE_COUNTS):
+        if k == 0:
+            pts = np.concatenate([np.zeros((1, 3)), 0.5 * fibonacci_sphere(n - 1)])
+        else:
+            pts = fibonacci_sphere(n, k * GOLDEN_ANGLE)
+        layers.append(pts)
+    for n in HIGHLIGHT_COUNTS:
+        layers.append(sunflower_disc(n))
+    return layers, [mean_nn_distance(p) for p in layers]
+
+
+def paper_template_geometry(points, light_dir, n_grid: int):
+    """Template points of every layer in light-frame units and their world placement data.
+
+    Returns (unit layers, D, q_over_s) where q_over_s[k] [n_k, 3] are the points' offsets
+    from p divided by the layer spacing, in light-frame coordinates (P6), and a function
+    place(ex, ey, ez, p) -> (world positions [npts, n_k, 3], levels [npts], spacing [npts])
+    per layer."""
+    layers, D = template_unit_layers()
+    n_levels = len(level_sizes(n_grid))
+    q_over_s = []
+    for k in range(N_DIFFUSE):
+        q_over_s.append(layers[k] / D[k])
+    for j in range(N_HIGHLIGHT):
+        k = N_DIFFUSE + j
+        off = layers[k].copy()
+        off[:, 2] += 2.0 * (j + 0.5)              # centre (j + 1/2) d / 4 = 2 (j + 1/2) radii
+        q_over_s.append(off / D[k])
+    u = -np.asarray(light_dir, dtype=np.float64)
+    u = u / np.linalg.norm(u)
+    p = np.asarray(points, dtype=np.float64)
+    d = np.maximum(exit_distance(p, u), 1.0 / n_grid)
+
+    def place(k, ex, ey, ez):
+        unit = layers[k]
+        if k < N_DIFFUSE:
+            radius = np.full(p.shape[0], 2.0 ** k * xi(k + 1) / (n_grid * D[k]))
+            centre = p
+            level = np.full(p.shape[0], min(k, n_levels - 1), dtype=np.int64)
+            margin = np.full(p.shape[0], np.inf)
+        else:
+            j = k - N_DIFFUSE
+            radius = d / 8.0
+            centre = p + u * ((j + 0.5) * d / 4.0)[:, None]
+            z = np.log2(radius * D[k] * n_grid) + 0.5
+            level = np.clip(np.floor(z), 0, n_levels - 1).astype(np.int64)
+            margin = np.abs(z - np.round(z))
+        off = (unit[None, :, 0:1] * ex[:, None, :] + unit[None, :, 1:2] * ey[:, None, :]
+               + unit[None, :, 2:3] * ez[:, None, :])
+        return centre[:, None, :] + radius[:, None, None] * off, level, radius * D[k], margin
+
+    return layers, D, q_over_s, place
+
+
+def paper_phase_table(g, n_alpha: int = N_ALPHA) -> np.ndarray:
+    """Phase features of the 266 template points over the alpha nodes: [266, n_alpha] (P6)."""
+    _, _, q_over_s, _ = paper_template_geometry(np.full((1, 3), 0.5), [0.0, 0.0, -1.0], 64)
+    q = np.concatenate(q_over_s)                                  # [266, 3]
+    return phase_feature(q[:, None, :], alpha_nodes(n_alpha)[None, :], g)
+
+
+def paper_gather(points, omegas, light_dir, levels, tlevels, ptable, g, level_w, level_b):
+    """Density, phase and volume-level transmission features at the paper's template points
+    (lists of 12 arrays [n, n_k]) and the SE squeeze v [n, 12, 8]."""
+    p = np.asarray(points, dtype=np.float64)
+    npts = p.shape[0]
+    n_grid = levels[0].shape[0]
+    ex, ey, ez = light_frame(omegas, light_dir)
+    alpha = view_angle(omegas, light_dir)
+    _, _, _, place = paper_template_geometry(p, light_dir, n_grid)
+    n_alpha = ptable.shape[-1]
+    t = alpha * ((n_alpha - 1) / math.pi)
+    ja = np.minimum(np.floor(t).astype(np.int64), n_alpha - 2)
+    wa = (t - ja)[:, None]
+    H_rho, H_f, H_T = [], [], []
+    v = np.zeros((npts, N_LAYERS, 8))
+    first = 0
+    for k, nk in enumerate(TEMPLATE_COUNTS):
+        x, lev, _, _ = place(k, ex, ey, ez)
+        rho = np.zeros((npts, nk))
+        for m in np.unique(lev):
+            sel = lev == m
+            rho[sel] = sample_border(levels[int(m)], x[sel], 0.0)
+        tf = np.full((npts, nk), float(level_b))
+        for m in range(len(levels)):
+            tf = tf + float(level_w[m]) * sample_T(tlevels, m, x)
+        rows = ptable[first:first + nk]                           # [n_k, A]
+        f = (1.0 - wa) * rows[:, ja].T + wa * rows[:, ja + 1].T
+        first += nk
+        H_rho.append(rho)
+        H_f.append(f)
+        H_T.append(tf)
+        for i, H in enumerate((rho, f, tf)):
+            v[:, k, i] = H.mean(axis=1)
+            v[:, k, 3 + i] = H.max(axis=1)
+    v[..., 6] = g
+    v[..., 7] = alpha[:, None]
+    return H_rho, H_f, H_T, v
+
+
+def shade_points_paper(points, omegas, light_dir, levels, tlevels, ptable, weights, mat,
+                       return_all=False):
+    """Radiance [n, 3] with the paper's templates and transmission feature (P1-P6)."""
+    g, albedo, inten = mat["g"], mat["albedo"], mat["intensity"]
+    H_rho, H_f, H_T, v = paper_gather(points, omegas, light_dir, levels, tlevels, ptable, g,
+                                      weights["level"]["w"], weights["level"]["b"][0])
+    w = se_weights(v, weights)
+    alpha = view_angle(omegas, light_dir)
+    c = config_vector(g, albedo, alpha)
+    X = [[w[:, k, i:i + 1] * H[k] for k in range(N_LAYERS)] for i, H in enumerate((H_rho, H_f, H_T))]
+    y = backbone(X[0], X[1], X[2], c, weights)
+    rgb = decode(y, albedo, inten)
+    if return_all:
+        return rgb, {"H_rho": H_rho, "H_f": H_f, "H_T": H_T, "v": v, "w": w, "y": y}
     return rgb
 
 

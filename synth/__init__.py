@@ -320,6 +320,75 @@ def pack_weights(w: dict) -> bytes:
     return head + payload
 
 
+# --- weights of the paper-template model (the paper's own template sets, a transmission
+# feature from per-level weights; no per-layer CNN) --------------------------------------
+PAPER_COUNTS = (6, 8, 12, 16, 24, 32, 48, 48, 32, 16, 16, 8)
+N_LEVEL_WEIGHTS = 11
+BLOB_MODEL_LATTICE, BLOB_MODEL_PAPER = 0, 1
+
+
+def make_weights_paper(seed: int, density_scale: float = 16.0) -> dict:
+    """Seeded random-init weights of the paper-template model: per-level transmission
+    weights (positive, summing to about 1), SE, blocks whose first layer takes the layer's
+    n_k template values + 5 configuration values, merges and head as make_weights."""
+    rng = np.random.default_rng(seed)
+    w = {"level": {"w": rng.uniform(0.5, 1.5, N_LEVEL_WEIGHTS) / N_LEVEL_WEIGHTS,
+                   "b": _bias(rng, 1)},
+         "se": [], "blocks": [[], [], []], "merge": [], "head": []}
+    for _ in range(N_LAYERS):
+        w["se"].append({
+            "w1": _he(rng, SE_HIDDEN, SE_IN, 0.3), "b1": _bias(rng, SE_HIDDEN, 0.5),
+            "w2": _he(rng, 3, SE_HIDDEN), "b2": _bias(rng, 3, 0.5),
+        })
+    for t in range(3):
+        for k in range(N_LAYERS):
+            d = PAPER_COUNTS[k]
+            w1 = _he(rng, WIDTH, d + N_CFG)
+            if t == 0:
+                w1[:, :d] /= density_scale
+            w["blocks"][t].append({
+                "w1": w1, "b1": _bias(rng, WIDTH),
+                "w2": _he(rng, WIDTH, WIDTH, 0.35), "b2": _bias(rng, WIDTH),
+            })
+    for _ in range(3):
+        w["merge"].append({"w": _he(rng, WIDTH, 2 * WIDTH, 0.7), "b": _bias(rng, WIDTH)})
+    w["head"].append({"w": _he(rng, WIDTH, 3 * WIDTH, 1.0), "b": _bias(rng, WIDTH)})
+    w["head"].append({"w": _he(rng, WIDTH, WIDTH, 1.0), "b": _bias(rng, WIDTH)})
+    w["head"].append({"w": _he(rng, N_OUT, WIDTH, 1.0), "b": _bias(rng, N_OUT, 0.2)})
+    return _as_f32(w)
+
+
+def weight_tensors_paper(w: dict):
+    """Blob order of the paper-template model: level weights [11], level bias [1], then SE,
+    blocks, merges and head in the order of weight_tensors."""
+    out = [w["level"]["w"], w["level"]["b"]]
+    for k in range(N_LAYERS):
+        s = w["se"][k]
+        out += [s["w1"], s["b1"], s["w2"], s["b2"]]
+    for t in range(3):
+        for k in range(N_LAYERS):
+            b = w["blocks"][t][k]
+            out += [b["w1"], b["b1"], b["w2"], b["b2"]]
+    for t in range(3):
+        out += [w["merge"][t]["w"], w["merge"][t]["b"]]
+    for h in w["head"]:
+        out += [h["w"], h["b"]]
+    return out
+
+
+def pack_weights_paper(w: dict) -> bytes:
+    """The blob of the paper-template model: header word 2 = 1 (model), word 6 = 266
+    template points, word 7 = 0 (no CNN), word 12 = 11 level weights."""
+    payload = b"".join(np.ascontiguousarray(t, dtype="<f4").tobytes() for t in weight_tensors_paper(w))
+    n_floats = len(payload) // 4
+    head = struct.pack("<16I", BLOB_MAGIC, BLOB_VERSION, BLOB_MODEL_PAPER, BLOB_HEADER_BYTES,
+                       N_LAYERS, N_DIFFUSE, sum(PAPER_COUNTS), 0, SE_HIDDEN, WIDTH, N_CFG, N_OUT,
+                       N_LEVEL_WEIGHTS, 0, 0, 0)
+    head += struct.pack("<QQ", n_floats, blob_checksum(payload))
+    assert len(head) == BLOB_HEADER_BYTES
+    return head + payload
+
+
 def n_params() -> int:
     return sum(t.size for t in weight_tensors(make_weights(0)))
 
