@@ -77,6 +77,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-shear-warp", action="store_true")
+    ap.add_argument("--no-paper-model", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=256)
     ap.add_argument("--ncu-case", choices=("f32", "bf16", "simt", "sweep"),
                     help="small case for ncu captures: shade 32,768 points of the 64^3 fBm "
@@ -338,6 +339,42 @@ def run_shear_warp(args, nis, ctx, v, w, cfg, img, hitmask, flush, stream, n_poi
             "max_rel_err_vs_marched_frame": float(e.max())}
 
 
+def run_paper_model(args, nis, ctx, v, cfg, flush, stream, n_points) -> dict:
+    """The same frame shaded by the paper-template model (the paper's own template point
+    sets and volume-level transmission feature; FP32 FFMA dense layers)."""
+    import torch
+    W = synth.make_weights_paper(cfg["weights_seed"], cfg["sigma_max"])
+    w = ctx.load_weights(synth.pack_weights_paper(W), nis.PREC_F32_SIMT)
+    light, mat, cam = cfg["light"], cfg["material"], cfg["camera"]
+    img = torch.empty((cam["height"], cam["width"], 3), dtype=torch.float32, device=flush.device)
+
+    def step():
+        ctx.build_pyramid(v)
+        lt = ctx.build_transmittance(v, light, 0.6)
+        ctx.render_frame(v, lt, w, mat, cam, out=img)
+
+    step()
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    times = []
+    steps = max(2, min(args.steps, 3))
+    for _ in range(steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ctx.profile(False)
+    fam = {f: ctx.profile_read(f) for f in nis.FAMILIES}
+    ctx.release(w)
+    return {"value": n_points * steps / (sum(times) / 1e3), "unit": UNIT,
+            "frame_ms": sum(times) / steps, "steps": steps,
+            "model": "paper templates (194 + 72 points), level-weighted transmission, FP32 FFMA",
+            "step_breakdown_ms": {f: round(fam[f][0] / steps, 4) for f in nis.FAMILIES}}
+
+
 def plume_transmittance(nis, local: int) -> dict:
     """Transmittance of the 1024^3 FP16 plume toward its light (all 11 levels) by the march
     and by shear-warp rays: one build each (timed after a warm-up build of the latter) and
@@ -578,6 +615,9 @@ def run_nis(args):
     if not args.no_shear_warp:
         sw = run_shear_warp(args, nis, ctx, v, w, cfg, img, hitmask, flush, stream, n_points)
 
+    paper = None if args.no_paper_model else run_paper_model(args, nis, ctx, v, cfg, flush,
+                                                             stream, n_points)
+
     # ---- end to end through the C ABI from page-locked host memory
     host_vol = torch.from_numpy(vol_np).pin_memory()
     host_img = torch.empty(img.shape, dtype=torch.float32).pin_memory()
@@ -662,6 +702,7 @@ def run_nis(args):
             "bf16": bf16,
             "fp8": fp8,
             "shear_warp": sw,
+            "paper_template_model": paper,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(vol_np.nbytes),
                     "d2h_bytes_per_step": int(img.numel() * 4),

@@ -173,9 +173,20 @@ nis_status nis_build_transmittance_method(nis_ctx *ctx, nis_volume vol, const fl
 
 /* Parses a weight blob (80-byte header, float32 tensors in the fixed order below, a
  * position-weighted word checksum) and uploads it at `precision`.  The caller keeps the
- * blob.  Tensor order: CNN[12]{w1 16x1x3x3x3, b1, w2 16x16x3x3x3, b2}, SE[12]{w1 2x8, b1,
- * w2 3x2, b2}, blocks[type rho,f,T][layer 0..11]{W1 200x(d+5), b1, W2 200x200, b2} with
- * d = 225, 225, 80, merge[3]{200x400, b}, head{200x600, b, 200x200, b, 3x200, b}. */
+ * blob.  Header word 2 names the network:
+ *   0, the lattice model: CNN[12]{w1 16x1x3x3x3, b1, w2 16x16x3x3x3, b2}, SE[12]{w1 2x8,
+ *      b1, w2 3x2, b2}, blocks[type rho,f,T][layer 0..11]{W1 200x(d+5), b1, W2 200x200, b2}
+ *      with d = 225, 225, 80, merge[3]{200x400, b}, head{200x600, b, 200x200, b, 3x200, b};
+ *   1, the paper-template model (the paper's own template sets, Sec. III.B.2: 6, 8, 12,
+ *      16, 24, 32, 48, 48 diffuse and 32, 16, 16, 8 highlight points per layer; a
+ *      volume-level transmission feature b + sum_m w_m T_m at each point, Fig. 3, in place
+ *      of the per-layer CNN): level w[11], level b[1], then SE, blocks with d = the layer's
+ *      point count for all three types, merges and head as above.  Header words 6, 7 and 12
+ *      are 266, 0 and 11.  It runs in FP32 (NIS_PREC_F32 or NIS_PREC_F32_SIMT, both on FP32
+ *      FFMA dense layers; other precisions return NIS_ERR_UNIMPLEMENTED), through
+ *      nis_shade_points, nis_shade_points_debug (features [n][266] at the start of the
+ *      H buffers) and the frame calls; mixed batches, the server and the allocation-free
+ *      call take the lattice model only (NIS_ERR_UNIMPLEMENTED). */
 nis_status nis_load_weights(nis_ctx *ctx, const void *blob, size_t bytes, int precision,
                             nis_stream stream, nis_weights *out);
 

@@ -741,7 +741,8 @@ def shade_points(points, omegas, light_dir, levels, tlevels, table, weights, mat
 #       d / 8 normal to u; spacing (d / 8) D(S_j), mip level clamp(floor(log2(spacing N) +
 #       1/2), 0, L-1).  Points are placed in the per-point light frame (e_x, e_y, e_z = -l).
 #   P5  volume-level transmission feature (Fig. 3: a weight per level, superimposed): at a
-#       template point x, T_f(x) = b + sum_m w_m T_m(x) over the volume's levels (w_0..w_10).
+#       template point x, T_f(x) = b + sum_m w_m T_m(x) over the volume's levels, at most the
+#       11 finest (w_0..w_10; a 1024^3 grid has 11).
 #   P6  phase feature of a template point: as R9 with the layer's spacing as the ball
 #       diameter, f*(q / spacing); it depends on alpha and g only (a table over alpha).
 #  The SE squeeze (R11, over a layer's points), the backbone, merges, head and decode are
@@ -837,11 +838,15 @@ def paper_template_geometry(points, light_dir, n_grid: int):
     return layers, D, q_over_s, place
 
 
-def paper_phase_table(g, n_alpha: int = N_ALPHA) -> np.ndarray:
-    """Phase features of the 266 template points over the alpha nodes: [266, n_alpha] (P6)."""
+def paper_phase_table(g, n_alpha: int = N_ALPHA, columns=None) -> np.ndarray:
+    """Phase features of the 266 template points over the alpha nodes: [266, n_alpha] (P6).
+    With ``columns`` only those alpha nodes are filled (the rest NaN)."""
     _, _, q_over_s, _ = paper_template_geometry(np.full((1, 3), 0.5), [0.0, 0.0, -1.0], 64)
     q = np.concatenate(q_over_s)                                  # [266, 3]
-    return phase_feature(q[:, None, :], alpha_nodes(n_alpha)[None, :], g)
+    cols = np.arange(n_alpha) if columns is None else np.unique(np.asarray(columns))
+    out = np.full((q.shape[0], n_alpha), np.nan)
+    out[:, cols] = phase_feature(q[:, None, :], alpha_nodes(n_alpha)[None, cols], g)
+    return out
 
 
 def paper_gather(points, omegas, light_dir, levels, tlevels, ptable, g, level_w, level_b):
@@ -867,7 +872,7 @@ def paper_gather(points, omegas, light_dir, levels, tlevels, ptable, g, level_w,
             sel = lev == m
             rho[sel] = sample_border(levels[int(m)], x[sel], 0.0)
         tf = np.full((npts, nk), float(level_b))
-        for m in range(len(levels)):
+        for m in range(min(len(levels), N_LEVEL_WEIGHTS)):
             tf = tf + float(level_w[m]) * sample_T(tlevels, m, x)
         rows = ptable[first:first + nk]                           # [n_k, A]
         f = (1.0 - wa) * rows[:, ja].T + wa * rows[:, ja + 1].T

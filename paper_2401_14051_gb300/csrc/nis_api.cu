@@ -126,6 +126,7 @@ struct nis_ctx {
     std::map<nis_handle, Light> lights;
     std::map<nis_handle, Weights> weights;
     std::map<std::vector<uint32_t>, float *> phase;   // by the bit patterns of the phase spec
+    std::map<std::vector<uint32_t>, float *> phase_paper;   // the paper model's [kAlpha][266]
     Workspace ws;
     WorkspaceBf wsb, wsx;                 // BF16 and split (FP32-accurate) tensor paths
     WorkspaceF8 ws8;
@@ -353,30 +354,40 @@ PhaseSpec phase_spec_g(float g) {
     return phase_spec(&m);
 }
 
+// The phase table of a phase function: over the lattice point sets, or (paper = true) over
+// the paper model's 266 template points.
 nis_status ensure_phase(nis_ctx *ctx, const PhaseSpec &ph, cudaStream_t s, float **out,
-                        bool rebuild = false) {
+                        bool rebuild = false, bool paper = false) {
     std::vector<uint32_t> key(1 + 2 * ph.n);
     key[0] = (uint32_t)ph.n;
     for (int i = 0; i < ph.n; ++i) {
         std::memcpy(&key[1 + 2 * i], &ph.g[i], 4);
         std::memcpy(&key[2 + 2 * i], &ph.w[i], 4);
     }
-    auto it = ctx->phase.find(key);
+    auto &cache = paper ? ctx->phase_paper : ctx->phase;
+    auto it = cache.find(key);
     float *t;
-    if (it != ctx->phase.end()) {
+    if (it != cache.end()) {
         *out = it->second;
         if (!rebuild) return NIS_OK;
         t = it->second;
     } else {
-        nis_status st = dev_alloc_t(ctx, (size_t)kAlpha * kPhaseSets * kLat, &t, s);
+        nis_status st = dev_alloc_t(ctx, (size_t)kAlpha * (paper ? kPaperPts : kPhaseSets * kLat), &t, s);
         if (st) return st;
     }
     {
         ProfScope ps(ctx, "phase", s);
-        launch_phase_table(ph, t, s);
+        if (paper) {
+            static double unit[kPaperPts][3], D[kLayers];
+            static float q[kPaperPts][3];
+            paper_template(unit, D, q);
+            launch_phase_points(ph, q, kPaperPts, t, s);
+        } else {
+            launch_phase_table(ph, t, s);
+        }
     }
     NIS_CUDA(cudaGetLastError());
-    ctx->phase[key] = t;
+    cache[key] = t;
     *out = t;
     return NIS_OK;
 }
@@ -623,12 +634,140 @@ nis_status shade_impl_fp8(nis_ctx *ctx, const Volume &vol, const Light &light, c
                           cudaStream_t s, const Mixed *mx);
 
 // Runs steps 3-6 for `n` points already on the device.
+// Steps 3-6 of the paper-template model: its gathers (density, phase and the volume-level
+// transmission feature at the 266 template points, SE), then the backbone on per-layer
+// widths with FP32 FFMA dense layers.
+nis_status shade_impl_paper(nis_ctx *ctx, const Volume &vol, const Light &light, const Weights &wt,
+                            const nis_material *m, const float *table, const float *pts,
+                            const float *om, int n, float *rgb, const nis_debug_out *dbg,
+                            cudaStream_t s) {
+    int chunk = pass_size(n);
+    nis_status st;
+    if ((st = ensure_workspace(ctx, chunk, s))) return st;
+    Workspace &w = ctx->ws;
+    const WeightOffsets &o = wt.off;
+    const float *W = wt.f32;
+    const size_t act_stride = (size_t)w.cap * kWidth;
+    auto act = [&](int i) { return w.act + i * act_stride; };
+    float dec_scale[3];
+    for (int c = 0; c < 3; ++c) dec_scale[c] = m->intensity[c] * powf(m->albedo[c], 4.0f);
+    PaperGatherArgs ga{};
+    {
+        static double unit[kPaperPts][3], D[kLayers];
+        static float q[kPaperPts][3];
+        paper_template(unit, D, q);
+        for (int t = 0; t < kPaperPts; ++t)
+            for (int c = 0; c < 3; ++c) ga.unit[t][c] = (float)unit[t][c];
+        for (int k = 0; k < kLayers; ++k) ga.D[k] = (float)D[k];
+    }
+    ga.rt = pair_view(vol, light);
+    ga.table = table;
+    ga.lx = light.dir[0]; ga.ly = light.dir[1]; ga.lz = light.dir[2];
+    ga.g = m->g;
+    for (int c = 0; c < 3; ++c) ga.albedo[c] = m->albedo[c];
+    ga.level_w = W + o.level_w;
+    ga.level_b = W + o.level_b;
+    ga.se = W;
+    for (int k = 0; k < kLayers; ++k) {
+        ga.se_w1[k] = o.se_w1[k]; ga.se_b1[k] = o.se_b1[k];
+        ga.se_w2[k] = o.se_w2[k]; ga.se_b2[k] = o.se_b2[k];
+    }
+    // the features [cnt][266] of each type in the lattice model's feature buffers
+    ga.H_rho = w.H_rho; ga.H_f = w.H_f; ga.H_T = w.H_T;
+    ga.v = w.v; ga.w_se = w.w_se; ga.cfg = w.cfg;
+    for (int off = 0; off < n; off += chunk) {
+        int cnt = n - off < chunk ? n - off : chunk;
+        ga.points = pts + 3 * (size_t)off;
+        ga.omega = om + 3 * (size_t)off;
+        ga.count = cnt;
+        {
+            ProfScope ps(ctx, "gather", s);
+            launch_gather_paper(ga, s);
+        }
+        for (int t = 0; t < 3; ++t) {
+            const float *X = t == 0 ? w.H_rho : (t == 1 ? w.H_f : w.H_T);
+            for (int chain = 0; chain < 2; ++chain) {
+                int k0 = chain == 0 ? 0 : kDiffuse, k1 = chain == 0 ? kDiffuse : kLayers;
+                float *h = nullptr;
+                int ping = 1;
+                for (int k = k0; k < k1; ++k) {
+                    const int d = paper_count(k);
+                    FcArgs f1{};
+                    f1.mode = kFcFeat; f1.count = cnt; f1.K = d + kCfg; f1.N = kWidth;
+                    f1.X = X + paper_first(k); f1.ldx = kPaperPts; f1.d = d;
+                    f1.w_se = w.w_se; f1.layer = k; f1.type = t; f1.cfg = w.cfg;
+                    f1.W = W + o.blk_w1[t][k]; f1.b = W + o.blk_b1[t][k];
+                    f1.relu = 1; f1.out = act(0); f1.ldo = kWidth;
+                    { ProfScope ps(ctx, "mlp", s); launch_fc_f32(f1, s); }
+                    FcArgs f2{};
+                    f2.mode = kFcSum; f2.count = cnt; f2.K = kWidth; f2.N = kWidth;
+                    f2.a0 = h; f2.a1 = act(0); f2.seg = kWidth;
+                    f2.W = W + o.blk_w2[t][k]; f2.b = W + o.blk_b2[t][k];
+                    f2.relu = 1; f2.resid = act(0); f2.ldo = kWidth;
+                    float *dst = (k == k1 - 1) ? act(3 + 2 * t + chain) : act(ping);
+                    f2.out = dst;
+                    { ProfScope ps(ctx, "mlp", s); launch_fc_f32(f2, s); }
+                    h = dst;
+                    ping = 3 - ping;
+                }
+            }
+            FcArgs mg{};
+            mg.mode = kFcCat; mg.count = cnt; mg.K = 2 * kWidth; mg.N = kWidth;
+            mg.a0 = act(3 + 2 * t); mg.a1 = act(4 + 2 * t); mg.seg = kWidth;
+            mg.W = W + o.mrg_w[t]; mg.b = W + o.mrg_b[t]; mg.relu = 1;
+            mg.out = act(9 + t); mg.ldo = kWidth;
+            { ProfScope ps(ctx, "mlp", s); launch_fc_f32(mg, s); }
+        }
+        FcArgs h1{};
+        h1.mode = kFcCat; h1.count = cnt; h1.K = 3 * kWidth; h1.N = kWidth;
+        h1.a0 = act(9); h1.a1 = act(10); h1.a2 = act(11); h1.seg = kWidth;
+        h1.W = W + o.head_w[0]; h1.b = W + o.head_b[0]; h1.relu = 1;
+        h1.out = act(12); h1.ldo = kWidth;
+        { ProfScope ps(ctx, "mlp", s); launch_fc_f32(h1, s); }
+        FcArgs h2{};
+        h2.mode = kFcSum; h2.count = cnt; h2.K = kWidth; h2.N = kWidth;
+        h2.a1 = act(12); h2.seg = kWidth;
+        h2.W = W + o.head_w[1]; h2.b = W + o.head_b[1]; h2.relu = 1;
+        h2.out = act(13); h2.ldo = kWidth;
+        { ProfScope ps(ctx, "mlp", s); launch_fc_f32(h2, s); }
+        FcArgs h3{};
+        h3.mode = kFcSum; h3.count = cnt; h3.K = kWidth; h3.N = 3;
+        h3.a1 = act(13); h3.seg = kWidth;
+        h3.W = W + o.head_w[2]; h3.b = W + o.head_b[2];
+        h3.decode = 1;
+        for (int c = 0; c < 3; ++c) h3.dec_scale[c] = dec_scale[c];
+        h3.y_out = (dbg && dbg->y) ? dbg->y + 3 * (size_t)off : nullptr;
+        h3.out = rgb + 3 * (size_t)off; h3.ldo = 3;
+        { ProfScope ps(ctx, "mlp", s); launch_fc_f32(h3, s); }
+        if (dbg) {
+            auto cp = [&](float *dst, const float *src, size_t per) -> cudaError_t {
+                if (!dst) return cudaSuccess;
+                return cudaMemcpyAsync(dst + per * off, src, per * cnt * sizeof(float),
+                                       cudaMemcpyDeviceToDevice, s);
+            };
+            NIS_CUDA(cp(dbg->H_rho, w.H_rho, (size_t)kPaperPts));
+            NIS_CUDA(cp(dbg->H_T, w.H_T, (size_t)kPaperPts));
+            NIS_CUDA(cp(dbg->H_f, w.H_f, (size_t)kPaperPts));
+            NIS_CUDA(cp(dbg->v, w.v, (size_t)kLayers * 8));
+            NIS_CUDA(cp(dbg->w_se, w.w_se, (size_t)kLayers * 3));
+        }
+        NIS_CUDA(cudaGetLastError());
+    }
+    return NIS_OK;
+}
+
 nis_status shade_impl(nis_ctx *ctx, const Volume &vol, const Light &light, const Weights &wt,
                       const nis_material *m, const float *pts, const float *om, int n,
                       float *rgb, const nis_debug_out *dbg, cudaStream_t s,
                       const Mixed *mx = nullptr) {
     float *table = nullptr;
     nis_status st;
+    if (wt.off.model == kModelPaper) {
+        if (mx) return fail(ctx, NIS_ERR_UNIMPLEMENTED, "mixed batches need lattice-model weights");
+        if ((st = ensure_phase(ctx, phase_spec(m), s, &table, false, true))) return st;
+        if (n <= 0) return NIS_OK;
+        return shade_impl_paper(ctx, vol, light, wt, m, table, pts, om, n, rgb, dbg, s);
+    }
     if (!mx && (st = ensure_phase(ctx, phase_spec(m), s, &table))) return st;
     if (n <= 0) return NIS_OK;
     if (wt.precision == NIS_PREC_FP8)
@@ -1227,6 +1366,39 @@ nis_status resolve_built_inputs(nis_ctx *ctx, nis_volume vol, nis_light light, n
     return NIS_OK;
 }
 
+void weight_offsets_paper(WeightOffsets *o) {
+    size_t p = 0;
+    o->model = kModelPaper;
+    o->level_w = p; p += kLevelWeights;
+    o->level_b = p; p += 1;
+    for (int k = 0; k < kLayers; ++k) o->cnn_w1[k] = o->cnn_b1[k] = o->cnn_w2[k] = o->cnn_b2[k] = 0;
+    for (int k = 0; k < kLayers; ++k) {
+        o->se_w1[k] = p; p += 2 * 8;
+        o->se_b1[k] = p; p += 2;
+        o->se_w2[k] = p; p += 3 * 2;
+        o->se_b2[k] = p; p += 3;
+    }
+    for (int t = 0; t < 3; ++t)
+        for (int k = 0; k < kLayers; ++k) {
+            const int d = paper_count(k);
+            o->blk_w1[t][k] = p; p += (size_t)kWidth * (d + kCfg);
+            o->blk_b1[t][k] = p; p += kWidth;
+            o->blk_w2[t][k] = p; p += (size_t)kWidth * kWidth;
+            o->blk_b2[t][k] = p; p += kWidth;
+        }
+    for (int t = 0; t < 3; ++t) {
+        o->mrg_w[t] = p; p += (size_t)kWidth * 2 * kWidth;
+        o->mrg_b[t] = p; p += kWidth;
+    }
+    o->head_w[0] = p; p += (size_t)kWidth * 3 * kWidth;
+    o->head_b[0] = p; p += kWidth;
+    o->head_w[1] = p; p += (size_t)kWidth * kWidth;
+    o->head_b[1] = p; p += kWidth;
+    o->head_w[2] = p; p += 3 * kWidth;
+    o->head_b[2] = p; p += 3;
+    o->total = p;
+}
+
 void weight_offsets(WeightOffsets *o) {
     size_t p = 0;
     for (int k = 0; k < kLayers; ++k) {
@@ -1261,6 +1433,11 @@ void weight_offsets(WeightOffsets *o) {
     o->head_b[2] = p; p += 3;
     o->total = p;
 }
+int weights_model(nis_ctx *ctx, nis_weights w) {
+    Weights *pw = lookup(ctx->weights, w);
+    return pw ? pw->off.model : -1;
+}
+
 }  // namespace nis
 
 extern "C" {
@@ -1524,13 +1701,18 @@ nis_status nis_load_weights(nis_ctx *ctx, const void *blob, size_t bytes, int pr
     std::memcpy(&n_floats, static_cast<const char *>(blob) + 64, 8);
     std::memcpy(&checksum, static_cast<const char *>(blob) + 72, 8);
     WeightOffsets o;
-    weight_offsets(&o);
-    const uint32_t expect[13] = {0x5753494Eu, 1u, 0u, 80u, (uint32_t)kLayers, (uint32_t)kDiffuse,
-                                 (uint32_t)kLat, (uint32_t)kCnnCh, 2u, (uint32_t)kWidth,
-                                 (uint32_t)kCfg, 3u, (uint32_t)kDT};
+    const bool paper = hd[2] == (uint32_t)kModelPaper;
+    if (paper) weight_offsets_paper(&o);
+    else weight_offsets(&o);
+    const uint32_t expect[13] = {0x5753494Eu, 1u, paper ? 1u : 0u, 80u, (uint32_t)kLayers,
+                                 (uint32_t)kDiffuse, paper ? (uint32_t)kPaperPts : (uint32_t)kLat,
+                                 paper ? 0u : (uint32_t)kCnnCh, 2u, (uint32_t)kWidth,
+                                 (uint32_t)kCfg, 3u, paper ? (uint32_t)kLevelWeights : (uint32_t)kDT};
     for (int i = 0; i < 13; ++i)
         if (hd[i] != expect[i])
             return fail(ctx, NIS_ERR_BAD_BLOB, "blob header field " + std::to_string(i) + " mismatch");
+    if (paper && precision != NIS_PREC_F32 && precision != NIS_PREC_F32_SIMT)
+        return fail(ctx, NIS_ERR_UNIMPLEMENTED, "the paper-template model runs in FP32 only");
     if (n_floats != o.total || bytes != 80 + 4 * n_floats)
         return fail(ctx, NIS_ERR_BAD_BLOB, "blob size does not match the network shape");
     const uint32_t *words = reinterpret_cast<const uint32_t *>(static_cast<const char *>(blob) + 80);
@@ -1547,7 +1729,8 @@ nis_status nis_load_weights(nis_ctx *ctx, const void *blob, size_t bytes, int pr
     cudaError_t e = cudaMemcpyAsync(w.f32, words, o.total * 4, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the caller may free the blob
     if (e != cudaSuccess) { dev_free(ctx, w.f32); return cuda_fail(ctx, e, "weights upload"); }
-    if (precision == NIS_PREC_FP8) st = pack_weights_fp8(ctx, w, s);
+    if (paper) st = NIS_OK;                                // FP32 FFMA dense layers
+    else if (precision == NIS_PREC_FP8) st = pack_weights_fp8(ctx, w, s);
     else if (precision != NIS_PREC_F32_SIMT) st = pack_weights_tc(ctx, w, precision == NIS_PREC_F32 ? 3 : 1, s);
     if (st) {
         dev_free(ctx, w.f32);
@@ -1965,6 +2148,8 @@ nis_status nis_shade_segments(nis_ctx *ctx, nis_weights w, const nis_segment *se
     if (nseg < 0 || (nseg > 0 && !segs)) return fail(ctx, NIS_ERR_INVALID_ARG, "bad segment list");
     Weights *pw = lookup(ctx->weights, w);
     if (!pw) return fail(ctx, NIS_ERR_NOT_READY, "unknown or released weights handle");
+    if (pw->off.model != kModelLattice)
+        return fail(ctx, NIS_ERR_UNIMPLEMENTED, "mixed batches need lattice-model weights");
     DeviceGuard g(ctx->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     std::vector<ReqDesc> descs(nseg);

@@ -32,7 +32,24 @@ constexpr int kCfg = 5;              // [g, albedo rgb, alpha]
 constexpr int kMaxLevels = 16;
 
 // ---- weight blob layout ------------------------------------------------------------------
+// The two networks a weight blob can hold (header word 2): the lattice model (5x5x9
+// lattices, per-layer 3D-CNN) and the paper-template model (the paper's own point sets of
+// 6..48 and 32..8 points per layer, a volume-level transmission feature from per-level
+// weights, no per-layer CNN).
+constexpr int kModelLattice = 0, kModelPaper = 1;
+constexpr int kPaperPts = 266;        // 194 diffuse + 72 highlight template points
+constexpr int kLevelWeights = 11;
+// points of the paper model's layer k, and the index of its first point
+__host__ __device__ constexpr int paper_count(int k) {
+    return k == 0 ? 6 : k == 1 ? 8 : k == 2 ? 12 : k == 3 ? 16 : k == 4 ? 24 : k == 5 ? 32
+         : k == 6 ? 48 : k == 7 ? 48 : k == 8 ? 32 : k == 9 ? 16 : k == 10 ? 16 : 8;
+}
+__host__ __device__ constexpr int paper_first(int k) { return k == 0 ? 0 : paper_first(k - 1) + paper_count(k - 1); }
+static_assert(paper_first(kLayers) == kPaperPts, "paper template size");
+
 struct WeightOffsets {                // float offsets into the FP32 weight buffer
+    int model = kModelLattice;
+    size_t level_w = 0, level_b = 0;  // paper model: transmission weights per level, bias
     size_t cnn_w1[kLayers], cnn_b1[kLayers], cnn_w2[kLayers], cnn_b2[kLayers];
     size_t se_w1[kLayers], se_b1[kLayers], se_w2[kLayers], se_b2[kLayers];
     size_t blk_w1[3][kLayers], blk_b1[3][kLayers], blk_w2[3][kLayers], blk_b2[3][kLayers];
@@ -41,6 +58,8 @@ struct WeightOffsets {                // float offsets into the FP32 weight buff
     size_t total;
 };
 void weight_offsets(WeightOffsets *o);   // fills the fixed blob order
+void weight_offsets_paper(WeightOffsets *o);   // ... of the paper-template model
+int weights_model(::nis_ctx *ctx, nis_weights w);   // kModel* of a weight set, -1 if unknown
 inline int feat_dim(int type) { return type == 2 ? kDT : kLat; }
 
 // ---- device helpers ---------------------------------------------------------------------
@@ -272,6 +291,35 @@ struct GatherArgs {
     float *cfg;                      // [count][5]
 };
 void launch_gather(const GatherArgs &a, cudaStream_t s);
+
+// ---- paper-template model (k_gather_paper.cu) -----------------------------------------------
+// Unit-radius point sets of the 12 layers (light-frame coordinates; Fibonacci sphere,
+// sunflower disc), their mean nearest-neighbour distances D[12] (Eq. 3) and every point's
+// offset from the shading point over its layer's spacing, q[266][3] (the phase offsets).
+void paper_template(double unit[kPaperPts][3], double D[kLayers], float q[kPaperPts][3]);
+struct PaperGatherArgs {
+    PairView rt;                     // density and transmittance of every level
+    const float *table;              // [kAlpha][266] phase features of the material
+    const float *points, *omega;     // [n][3]
+    int count;
+    float lx, ly, lz;                // unit light propagation direction
+    float g;
+    float albedo[3];
+    float D[kLayers];                // unit-set spacings
+    float unit[kPaperPts][3];        // unit-radius template points (from paper_template)
+    const float *level_w, *level_b;  // device: per-level transmission weights, bias
+    const float *se;                 // FP32 weights base; SE offsets below
+    size_t se_w1[kLayers], se_b1[kLayers], se_w2[kLayers], se_b2[kLayers];
+    float *H_rho, *H_f, *H_T;        // [count][266]
+    float *v;                        // [count][12][8] (may be null)
+    float *w_se;                     // [count][12][3]
+    float *cfg;                      // [count][5]
+};
+void launch_gather_paper(const PaperGatherArgs &a, cudaStream_t s);
+// phase features of arbitrary template offsets q (in spacings, light frame) over the alpha
+// nodes: table[a][t], t < n_pts <= kPaperPts
+void launch_phase_points(const PhaseSpec &ph, const float (*q)[3], int n_pts, float *table,
+                         cudaStream_t s);
 
 // FP32 CNN (FP32 FFMA): outputs X_T (FP32, optional) and X_T_bf (BF16, optional; three
 // split parts `split_part` elements apart when split_part != 0), [count][12][80].

@@ -71,6 +71,8 @@ extern "C" nis_status nis_shade_points_static(nis_ctx *ctx, nis_volume vol, nis_
     for (int c = 0; c < 3; ++c)
         if (!(m->albedo[c] > 0.f && m->albedo[c] <= 1.f) || !isfinite(m->intensity[c]))
             return record_error(ctx, NIS_ERR_INVALID_ARG, "albedo must lie in (0, 1], intensity finite");
+    if (weights_model(ctx, w) == kModelPaper)
+        return record_error(ctx, NIS_ERR_UNIMPLEMENTED, "nis_shade_points_static takes lattice-model weights");
     ResolvedInputs in;
     nis_status st = resolve_built_inputs(ctx, vol, light, w, m, &in);
     if (st) return st;

@@ -446,6 +446,8 @@ nis_status nis_server_create(nis_ctx *ctx, nis_weights w, const nis_server_confi
     if (cfg->transmittance_method != NIS_TRANSMITTANCE_MARCH &&
         cfg->transmittance_method != NIS_TRANSMITTANCE_SHEAR_WARP)
         return record_error(ctx, NIS_ERR_INVALID_ARG, "unknown transmittance method");
+    if (weights_model(ctx, w) != kModelLattice)
+        return record_error(ctx, NIS_ERR_UNIMPLEMENTED, "the server batches lattice-model weights");
     nis_server *S = new nis_server();
     S->ctx = ctx;
     cudaSetDevice(ctx_device(ctx));
