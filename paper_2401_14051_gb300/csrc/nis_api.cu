@@ -354,6 +354,20 @@ PhaseSpec phase_spec_g(float g) {
     return phase_spec(&m);
 }
 
+// The paper model's template, computed once per process (thread-safe initialisation).
+struct PaperTemplate {
+    double unit[kPaperPts][3], D[kLayers];
+    float q[kPaperPts][3];
+};
+const PaperTemplate &paper_tpl() {
+    static const PaperTemplate tpl = [] {
+        PaperTemplate t{};
+        paper_template(t.unit, t.D, t.q);
+        return t;
+    }();
+    return tpl;
+}
+
 // The phase table of a phase function: over the lattice point sets, or (paper = true) over
 // the paper model's 266 template points.
 nis_status ensure_phase(nis_ctx *ctx, const PhaseSpec &ph, cudaStream_t s, float **out,
@@ -378,10 +392,7 @@ nis_status ensure_phase(nis_ctx *ctx, const PhaseSpec &ph, cudaStream_t s, float
     {
         ProfScope ps(ctx, "phase", s);
         if (paper) {
-            static double unit[kPaperPts][3], D[kLayers];
-            static float q[kPaperPts][3];
-            paper_template(unit, D, q);
-            launch_phase_points(ph, q, kPaperPts, t, s);
+            launch_phase_points(ph, paper_tpl().q, kPaperPts, t, s);
         } else {
             launch_phase_table(ph, t, s);
         }
@@ -653,12 +664,10 @@ nis_status shade_impl_paper(nis_ctx *ctx, const Volume &vol, const Light &light,
     for (int c = 0; c < 3; ++c) dec_scale[c] = m->intensity[c] * powf(m->albedo[c], 4.0f);
     PaperGatherArgs ga{};
     {
-        static double unit[kPaperPts][3], D[kLayers];
-        static float q[kPaperPts][3];
-        paper_template(unit, D, q);
+        const PaperTemplate &tpl = paper_tpl();
         for (int t = 0; t < kPaperPts; ++t)
-            for (int c = 0; c < 3; ++c) ga.unit[t][c] = (float)unit[t][c];
-        for (int k = 0; k < kLayers; ++k) ga.D[k] = (float)D[k];
+            for (int c = 0; c < 3; ++c) ga.unit[t][c] = (float)tpl.unit[t][c];
+        for (int k = 0; k < kLayers; ++k) ga.D[k] = (float)tpl.D[k];
     }
     ga.rt = pair_view(vol, light);
     ga.table = table;
