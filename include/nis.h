@@ -182,11 +182,11 @@ nis_status nis_build_transmittance_method(nis_ctx *ctx, nis_volume vol, const fl
  *      volume-level transmission feature b + sum_m w_m T_m at each point, Fig. 3, in place
  *      of the per-layer CNN): level w[11], level b[1], then SE, blocks with d = the layer's
  *      point count for all three types, merges and head as above.  Header words 6, 7 and 12
- *      are 266, 0 and 11.  It runs in FP32 (NIS_PREC_F32 or NIS_PREC_F32_SIMT, both on FP32
- *      FFMA dense layers; other precisions return NIS_ERR_UNIMPLEMENTED), through
- *      nis_shade_points, nis_shade_points_debug (features [n][266] at the start of the
- *      H buffers) and the frame calls; mixed batches, the server and the allocation-free
- *      call take the lattice model only (NIS_ERR_UNIMPLEMENTED). */
+ *      are 266, 0 and 11.  It runs at NIS_PREC_F32, NIS_PREC_BF16 (tensor cores) or
+ *      NIS_PREC_F32_SIMT (FFMA); NIS_PREC_FP8 returns NIS_ERR_UNIMPLEMENTED.  It shades
+ *      through nis_shade_points, nis_shade_points_debug (features [n][266] at the start of
+ *      the H buffers; no X_T) and the frame calls; mixed batches, the server and the
+ *      allocation-free call take the lattice model only (NIS_ERR_UNIMPLEMENTED). */
 nis_status nis_load_weights(nis_ctx *ctx, const void *blob, size_t bytes, int precision,
                             nis_stream stream, nis_weights *out);
 

@@ -69,7 +69,7 @@ void paper_template(double unit[kPaperPts][3], double D[kLayers], float q[kPaper
 // density at its layer's level and the transmittance at every level (both from the
 // interleaved pairs), reads its phase column; the squeeze statistics of each layer are then
 // summed in point order by one thread per layer (deterministic) and the SE excitation follows.
-__global__ void __launch_bounds__(288) gather_paper_kernel(const __grid_constant__ PaperGatherArgs a) {
+__global__ void __launch_bounds__(288, 4) gather_paper_kernel(const __grid_constant__ PaperGatherArgs a) {
     __shared__ float s_rho[kPaperPts], s_f[kPaperPts], s_T[kPaperPts];
     __shared__ float s_alpha;
     const int p = blockIdx.x, t = threadIdx.x;
@@ -134,11 +134,47 @@ __global__ void __launch_bounds__(288) gather_paper_kernel(const __grid_constant
         const float f0 = __ldg(a.table + (size_t)ja * kPaperPts + t);
         const float f1 = __ldg(a.table + (size_t)(ja + 1) * kPaperPts + t);
         const float f = f0 + wa * (f1 - f0);
-        const size_t o = (size_t)p * kPaperPts + t;
-        a.H_rho[o] = rho;
-        a.H_f[o] = f;
-        a.H_T[o] = T;
+        if (a.H_rho) {
+            const size_t o = (size_t)p * kPaperPts + t;
+            a.H_rho[o] = rho;
+            a.H_f[o] = f;
+            a.H_T[o] = T;
+        }
+        if (a.Hb_rho) {                        // BF16 parts, the layer's padded columns
+            const int col = paper_first_pad(k) + (t - paper_first(k));
+            __nv_bfloat16 *dr = a.Hb_rho + (size_t)p * a.ld_rf + col;
+            __nv_bfloat16 *df = a.Hb_f + (size_t)p * a.ld_rf + col;
+            __nv_bfloat16 *dt = a.Hb_T + (size_t)p * a.ld_t + col;
+            float r0 = rho, r1 = f, r2 = T;
+            for (int q = 0; q < a.parts; ++q) {
+                const __nv_bfloat16 b0 = __float2bfloat16_rn(r0), b1 = __float2bfloat16_rn(r1),
+                                    b2 = __float2bfloat16_rn(r2);
+                dr[q * a.part_rf] = b0;
+                df[q * a.part_rf] = b1;
+                dt[q * a.part_t] = b2;
+                r0 -= __bfloat162float(b0);
+                r1 -= __bfloat162float(b1);
+                r2 -= __bfloat162float(b2);
+            }
+        }
         s_rho[t] = rho; s_f[t] = f; s_T[t] = T;
+    } else if (a.Hb_rho) {
+        // zeros in the layers' padding columns and the tail: the MMAs read whole 32-column
+        // boxes, whose columns beyond a layer meet zero weights (and must be finite)
+        for (int z = t - kPaperPts; z < kPaperPadTail - kPaperPts; z += blockDim.x - kPaperPts) {
+            int col = -1, seen = 0;
+            for (int k = 0; k < kLayers && col < 0; ++k) {
+                const int padn = paper_count_pad(k) - paper_count(k);
+                if (z < seen + padn) col = paper_first_pad(k) + paper_count(k) + (z - seen);
+                seen += padn;
+            }
+            if (col < 0) col = kPaperPad + (z - seen);
+            for (int q = 0; q < a.parts; ++q) {
+                a.Hb_rho[(size_t)p * a.ld_rf + col + q * a.part_rf] = __float2bfloat16_rn(0.f);
+                a.Hb_f[(size_t)p * a.ld_rf + col + q * a.part_rf] = __float2bfloat16_rn(0.f);
+                a.Hb_T[(size_t)p * a.ld_t + col + q * a.part_t] = __float2bfloat16_rn(0.f);
+            }
+        }
     }
     if (t == 0) s_alpha = alpha;
     __syncthreads();

@@ -496,7 +496,7 @@ nis_status pack_weights_tc(nis_ctx *ctx, Weights &w, int parts, cudaStream_t s) 
     const WeightOffsets &o = w.off;
     for (int t = 0; t < 3; ++t)
         for (int k = 0; k < kLayers; ++k) {
-            int d = feat_dim(t);
+            int d = o.model == kModelPaper ? paper_count(k) : feat_dim(t);
             mats.push_back({w.f32 + o.blk_w1[t][k], kWidth, d, d + kCfg, &w.map_fc1[t][k]});
             mats.push_back({w.f32 + o.blk_w2[t][k], kWidth, kWidth, kWidth, &w.map_fc2[t][k]});
         }
@@ -645,9 +645,34 @@ nis_status shade_impl_fp8(nis_ctx *ctx, const Volume &vol, const Light &light, c
                           cudaStream_t s, const Mixed *mx);
 
 // Runs steps 3-6 for `n` points already on the device.
-// Steps 3-6 of the paper-template model: its gathers (density, phase and the volume-level
-// transmission feature at the 266 template points, SE), then the backbone on per-layer
-// widths with FP32 FFMA dense layers.
+// The paper model's gather arguments of one (volume, light, weights, material): everything
+// but the points and the outputs.
+PaperGatherArgs paper_gather_args(const Volume &vol, const Light &light, const Weights &wt,
+                                  const nis_material *m, const float *table) {
+    PaperGatherArgs ga{};
+    const PaperTemplate &tpl = paper_tpl();
+    for (int t = 0; t < kPaperPts; ++t)
+        for (int c = 0; c < 3; ++c) ga.unit[t][c] = (float)tpl.unit[t][c];
+    for (int k = 0; k < kLayers; ++k) ga.D[k] = (float)tpl.D[k];
+    const WeightOffsets &o = wt.off;
+    ga.rt = pair_view(vol, light);
+    ga.table = table;
+    ga.lx = light.dir[0]; ga.ly = light.dir[1]; ga.lz = light.dir[2];
+    ga.g = m->g;
+    for (int c = 0; c < 3; ++c) ga.albedo[c] = m->albedo[c];
+    ga.level_w = wt.f32 + o.level_w;
+    ga.level_b = wt.f32 + o.level_b;
+    ga.se = wt.f32;
+    for (int k = 0; k < kLayers; ++k) {
+        ga.se_w1[k] = o.se_w1[k]; ga.se_b1[k] = o.se_b1[k];
+        ga.se_w2[k] = o.se_w2[k]; ga.se_b2[k] = o.se_b2[k];
+    }
+    return ga;
+}
+
+// Steps 3-6 of the paper-template model with FP32 FFMA dense layers (NIS_PREC_F32_SIMT):
+// its gathers (density, phase and the volume-level transmission feature at the 266 template
+// points, SE), then the backbone on per-layer widths.
 nis_status shade_impl_paper(nis_ctx *ctx, const Volume &vol, const Light &light, const Weights &wt,
                             const nis_material *m, const float *table, const float *pts,
                             const float *om, int n, float *rgb, const nis_debug_out *dbg,
@@ -662,25 +687,7 @@ nis_status shade_impl_paper(nis_ctx *ctx, const Volume &vol, const Light &light,
     auto act = [&](int i) { return w.act + i * act_stride; };
     float dec_scale[3];
     for (int c = 0; c < 3; ++c) dec_scale[c] = m->intensity[c] * powf(m->albedo[c], 4.0f);
-    PaperGatherArgs ga{};
-    {
-        const PaperTemplate &tpl = paper_tpl();
-        for (int t = 0; t < kPaperPts; ++t)
-            for (int c = 0; c < 3; ++c) ga.unit[t][c] = (float)tpl.unit[t][c];
-        for (int k = 0; k < kLayers; ++k) ga.D[k] = (float)tpl.D[k];
-    }
-    ga.rt = pair_view(vol, light);
-    ga.table = table;
-    ga.lx = light.dir[0]; ga.ly = light.dir[1]; ga.lz = light.dir[2];
-    ga.g = m->g;
-    for (int c = 0; c < 3; ++c) ga.albedo[c] = m->albedo[c];
-    ga.level_w = W + o.level_w;
-    ga.level_b = W + o.level_b;
-    ga.se = W;
-    for (int k = 0; k < kLayers; ++k) {
-        ga.se_w1[k] = o.se_w1[k]; ga.se_b1[k] = o.se_b1[k];
-        ga.se_w2[k] = o.se_w2[k]; ga.se_b2[k] = o.se_b2[k];
-    }
+    PaperGatherArgs ga = paper_gather_args(vol, light, wt, m, table);
     // the features [cnt][266] of each type in the lattice model's feature buffers
     ga.H_rho = w.H_rho; ga.H_f = w.H_f; ga.H_T = w.H_T;
     ga.v = w.v; ga.w_se = w.w_se; ga.cfg = w.cfg;
@@ -775,7 +782,9 @@ nis_status shade_impl(nis_ctx *ctx, const Volume &vol, const Light &light, const
         if (mx) return fail(ctx, NIS_ERR_UNIMPLEMENTED, "mixed batches need lattice-model weights");
         if ((st = ensure_phase(ctx, phase_spec(m), s, &table, false, true))) return st;
         if (n <= 0) return NIS_OK;
-        return shade_impl_paper(ctx, vol, light, wt, m, table, pts, om, n, rgb, dbg, s);
+        if (wt.precision == NIS_PREC_F32_SIMT)
+            return shade_impl_paper(ctx, vol, light, wt, m, table, pts, om, n, rgb, dbg, s);
+        return shade_impl_bf16(ctx, vol, light, wt, m, table, pts, om, n, rgb, dbg, s, nullptr);
     }
     if (!mx && (st = ensure_phase(ctx, phase_spec(m), s, &table))) return st;
     if (n <= 0) return NIS_OK;
@@ -906,6 +915,7 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
                            cudaStream_t s, const Mixed *mx) {
     int chunk = pass_size(n);
     const bool split = wt.precision == NIS_PREC_F32;
+    const bool paper = wt.off.model == kModelPaper;
     WorkspaceBf &w = split ? ctx->wsx : ctx->wsb;
     const int P = split ? 3 : 1;
     nis_status st = ensure_workspace_tc(ctx, w, P, chunk, s);
@@ -954,11 +964,27 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
         }
         ga.v = dbg ? w.v : nullptr; ga.w_se = w.w_se; ga.cfg = w.cfg;
         if (mx) { ga.descs = mx->descs; ga.req_of_point = mx->req_of_point + off; }
-        {
+        if (paper) {
+            // the paper model: its gathers write the operands of all three types (the
+            // transmission feature in the CNN output's buffer); no CNN
+            PaperGatherArgs pg = paper_gather_args(vol, light, wt, m, table);
+            pg.points = ga.points; pg.omega = ga.omega; pg.count = cnt;
+            if (dbg && dbg->H_rho && dbg->H_f && dbg->H_T) {
+                pg.H_rho = dbg->H_rho + (size_t)off * kPaperPts;
+                pg.H_f = dbg->H_f + (size_t)off * kPaperPts;
+                pg.H_T = dbg->H_T + (size_t)off * kPaperPts;
+            }
+            pg.Hb_rho = w.Hb_rho; pg.Hb_f = w.Hb_f; pg.Hb_T = w.XTb;
+            pg.parts = P; pg.ld_rf = kLayers * kLatPad; pg.ld_t = kLayers * kDT;
+            pg.part_rf = cap * kLayers * kLatPad; pg.part_t = cap * kLayers * kDT;
+            pg.v = dbg ? w.v : nullptr; pg.w_se = w.w_se; pg.cfg = w.cfg;
             ProfScope ps(ctx, "gather", s);
-            launch_gather(ga, s);
-        }
-        {
+            launch_gather_paper(pg, s);
+        } else {
+            {
+                ProfScope ps(ctx, "gather", s);
+                launch_gather(ga, s);
+            }
             ProfScope ps(ctx, "cnn", s);
             float *xt_dbg = (dbg && dbg->X_T) ? dbg->X_T + (size_t)off * kLayers * kDT : nullptr;
             if (split)      // FP32: the FP32 CNN, its output split into three BF16 parts
@@ -969,15 +995,19 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
         {
             ProfScope pm(ctx, "mlp", s);   // the pass's dense layers as one timed block
             for (int t = 0; t < 3; ++t) {
-                const int d = feat_dim(t);
                 const CUtensorMap &fmap = t == 0 ? w.map_rho : (t == 1 ? w.map_f : w.map_xt);
                 const int fstride = t == 2 ? kDT : kLatPad;
                 for (int chain = 0; chain < 2; ++chain) {
                     int k0 = chain == 0 ? 0 : kDiffuse, k1 = chain == 0 ? kDiffuse : kLayers;
                     for (int k = k0; k < k1; ++k) {
+                        // the layer's input width d (its weights' columns before the 5 of the
+                        // configuration) and operand columns: the paper model's padded layout
+                        const int d = paper ? paper_count(k) : feat_dim(t);
                         TcGemmArgs f1{};
-                        f1.M = cnt; f1.N = kWidth; f1.K = d; f1.n_mma = 208; f1.k_tiles = (d + 63) / 64;
-                        f1.a_col0 = k * fstride; f1.epi = kEpiFc1; f1.err = ctx->d_err;
+                        f1.M = cnt; f1.N = kWidth; f1.K = paper ? paper_count_pad(k) : d;
+                        f1.n_mma = 208; f1.k_tiles = (f1.K + 63) / 64;
+                        f1.a_col0 = paper ? paper_first_pad(k) : k * fstride;
+                        f1.epi = kEpiFc1; f1.err = ctx->d_err;
                         f1.out_e = w.E; f1.out_s = w.S; f1.ldo = kWidth;
                         f1.out_e_f32 = split ? w.E32 : nullptr;
                         f1.out_part = cap * kWidth;
@@ -1049,7 +1079,7 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
                 return cudaMemcpyAsync(dst + per * off, src, per * cnt * sizeof(float),
                                        cudaMemcpyDeviceToDevice, s);
             };
-            NIS_CUDA(cp(dbg->H_T, w.H_T, (size_t)kLayers * kLat));
+            if (!paper) NIS_CUDA(cp(dbg->H_T, w.H_T, (size_t)kLayers * kLat));   // paper: by the gather
             NIS_CUDA(cp(dbg->v, w.v, (size_t)kLayers * 8));
             NIS_CUDA(cp(dbg->w_se, w.w_se, (size_t)kLayers * 3));
         }
@@ -1720,8 +1750,8 @@ nis_status nis_load_weights(nis_ctx *ctx, const void *blob, size_t bytes, int pr
     for (int i = 0; i < 13; ++i)
         if (hd[i] != expect[i])
             return fail(ctx, NIS_ERR_BAD_BLOB, "blob header field " + std::to_string(i) + " mismatch");
-    if (paper && precision != NIS_PREC_F32 && precision != NIS_PREC_F32_SIMT)
-        return fail(ctx, NIS_ERR_UNIMPLEMENTED, "the paper-template model runs in FP32 only");
+    if (paper && precision == NIS_PREC_FP8)
+        return fail(ctx, NIS_ERR_UNIMPLEMENTED, "the paper-template model runs in FP32 or BF16");
     if (n_floats != o.total || bytes != 80 + 4 * n_floats)
         return fail(ctx, NIS_ERR_BAD_BLOB, "blob size does not match the network shape");
     const uint32_t *words = reinterpret_cast<const uint32_t *>(static_cast<const char *>(blob) + 80);
@@ -1738,8 +1768,7 @@ nis_status nis_load_weights(nis_ctx *ctx, const void *blob, size_t bytes, int pr
     cudaError_t e = cudaMemcpyAsync(w.f32, words, o.total * 4, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the caller may free the blob
     if (e != cudaSuccess) { dev_free(ctx, w.f32); return cuda_fail(ctx, e, "weights upload"); }
-    if (paper) st = NIS_OK;                                // FP32 FFMA dense layers
-    else if (precision == NIS_PREC_FP8) st = pack_weights_fp8(ctx, w, s);
+    if (precision == NIS_PREC_FP8) st = pack_weights_fp8(ctx, w, s);
     else if (precision != NIS_PREC_F32_SIMT) st = pack_weights_tc(ctx, w, precision == NIS_PREC_F32 ? 3 : 1, s);
     if (st) {
         dev_free(ctx, w.f32);

@@ -46,6 +46,13 @@ __host__ __device__ constexpr int paper_count(int k) {
 }
 __host__ __device__ constexpr int paper_first(int k) { return k == 0 ? 0 : paper_first(k - 1) + paper_count(k - 1); }
 static_assert(paper_first(kLayers) == kPaperPts, "paper template size");
+// tensor-core operand layout of the paper model's features: each layer's columns padded to a
+// multiple of 8 (16-byte TMA coordinates), 272 in all, then a zero tail as wide as the
+// widest operand box (64 columns: a layer's box reaches past its end into zero weights)
+__host__ __device__ constexpr int paper_count_pad(int k) { return (paper_count(k) + 7) & ~7; }
+__host__ __device__ constexpr int paper_first_pad(int k) { return k == 0 ? 0 : paper_first_pad(k - 1) + paper_count_pad(k - 1); }
+constexpr int kPaperPad = paper_first_pad(kLayers);           // 272
+constexpr int kPaperPadTail = kPaperPad + 64;
 
 struct WeightOffsets {                // float offsets into the FP32 weight buffer
     int model = kModelLattice;
@@ -310,7 +317,11 @@ struct PaperGatherArgs {
     const float *level_w, *level_b;  // device: per-level transmission weights, bias
     const float *se;                 // FP32 weights base; SE offsets below
     size_t se_w1[kLayers], se_b1[kLayers], se_w2[kLayers], se_b2[kLayers];
-    float *H_rho, *H_f, *H_T;        // [count][266]
+    float *H_rho, *H_f, *H_T;        // [count][266] FP32 (may be null)
+    // tensor-core operands (may be null): BF16 [parts][count][row] in the padded layout, the
+    // parts of the three-way split `part` elements apart; rows of ld_rf (rho, f), ld_t (T)
+    __nv_bfloat16 *Hb_rho, *Hb_f, *Hb_T;
+    int parts; size_t part_rf, part_t; int ld_rf, ld_t;
     float *v;                        // [count][12][8] (may be null)
     float *w_se;                     // [count][12][3]
     float *cfg;                      // [count][5]

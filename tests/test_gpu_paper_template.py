@@ -63,12 +63,16 @@ def _oracle(setup, p, om):
                                 return_all=True)
 
 
-def test_features_and_radiance_match_oracle(nis, setup):
+@pytest.mark.parametrize("prec", ["f32_simt", "f32"])
+def test_features_and_radiance_match_oracle(nis, setup, prec):
+    # FP32 FFMA dense layers, and the FP32-accurate tensor-core path (three-way BF16 split)
     ctx, cfg = setup["ctx"], setup["cfg"]
+    w = setup["w"] if prec == "f32_simt" else ctx.load_weights(synth.pack_weights_paper(setup["W"]),
+                                                               nis.PREC_F32)
     p, om, keep = _points(128, 606, cfg)
     assert keep.mean() > 0.95
     dev = torch.device("cuda:0")
-    r = ctx.shade_points_debug(setup["v"], setup["l"], setup["w"], cfg["material"],
+    r = ctx.shade_points_debug(setup["v"], setup["l"], w, cfg["material"],
                                torch.from_numpy(p).to(dev), torch.from_numpy(om).to(dev))
     rgb_ref, ref = _oracle(setup, p[keep], om[keep])
     n_keep = int(keep.sum())
@@ -81,15 +85,36 @@ def test_features_and_radiance_match_oracle(nis, setup):
         assert (err / bound).max() <= 1.0, f"{name}: max err {err.max():.3g}"
     v = r["v"].cpu().numpy()[keep]
     np.testing.assert_allclose(v, ref["v"], rtol=2e-5, atol=2e-5 * np.abs(ref["v"]).max())
-    rgb = ctx.shade_points(setup["v"], setup["l"], setup["w"], cfg["material"],
+    rgb = ctx.shade_points(setup["v"], setup["l"], w, cfg["material"],
                            torch.from_numpy(p[keep]).to(dev), torch.from_numpy(om[keep]).to(dev))
     ctx.sync(timeout_ms=60000)
     got = rgb.cpu().numpy().astype(np.float64)
     floor = 5e-2 * np.abs(rgb_ref).max(axis=0, keepdims=True)
     e = np.abs(got - rgb_ref) / np.maximum(np.abs(rgb_ref), floor)
     nw = (np.abs(got - rgb_ref).max(axis=0) / np.abs(rgb_ref).max(axis=0)).max()
-    print(f"\n[parity] paper-template model, {n_keep} points: max rel {e.max():.3g}, normwise {nw:.3g}")
+    print(f"\n[parity] paper-template model ({prec}), {n_keep} points: max rel {e.max():.3g}, "
+          f"normwise {nw:.3g}")
     assert e.max() <= 1e-4 and nw <= 1e-5
+    if w != setup["w"]:
+        ctx.release(w)
+
+
+def test_bf16_against_the_oracle(nis, setup):
+    # BF16 operands (FP32 accumulation): the lattice model's BF16 bound on the mean
+    ctx, cfg = setup["ctx"], setup["cfg"]
+    w = ctx.load_weights(synth.pack_weights_paper(setup["W"]), nis.PREC_BF16)
+    p, om, keep = _points(256, 707, cfg)
+    dev = torch.device("cuda:0")
+    rgb = ctx.shade_points(setup["v"], setup["l"], w, cfg["material"],
+                           torch.from_numpy(p[keep]).to(dev), torch.from_numpy(om[keep]).to(dev))
+    ctx.sync(timeout_ms=60000)
+    rgb_ref, _ = _oracle(setup, p[keep], om[keep])
+    got = rgb.cpu().numpy().astype(np.float64)
+    floor = 5e-2 * np.abs(rgb_ref).max(axis=0, keepdims=True)
+    e = np.abs(got - rgb_ref) / np.maximum(np.abs(rgb_ref), floor)
+    print(f"\n[precision] paper-template model BF16 vs FP64: mean rel {e.mean():.3g}, max {e.max():.3g}")
+    assert e.mean() <= 2e-2
+    ctx.release(w)
 
 
 def test_render_frame_equals_its_shading_points(nis, setup):
@@ -112,7 +137,7 @@ def test_lattice_only_calls_refuse_paper_weights(nis, setup):
     ctx, cfg = setup["ctx"], setup["cfg"]
     blob = synth.pack_weights_paper(setup["W"])
     with pytest.raises(nis.NisError, match="UNIMPLEMENTED"):
-        ctx.load_weights(blob, nis.PREC_BF16)
+        ctx.load_weights(blob, nis.PREC_FP8)
     dev = torch.device("cuda:0")
     p, om = synth.shading_points(16, 1)
     pt, ot = torch.from_numpy(p).to(dev), torch.from_numpy(om).to(dev)
