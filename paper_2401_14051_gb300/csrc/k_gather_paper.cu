@@ -159,8 +159,9 @@ __global__ void __launch_bounds__(288, 4) gather_paper_kernel(const __grid_const
         }
         s_rho[t] = rho; s_f[t] = f; s_T[t] = T;
     } else if (a.Hb_rho) {
-        // zeros in the layers' padding columns and the tail: the MMAs read whole 32-column
-        // boxes, whose columns beyond a layer meet zero weights (and must be finite)
+        // zeros in the layers' padding columns and the tail: the MMAs read whole operand
+        // boxes (32 or 64 columns), whose columns beyond a layer meet zero weights and so
+        // must hold finite values
         for (int z = t - kPaperPts; z < kPaperPadTail - kPaperPts; z += blockDim.x - kPaperPts) {
             int col = -1, seen = 0;
             for (int k = 0; k < kLayers && col < 0; ++k) {
