@@ -66,14 +66,13 @@ void paper_template(double unit[kPaperPts][3], double D[kLayers], float q[kPaper
 }
 
 // One CTA per shading point, thread t < 266 owns template point t.  Each samples the
-// density at its layer's level and the transmittance at every level (both from the
-// interleaved pairs), reads its phase column; the squeeze statistics of each layer are then
-// summed in point order by one thread per layer (deterministic) and the SE excitation follows.
+// density at its layer's level and the transmittance at every level, reads its phase
+// column; the squeeze statistics of each layer are then summed in point order by one thread
+// per layer (deterministic) and the SE excitation follows.
 __global__ void __launch_bounds__(288, 4) gather_paper_kernel(const __grid_constant__ PaperGatherArgs a) {
     __shared__ float s_rho[kPaperPts], s_f[kPaperPts], s_T[kPaperPts];
     __shared__ float s_alpha;
     const int p = blockIdx.x, t = threadIdx.x;
-    const PairView &RT = a.rt;
     const float lx = a.lx, ly = a.ly, lz = a.lz;
     const float px = a.points[3 * p], py = a.points[3 * p + 1], pz = a.points[3 * p + 2];
     float ox = a.omega[3 * p], oy = a.omega[3 * p + 1], oz = a.omega[3 * p + 2];
@@ -102,7 +101,7 @@ __global__ void __launch_bounds__(288, 4) gather_paper_kernel(const __grid_const
     float tt = fminf(fmaxf(alpha * ((kAlpha - 1) / 3.14159265358979f), 0.f), (float)(kAlpha - 1));
     const int ja = min((int)floorf(tt), kAlpha - 2);
     const float wa = tt - ja;
-    const int N = RT.n[0], L = RT.levels;
+    const int N = a.rho.n[0], L = a.rho.levels;
     if (t < kPaperPts) {
         int k = 0;
         while (k + 1 < kLayers && t >= paper_first(k + 1)) ++k;
@@ -124,13 +123,13 @@ __global__ void __launch_bounds__(288, 4) gather_paper_kernel(const __grid_const
         const float sx = cx + radius * (ux * exx + uy * eyx + uz * ezx);
         const float sy = cy + radius * (ux * exy + uy * eyy + uz * ezy);
         const float sz = cz + radius * (ux * exz + uy * eyz + uz * ezz);
-        // the transmission feature weighs the 11 finest levels (a grid has at most 12)
-        float rho = 0.f, T = __ldg(a.level_b);
-        for (int lv = 0; lv < L; ++lv) {
-            const float2 rt = sample_pair(RT.lv[lv], RT.n[lv], sx, sy, sz);
-            if (lv == m) rho = rt.x;
-            if (lv < kLevelWeights) T = fmaf(__ldg(a.level_w + lv), rt.y, T);
-        }
+        // the density at the layer's level; the transmission feature weighs the 11 finest
+        // levels (a grid has at most 12).  Plain float grids, not the interleaved pairs: the
+        // transmittance alone is read at every level (measured 2 % faster than the pairs)
+        const float rho = sample_border(a.rho.lv[m], a.rho.n[m], sx, sy, sz, 0.0f);
+        float T = __ldg(a.level_b);
+        for (int lv = 0; lv < L && lv < kLevelWeights; ++lv)
+            T = fmaf(__ldg(a.level_w + lv), sample_border(a.T.lv[lv], a.T.n[lv], sx, sy, sz, 1.0f), T);
         const float f0 = __ldg(a.table + (size_t)ja * kPaperPts + t);
         const float f1 = __ldg(a.table + (size_t)(ja + 1) * kPaperPts + t);
         const float f = f0 + wa * (f1 - f0);

@@ -655,7 +655,8 @@ PaperGatherArgs paper_gather_args(const Volume &vol, const Light &light, const W
         for (int c = 0; c < 3; ++c) ga.unit[t][c] = (float)tpl.unit[t][c];
     for (int k = 0; k < kLayers; ++k) ga.D[k] = (float)tpl.D[k];
     const WeightOffsets &o = wt.off;
-    ga.rt = pair_view(vol, light);
+    ga.rho = view_of(vol, vol.data);
+    ga.T = view_of(vol, light.data);
     ga.table = table;
     ga.lx = light.dir[0]; ga.ly = light.dir[1]; ga.lz = light.dir[2];
     ga.g = m->g;

@@ -305,7 +305,7 @@ void launch_gather(const GatherArgs &a, cudaStream_t s);
 // offset from the shading point over its layer's spacing, q[266][3] (the phase offsets).
 void paper_template(double unit[kPaperPts][3], double D[kLayers], float q[kPaperPts][3]);
 struct PaperGatherArgs {
-    PairView rt;                     // density and transmittance of every level
+    PyramidView rho, T;              // density and transmittance levels (plain float grids)
     const float *table;              // [kAlpha][266] phase features of the material
     const float *points, *omega;     // [n][3]
     int count;
