@@ -156,17 +156,21 @@ nis_status nis_build_transmittance(nis_ctx *ctx, nis_volume vol, const float lig
  * marches every voxel).  NIS_TRANSMITTANCE_SHEAR_WARP approximates Eq. 1's depth for large
  * grids: parallel rays toward the light cross the slices normal to the axis a where
  * |light_dir| is largest at positions that shift by r = u_perp / |u_a| per slice (u =
- * -light_dir); each ray sums, slice by slice, the density at the midpoint of its part inside
- * the cube times that part's length; each voxel centre takes the mean density (depth / exit
- * distance) of the four rays around it, bilinear weights over those whose crossing lies
- * strictly inside the cube, times its own exit distance.  No stop rule.  A light along an
- * axis reproduces the march (to rounding), a homogeneous medium gives the exact depth, and
- * otherwise the error is an interpolation error made once per voxel: second order in the
- * voxel size on average, first order on rays through a cube edge.  It takes N_0 + 1
- * launches of one kernel (all levels together) and a ray scratch of about
- * 2 (1 + |r_p|)(1 + |r_q|) N^2 floats per level, owned by the context (grow-only; calls on
- * one context that overlap on the GPU race on it).  A light is identified by volume,
- * direction, lambda and method.  Unknown methods return NIS_ERR_INVALID_ARG. */
+ * -light_dir); each ray sums, slice by slice, the part of its step that lies inside the cube
+ * (its in-cube length) and that length times the density at the part's midpoint (its
+ * depth); each voxel centre takes the bilinearly weighted mean density of the four rays
+ * around it (depth / length, or the density at the crossing for a ray that has not met the
+ * cube) times its own exit distance.  No stop rule.  A light along an axis reproduces the
+ * march (to rounding), a homogeneous medium gives the exact depth, the field is continuous
+ * in the light direction, and otherwise the error is an interpolation error made once per
+ * voxel: second order in the voxel size on average, first order on rays through a cube
+ * edge.  It takes N_0 + 1 launches of one kernel (all levels together) and a ray scratch of
+ * 4 floats per ray, about (1 + |r_p|)(1 + |r_q|) N^2 rays per level, owned by the context
+ * (grow-only; calls on one context that overlap on the GPU race on it).  For lights whose
+ * |x| component is largest the volume also keeps an x-major copy of its pyramid (about the
+ * pyramid's size, with its occupancy), and the context an output buffer of the same size.
+ * A light is identified by volume, direction, lambda and method.  Unknown methods return
+ * NIS_ERR_INVALID_ARG. */
 nis_status nis_build_transmittance_method(nis_ctx *ctx, nis_volume vol, const float light_dir[3],
                                           float lambda, int method, nis_stream stream,
                                           nis_light *out);
