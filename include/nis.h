@@ -379,8 +379,9 @@ nis_status nis_find_hits(nis_ctx *ctx, nis_volume vol, const nis_camera *cam, in
 
 /* Kernel timing: with profiling on, the kernels the context launches are bracketed by CUDA
  * events on their stream, accumulated per kernel family: each kernel on its own, except the
- * dense layers of one shading pass, which are one bracketed block (no event between two of
- * their launches, which overlap as programmatic dependent launches).  nis_profile(ctx, 1)
+ * tensor-core dense layers of one shading pass and the launches of one shear-warp
+ * transmittance build, which are one bracketed block each (no event between two of their
+ * launches, which overlap as programmatic dependent launches).  nis_profile(ctx, 1)
  * clears and starts, nis_profile(ctx, 0) stops.  nis_profile_read waits for the recorded
  * events and returns the summed device time and the number of kernels launched inside the
  * brackets of one family: "pyramid", "march", "phase", "hits", "gather", "cnn", "mlp" or
