@@ -629,7 +629,9 @@ def cnn(H_T: np.ndarray, weights: dict) -> np.ndarray:
 # Step 5: SE channel attention (Eq. 24-26, R14)
 # ----------------------------------------------------------------------------------------
 def sigmoid(x):
-    return 1.0 / (1.0 + np.exp(-x))
+    # exp(-x) overflows to inf for x below about -709; 1 / (1 + inf) is the correct limit 0
+    with np.errstate(over="ignore"):
+        return 1.0 / (1.0 + np.exp(-x))
 
 
 def se_weights(v: np.ndarray, weights: dict) -> np.ndarray:
