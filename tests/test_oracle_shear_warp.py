@@ -101,3 +101,39 @@ def test_continuous_in_the_light_direction(light):
     for _ in range(3):
         nudged = l + 1e-9 * rng.standard_normal(3)
         np.testing.assert_allclose(O.shear_warp_level(v, 0, nudged), base, rtol=0, atol=1e-6)
+
+
+@pytest.mark.parametrize("u_raw,level", [((1.0, 0.04, -0.03), 0), ((-0.05, -1.0, 0.035), 1),
+                                         ((0.03, 0.045, -1.0), 2)])
+def test_exact_on_a_field_affine_across_the_dominant_axis(u_raw, level):
+    # rho affine in a coordinate c normal to the dominant axis of u and constant in the
+    # other two.  Away from the side faces every ray enters through the light face, so the
+    # rays' paths to slice k are translates of one another and each carries the field's
+    # value at its path's midpoint; bilinear weights reproduce an affine function, and S(x)
+    # is the exact line integral d (a + b (c0 + u_c d / 2)).  The light is passed
+    # unnormalised.
+    n, a, b = 16, 0.9, 1.8
+    u = np.asarray(u_raw) / np.linalg.norm(u_raw)
+    dom = int(np.argmax(np.abs(u)))
+    c = (dom + 1) % 3                        # the affine coordinate
+    cc = (np.arange(n) + 0.5) / n
+    shape = [1, 1, 1]
+    shape[2 - c] = n                         # array order is [z, y, x]
+    grid = np.broadcast_to((a + b * cc).reshape(shape), (n, n, n)).copy()
+    t = O.shear_warp_level(grid, level, -2.5 * np.asarray(u_raw))
+    x = O.voxel_centres(n)
+    d = O.exit_distance(x, u)
+    s_exact = d * (a + b * (x[..., c] + 0.5 * u[c] * d))
+    # voxels at least 3 from every side face: their paths and their four rays stay inside
+    # the cube's interior across the dominant axis (the drift is below one voxel)
+    inner = np.ones((n, n, n), dtype=bool)
+    for ax in range(3):
+        if ax != dom:
+            idx = np.arange(n)
+            keep = (idx >= 3) & (idx <= n - 4)
+            sh = [1, 1, 1]
+            sh[2 - ax] = n
+            inner &= keep.reshape(sh)
+    assert inner.sum() > 1000
+    s = -np.log(t) / 0.6 ** (level + 1)
+    np.testing.assert_allclose(s[inner], s_exact[inner], rtol=1e-12, atol=1e-14)

@@ -92,3 +92,24 @@ def test_exit_distance_closed_form():
     assert O.exit_distance(x, np.array([0, 0, -1.0]))[0] == pytest.approx(0.75)
     u = np.array([1.0, 1.0, 0]) / math.sqrt(2)
     assert O.exit_distance(x, u)[0] == pytest.approx(0.5 * math.sqrt(2))
+
+
+@pytest.mark.parametrize("u_raw,level", [((0.8, 0.05, 0.6), 0), ((-0.3, -0.04, 0.9), 2),
+                                         ((0.55, 0.06, -0.8), 1)])
+def test_march_is_exact_on_a_field_affine_along_the_ray(u_raw, level):
+    # rho = a + b y, constant in x and z.  Trilinear interpolation reproduces it wherever y
+    # lies between the first and last voxel centre, and the midpoint rule integrates an
+    # affine function exactly on every step, the partial last step included; the light is
+    # passed unnormalised.  tau = lambda^(m+1) (a d + b (y0 d + u_y d^2 / 2)).
+    n, a, b = 8, 0.7, 2.5
+    yc = (np.arange(n) + 0.5) / n
+    grid = np.broadcast_to((a + b * yc).reshape(1, n, 1), (n, n, n)).copy()
+    u = np.asarray(u_raw) / np.linalg.norm(u_raw)
+    rng = np.random.default_rng(level)
+    x = rng.uniform(0.0, 1.0, (300, 3))
+    x[:, 1] = rng.uniform(0.2, 0.8, 300)
+    d = O.exit_distance(x, u)
+    assert np.all(np.abs(u[1]) * d < 0.1)   # every path keeps y inside [1/16, 15/16]
+    t = O.march(grid, level, x, -3.7 * np.asarray(u_raw))
+    tau = 0.6 ** (level + 1) * (a * d + b * (x[:, 1] * d + 0.5 * u[1] * d * d))
+    np.testing.assert_allclose(-np.log(t), tau, rtol=1e-12, atol=1e-15)
