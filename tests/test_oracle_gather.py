@@ -153,3 +153,194 @@ def test_squeeze_vector_layout():
     np.testing.assert_allclose(v[..., 1], Hf.mean(-1))
     assert np.all(v[..., 6] == 0.3)
     np.testing.assert_allclose(v[:, 0, 7], O.view_angle(om, l))
+
+
+# ----------------------------------------------------------------------------------------
+# Absolute placement of the template points, written out from the geometry of Sec. III.B
+# (readings R5-R7): the light frame e_z = -l, e_x = omega's part normal to e_z, e_y = e_z x
+# e_x; flat lattice index t = ((a+2)*5 + (b+2))*9 + (c+4); diffuse layer k centred on p with
+# spacing 2^k xi_(k+1) / N, xi_i = 1 - 0.08 min(i, 5); highlight layer j centred (j + 1/2)
+# d / 4 toward the light with spacing d / 36, d the exit distance toward the light (at
+# least 1/N).
+# ----------------------------------------------------------------------------------------
+def _frame(om, l):
+    ez = -np.asarray(l, dtype=np.float64)
+    ez = ez / np.linalg.norm(ez)
+    om = om / np.linalg.norm(om, axis=1, keepdims=True)
+    w = om - (om @ ez)[:, None] * ez
+    ex = w / np.linalg.norm(w, axis=1, keepdims=True)
+    ey = np.cross(np.broadcast_to(ez, ex.shape), ex)
+    return ex, ey, np.broadcast_to(ez, ex.shape)
+
+
+def _exit(p, u):
+    t = np.full(p.shape[0], np.inf)
+    for a in range(3):
+        if u[a] > 0:
+            t = np.minimum(t, (1 - p[:, a]) / u[a])
+        elif u[a] < 0:
+            t = np.minimum(t, p[:, a] / -u[a])
+    return t
+
+
+def _placed(p, om, l, n):
+    """Sample positions [npts, 12, 225, 3] and spacings [npts, 12]."""
+    ex, ey, ez = _frame(om, l)
+    t = np.arange(225)
+    qa, qb, qc = t // 45 - 2, (t // 9) % 5 - 2, t % 9 - 4
+    off = (qa[None, :, None] * ex[:, None] + qb[None, :, None] * ey[:, None]
+           + qc[None, :, None] * ez[:, None])                          # [npts, 225, 3]
+    u = ez[0]
+    d = np.maximum(_exit(p, u), 1.0 / n)
+    pos = np.zeros((p.shape[0], 12, 225, 3))
+    h = np.zeros((p.shape[0], 12))
+    for k in range(8):
+        h[:, k] = 2.0 ** k * (1 - 0.08 * min(k + 1, 5)) / n
+        pos[:, k] = p[:, None] + h[:, k, None, None] * off
+    for j in range(4):
+        h[:, 8 + j] = d / 36
+        c = p + u * ((j + 0.5) * d / 4)[:, None]
+        pos[:, 8 + j] = c[:, None] + h[:, 8 + j, None, None] * off
+    return pos, h, (ex, ey, ez)
+
+
+def _setup(n, seed, near_face=False):
+    rng = np.random.default_rng(seed)
+    l = synth.unit_vector(500 + seed)
+    om = rng.normal(size=(5, 3))
+    p = 0.5 + rng.uniform(-0.03, 0.03, (5, 3))
+    if near_face:                         # points close to several faces
+        p = rng.choice([0.02, 0.97], size=(5, 3)) + rng.uniform(-0.01, 0.01, (5, 3))
+    return p, om, l
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_template_points_sit_where_the_geometry_puts_them(seed):
+    # affine density and transmittance fields: trilinear lookups inside a level's centre
+    # hull return the field at the sample position itself, so every such feature names the
+    # position its point was placed at
+    n = 32
+    p, om, l = _setup(n, seed)
+    c = (np.arange(n) + 0.5) / n
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    rho = 2.0 + 1.5 * x - 0.7 * y + 0.9 * z
+    levels = O.build_pyramid(rho)
+    tlev = []
+    for g in levels:
+        cm = (np.arange(g.shape[0]) + 0.5) / g.shape[0]
+        zz, yy, xx = np.meshgrid(cm, cm, cm, indexing="ij")
+        tlev.append(0.5 - 0.2 * xx + 0.1 * yy + 0.15 * zz)
+    tab = O.phase_table(0.5, n_alpha=9)
+    Hr, Ht, _, _ = O.gather(p, om, l, levels, tlev, tab, 0.5)
+    pos, _, _ = _placed(p, om, l, n)
+    _, _, lev, _, _ = O.layer_geometry(p, l, n)
+    checked = np.zeros(12, dtype=int)
+    for k in range(12):
+        for i in range(p.shape[0]):
+            nm = levels[lev[i, k]].shape[0]
+            s = pos[i, k]
+            inside = np.all((s >= 0.5 / nm - 1e-12) & (s <= 1 - 0.5 / nm + 1e-12), axis=1)
+            want_r = 2.0 + 1.5 * s[:, 0] - 0.7 * s[:, 1] + 0.9 * s[:, 2]
+            want_t = 0.5 - 0.2 * s[:, 0] + 0.1 * s[:, 1] + 0.15 * s[:, 2]
+            np.testing.assert_allclose(Hr[i, k, inside], want_r[inside], rtol=1e-12)
+            np.testing.assert_allclose(Ht[i, k, inside], want_t[inside], rtol=1e-12)
+            checked[k] += inside.sum()
+    assert np.all(checked[[0, 1, 2, 8, 9, 10, 11]] >= 5 * 100), checked
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_outside_the_grid_density_is_zero_and_transmittance_one(seed):
+    # constant grids: the zero-border (density) and one-border (transmittance) lookups are
+    # the constant times the in-grid share of the tent weights, per axis
+    # clip(min(g + 1, n - g), 0, 1) with g = x n - 1/2
+    n, sigma, tau0 = 8, 3.0, 0.4
+    p, om, l = _setup(n, seed, near_face=True)
+    levels = O.build_pyramid(np.full((n, n, n), sigma))
+    tlev = [np.full(g.shape, tau0) for g in levels]
+    tab = O.phase_table(0.5, n_alpha=9)
+    Hr, Ht, _, _ = O.gather(p, om, l, levels, tlev, tab, 0.5)
+    pos, _, _ = _placed(p, om, l, n)
+    _, _, lev, _, _ = O.layer_geometry(p, l, n)
+    n_out = 0
+    for k in range(12):
+        for i in range(p.shape[0]):
+            nm = levels[lev[i, k]].shape[0]
+            g = pos[i, k] * nm - 0.5
+            share = np.prod(np.clip(np.minimum(g + 1, nm - g), 0, 1), axis=1)
+            np.testing.assert_allclose(Hr[i, k], sigma * share, rtol=1e-12, atol=1e-14)
+            np.testing.assert_allclose(Ht[i, k], 1 - (1 - tau0) * share, rtol=1e-12)
+            n_out += np.sum(share < 1)
+    assert n_out > 1000
+
+
+def test_phase_offsets_are_the_placed_offsets():
+    # the phase feature of template point t describes the point the gather samples: its
+    # offset from p in the light frame, in units of the layer's spacing
+    n = 64
+    p, om, l = _setup(n, 5)
+    pos, h, (ex, ey, ez) = _placed(p, om, l, n)
+    _, _, _, sets, _ = O.layer_geometry(p, l, n)
+    for k in range(12):
+        rel = (pos[:, k] - p[:, None]) / h[:, k, None, None]
+        q = np.stack([np.sum(rel * ex[:, None], -1), np.sum(rel * ey[:, None], -1),
+                      np.sum(rel * ez[:, None], -1)], axis=-1)
+        for i in range(p.shape[0]):
+            np.testing.assert_allclose(O.phase_set_offsets(sets[k]), q[i], atol=1e-9)
+
+
+def test_unnormalised_light_and_view_give_the_same_features():
+    n = 8
+    rng = np.random.default_rng(6)
+    lv = O.build_pyramid(rng.uniform(0, 4, (n, n, n)))
+    l = synth.unit_vector(8)
+    p, om = synth.shading_points(6, 3)
+    om = om.astype(np.float64)
+    tab = O.phase_table(0.4, n_alpha=9)
+    a = O.gather(p, om, l, lv, O.build_transmittance(lv, l), tab, 0.4)
+    scale = rng.uniform(0.2, 5.0, (6, 1))
+    b = O.gather(p, om * scale, 2.7 * l, lv, O.build_transmittance(lv, 2.7 * l), tab, 0.4)
+    for x, y in zip(a, b):
+        np.testing.assert_allclose(x, y, rtol=1e-12, atol=1e-15)
+
+
+@pytest.mark.parametrize("m", [2, 5, 7])
+def test_highlight_level_is_the_nearest_in_log_scale(m):
+    # light along -z: d = 1 - p_z.  Spacing h = d / 36 with h N = 2^m exactly reads level m;
+    # just below and above h N = 2^(m + 1/2) the choice moves from m to m + 1
+    n = 1024
+    l = np.array([0.0, 0.0, -1.0])
+    def level_of(hn):
+        d = 36.0 * hn / n
+        _, h, lev, _, margin = O.layer_geometry(np.array([[0.4, 0.6, 1.0 - d]]), l, n)
+        assert h[0, 8] == pytest.approx(hn / n, rel=1e-12)
+        return lev[0, 8:].tolist(), margin[0]
+    lv, mg = level_of(2.0 ** m)
+    assert lv == [m] * 4 and np.allclose(mg, 0.5)
+    lv, mg = level_of(2.0 ** (m + 0.5) * (1 - 1e-9))
+    assert lv == [m] * 4 and np.all(mg < 1e-8)
+    lv, _ = level_of(2.0 ** (m + 0.5) * (1 + 1e-9))
+    assert lv == [m + 1] * 4
+
+
+def test_table_columns_hold_every_node_a_lookup_reads():
+    alpha = np.random.default_rng(7).uniform(0, math.pi, 40)
+    alpha[:2] = (0.0, math.pi)
+    full = O.phase_table(0.7, n_alpha=17)
+    part = O.phase_table(0.7, n_alpha=17, columns=O.table_columns(alpha, 17))
+    for s in range(5):
+        got = O.table_lookup(part, s, alpha)
+        assert np.isfinite(got).all()
+        np.testing.assert_array_equal(got, O.table_lookup(full, s, alpha))
+
+
+def test_sample_border_top_faces():
+    # mirror of the bottom-face rule above: on a top face half the edge value, half a voxel
+    # beyond it nothing
+    g1 = np.full((4, 4, 4), 2.0)
+    for a in range(3):
+        x = np.full((1, 3), 0.5)
+        x[0, a] = 1.0
+        assert O.sample_border(g1, x, 0.0)[0] == pytest.approx(1.0)
+        x[0, a] = 1.0 + 0.5 / 4
+        assert O.sample_border(g1, x, 0.0)[0] == 0.0
+        assert O.sample_border(g1, x, 5.0)[0] == 5.0

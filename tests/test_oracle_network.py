@@ -120,3 +120,46 @@ def test_parameter_count():
     # 3D-CNN 12 x 7376, SE 12 x 27, blocks 24 x 86400 + 12 x 57400, merges 3 x 80200,
     # head 161003
     assert synth.n_params() == 12 * 7376 + 12 * 27 + 24 * 86400 + 12 * 57400 + 3 * 80200 + 161003
+
+
+def test_config_vector_layout():
+    # Sec. III.C.2: c = [g, albedo (r, g, b), alpha], one row per point
+    c = O.config_vector(0.3, (0.1, 0.2, 0.4), np.array([0.7, 1.1]))
+    np.testing.assert_array_equal(c, [[0.3, 0.1, 0.2, 0.4, 0.7], [0.3, 0.1, 0.2, 0.4, 1.1]])
+
+
+def test_head_biases_enter_in_order():
+    # head: z1 = ReLU(W0 m + b0), z2 = ReLU(W1 z1 + b1), y = W2 z2 + b2.  With every weight 0
+    # but W1[0, 0] = 1 and W2's columns 0 and 1: z1 = ReLU(b0), z2 = ReLU(z1[0] e_0 + b1)
+    w = _zero_weights()
+    hd = w["head"]
+    hd[0]["b"][0] = 2.0
+    hd[1]["b"][1] = 4.0
+    hd[1]["w"][0, 0] = 1.0
+    hd[2]["w"][:, 0] = [1.0, 2.0, 3.0]
+    hd[2]["w"][0, 1] = 10.0
+    hd[2]["b"][:] = [0.1, 0.2, 0.3]
+    n = 2
+    X = [np.zeros((n, 12, 225)), np.zeros((n, 12, 225)), np.zeros((n, 12, 80))]
+    y = O.backbone(*X, O.config_vector(0.5, [1, 1, 1], np.ones(n)), w)
+    np.testing.assert_allclose(y, [[2.0 + 40.0 + 0.1, 4.0 + 0.2, 6.0 + 0.3]] * n, rtol=1e-15)
+
+
+def test_merge_bias_and_config_g_reach_the_output():
+    # the g column of c routed through diffuse layer 0 of the rho chain; the merge bias of
+    # the T chain adds to the same head unit
+    w = _path_weights(0, 0, 225 + 0)
+    w["merge"][2]["b"][0] = 0.25
+    w["head"][0]["w"][0, 400] = 1.0
+    n = 3
+    X = [np.zeros((n, 12, 225)), np.zeros((n, 12, 225)), np.zeros((n, 12, 80))]
+    y = O.backbone(*X, O.config_vector(0.6, [0.9, 0.8, 0.7], np.ones(n)), w)
+    np.testing.assert_allclose(y, [[0.85, 1.7, 2.55]] * n, rtol=1e-14)
+
+
+def test_material_phase_takes_lobes_from_two_on():
+    one = {"g": 0.85, "lobes": [(0.85, 1.0)]}
+    two = {"g": 0.85, "lobes": [(0.9, 0.6), (-0.3, 0.4)]}
+    assert O.material_phase({"g": 0.4}) == 0.4
+    assert O.material_phase(one) == 0.85
+    assert O.material_phase(two) == [(0.9, 0.6), (-0.3, 0.4)]
