@@ -163,3 +163,30 @@ def test_material_phase_takes_lobes_from_two_on():
     assert O.material_phase({"g": 0.4}) == 0.4
     assert O.material_phase(one) == 0.85
     assert O.material_phase(two) == [(0.9, 0.6), (-0.3, 0.4)]
+
+
+@pytest.mark.parametrize("t,k,i", [(0, 1, 100), (1, 10, 7)])
+def test_shade_points_scales_features_by_the_se_weights(t, k, i):
+    # SE with zero weights and biases (0, ln 3, -ln 3) scales rho by 1/2, phase by 3/4 and
+    # transmission by 1/4; the routed feature reaches y scaled by its type's weight, and
+    # the radiance is its decode
+    n = 8
+    rng = np.random.default_rng(11)
+    lv = O.build_pyramid(rng.uniform(0.5, 4, (n, n, n)))
+    l = synth.unit_vector(4)
+    tl = O.build_transmittance(lv, l)
+    tab = O.phase_table(0.6, n_alpha=9)
+    p = rng.uniform(0.35, 0.65, (3, 3))
+    om = rng.normal(size=(3, 3))
+    w = _path_weights(t, k, i)
+    for se in w["se"]:
+        se["b2"][:] = [0.0, math.log(3.0), -math.log(3.0)]
+    mat = {"g": 0.6, "albedo": [0.9, 0.8, 0.7], "intensity": [1.0, 2.0, 3.0]}
+    rgb, d = O.shade_points(p, om, l, lv, tl, tab, w, mat, return_all=True)
+    H = O.gather(p, om, l, lv, tl, tab, 0.6)
+    src = (H[0], H[2])[t][:, k, i]                               # H_rho, H_f
+    assert np.all(src > 0)
+    np.testing.assert_allclose(d["w"], np.broadcast_to([0.5, 0.75, 0.25], d["w"].shape), rtol=1e-15)
+    scale = (0.5, 0.75)[t]
+    np.testing.assert_allclose(d["y"], scale * src[:, None] * np.array([1.0, 2.0, 3.0]), rtol=1e-13)
+    np.testing.assert_allclose(rgb, O.decode(d["y"], mat["albedo"], mat["intensity"]), rtol=1e-14)

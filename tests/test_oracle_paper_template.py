@@ -271,6 +271,10 @@ def test_point_set_construction():
     for j, n in enumerate((32, 16, 16, 8)):
         r = np.linalg.norm(layers[8 + j], axis=1)
         np.testing.assert_allclose(r, np.sqrt((np.arange(n) + 0.5) / n), rtol=1e-14)
+        # Vogel's sunflower: point i at azimuth i golden angles
+        az = np.arctan2(layers[8 + j][:, 1], layers[8 + j][:, 0])
+        want = np.arange(n) * g
+        np.testing.assert_allclose(np.angle(np.exp(1j * (az - want))), 0, atol=1e-12)
 
 
 def test_squeeze_vector_layout():
@@ -291,3 +295,133 @@ def test_squeeze_vector_layout():
             np.testing.assert_array_equal(v[:, k, 3 + i], np.max(H[k], axis=1))
     np.testing.assert_array_equal(v[..., 6], 0.4)
     np.testing.assert_allclose(v[:, 0, 7], O.view_angle(om, l), rtol=1e-15)
+
+
+@pytest.mark.parametrize("m", [1, 4, 6])
+def test_highlight_level_is_the_nearest_in_log_scale(m):
+    # P4: light along -z, d = 1 - p_z; layer j's spacing (d / 8) D_j read at level
+    # floor(log2(spacing N) + 1/2): spacing N = 2^m reads m, and the choice moves to m + 1
+    # across spacing N = 2^(m + 1/2)
+    n = 1024
+    l = np.array([0.0, 0.0, -1.0])
+    om = np.array([[0.6, 0.0, 0.8]])
+    ex, ey, ez = O.light_frame(om, l)
+    _, D, _, _ = O.paper_template_geometry(np.full((1, 3), 0.5), l, n)
+    for j in range(4):
+        def level(sn):
+            d = 8.0 * sn / (D[8 + j] * n)
+            _, _, _, place = O.paper_template_geometry(np.array([[0.3, 0.6, 1.0 - d]]), l, n)
+            _, lev, spacing, margin = place(8 + j, ex, ey, ez)
+            assert spacing[0] * n == pytest.approx(sn, rel=1e-9)
+            return lev[0], margin[0]
+        lev, mg = level(2.0 ** m)
+        assert lev == m and mg == pytest.approx(0.5)
+        lev, mg = level(2.0 ** (m + 0.5) * (1 - 1e-9))
+        assert lev == m and mg < 1e-8
+        assert level(2.0 ** (m + 0.5) * (1 + 1e-9))[0] == m + 1
+
+
+def test_exit_face_point_takes_the_floor_distance():
+    # a shading point on the face toward the light: d is floored at 1/N (P4)
+    n = 64
+    l = np.array([0.0, 0.0, -1.0])
+    om = np.array([[0.0, 0.6, 0.8]])
+    ex, ey, ez = O.light_frame(om, l)
+    _, D, _, place = O.paper_template_geometry(np.array([[0.5, 0.5, 1.0]]), l, n)
+    for j in range(4):
+        _, _, spacing, _ = place(8 + j, ex, ey, ez)
+        assert spacing[0] == pytest.approx(D[8 + j] / (8 * n), rel=1e-12)
+
+
+def test_phase_lookup_at_and_between_table_nodes():
+    # light along -z and omega = (sin a, 0, -cos a): the view angle is a; at a node the
+    # features are the table's column, halfway between two nodes their mean
+    n_alpha = 9
+    ptab = O.paper_phase_table(0.7, n_alpha=n_alpha)
+    nodes = O.alpha_nodes(n_alpha)
+    a = np.array([nodes[0], nodes[3], nodes[8], 0.5 * (nodes[5] + nodes[6]), 0.75 * nodes[1] + 0.25 * nodes[2]])
+    om = np.stack([np.sin(a), np.zeros_like(a), -np.cos(a)], axis=1)
+    l = np.array([0.0, 0.0, -1.0])
+    lv = O.build_pyramid(np.ones((4, 4, 4)))
+    tl = [np.ones_like(g) for g in lv]
+    p = np.full((len(a), 3), 0.5)
+    _, H_f, _, _ = O.paper_gather(p, om, l, lv, tl, ptab, 0.7, np.zeros(11), 0.0)
+    f = np.concatenate(H_f, axis=1)                                # [5, 266]
+    np.testing.assert_allclose(f[0], ptab[:, 0], rtol=1e-9)
+    np.testing.assert_allclose(f[1], ptab[:, 3], rtol=1e-9)
+    np.testing.assert_allclose(f[2], ptab[:, 8], rtol=1e-9)
+    np.testing.assert_allclose(f[3], 0.5 * (ptab[:, 5] + ptab[:, 6]), rtol=1e-9)
+    np.testing.assert_allclose(f[4], 0.75 * ptab[:, 1] + 0.25 * ptab[:, 2], rtol=1e-9)
+    assert np.ptp(ptab[:, 0] - ptab[:, 8]) > 0
+
+
+def test_outside_the_grid_density_is_zero_and_transmittance_one():
+    # constant grids near faces: density sigma times the in-grid share of the tent weights
+    # (per axis clip(min(g + 1, n - g), 0, 1), g = x n - 1/2), transmittance 1 outside
+    n, sigma, tau0 = 8, 3.0, 0.4
+    rng = np.random.default_rng(9)
+    p = rng.choice([0.02, 0.97], size=(5, 3)) + rng.uniform(-0.01, 0.01, (5, 3))
+    om = rng.normal(size=(5, 3))
+    l = synth.unit_vector(77)
+    lv = O.build_pyramid(np.full((n, n, n), sigma))
+    tl = [np.full(g.shape, tau0) for g in lv]
+    w = np.zeros(11)
+    w[: len(lv)] = rng.uniform(0.1, 1.0, len(lv))
+    ptab = O.paper_phase_table(0.5, n_alpha=9)
+    H_rho, _, H_T, _ = O.paper_gather(p, om, l, lv, tl, ptab, 0.5, w, 0.3)
+    ex, ey, ez = O.light_frame(om, l)
+    _, _, _, place = O.paper_template_geometry(p, l, n)
+    n_out = 0
+    for k in range(12):
+        x, lev, _, _ = place(k, ex, ey, ez)
+        def share(nm):
+            g = x * nm - 0.5
+            return np.prod(np.clip(np.minimum(g + 1, nm - g), 0, 1), axis=-1)
+        for i in range(p.shape[0]):
+            nm = lv[lev[i]].shape[0]
+            np.testing.assert_allclose(H_rho[k][i], sigma * share(nm)[i], rtol=1e-12, atol=1e-14)
+        want_t = 0.3 + sum(w[m] * (1 - (1 - tau0) * share(lv[m].shape[0])) for m in range(len(lv)))
+        np.testing.assert_allclose(H_T[k], want_t, rtol=1e-12)
+        n_out += np.sum(share(n) < 1)
+    assert n_out > 100
+
+
+def test_network_inputs_are_rho_phase_transmission_in_order():
+    # SE with zero weights and biases (0, ln 3, -ln 3): scales 1/2, 3/4, 1/4 per type;
+    # weights that route one feature of type t, layer k to y = (1, 2, 3) x:
+    # shade_points_paper's y is that feature of paper_gather times its type's scale
+    cfg = synth.config(1)
+    lv = O.build_pyramid(cfg["volume"]().astype(np.float64))
+    tl = O.build_transmittance(lv, cfg["light"])
+    ptab = O.paper_phase_table(cfg["material"]["g"], n_alpha=17)
+    p, om = synth.shading_points(4, 8)
+    W0 = synth.make_weights_paper(2, 16.0)
+    feats = O.paper_gather(p, om, cfg["light"], lv, tl, ptab, cfg["material"]["g"],
+                           W0["level"]["w"], W0["level"]["b"][0])
+    for t, k, i in ((0, 2, 5), (1, 9, 3), (2, 6, 40), (2, 11, 0)):
+        W = {"level": W0["level"], "se": [], "blocks": [], "merge": [], "head": []}
+        for _ in range(12):
+            W["se"].append({"w1": np.zeros((2, 8)), "b1": np.zeros(2), "w2": np.zeros((3, 2)),
+                            "b2": np.array([0.0, math.log(3.0), -math.log(3.0)])})
+        for tt in range(3):
+            W["blocks"].append([{"w1": np.zeros((200, nk + 5)), "b1": np.zeros(200),
+                                 "w2": np.zeros((200, 200)), "b2": np.zeros(200)}
+                                for nk in O.TEMPLATE_COUNTS])
+            W["merge"].append({"w": np.zeros((200, 400)), "b": np.zeros(200)})
+        W["head"] = [{"w": np.zeros((200, 600)), "b": np.zeros(200)},
+                     {"w": np.zeros((200, 200)), "b": np.zeros(200)},
+                     {"w": np.zeros((3, 200)), "b": np.zeros(3)}]
+        W["blocks"][t][k]["w1"][0, i] = 1.0
+        for kk in range(k + 1, 8 if k < 8 else 12):
+            W["blocks"][t][kk]["w2"][0, 0] = 1.0
+        W["merge"][t]["w"][0, 0 if k < 8 else 200] = 1.0
+        W["head"][0]["w"][0, 200 * t] = 1.0
+        W["head"][1]["w"][0, 0] = 1.0
+        W["head"][2]["w"][:, 0] = [1.0, 2.0, 3.0]
+        _, d = O.shade_points_paper(p, om, cfg["light"], lv, tl, ptab, W, cfg["material"],
+                                    return_all=True)
+        src = feats[t][k][:, i]
+        assert np.all(src > 0)
+        scale = (0.5, 0.75, 0.25)[t]
+        np.testing.assert_allclose(d["y"], scale * src[:, None] * np.array([1.0, 2.0, 3.0]),
+                                   rtol=1e-12)

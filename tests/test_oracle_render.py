@@ -82,3 +82,30 @@ def test_render_frame_lights_is_the_sum_over_lights():
     other, _, _ = O.render_frame(vol, 8.0, l2, cam, weights, mat, levels, t2, table)
     np.testing.assert_allclose(two, one + other, rtol=1e-15, atol=0)
     assert np.abs(other - one).max() > 0          # the second light changes the radiance
+
+
+def test_camera_rays_of_every_pixel():
+    # pinhole with square pixels: pixel (i, j) has screen coordinates x = 2 (j + 1/2) / W - 1
+    # (left to right), y = 1 - 2 (i + 1/2) / H (top to bottom) and looks along
+    # fwd + x tan(fov_y / 2) (W / H) right + y tan(fov_y / 2) up.  The image is not mirrored:
+    # (right, up, -fwd) is right-handed, so looking along +z with up +y, right is -x.  The
+    # orthographic camera shifts the origin instead, by half the height per unit of screen.
+    W, H = 4, 2
+    x = 2 * (np.arange(W) + 0.5) / W - 1
+    y = 1 - 2 * (np.arange(H) + 0.5) / H
+    right, up, fwd = np.array([-1.0, 0, 0]), np.array([0, 1.0, 0]), np.array([0, 0, 1.0])
+    cam = synth.persp_camera(fwd, W, H, fov_y_deg=50.0)
+    o, d = O.camera_rays(cam)
+    t = math.tan(math.radians(25.0))
+    for i in range(H):
+        for j in range(W):
+            want = fwd + x[j] * t * (W / H) * right + y[i] * t * up
+            np.testing.assert_allclose(d[i, j], want / np.linalg.norm(want), atol=1e-15)
+            np.testing.assert_allclose(o[i, j], cam["eye"], atol=0)
+    oc = synth.ortho_camera(fwd, W, H, ortho_height=1.5)
+    o2, d2 = O.camera_rays(oc)
+    for i in range(H):
+        for j in range(W):
+            want = np.asarray(oc["eye"]) + x[j] * 0.75 * (W / H) * right + y[i] * 0.75 * up
+            np.testing.assert_allclose(o2[i, j], want, atol=1e-15)
+            np.testing.assert_allclose(d2[i, j], fwd, atol=0)
