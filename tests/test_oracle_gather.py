@@ -55,6 +55,15 @@ def test_frame_is_orthonormal_and_puts_omega_in_xz_plane():
     np.testing.assert_allclose(np.sum(om * ey, axis=1), 0, atol=1e-14)
     np.testing.assert_allclose(np.sum(om * ez, axis=1), -np.cos(a), atol=1e-14)
     np.testing.assert_allclose(a, np.arccos(np.clip(om @ l, -1, 1)), atol=1e-7)
+    # omega along the light (either way) leaves e_x free: still an orthonormal right-handed
+    # frame with e_z = -l, also for a light along z
+    for ll in (l, np.array([0.0, 0.0, -1.0])):
+        ex, ey, ez = O.light_frame(np.stack([ll, -ll, 3.0 * ll]), ll)
+        for e in (ex, ey, ez):
+            np.testing.assert_allclose(np.linalg.norm(e, axis=1), 1.0, rtol=1e-14)
+        np.testing.assert_allclose(np.sum(ex * ez, axis=1), 0, atol=1e-14)
+        np.testing.assert_allclose(np.sum(np.cross(ex, ey) * ez, axis=1), 1, atol=1e-14)
+        np.testing.assert_allclose(ez, np.broadcast_to(-ll, ez.shape), atol=1e-15)
 
 
 def test_trilinear_reproduces_affine_fields_inside():
@@ -322,11 +331,20 @@ def test_highlight_level_is_the_nearest_in_log_scale(m):
     assert lv == [m + 1] * 4
 
 
-def test_table_columns_hold_every_node_a_lookup_reads():
-    alpha = np.random.default_rng(7).uniform(0, math.pi, 40)
-    alpha[:2] = (0.0, math.pi)
+@pytest.mark.parametrize("alpha", [(0.0,), (math.pi,), (0.1, 1.9), (2.3, 0.6, 3.0)])
+def test_table_columns_hold_every_node_a_lookup_reads(alpha):
+    # a few angles: the filled columns are exactly the two nodes around each (the last
+    # interval closed at pi), and the partial table gives the full table's lookups
+    alpha = np.asarray(alpha)
     full = O.phase_table(0.7, n_alpha=17)
-    part = O.phase_table(0.7, n_alpha=17, columns=O.table_columns(alpha, 17))
+    cols = O.table_columns(alpha, 17)
+    step = math.pi / 16
+    want = set()
+    for a in alpha:
+        j = min(int(a // step), 15)
+        want |= {j, j + 1}
+    assert sorted(cols.tolist()) == sorted(want)
+    part = O.phase_table(0.7, n_alpha=17, columns=cols)
     for s in range(5):
         got = O.table_lookup(part, s, alpha)
         assert np.isfinite(got).all()

@@ -202,6 +202,13 @@ def test_features_invariant_under_cube_rotations(ri):
         for x, y in zip(a, b):
             np.testing.assert_allclose(x, y, rtol=1e-9, atol=1e-12)
     np.testing.assert_allclose(out[0][3], out[1][3], rtol=1e-9, atol=1e-12)
+    # an unnormalised light and view give the same features
+    lv = O.build_pyramid(vol)
+    tl = O.build_transmittance(lv, l)
+    scaled = O.paper_gather(p, 2.5 * om, 3.0 * l, lv, tl, ptab, 0.6, w, 0.1)
+    for a, b in zip(out[0][:3], scaled[:3]):
+        for x, y in zip(a, b):
+            np.testing.assert_allclose(x, y, rtol=1e-12, atol=1e-15)
 
 
 def test_shading_wiring():
@@ -329,8 +336,9 @@ def test_exit_face_point_takes_the_floor_distance():
     ex, ey, ez = O.light_frame(om, l)
     _, D, _, place = O.paper_template_geometry(np.array([[0.5, 0.5, 1.0]]), l, n)
     for j in range(4):
-        _, _, spacing, _ = place(8 + j, ex, ey, ez)
+        _, lev, spacing, _ = place(8 + j, ex, ey, ez)
         assert spacing[0] == pytest.approx(D[8 + j] / (8 * n), rel=1e-12)
+        assert lev[0] == 0                  # log2(spacing N) < -1/2: clamped at the finest
 
 
 def test_phase_lookup_at_and_between_table_nodes():

@@ -18,6 +18,9 @@ def test_ray_box():
     assert not t1[1] > t0[1]
     assert (t0[2], t1[2]) == (0.0, 0.5)
     assert (t0[3], t1[3]) == (1.0, 2.0)
+    # an oblique ray: slabs x in [0.5, 1.5] / 0.8 and y in [-0.1, 0.9] / 0.6
+    t0, t1 = O.ray_box(np.array([[-0.5, 0.1, 0.5]]), np.array([[0.8, 0.6, 0.0]]))
+    assert t0[0] == pytest.approx(0.625, rel=1e-15) and t1[0] == pytest.approx(1.5, rel=1e-15)
 
 
 def test_camera_centre_and_edge_rays():
