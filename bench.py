@@ -62,7 +62,7 @@ def mlp_bytes_per_point(op: int, st: int) -> int:
                 total += op * width + st * width + (op * width if k == last else st * width)
         total += op * 2 * width + op * width         # merge 400 -> 200
     total += op * 3 * width + op * width             # head 600 -> 200
-    total += 2 * (op * width + op * width)           # head 200 -> 200
+    total += op * width + op * width                 # head 200 -> 200
     total += op * width + 12                         # head 200 -> 3, RGB out
     return total
 

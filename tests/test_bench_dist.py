@@ -100,3 +100,19 @@ def test_reference_arm_under_torchrun_prints_once_from_rank_zero():
     assert line["cpu_baseline"]["kind"] == "oracle"
     assert line["e2e"]["value"] == line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_dense_layer_bytes_per_point_hand_count():
+    # Counted by hand, w = 200.  A chain of n blocks over features of width d moves
+    # op (n (d + 2w) + w) + st w (4n - 2) + 24 n bytes:
+    #   FC-1 reads x (op d) and 24 B of row constants, and h_prev from the second block
+    #   on; it writes e (st w) and s (op w).
+    #   FC-2 reads s and e, and writes h (st w, op w at the chain's end).
+    # Per type the chains have 8 and 4 blocks, and the merge reads 2w and writes w at op:
+    #   op (12 d + 29 w) + 44 st w + 288.
+    # Summed over d = 225, 225, 80: 23,760 op + 26,400 st + 864.
+    # The head 600 -> 200 -> 200 -> 3 adds op (4w + 2w + w) plus 12 B of RGB:
+    #   25,160 op + 26,400 st + 876 in all.
+    import bench
+    for op, st in ((6, 4), (2, 2), (1, 2)):
+        assert bench.mlp_bytes_per_point(op, st) == 25160 * op + 26400 * st + 876
