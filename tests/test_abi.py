@@ -56,3 +56,35 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(nis, "LIB_PATH", str(tmp_path / "libnis.so"))
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         nis.lib()
+
+
+def _imports(path):
+    import ast
+    tree = ast.parse(open(path).read())
+    out = set()
+    for node in ast.walk(tree):
+        if isinstance(node, ast.Import):
+            out |= {a.name.split(".")[0] for a in node.names}
+        elif isinstance(node, ast.ImportFrom) and node.module and node.level == 0:
+            out.add(node.module.split(".")[0])
+    return out
+
+
+def test_oracle_and_cuda_path_share_nothing():
+    # the product package and the input generators never import the oracle, the oracle
+    # never imports the product package, and no CUDA or C source reaches into oracle/
+    pkg = os.path.join(ROOT, "paper_2401_14051_gb300")
+    for base, names in ((pkg, ("oracle",)), (os.path.join(ROOT, "synth"), ("oracle", "paper_2401_14051_gb300"))):
+        for dirpath, _, files in os.walk(base):
+            for f in files:
+                p = os.path.join(dirpath, f)
+                if f.endswith(".py"):
+                    assert not (_imports(p) & set(names)), p
+                elif f.endswith((".cu", ".h", ".c", ".cpp")):
+                    assert "oracle" not in open(p).read(), p
+    for f in os.listdir(os.path.join(ROOT, "oracle")):
+        if f.endswith(".py"):
+            assert "paper_2401_14051_gb300" not in _imports(os.path.join(ROOT, "oracle", f))
+    # outside tests/, only the smoke entry point and bench.py's CPU legs import the oracle
+    users = {f for f in os.listdir(ROOT) if f.endswith(".py") and "oracle" in _imports(os.path.join(ROOT, f))}
+    assert users <= {"__graft_entry__.py", "bench.py"}, users
