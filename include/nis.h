@@ -326,7 +326,10 @@ nis_status nis_server_create(nis_ctx *ctx, nis_weights w, const nis_server_confi
 /* Queues a request (copies the struct; the buffers it points to stay the caller's). */
 nis_status nis_server_submit(nis_server *srv, const nis_request *req, uint64_t *id);
 /* Waits up to timeout_ms (<= 0: no limit) for request `id`; NIS_ERR_TIMEOUT if not done.
- * latency_ms (may be NULL) receives submit-to-completion time. */
+ * latency_ms (may be NULL) receives submit-to-completion time.  A request that failed
+ * returns its error: NIS_ERR_BUDGET if it can never fit the budget, else the status of the
+ * step that failed (upload, builds, shading or the image read-back); its rgb_out is then
+ * undefined. */
 nis_status nis_server_wait(nis_server *srv, uint64_t id, int timeout_ms, double *latency_ms);
 nis_status nis_server_get_stats(nis_server *srv, nis_server_stats *out);
 /* Stops the loop after the admitted requests finish and frees the server's buffers. */

@@ -32,12 +32,14 @@ using Clock = std::chrono::steady_clock;
 
 namespace {
 
-enum { kQueued = 0, kPrep = 1, kReady = 2, kFinishing = 3, kDone = 4, kFailed = 5 };
+// kFailing: every point was handed out but the image can never be produced (a shading or
+// read-back error); the loop retires it as failed.
+enum { kQueued = 0, kPrep = 1, kReady = 2, kFinishing = 3, kDone = 4, kFailed = 5, kFailing = 6 };
 
 struct Req {
     uint64_t id = 0;
     nis_request r{};
-    int state = kQueued;
+    std::atomic<int> state{kQueued};   // written by the server thread, read by waiters
     Clock::time_point t_submit, t_done;
     nis_volume vol = 0;
     nis_light light = 0;
@@ -373,14 +375,17 @@ void loop(nis_server *S) {
             if (q->state == kPrep && cudaEventQuery(q->ev_prep) == cudaSuccess) {
                 q->n_points = *q->h_count;
                 q->state = kReady;
-                if (q->n_points == 0 && schedule_output(S, q) != NIS_OK) q->err = NIS_ERR_CUDA;
+                if (q->n_points == 0 && schedule_output(S, q) != NIS_OK) {
+                    q->err = NIS_ERR_CUDA;
+                    q->state = kFailing;
+                }
                 worked = true;
             }
         // 3. one mixed batch at a time (the host prepares the next while it runs)
         if (S->batch_in_flight && cudaEventQuery(S->ev_batch) == cudaSuccess) S->batch_in_flight = false;
         if (!S->batch_in_flight) {
             std::vector<nis_segment> segs;
-            std::vector<Req *> last;
+            std::vector<Req *> last, in_batch;
             int room = S->cfg.max_batch_points;
             for (Req *q : S->active) {
                 if (room <= 0) break;
@@ -393,6 +398,7 @@ void loop(nis_server *S) {
                 sg.n = take;
                 sg.d_rgb_out = q->rgb + 3 * (size_t)q->shaded;
                 segs.push_back(sg);
+                in_batch.push_back(q);
                 q->shaded += take;
                 room -= take;
                 if (q->shaded == q->n_points) last.push_back(q);
@@ -400,15 +406,18 @@ void loop(nis_server *S) {
             if (!segs.empty()) {
                 nis_status rc = nis_shade_segments(S->ctx, S->w, segs.data(), (int)segs.size(),
                                                    reinterpret_cast<nis_stream>(S->shade));
-                for (Req *q : last)
-                    if (!rc) rc = schedule_output(S, q);
+                if (rc)                           // every request of the batch has lost points
+                    for (Req *q : in_batch) q->err = rc;
+                for (Req *q : last) {
+                    const nis_status ro = rc ? rc : schedule_output(S, q);
+                    if (ro) { q->err = ro; q->state = kFailing; }
+                }
                 cudaEventRecord(S->ev_batch, S->shade);
                 S->batch_in_flight = true;
                 ++S->batches;
                 S->batch_points_sum += S->cfg.max_batch_points - room;
                 S->batch_reqs_sum += segs.size();
                 S->points += S->cfg.max_batch_points - room;
-                if (rc) for (Req *q : last) q->err = rc;
                 worked = true;
             }
         }
@@ -421,6 +430,16 @@ void loop(nis_server *S) {
                 free_request(S, q);
                 { std::lock_guard<std::mutex> lk(S->mu); S->active.erase(S->active.begin() + i); }
                 finish(S, q, err ? kFailed : kDone, err);
+                worked = true;
+            } else if (q->state == kFailing) {
+                // its buffers are freed in stream order after the batch that used them; a
+                // read-back that may have been issued is waited for before its staging goes
+                cudaStreamSynchronize(S->shade);
+                cudaGetLastError();
+                const nis_status err = q->err ? q->err : NIS_ERR_CUDA;
+                free_request(S, q);
+                { std::lock_guard<std::mutex> lk(S->mu); S->active.erase(S->active.begin() + i); }
+                finish(S, q, kFailed, err);
                 worked = true;
             } else {
                 ++i;
