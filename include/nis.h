@@ -323,7 +323,9 @@ typedef struct nis_server_stats {
 
 nis_status nis_server_create(nis_ctx *ctx, nis_weights w, const nis_server_config *cfg,
                              nis_server **out);
-/* Queues a request (copies the struct; the buffers it points to stay the caller's). */
+/* Queues a request (copies the struct; the buffers it points to stay the caller's).
+ * NIS_ERR_INVALID_ARG, and nothing queued, for a malformed request: NULL buffers, grid
+ * size outside 1..2048, dtype, image size, or a material nis_shade_points would refuse. */
 nis_status nis_server_submit(nis_server *srv, const nis_request *req, uint64_t *id);
 /* Waits up to timeout_ms (<= 0: no limit) for request `id`; NIS_ERR_TIMEOUT if not done.
  * latency_ms (may be NULL) receives submit-to-completion time.  A request that failed

@@ -609,24 +609,8 @@ nis_status ensure_workspace_fp8(nis_ctx *ctx, int cap, cudaStream_t s) {
 }
 
 nis_status check_material(nis_ctx *ctx, const nis_material *m) {
-    if (!m) return fail(ctx, NIS_ERR_INVALID_ARG, "material is NULL");
-    if (!(m->g > -1.f && m->g < 1.f)) return fail(ctx, NIS_ERR_INVALID_ARG, "g must lie in (-1, 1)");
-    if (m->n_lobes < 0 || m->n_lobes > 3)
-        return fail(ctx, NIS_ERR_INVALID_ARG, "n_lobes must be 0..3");
-    if (m->n_lobes >= 2) {
-        float sum = 0.f;
-        for (int i = 0; i < m->n_lobes; ++i) {
-            if (!(m->lobe_g[i] > -1.f && m->lobe_g[i] < 1.f) || !(m->lobe_w[i] >= 0.f))
-                return fail(ctx, NIS_ERR_INVALID_ARG, "lobe g must lie in (-1, 1), weights >= 0");
-            sum += m->lobe_w[i];
-        }
-        if (std::fabs(sum - 1.f) > 1e-4f)
-            return fail(ctx, NIS_ERR_INVALID_ARG, "lobe weights must sum to 1");
-    }
-    for (int c = 0; c < 3; ++c)
-        if (!(m->albedo[c] > 0.f && m->albedo[c] <= 1.f) || !std::isfinite(m->intensity[c]))
-            return fail(ctx, NIS_ERR_INVALID_ARG, "albedo must lie in (0, 1], intensity finite");
-    return NIS_OK;
+    const char *why = material_problem(m);
+    return why ? fail(ctx, NIS_ERR_INVALID_ARG, why) : NIS_OK;
 }
 
 struct Mixed {                        // per-point request descriptors of a mixed batch
@@ -1289,6 +1273,25 @@ struct DeviceGuard {
 }  // namespace
 
 namespace nis {
+
+const char *material_problem(const nis_material *m) {
+    if (!m) return "material is NULL";
+    if (!(m->g > -1.f && m->g < 1.f)) return "g must lie in (-1, 1)";
+    if (m->n_lobes < 0 || m->n_lobes > 3) return "n_lobes must be 0..3";
+    if (m->n_lobes >= 2) {
+        float sum = 0.f;
+        for (int i = 0; i < m->n_lobes; ++i) {
+            if (!(m->lobe_g[i] > -1.f && m->lobe_g[i] < 1.f) || !(m->lobe_w[i] >= 0.f))
+                return "lobe g must lie in (-1, 1), weights >= 0";
+            sum += m->lobe_w[i];
+        }
+        if (std::fabs(sum - 1.f) > 1e-4f) return "lobe weights must sum to 1";
+    }
+    for (int c = 0; c < 3; ++c)
+        if (!(m->albedo[c] > 0.f && m->albedo[c] <= 1.f) || !std::isfinite(m->intensity[c]))
+            return "albedo must lie in (0, 1], intensity finite";
+    return nullptr;
+}
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 namespace {

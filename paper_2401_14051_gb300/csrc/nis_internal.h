@@ -473,6 +473,8 @@ struct ResolvedInputs {
 nis_status resolve_built_inputs(nis_ctx *ctx, nis_volume vol, nis_light light, nis_weights w,
                                 const nis_material *m, ResolvedInputs *out);
 nis_status record_error(nis_ctx *ctx, nis_status s, const char *msg);
+// Why a material cannot be shaded (its phase function, albedo or intensity), or nullptr.
+const char *material_problem(const nis_material *m);
 int ctx_device(const nis_ctx *ctx);
 // First hits of a camera, compacted: points, omegas and pixel indices of the hits, and their
 // number in *d_count (device).  Buffers hold width * height entries.

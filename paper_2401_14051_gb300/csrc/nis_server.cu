@@ -488,7 +488,8 @@ nis_status nis_server_submit(nis_server *S, const nis_request *r, uint64_t *id) 
     if (!S || !r || !id) return NIS_ERR_INVALID_ARG;
     if (!r->density || !r->rgb_out || r->n < 1 || r->n > 2048 ||
         (r->dtype != NIS_DTYPE_F32 && r->dtype != NIS_DTYPE_F16) || r->camera.width < 1 ||
-        r->camera.height < 1 || (long long)r->camera.width * r->camera.height > (1LL << 26))
+        r->camera.height < 1 || (long long)r->camera.width * r->camera.height > (1LL << 26) ||
+        material_problem(&r->material))          // refused here, not in a shared batch
         return NIS_ERR_INVALID_ARG;
     Req *q = new Req();
     q->r = *r;
