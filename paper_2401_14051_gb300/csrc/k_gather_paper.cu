@@ -103,8 +103,7 @@ __global__ void __launch_bounds__(288, 4) gather_paper_kernel(const __grid_const
     const float wa = tt - ja;
     const int N = a.rho.n[0], L = a.rho.levels;
     if (t < kPaperPts) {
-        int k = 0;
-        while (k + 1 < kLayers && t >= paper_first(k + 1)) ++k;
+        const int k = paper_layer_of(t);
         const float ux = a.unit[t][0], uy = a.unit[t][1], uz = a.unit[t][2];
         float cx = px, cy = py, cz = pz, radius;
         int m;

@@ -44,13 +44,39 @@ __host__ __device__ constexpr int paper_count(int k) {
     return k == 0 ? 6 : k == 1 ? 8 : k == 2 ? 12 : k == 3 ? 16 : k == 4 ? 24 : k == 5 ? 32
          : k == 6 ? 48 : k == 7 ? 48 : k == 8 ? 32 : k == 9 ? 16 : k == 10 ? 16 : 8;
 }
-__host__ __device__ constexpr int paper_first(int k) { return k == 0 ? 0 : paper_first(k - 1) + paper_count(k - 1); }
-static_assert(paper_first(kLayers) == kPaperPts, "paper template size");
+// First point of layer k (0..12) in template order.  Closed forms rather than recursion:
+// device code calls a recursive function through a stack frame at every use.
+__host__ __device__ constexpr int paper_first(int k) {
+    return k <= 0 ? 0 : k == 1 ? 6 : k == 2 ? 14 : k == 3 ? 26 : k == 4 ? 42 : k == 5 ? 66
+         : k == 6 ? 98 : k == 7 ? 146 : k == 8 ? 194 : k == 9 ? 226 : k == 10 ? 242
+         : k == 11 ? 258 : 266;
+}
+// The layer of template point t (0..265): the k with paper_first(k) <= t < paper_first(k + 1).
+__host__ __device__ constexpr int paper_layer_of(int t) {
+    return (t >= 6) + (t >= 14) + (t >= 26) + (t >= 42) + (t >= 66) + (t >= 98) + (t >= 146) +
+           (t >= 194) + (t >= 226) + (t >= 242) + (t >= 258);
+}
 // tensor-core operand layout of the paper model's features: each layer's columns padded to a
 // multiple of 8 (16-byte TMA coordinates), 272 in all, then a zero tail as wide as the
 // widest operand box (64 columns: a layer's box reaches past its end into zero weights)
 __host__ __device__ constexpr int paper_count_pad(int k) { return (paper_count(k) + 7) & ~7; }
-__host__ __device__ constexpr int paper_first_pad(int k) { return k == 0 ? 0 : paper_first_pad(k - 1) + paper_count_pad(k - 1); }
+__host__ __device__ constexpr int paper_first_pad(int k) {
+    return k <= 0 ? 0 : k == 1 ? 8 : k == 2 ? 16 : k == 3 ? 32 : k == 4 ? 48 : k == 5 ? 72
+         : k == 6 ? 104 : k == 7 ? 152 : k == 8 ? 200 : k == 9 ? 232 : k == 10 ? 248
+         : k == 11 ? 264 : 272;
+}
+constexpr bool paper_layout_consistent() {
+    if (paper_first(0) != 0 || paper_first_pad(0) != 0) return false;
+    for (int k = 0; k < kLayers; ++k) {
+        if (paper_first(k + 1) != paper_first(k) + paper_count(k)) return false;
+        if (paper_first_pad(k + 1) != paper_first_pad(k) + paper_count_pad(k)) return false;
+        for (int t = paper_first(k); t < paper_first(k + 1); ++t)
+            if (paper_layer_of(t) != k) return false;
+    }
+    return true;
+}
+static_assert(paper_layout_consistent(), "paper template offsets are the counts' prefix sums");
+static_assert(paper_first(kLayers) == kPaperPts, "paper template size");
 constexpr int kPaperPad = paper_first_pad(kLayers);           // 272
 constexpr int kPaperPadTail = kPaperPad + 64;
 
