@@ -49,7 +49,7 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
 __global__ void __launch_bounds__(kThreadsTC, 2)
     cnn_tc_kernel(const float *__restrict__ H_T, int count, const float *__restrict__ wbase,
                   const __grid_constant__ WeightOffsets o, float *__restrict__ X_T,
-                  __nv_bfloat16 *__restrict__ X_T_bf, uint8_t *__restrict__ X_T_f8, unsigned *err) {
+                  __nv_bfloat16 *__restrict__ X_T_bf, uint8_t *__restrict__ X_T_f8, unsigned *err, int xt_ld) {
     extern __shared__ __align__(1024) uint8_t sm[];
     const int k = blockIdx.y;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2)
                     uint32_t pk[8];
 #pragma unroll
                     for (int j = 0; j < 8; ++j) pk[j] = pack_bf16x2(z[2 * j], z[2 * j + 1]);
-                    uint4 *dst = reinterpret_cast<uint4 *>(X_T_bf + off);
+                    uint4 *dst = reinterpret_cast<uint4 *>(X_T_bf + ((size_t)(p0 + p) * kLayers + k) * xt_ld + w * 16);
                     dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                     dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
                 }
@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2)
 
 void launch_cnn_tc(const float *H_T, int count, const float *wbase, const WeightOffsets &o,
                    float *X_T, __nv_bfloat16 *X_T_bf, uint8_t *X_T_f8, unsigned *err, int num_sms,
-                   cudaStream_t s) {
+                   cudaStream_t s, int xt_ld) {
     if (count <= 0) return;
     static bool attr_set = false;
     if (!attr_set) {
@@ -272,7 +272,7 @@ void launch_cnn_tc(const float *H_T, int count, const float *wbase, const Weight
     if (per_layer > n_groups) per_layer = n_groups;
     note_launch();
     cnn_tc_kernel<<<dim3(per_layer, kLayers), kThreadsTC, kSmemTC, s>>>(H_T, count, wbase, o, X_T,
-                                                                        X_T_bf, X_T_f8, err);
+                                                                        X_T_bf, X_T_f8, err, xt_ld);
 }
 
 }  // namespace nis

@@ -87,7 +87,9 @@ __global__ void __launch_bounds__(kLayers * 32, kF8 ? 2 : 3) gather_kernel(const
     const float *row0 = table + ((size_t)ja * kPhaseSets + set) * kLat;
     const float *row1 = row0 + kPhaseSets * kLat;
     const size_t obase = ((size_t)p * kLayers + k) * kLat;
-    const size_t obase_b = ((size_t)p * kLayers + k) * kLatPad;
+    // BF16 rows per layer: kLatPad, or kFuseLatLd with the fused backbone's configuration
+    // operand after the features
+    const size_t obase_b = ((size_t)p * kLayers + k) * (a.fused ? kFuseLatLd : kLatPad);
 
     float s0 = 0.f, s1 = 0.f, s2 = 0.f;
     float m0 = -3.0e38f, m1 = -3.0e38f, m2 = -3.0e38f;
@@ -132,7 +134,7 @@ __global__ void __launch_bounds__(kLayers * 32, kF8 ? 2 : 3) gather_kernel(const
                 keep_rho[i] = rho;
                 keep_f[i] = f;
             }
-        } else if (a.Hb_rho && t < kLatPad) {     // zero the BF16 row padding
+        } else if (a.Hb_rho && t < kLatPad && !a.fused) {     // zero the BF16 row padding
             for (int q = 0; q < (a.split ? 3 : 1); ++q) {
                 a.Hb_rho[obase_b + t + q * a.part] = __float2bfloat16_rn(0.f);
                 a.Hb_f[obase_b + t + q * a.part] = __float2bfloat16_rn(0.f);
@@ -178,13 +180,39 @@ __global__ void __launch_bounds__(kLayers * 32, kF8 ? 2 : 3) gather_kernel(const
             for (int q = 0; q < 8; ++q) acc += w1[r * 8 + q] * v[q];
             z[r] = fmaxf(acc, 0.f);
         }
-        for (int r = 0; r < 3; ++r)
-            a.w_se[((size_t)p * kLayers + k) * 3 + r] =
-                sigmoidf_(b2[r] + w2[r * 2] * z[0] + w2[r * 2 + 1] * z[1]);
+        float wse[3];
+        for (int r = 0; r < 3; ++r) {
+            wse[r] = sigmoidf_(b2[r] + w2[r * 2] * z[0] + w2[r * 2 + 1] * z[1]);
+            a.w_se[((size_t)p * kLayers + k) * 3 + r] = wse[r];
+        }
+        const float *alb = d ? d->albedo : a.albedo;
         if (k == 0) {
             float *c = a.cfg + (size_t)p * kCfg;
-            const float *alb = d ? d->albedo : a.albedo;
             c[0] = gg; c[1] = alb[0]; c[2] = alb[1]; c[3] = alb[2]; c[4] = alpha;
+        }
+        if (a.fused) {
+            // the fused backbone's configuration operand of this layer, per type: c / w and
+            // 1 / w as two BF16 parts each (hi, lo), then zeros to the end of the row; rho and
+            // f in their feature rows after the 225 features, T ahead of the CNN's 80 outputs
+            const float c5[5] = {gg, alb[0], alb[1], alb[2], alpha};
+            for (int r = 0; r < 3; ++r) {
+                const float u = 1.0f / fmaxf(wse[r], kSeFloor);
+                float row[16];
+                for (int q = 0; q < 5; ++q) {
+                    const float x = c5[q] * u;
+                    const float hi = __bfloat162float(__float2bfloat16_rn(x));
+                    row[q] = hi;
+                    row[5 + q] = x - hi;
+                }
+                const float uh = __bfloat162float(__float2bfloat16_rn(u));
+                row[10] = uh; row[11] = uh; row[12] = u - uh;
+                row[13] = row[14] = row[15] = 0.f;
+                __nv_bfloat16 *dst = r == 0 ? a.Hb_rho + obase_b + kLat
+                                   : r == 1 ? a.Hb_f + obase_b + kLat
+                                            : a.XT_cfg + ((size_t)p * kLayers + k) * kFuseXtLd + kDT;
+                const int n = r == 2 ? kFuseXtLd - kDT : kFuseLatLd - kLat;
+                for (int q = 0; q < n; ++q) dst[q] = __float2bfloat16_rn(row[q]);
+            }
         }
     }
 }

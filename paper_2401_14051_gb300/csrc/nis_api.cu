@@ -62,6 +62,11 @@ struct Weights {
     uint8_t *f8 = nullptr;
     float *f8_scales = nullptr;
     const float *sc_fc1[3][kLayers] = {}, *sc_fc2[3][kLayers] = {}, *sc_mrg[3] = {}, *sc_head[3] = {};
+    // BF16: the fused backbone's op program and pre-swizzled weight slabs
+    uint8_t *fused_w = nullptr;
+    FusedOp *fused_ops = nullptr;
+    FusedPackOp *fused_pack = nullptr;
+    int fused_n_ops = 0;
 };
 
 struct WorkspaceF8 {                  // scratch of the FP8 path, grow-only
@@ -85,6 +90,10 @@ struct WorkspaceBf {                  // scratch of the tensor-core paths, grow-
     // epilogue output maps (TMA stores): e, h (FP32 with the split), s, the chain ends
     // (per type and chain), the merges (per type) and the head activations
     CUtensorMap out_e, out_h, out_s, out_mrg[3][2], out_head[3], out_z1, out_z2;
+    // BF16 fused backbone: chain ends and merge outputs, and the operand maps of its sources
+    // (the features in Hb_rho, Hb_f and XTb with rows of kFuseLatLd / kFuseXtLd per layer)
+    __nv_bfloat16 *mrg_f = nullptr, *head_f = nullptr;
+    FusedMaps fmaps{};
 };
 
 struct Workspace {                    // scratch of nis_shade_points, grow-only
@@ -430,13 +439,16 @@ nis_status ensure_workspace_tc(nis_ctx *ctx, WorkspaceBf &w, int parts, int cap,
     for (auto **b : bb) { dev_free(ctx, *b); *b = nullptr; }
     float **ff[] = {&w.H_T, &w.w_se, &w.cfg, &w.v, &w.E32, &w.H32};
     for (float **f : ff) { dev_free(ctx, *f); *f = nullptr; }
+    for (auto **b : {&w.mrg_f, &w.head_f}) { dev_free(ctx, *b); *b = nullptr; }
     w.cap = 0;
     w.parts = parts;
     const size_t n = (size_t)cap, P = (size_t)parts;
     nis_status st;
-    if ((st = dev_alloc_t(ctx, P * n * kLayers * kLatPad, &w.Hb_rho, s))) return st;
-    if ((st = dev_alloc_t(ctx, P * n * kLayers * kLatPad, &w.Hb_f, s))) return st;
-    if ((st = dev_alloc_t(ctx, P * n * kLayers * kDT, &w.XTb, s))) return st;
+    // BF16 (one part): rows wide enough for the fused backbone's layout as well
+    const size_t lat_ld = parts == 1 ? kFuseLatLd : kLatPad, xt_ld = parts == 1 ? kFuseXtLd : kDT;
+    if ((st = dev_alloc_t(ctx, P * n * kLayers * lat_ld, &w.Hb_rho, s))) return st;
+    if ((st = dev_alloc_t(ctx, P * n * kLayers * lat_ld, &w.Hb_f, s))) return st;
+    if ((st = dev_alloc_t(ctx, P * n * kLayers * xt_ld, &w.XTb, s))) return st;
     for (auto **b : {&w.S, &w.Z1, &w.Z2})
         if ((st = dev_alloc_t(ctx, P * n * kWidth, b, s))) return st;
     if (parts == 1) {
@@ -478,6 +490,19 @@ nis_status ensure_workspace_tc(nis_ctx *ctx, WorkspaceBf &w, int parts, int cap,
                                      2 * kWidth * 2, n * 2 * kWidth * 2);
         ok = ok && make_tmap_out(&w.out_head[t], w.head_in + t * kWidth, false, kWidth, n, parts,
                                  3 * kWidth * 2, n * 3 * kWidth * 2);
+    }
+    if (parts == 1) {
+        // the fused backbone's operand sources: 64-column boxes of 128 rows (128-byte swizzle)
+        if ((st = dev_alloc_t(ctx, n * 3 * kFuseMrgLd, &w.mrg_f, s))) return st;
+        if ((st = dev_alloc_t(ctx, n * kFuseHeadLd, &w.head_f, s))) return st;
+        struct Src { int id; const void *base; uint64_t cols; };
+        const Src srcs[] = {{kSrcRho, w.Hb_rho, kLayers * kFuseLatLd},
+                            {kSrcF, w.Hb_f, kLayers * kFuseLatLd},
+                            {kSrcT, w.XTb, kLayers * kFuseXtLd},
+                            {kSrcMrg, w.mrg_f, 3 * kFuseMrgLd},
+                            {kSrcHead, w.head_f, kFuseHeadLd}};
+        w.fmaps = FusedMaps{};
+        for (const Src &q : srcs) ok = ok && make_tmap_bf16(&w.fmaps.m64[q.id], q.base, q.cols, n, q.cols * 2, 64, 128);
     }
     if (!ok) return fail(ctx, NIS_ERR_CUDA, "cuTensorMapEncodeTiled failed for the tensor-core workspace");
     w.cap = cap;
@@ -521,6 +546,27 @@ nis_status pack_weights_tc(nis_ctx *ctx, Weights &w, int parts, cudaStream_t s) 
                             (uint32_t)np))
             return fail(ctx, NIS_ERR_CUDA, "cuTensorMapEncodeTiled failed for a weight matrix");
         off += (size_t)parts * np * kp;
+    }
+    if (parts == 1 && o.model == kModelLattice) {
+        // the fused backbone: its op program and weight slabs
+        FusedOp ops[kFuseMaxOps];
+        FusedPackOp pk[kFuseMaxOps];
+        int n_ops = 0;
+        size_t bytes = 0;
+        fused_program(o, w.f32, ops, pk, &n_ops, &bytes);
+        if ((st = dev_alloc_t(ctx, bytes, &w.fused_w, s))) return st;
+        if ((st = dev_alloc_t(ctx, (size_t)n_ops, &w.fused_ops, s))) return st;
+        if ((st = dev_alloc_t(ctx, (size_t)n_ops, &w.fused_pack, s))) return st;
+        NIS_CUDA(cudaMemcpyAsync(w.fused_ops, ops, n_ops * sizeof(FusedOp), cudaMemcpyHostToDevice, s));
+        NIS_CUDA(cudaMemcpyAsync(w.fused_pack, pk, n_ops * sizeof(FusedPackOp), cudaMemcpyHostToDevice, s));
+        {
+            ProfScope ps(ctx, "other", s);
+            launch_fused_pack(w.fused_pack, n_ops, w.fused_w, s);
+        }
+
+        // the host arrays above are read by the copies before this returns
+        NIS_CUDA(cudaStreamSynchronize(s));
+        w.fused_n_ops = n_ops;
     }
     NIS_CUDA(cudaGetLastError());
     return NIS_OK;
@@ -923,6 +969,8 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
         launch_tc_gemm(a, ma, mb, ctx->num_sms, s, o1, o2, pre);
     };
     const int k_e = split ? kOutF32 : kOutBf16;     // kind of e and h
+    // BF16 lattice model: the whole network after the features in one fused kernel
+    const bool fused = !split && !paper && wt.fused_n_ops > 0;
     for (int off = 0; off < n; off += chunk) {
         int cnt = n - off < chunk ? n - off : chunk;
         GatherArgs ga{};
@@ -948,6 +996,7 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
             ga.H_f = dbg->H_f + (size_t)off * kLayers * kLat;
         }
         ga.v = dbg ? w.v : nullptr; ga.w_se = w.w_se; ga.cfg = w.cfg;
+        if (fused) { ga.fused = 1; ga.XT_cfg = w.XTb; }
         if (mx) { ga.descs = mx->descs; ga.req_of_point = mx->req_of_point + off; }
         if (paper) {
             // the paper model: its gathers write the operands of all three types (the
@@ -975,9 +1024,21 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
             if (split)      // FP32: the FP32 CNN, its output split into three BF16 parts
                 launch_cnn_f32(w.H_T, cnt, W, o, xt_dbg, w.XTb, s, cap * kLayers * kDT);
             else            // BF16: the CNN with BF16 operands on the tensor cores
-                launch_cnn_tc(w.H_T, cnt, W, o, xt_dbg, w.XTb, nullptr, ctx->d_err, ctx->num_sms, s);
+                launch_cnn_tc(w.H_T, cnt, W, o, xt_dbg, w.XTb, nullptr, ctx->d_err, ctx->num_sms, s,
+                              fused ? kFuseXtLd : kDT);
         }
-        {
+        if (fused) {
+            ProfScope pm(ctx, "mlp", s);
+            FusedArgs fa{};
+            fa.M = cnt; fa.n_ops = wt.fused_n_ops; fa.ops = wt.fused_ops; fa.wpack = wt.fused_w;
+            fa.w_se = w.w_se; fa.mrg = w.mrg_f; fa.head = w.head_f;
+            fa.rgb = rgb + 3 * (size_t)off;
+            fa.y_out = (dbg && dbg->y) ? dbg->y + 3 * (size_t)off : nullptr;
+            fa.dec_rows = mx ? mx->dec_rows + 3 * (size_t)off : nullptr;
+            for (int c = 0; c < 3; ++c) fa.dec_scale[c] = dec_scale[c];
+            fa.err = ctx->d_err;
+            launch_mlp_fused(fa, w.fmaps, ctx->num_sms, s);
+        } else {
             ProfScope pm(ctx, "mlp", s);   // the pass's dense layers as one timed block
             for (int t = 0; t < 3; ++t) {
                 const CUtensorMap &fmap = t == 0 ? w.map_rho : (t == 1 ? w.map_f : w.map_xt);
@@ -1779,6 +1840,9 @@ nis_status nis_load_weights(nis_ctx *ctx, const void *blob, size_t bytes, int pr
         dev_free(ctx, w.bf);
         dev_free(ctx, w.f8);
         dev_free(ctx, w.f8_scales);
+        dev_free(ctx, w.fused_w);
+        dev_free(ctx, w.fused_ops);
+        dev_free(ctx, w.fused_pack);
         return st;
     }
     nis_handle h = ctx->next++;
@@ -1938,6 +2002,9 @@ nis_status nis_release(nis_ctx *ctx, nis_handle h) {
         dev_free(ctx, w->bf);
         dev_free(ctx, w->f8);
         dev_free(ctx, w->f8_scales);
+        dev_free(ctx, w->fused_w);
+        dev_free(ctx, w->fused_ops);
+        dev_free(ctx, w->fused_pack);
         ctx->weights.erase(h);
         return NIS_OK;
     }

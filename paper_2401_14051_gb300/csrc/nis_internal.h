@@ -322,6 +322,11 @@ struct GatherArgs {
     float *v;                        // [count][12][8] (may be null)
     float *w_se;                     // [count][12][3]
     float *cfg;                      // [count][5]
+    // fused backbone (BF16): Hb_* rows of kFuseLatLd per layer with the configuration
+    // operand in columns 225..237, and the same operand of type T in XT_cfg (rows of
+    // kFuseXtLd per layer, columns 80..92) ahead of the CNN's outputs
+    int fused;
+    __nv_bfloat16 *XT_cfg;
 };
 void launch_gather(const GatherArgs &a, cudaStream_t s);
 
@@ -366,7 +371,7 @@ void launch_cnn_f32(const float *H_T, int count, const float *wbase, const Weigh
 // (FP32, optional), X_T_bf (BF16, optional), X_T_f8 (e4m3, optional), [count][12][80].
 void launch_cnn_tc(const float *H_T, int count, const float *wbase, const WeightOffsets &o,
                    float *X_T, __nv_bfloat16 *X_T_bf, uint8_t *X_T_f8, unsigned *err, int num_sms,
-                   cudaStream_t s);
+                   cudaStream_t s, int xt_ld = kDT);   // xt_ld: X_T_bf row per layer
 // FP8 weights: scale[n] = max_k |W[n][k]| / 448 (1 for empty rows), dst = e4m3(W / scale)
 void launch_pack_fp8(const float *src, int N, int K, int ld_src, uint8_t *dst, float *scale,
                      int Np, int Kp, cudaStream_t s);
@@ -483,6 +488,72 @@ bool make_tmap_bf16(CUtensorMap *map, const void *base, uint64_t inner, uint64_t
 // swizzle) or BF16 (64-byte swizzle), box 32 columns x 32 rows x all parts.
 bool make_tmap_out(CUtensorMap *map, const void *base, bool f32, uint64_t cols, uint64_t rows,
                    uint32_t parts, uint64_t row_bytes, uint64_t part_bytes);
+
+// ---- fused backbone (k_mlp_fused.cu) --------------------------------------------------------
+// The whole network after the features (Sec. III.C.2, Fig. 6: per type and template the
+// chains of FC-1 / FC-2 blocks, the merge of each type, the head, the decode of Eq. 21) in one
+// persistent tcgen05 kernel over 128-point tiles, BF16 operands and FP32 accumulation.  A
+// program of ops runs per tile; the running state e / h stays on chip in FP32, the chain
+// ends and merge outputs make one trip through global memory (BF16) for the next op's
+// operand.  Biases ride in the operands: FC-1's bias and configuration part (W_c c + b) come
+// from 13 columns after each layer's features holding c / w_se and 1 / w_se per (point,
+// layer, type), so that e = w_se * ReLU(acc); the other layers read two columns of ones
+// against the bias's two BF16 parts.
+constexpr int kFuseFc1 = 0, kFuseFc2 = 1, kFuseMerge = 2, kFuseHead1 = 3, kFuseHead2 = 4, kFuseHead3 = 5;
+// operand sources read by TMA (the features rho, f, T; the chain ends; the merge outputs) and
+// the on-chip s buffer (FC-2 and the head's second and third layers)
+constexpr int kSrcRho = 0, kSrcF = 1, kSrcT = 2, kSrcMrg = 3, kSrcHead = 4, kSrcS = 5;
+constexpr int kFuseSrcs = 5;
+constexpr int kFuseLatLd = 240;              // BF16 rho / f row per layer: 225 + 13 + 2 zeros
+constexpr int kFuseXtLd = 96;                // BF16 T row per layer: 80 + 13 + 3 zeros
+constexpr int kFuseCfgCols = 13;             // [c/w hi (5), c/w lo (5), 1/w hi, 1/w hi, 1/w lo]
+constexpr int kFuseMrgLd = 416;              // chain-end row per type: 2 x 200, then [1, 1, 0...]
+constexpr int kFuseHeadLd = 608;             // merge outputs: 3 x 200, then [1, 1, 0...]
+constexpr int kFuseMaxOps = 96;
+struct FusedOp {
+    uint8_t kind, src, type, layer;
+    uint8_t chain, flags;                    // flags: 1 first layer of its chain, 2 last, 4 on
+                                             // accumulator Y, 8 merge operand complete,
+                                             // 16 head operand complete
+    uint16_t a_col0, n_mma, k;               // operand column; 208 or 16 outputs; K (x16)
+    uint32_t b_off;                          // byte offset of the op's weight blocks
+};
+static_assert(sizeof(FusedOp) == 16, "FusedOp layout");
+// Per op, how its weight blocks are made from the FP32 weights (host -> pack kernel).
+struct FusedPackOp {
+    const float *W; int ld;                  // weight rows [n_out][ld]
+    int n_out, k_main;                       // outputs; input columns of the main operand
+    const float *bias;                       // [n_out]
+    int bias_main;                           // bias in columns k_main, k_main + 1
+    int cfg;                                 // FC-1: W_c (the ld - k_main columns after the
+                                             // features) and the bias in columns k_main..+12
+    int k, n_mma, s_tail;                    // K; outputs; last block 16 wide (s buffer tail)
+    uint32_t b_off;
+};
+struct FusedMaps {                           // per TMA source: 64-column boxes of 128 rows,
+    CUtensorMap m64[kFuseSrcs];              // 128-byte swizzle
+};
+struct FusedArgs {
+    int M, n_ops;
+    const FusedOp *ops;                      // device, n_ops <= kFuseMaxOps
+    const uint8_t *wpack;                    // weight blocks, pre-swizzled
+    const float *w_se;                       // [M][12][3]
+    __nv_bfloat16 *mrg;                      // [rows][3][kFuseMrgLd]
+    __nv_bfloat16 *head;                     // [rows][kFuseHeadLd]
+    float *rgb;                              // [M][3]
+    float *y_out;                            // optional [M][3] network output before decode
+    const float *dec_rows;                   // optional per-row decode scales [M][3]
+    float dec_scale[3];                      // I * albedo^4
+    unsigned *err;
+};
+// The op program and the pack list of a weight set (lattice model: feature columns
+// k * kFuseLatLd for rho and f, k * kFuseXtLd for T).
+void fused_program(const WeightOffsets &o, const float *W, FusedOp *ops, FusedPackOp *pack,
+                   int *n_ops, size_t *bytes);
+void launch_fused_pack(const FusedPackOp *pack_dev, int n_ops, uint8_t *dst, cudaStream_t s);
+void launch_mlp_fused(const FusedArgs &a, const FusedMaps &maps, int num_sms, cudaStream_t s);
+// SE weights are floored at kSeFloor where the configuration operand divides by them.
+constexpr float kSeFloor = 1e-20f;
 
 // Device pointers of a resolved (volume, light, weights, phase table) set, for entry points
 // that must not build or allocate anything.  Fails with NIS_ERR_NOT_READY if the pyramid or
