@@ -45,6 +45,14 @@ MLP_FLOP_PER_POINT = 2 * (24 * (230 * 200 + 200 * 200) + 12 * (85 * 200 + 200 * 
                           + 3 * 400 * 200 + 600 * 200 + 200 * 200 + 200 * 3)
 CNN_FLOP_PER_POINT = 2 * 12 * (63 * 16 * 27 + 5 * 16 * 16 * 27)
 GATHER_BYTES_PER_POINT = 4 * (3 * 12 * 225 + 12 * 8 + 12 * 3 + 5 + 6)
+# The gather's algorithmic bytes: the 5400 feature values a point needs (rho, phase and
+# transmittance at 12 x 225 template points; FP32) written once, plus the density pyramid
+# and the transmittance pyramid read once per frame (levels sum to ~8/7 of the finest).
+GATHER_FEATURE_BYTES = 4 * 5400
+
+
+def gather_algorithmic_bytes(n_points: int, n: int) -> float:
+    return GATHER_FEATURE_BYTES * n_points + 2 * (8.0 / 7.0) * n ** 3 * 4
 
 
 def mlp_bytes_per_point(op: int, st: int) -> int:
@@ -79,6 +87,9 @@ def parse():
     ap.add_argument("--no-shear-warp", action="store_true")
     ap.add_argument("--no-paper-model", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=256)
+    ap.add_argument("--no-plume-loop", action="store_true")
+    ap.add_argument("--plume-march-frames", type=int, default=8)
+    ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--ncu-case", choices=("f32", "bf16", "simt", "sweep"),
                     help="small case for ncu captures: shade 32,768 points of the 64^3 fBm "
                          "volume twice at this precision (sweep: one shear-warp "
@@ -259,6 +270,71 @@ def cpu_baseline(cfg, vol, weights, target_s: float = 12.0) -> dict:
             "seconds": round(secs, 2)}
 
 
+def oracle_single_thread(workload: int, n_pixels: int = 160) -> dict:
+    """The oracle on one host thread: a child process with every BLAS / OpenMP pool limited
+    to one thread runs one bounded sample of the frame."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               NUMEXPR_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", str(n_pixels),
+                            "--workload", str(workload)], env=env, capture_output=True, text=True,
+                           timeout=900)
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+    except (subprocess.SubprocessError, ValueError, IndexError) as e:
+        return {"value": None, "threads": 1, "error": str(e)[:200]}
+    return {"value": d["points"] / d["seconds"] if d["seconds"] > 0 else None, "unit": UNIT,
+            "threads": 1, "points": d["points"], "seconds": round(d["seconds"], 2),
+            "sample": f"{n_pixels} random pixels of the same frame"}
+
+
+def run_oracle_sample(args):
+    """Child of oracle_single_thread: one sample, printed as JSON."""
+    cfg = synth.config(args.workload)
+    vol = cfg["volume"]()
+    weights = synth.make_weights(cfg["weights_seed"], cfg["sigma_max"])
+    n, secs = oracle_sample(cfg, vol, weights, args.oracle_sample, seed=2000)
+    print(json.dumps({"points": n, "seconds": secs}), flush=True)
+
+
+def compact_summary(line: dict) -> dict:
+    """The line's figures in a few hundred bytes, placed last in the line (a log that keeps
+    only the end of the output still has them)."""
+    r = lambda x, n=3: None if x is None else round(float(x), n)
+    out = {"f32": {"frame_ms": r(line["frame_ms"]), "mpts_s": r(line["value"] / 1e6),
+                   "ms": line["step_breakdown_ms"],
+                   "mlp_tensor_frac": r(line["roofline"]["frac"]) if line["roofline"]["bound"] == "tensor" else None,
+                   "gather_hbm_frac": r(line["gather_roofline"]["frac"])},
+           "e2e_mpts_s": r(line["e2e"]["value"] / 1e6)}
+    for k in ("bf16", "fp8"):
+        b = line.get(k)
+        if b:
+            out[k] = {"frame_ms": r(b["frame_ms"]), "mpts_s": r(b["value"] / 1e6),
+                      "err_vs_f32": r(b["mean_rel_err_vs_fp32"], 5), "mlp_ms": b["step_breakdown_ms"]["mlp"],
+                      "mlp_tensor_frac": r(b["roofline"]["frac"])}
+    if line.get("paper_template_model"):
+        p = line["paper_template_model"]
+        out["paper_model_frame_ms"] = r(p.get("frame_ms"))
+    sw = line.get("shear_warp")
+    if sw:
+        out["shear_warp_frame_ms"] = r(sw.get("frame_ms"))
+    for k in ("serving", "serving_shear_warp"):
+        sv = line.get(k)
+        if sv:
+            out[k] = {"req_s": r(sv.get("throughput_req_s")), "p50_ms": r(sv.get("p50_ms"), 1),
+                      "p99_ms": r(sv.get("p99_ms"), 1), "batch_reqs": r(sv.get("mean_batch_requests"))}
+            if sv.get("load_sweep"):
+                out[k]["sweep"] = [[x["load"], x["throughput_req_s"], x["p50_ms"], x["p99_ms"],
+                                    x["mean_batch_requests"]] for x in sv["load_sweep"]]
+    pl = line.get("plume1024_60f")
+    if pl:
+        out["plume_60f"] = {m: [pl[m]["frames"], pl[m]["frame_ms_median"], pl[m]["frame_ms_p99"]]
+                            for m in ("shear_warp", "march") if m in pl}
+    cb = line.get("cpu_baseline")
+    if cb:
+        out["oracle_pts_s"] = [r(cb.get("value")), r((cb.get("single_thread") or {}).get("value"))]
+    return out
+
+
 def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
@@ -408,6 +484,58 @@ def plume_transmittance(nis, local: int) -> dict:
     return out
 
 
+def run_plume_loop(args, nis, local: int) -> dict:
+    """The 1024^3 FP16 plume (11 levels) rendered as an animation at 3840x2160 with the BF16
+    network: the light turns 6 degrees a frame and its transmittance is rebuilt every frame,
+    by shear-warp rays for 60 frames and by the exact march for the first
+    args.plume_march_frames (about 1.1 s per build: O(N^4)).  Each frame's transmittance
+    build and its shading (pairs, first hits, gathers, CNN, network, image) are timed with
+    CUDA events; the light of the previous frame is released before the next is built."""
+    import torch
+    cfg = synth.config(5)
+    dev = f"cuda:{local}"
+    vol = synth.plume_volume_torch(1024, 9, 128.0, device=dev)
+    ctx = nis.Context(local)
+    stream = torch.cuda.current_stream()
+    v = ctx.upload_volume(vol)
+    del vol
+    ctx.build_pyramid(v)
+    w = ctx.load_weights(synth.pack_weights(synth.make_weights(cfg["weights_seed"], cfg["sigma_max"])),
+                         nis.PREC_BF16)
+    mat, cam = cfg["material"], cfg["camera"]
+    ctx.build_phase_table(mat["g"])
+    img = torch.empty((cam["height"], cam["width"], 3), dtype=torch.float32, device=dev)
+    out = {"volume": "1024^3 float16 plume, 11 levels", "image": "3840x2160 perspective",
+           "precision": "bf16", "light": "turns 6 degrees per frame about +y"}
+    for name, method, frames in (("shear_warp", nis.TRANSMITTANCE_SHEAR_WARP, 60),
+                                 ("march", nis.TRANSMITTANCE_MARCH, args.plume_march_frames)):
+        if frames <= 0:
+            continue
+        lt = ctx.build_transmittance(v, synth.rotating_light(cfg["light"], -1), 0.6, method=method)
+        ctx.render_frame(v, lt, w, mat, cam, out=img)               # warm-up frame
+        ctx.sync(timeout_ms=600000)
+        ctx.release(lt)
+        build, shade = [], []
+        for f in range(frames):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(stream)
+            lt = ctx.build_transmittance(v, synth.rotating_light(cfg["light"], f), 0.6, method=method)
+            ev[1].record(stream)
+            ctx.render_frame(v, lt, w, mat, cam, out=img)
+            ev[2].record(stream)
+            ev[2].synchronize()
+            build.append(ev[0].elapsed_time(ev[1]))
+            shade.append(ev[1].elapsed_time(ev[2]))
+            ctx.release(lt)
+        frame = np.array(build) + np.array(shade)
+        out[name] = {"frames": frames, "frame_ms_median": round(float(np.median(frame)), 3),
+                     "frame_ms_p99": round(float(np.percentile(frame, 99)), 3),
+                     "build_ms_median": round(float(np.median(build)), 3),
+                     "shade_ms_median": round(float(np.median(shade)), 3)}
+    ctx.close()
+    return out
+
+
 def serving_volumes(args, local: int):
     import torch
     reqs = synth.serving_requests(args.serving_requests)
@@ -420,11 +548,12 @@ def serving_volumes(args, local: int):
     return reqs, pinned, time.perf_counter() - t0
 
 
-def run_serving(args, nis, blob, local: int, workload, method: int = 0) -> dict:
+def run_serving(args, nis, blob, local: int, workload, method: int = 0, sweep=()) -> dict:
     """256 Poisson-arriving render requests (grids 128^3-512^3 FP16, images 256^2 to 1080p,
     g and albedo per request) through the continuous-batching server under a 120 GB HBM
     budget, BF16 network.  The arrival rate targets ~70 % GPU load from a measured
-    back-to-back service time.  `method`: the server's transmittance method."""
+    back-to-back service time.  `method`: the server's transmittance method.  `sweep`: further
+    loads (fractions of the service rate) run on the first 128 requests."""
     reqs, pinned, gen_s = workload
     vols = [t.numpy() for t in pinned]
     ctx = nis.Context(local, torch_allocator=False)
@@ -440,40 +569,57 @@ def run_serving(args, nis, blob, local: int, workload, method: int = 0) -> dict:
         srv.wait(rid)
     service_s = (time.perf_counter() - t0) / 8
     srv.close()
-    rate = 0.7 / service_s
-    rng = np.random.default_rng(7)
-    gaps = rng.exponential(1.0 / rate, size=len(reqs))
-    srv = nis.Server(ctx, w, budget_bytes=budget, max_batch_points=65536, max_inflight=32,
-                     transmittance_method=method)
-    ids = []
-    start = time.perf_counter()
-    due = start
-    for i, r in enumerate(reqs):
-        due += gaps[i]
-        delay = due - time.perf_counter()
-        if delay > 0:
-            time.sleep(delay)
-        ids.append(srv.submit(vols[i], 1 + i, r["light"], 0.6, r["material"], r["camera"]))
-    for rid in ids:
-        srv.wait(rid)
-    st = srv.stats()
-    srv.close()
+
+    def arrivals(load: float, n: int) -> dict:
+        rate = load / service_s
+        rng = np.random.default_rng(7)
+        gaps = rng.exponential(1.0 / rate, size=n)
+        srv = nis.Server(ctx, w, budget_bytes=budget, max_batch_points=65536, max_inflight=32,
+                         transmittance_method=method)
+        ids = []
+        due = time.perf_counter()
+        for i, r in enumerate(reqs[:n]):
+            due += gaps[i]
+            delay = due - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            ids.append(srv.submit(vols[i], 1 + i, r["light"], 0.6, r["material"], r["camera"]))
+        for rid in ids:
+            srv.wait(rid)
+        st = srv.stats()
+        srv.close()
+        st["rate"] = rate
+        return st
+
+    st = arrivals(0.7, len(reqs))
+    out_sweep = []
+    for load in sweep:
+        s2 = arrivals(load, min(128, len(reqs)))
+        out_sweep.append({"load": load, "requests": s2["completed"] + s2["failed"],
+                          "arrival_req_s": round(s2["rate"], 2),
+                          "throughput_req_s": round(s2["completed"] / s2["span_seconds"], 2),
+                          "p50_ms": round(s2["p50_ms"], 1), "p99_ms": round(s2["p99_ms"], 1),
+                          "mean_batch_requests": round(s2["mean_batch_requests"], 3),
+                          "failed": s2["failed"]})
     ctx.close()
     pixels = sum(r["camera"]["width"] * r["camera"]["height"] for r in reqs)
-    return {"requests": len(reqs), "precision": "bf16", "hbm_budget_gb": 120,
-            "transmittance": "shear-warp" if method else "march",
-            "arrival": f"Poisson, {rate:.1f} req/s (0.7 / back-to-back service time "
-                       f"{1e3 * service_s:.1f} ms)",
-            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
-            "max_ms": st["max_ms"], "throughput_req_s": st["completed"] / st["span_seconds"],
-            "points_per_s": st["points_shaded"] / st["span_seconds"],
-            "pixels": pixels, "completed": st["completed"], "failed": st["failed"],
-            "mean_batch_points": st["mean_batch_points"],
-            "mean_batch_requests": st["mean_batch_requests"],
-            "cache": {"volume_hits": st["volume_hits"], "volume_misses": st["volume_misses"],
-                      "light_hits": st["light_hits"], "light_misses": st["light_misses"],
-                      "evictions": st["evictions"]},
-            "peak_gb": st["peak_bytes"] / 2 ** 30, "volume_generation_s": round(gen_s, 1)}
+    out = {"requests": len(reqs), "precision": "bf16", "hbm_budget_gb": 120,
+           "transmittance": "shear-warp" if method else "march",
+           "arrival": f"Poisson, {st['rate']:.1f} req/s (0.7 / back-to-back service time "
+                      f"{1e3 * service_s:.1f} ms)",
+           "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+           "max_ms": st["max_ms"], "throughput_req_s": st["completed"] / st["span_seconds"],
+           "points_per_s": st["points_shaded"] / st["span_seconds"],
+           "pixels": pixels, "completed": st["completed"], "failed": st["failed"],
+           "mean_batch_points": st["mean_batch_points"],
+           "mean_batch_requests": st["mean_batch_requests"],
+           "cache": {"volume_hits": st["volume_hits"], "volume_misses": st["volume_misses"],
+                     "light_hits": st["light_hits"], "light_misses": st["light_misses"],
+                     "evictions": st["evictions"]},
+           "peak_gb": st["peak_bytes"] / 2 ** 30, "volume_generation_s": round(gen_s, 1)}
+    if out_sweep:
+        out["load_sweep"] = out_sweep
+    return out
 
 
 def run_nis(args):
@@ -565,19 +711,17 @@ def run_nis(args):
     peaks_bf = measured_peaks()
     mlp_ms, mlp_n = fam_bf["mlp"]
     mlp_tf = MLP_FLOP_PER_POINT * n_points * args.steps / (mlp_ms / 1e3) / 1e12
-    mlp_gbs = mlp_bytes_per_point(2, 2) * n_points * args.steps / (mlp_ms / 1e3) / 1e9
     bf16 = {"value": value_bf, "unit": UNIT,
             "frame_ms": total_bf / args.steps,
             "mean_rel_err_vs_fp32": float(e_bf.mean()), "max_rel_err_vs_fp32": float(e_bf.max()),
             "step_breakdown_ms": {f: round(fam_bf[f][0] / args.steps, 4) for f in nis.FAMILIES},
-            "roofline": {"bound": "hbm", "unit": "GB/s", "kernel": "tc_gemm_kernel (tcgen05, BF16)",
-                         "achieved": mlp_gbs, "peak": peaks_bf["hbm_gbs"],
-                         "frac": mlp_gbs / peaks_bf["hbm_gbs"],
-                         "peak_source": f"{peaks_bf['source']} STREAM copy",
-                         "intensity_flop_per_byte": MLP_FLOP_PER_POINT / mlp_bytes_per_point(2, 2),
-                         "tensor_tflops": mlp_tf,
-                         "tensor_frac": mlp_tf / peaks_bf["bf16_tflops_sustained"],
-                         "launches": mlp_n, "avg_launch_ms": mlp_ms / max(mlp_n, 1),
+            "roofline": {"bound": "tensor", "unit": "TFLOP/s",
+                         "kernel": "mlp_fused_kernel (tcgen05, BF16, whole network per 128-point tile)",
+                         "achieved": mlp_tf, "peak": peaks_bf["bf16_tflops_sustained"],
+                         "frac": mlp_tf / peaks_bf["bf16_tflops_sustained"],
+                         "peak_source": f"{peaks_bf['source']} cuBLAS BF16 sustained",
+                         "work": "6.30 MFLOP per point", "launches": mlp_n,
+                         "avg_launch_ms": mlp_ms / max(mlp_n, 1),
                          "traffic": (recorded_traffic("mlp_bf16") or {}).get("bytes_per_launch")}}
 
     # ---- the same frames in FP8 e4m3 (dense layers)
@@ -603,19 +747,15 @@ def run_nis(args):
     e_f8 = ((a_f8 - a_32).abs() / torch.maximum(a_32.abs(), floor))
     mlp8_ms = fam_f8["mlp"][0]
     mlp8_tf = MLP_FLOP_PER_POINT * n_points * args.steps / (mlp8_ms / 1e3) / 1e12
-    mlp8_gbs = mlp_bytes_per_point(1, 2) * n_points * args.steps / (mlp8_ms / 1e3) / 1e9
     fp8 = {"value": value_f8, "unit": UNIT,
            "frame_ms": total_f8 / args.steps,
            "mean_rel_err_vs_fp32": float(e_f8.mean()), "max_rel_err_vs_fp32": float(e_f8.max()),
            "step_breakdown_ms": {f: round(fam_f8[f][0] / args.steps, 4) for f in nis.FAMILIES},
-           "roofline": {"bound": "hbm", "unit": "GB/s", "kernel": "tc_gemm_kernel (tcgen05 kind::f8f6f4, e4m3)",
-                        "achieved": mlp8_gbs, "peak": peaks_bf["hbm_gbs"],
-                        "frac": mlp8_gbs / peaks_bf["hbm_gbs"],
-                        "peak_source": f"{peaks_bf['source']} STREAM copy",
-                        "intensity_flop_per_byte": MLP_FLOP_PER_POINT / mlp_bytes_per_point(1, 2),
-                        "tensor_tflops": mlp8_tf,
-                        "tensor_frac": mlp8_tf / (2 * peaks_bf["bf16_tflops_sustained"]),
-                        "tensor_peak_source": f"{peaks_bf['source']} cuBLAS BF16 sustained x 2 (nominal FP8/BF16 ratio)"}}
+           "roofline": {"bound": "tensor", "unit": "TFLOP/s",
+                        "kernel": "tc_gemm_kernel (tcgen05 kind::f8f6f4, e4m3)",
+                        "achieved": mlp8_tf, "peak": 2 * peaks_bf["bf16_tflops_sustained"],
+                        "frac": mlp8_tf / (2 * peaks_bf["bf16_tflops_sustained"]),
+                        "peak_source": f"{peaks_bf['source']} cuBLAS BF16 sustained x 2 (nominal FP8/BF16 ratio)"}}
 
     # ---- the same frames with the transmittance from shear-warp rays (O(N^3) per level)
     sw = None
@@ -653,24 +793,26 @@ def run_nis(args):
     per_launch_s = dom_ms / 1e3 / max(dom_n, 1)
     n_levels = len(range(int(math.log2(cfg["n"])) + 1))
     if dom == "mlp":
-        # FP32-accurate dense layers: each FP32 product is six BF16 tcgen05 products of the
-        # operands' three-way splits (tensor ceiling: BF16 sustained / 6).  Per launch the
-        # layer's FLOPs over its algorithmic bytes are ~25 FLOP/B, below the ridge of that
-        # ceiling and the HBM copy rate (~41 FLOP/B): the layers are bound by HBM.
+        # FP32-accurate dense layers on the tensor pipe: each FP32 product is issued as six
+        # BF16 tcgen05 products of the operands' three-way splits, so the work per launch is
+        # 6 x the layers' FLOPs and the ceiling the measured BF16 rate (sustained: the kernel
+        # runs inside a long step).  The launches' HBM rate on the bytes this launch design
+        # moves (activations round-tripping between layers) is kept as a side figure.
         flops = MLP_FLOP_PER_POINT * n_points * args.steps / max(dom_n, 1)
-        work = mlp_bytes_per_point(6, 4) * n_points * args.steps / max(dom_n, 1)
-        achieved = work / per_launch_s / 1e9
-        peak = peaks["hbm_gbs"]
-        tensor_peak = peaks["bf16_tflops_sustained"] / 6.0
-        roof = {"bound": "hbm", "unit": "GB/s",
+        work = 6 * flops / 1e12
+        achieved = work / per_launch_s
+        peak = peaks["bf16_tflops_sustained"]
+        design = mlp_bytes_per_point(6, 4) * n_points * args.steps / max(dom_n, 1)
+        roof = {"bound": "tensor", "unit": "TFLOP/s",
                 "kernel": "tc_gemm_kernel (tcgen05, FP32 via 3-way BF16 split, 6 products)",
-                "peak_source": f"{peaks['source']} STREAM copy",
-                "intensity_flop_per_byte": flops / work,
-                "ridge_flop_per_byte": tensor_peak * 1e12 / (peak * 1e9),
-                "tensor_tflops": flops / per_launch_s / 1e12,
-                "tensor_frac": flops / per_launch_s / 1e12 / tensor_peak,
-                "tensor_peak_source": f"{peaks['source']} cuBLAS BF16 sustained "
-                                      f"{peaks['bf16_tflops_sustained']:.0f} TFLOP/s / 6"}
+                "peak_source": f"{peaks['source']} cuBLAS BF16 sustained",
+                "work": "6 BF16 products x 6.30 MFLOP per point (issued TFLOP per launch)",
+                "fp32_tflops": flops / per_launch_s / 1e12,
+                "hbm_launch_design": {"gb_s": design / per_launch_s / 1e9,
+                                      "frac": design / per_launch_s / 1e9 / peaks["hbm_gbs"],
+                                      "bytes_per_point": mlp_bytes_per_point(6, 4),
+                                      "note": "bytes of this launch design (activations round-trip "
+                                              "between layers), not algorithmic bytes"}}
     elif dom == "cnn":
         work = CNN_FLOP_PER_POINT * n_points * args.steps / max(dom_n, 1)
         achieved = work / per_launch_s / 1e12
@@ -688,6 +830,16 @@ def run_nis(args):
         roof = {"bound": "hbm", "unit": "GB/s", "kernel": dom,
                 "peak_source": f"{peaks['source']} STREAM copy"}
     tr = recorded_traffic(dom)
+    # the gather against HBM on its algorithmic bytes (feature writes + the pyramid and the
+    # transmittance read once)
+    g_ms, g_n = fam["gather"]
+    g_bytes = gather_algorithmic_bytes(n_points, cfg["n"]) * args.steps / max(g_n, 1)
+    g_gbs = g_bytes / (g_ms / 1e3 / max(g_n, 1)) / 1e9
+    gather_roof = {"bound": "hbm", "unit": "GB/s", "kernel": "gather_kernel<0>",
+                   "achieved": g_gbs, "peak": peaks["hbm_gbs"], "frac": g_gbs / peaks["hbm_gbs"],
+                   "work_per_launch": g_bytes, "avg_launch_ms": g_ms / max(g_n, 1),
+                   "peak_source": f"{peaks['source']} STREAM copy",
+                   "work": "5400 FP32 features per point + density and transmittance pyramids once"}
     roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak,
                  "traffic": tr["bytes_per_launch"] if tr else None,
                  "family": dom, "launches": dom_n, "avg_launch_ms": dom_ms / max(dom_n, 1),
@@ -706,6 +858,7 @@ def run_nis(args):
             "gpu_launches": int(launches),
             "step_breakdown_ms": {f: round(fam[f][0] / args.steps, 4) for f in nis.FAMILIES},
             "roofline": roof,
+            "gather_roofline": gather_roof,
             "bf16": bf16,
             "fp8": fp8,
             "shear_warp": sw,
@@ -721,12 +874,16 @@ def run_nis(args):
         line["serving"] = run_serving(args, nis, blob, local, workload)
         if not args.no_shear_warp:
             line["serving_shear_warp"] = run_serving(args, nis, blob, local, workload,
-                                                     nis.TRANSMITTANCE_SHEAR_WARP)
+                                                     nis.TRANSMITTANCE_SHEAR_WARP, sweep=(1.0, 1.3))
         del workload
     if not args.no_shear_warp:
         line["shear_warp"]["plume1024"] = plume_transmittance(nis, local)
+    if not args.no_plume_loop:
+        line["plume1024_60f"] = run_plume_loop(args, nis, local)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, vol_np, weights)
+        line["cpu_baseline"]["single_thread"] = oracle_single_thread(args.workload)
+    line["summary"] = compact_summary(line)
     print(json.dumps(line), flush=True)
 
 
@@ -759,6 +916,9 @@ def run_ncu_case(args):
 
 def main():
     args = parse()
+    if args.oracle_sample:
+        run_oracle_sample(args)
+        return
     if args.ncu_case:
         run_ncu_case(args)
         return

@@ -245,6 +245,10 @@ nis_status nis_update_volume(nis_ctx *ctx, nis_volume vol, const void *density, 
  *   otherwise NIS_ERR_NOT_READY.  So must the light's copy of the density it shades with:
  *   after a pyramid rebuild, build the light again or shade once through nis_shade_points
  *   (which refreshes that copy), else NIS_ERR_NOT_READY.
+ * - The dense layers run in FP32 on the CUDA cores (the FP32 copy of the weights), whatever
+ *   precision the weights were loaded with: BF16- or FP8-loaded weights give the FP32
+ *   result.  Paper-template weights are refused with NIS_ERR_UNIMPLEMENTED; materials are
+ *   checked as for nis_shade_points (NIS_ERR_INVALID_ARG).
  * - The first call on a device looks up the array's device address; make that first call
  *   before any stream capture.
  * - All calls in the process share the one array and leave their intermediates in it; the
@@ -336,6 +340,13 @@ nis_status nis_server_wait(nis_server *srv, uint64_t id, int timeout_ms, double 
 nis_status nis_server_get_stats(nis_server *srv, nis_server_stats *out);
 /* Stops the loop after the admitted requests finish and frees the server's buffers. */
 void nis_server_destroy(nis_server *srv);
+/* Test hook (no counterpart in the paper): the next batch that shades points of request
+ * `id` is treated, for that request only, as if its shading had returned `status` (< 0,
+ * else NIS_ERR_INVALID_ARG).  The failure is made on the host; nothing faults on the GPU.
+ * The request shades no further points and completes with `status`; the other requests
+ * complete as usual.  Call it before the request's points are batched (for example right
+ * after nis_server_submit; ids are 1, 2, ... in submit order). */
+nis_status nis_server_inject_failure(nis_server *srv, uint64_t id, nis_status status);
 
 /* Frees a volume (and its lights), a light or a weight set. */
 nis_status nis_release(nis_ctx *ctx, nis_handle h);

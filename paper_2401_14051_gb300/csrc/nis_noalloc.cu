@@ -66,11 +66,8 @@ extern "C" nis_status nis_shade_points_static(nis_ctx *ctx, nis_volume vol, nis_
                             "points per call");
     if (n > 0 && (!d_points || !d_omega || !d_rgb_out))
         return record_error(ctx, NIS_ERR_INVALID_ARG, "NULL points, omega or output");
-    if (!m || !(m->g > -1.f && m->g < 1.f))
-        return record_error(ctx, NIS_ERR_INVALID_ARG, "material NULL or g outside (-1, 1)");
-    for (int c = 0; c < 3; ++c)
-        if (!(m->albedo[c] > 0.f && m->albedo[c] <= 1.f) || !isfinite(m->intensity[c]))
-            return record_error(ctx, NIS_ERR_INVALID_ARG, "albedo must lie in (0, 1], intensity finite");
+    // the same material checks as every other shading call (phase lobes included)
+    if (const char *why = material_problem(m)) return record_error(ctx, NIS_ERR_INVALID_ARG, why);
     if (weights_model(ctx, w) == kModelPaper)
         return record_error(ctx, NIS_ERR_UNIMPLEMENTED, "nis_shade_points_static takes lattice-model weights");
     ResolvedInputs in;

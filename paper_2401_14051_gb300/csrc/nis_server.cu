@@ -139,6 +139,8 @@ struct nis_server {
     size_t peak = 0;
     Clock::time_point t_first, t_last;
     bool any_submit = false;
+    // test hook: requests whose shading is to be treated as failed, with the status
+    std::map<uint64_t, nis_status> injected;
 };
 
 namespace {
@@ -389,6 +391,10 @@ void loop(nis_server *S) {
             int room = S->cfg.max_batch_points;
             for (Req *q : S->active) {
                 if (room <= 0) break;
+                if (q->state == kReady && q->err) {   // an earlier batch failed: shade no more
+                    q->state = kFailing;              // of it; retired after its batches drain
+                    continue;
+                }
                 if (q->state != kReady || q->shaded >= q->n_points) continue;
                 int take = std::min(q->n_points - q->shaded, room);
                 nis_segment sg{};
@@ -408,8 +414,15 @@ void loop(nis_server *S) {
                                                    reinterpret_cast<nis_stream>(S->shade));
                 if (rc)                           // every request of the batch has lost points
                     for (Req *q : in_batch) q->err = rc;
+                {
+                    std::lock_guard<std::mutex> lk(S->mu);
+                    for (Req *q : in_batch) {
+                        auto it = S->injected.find(q->id);
+                        if (it != S->injected.end()) { q->err = it->second; S->injected.erase(it); }
+                    }
+                }
                 for (Req *q : last) {
-                    const nis_status ro = rc ? rc : schedule_output(S, q);
+                    const nis_status ro = q->err ? q->err : schedule_output(S, q);
                     if (ro) { q->err = ro; q->state = kFailing; }
                 }
                 cudaEventRecord(S->ev_batch, S->shade);
@@ -456,6 +469,13 @@ void loop(nis_server *S) {
 }  // namespace
 
 extern "C" {
+
+nis_status nis_server_inject_failure(nis_server *srv, uint64_t id, nis_status status) {
+    if (!srv || status >= 0) return NIS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->injected[id] = status;
+    return NIS_OK;
+}
 
 nis_status nis_server_create(nis_ctx *ctx, nis_weights w, const nis_server_config *cfg,
                              nis_server **out) {

@@ -139,6 +139,7 @@ _SIGS = {
     "nis_server_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int, C.POINTER(C.c_double)]),
     "nis_server_get_stats": (C.c_int, [C.c_void_p, C.POINTER(ServerStats)]),
     "nis_server_destroy": (None, [C.c_void_p]),
+    "nis_server_inject_failure": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int]),
     "nis_shade_points_static": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint64,
                                           C.POINTER(Material), C.c_void_p, C.c_void_p, C.c_int,
                                           C.c_void_p, C.c_void_p]),
@@ -324,6 +325,15 @@ class Context:
                             stream=None):
         """nis_shade_points_static: no device allocation inside the call; `out` must be
         preallocated [n, 3] float32 on the device, n <= STATIC_MAX_POINTS."""
+        # the library writes n rows of `out` and reads n rows of the inputs: check their
+        # shapes, types, layout and device here, where a mismatch can still be reported
+        n = points.shape[0]
+        for name, t in (("points", points), ("omega", omega), ("out", out)):
+            if not (torch.is_tensor(t) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+                    and t.dim() == 2 and t.shape[0] == n and t.shape[1] == 3):
+                raise ValueError(f"{name} must be a contiguous float32 CUDA tensor of shape ({n}, 3)")
+            if t.device.index != self.device:
+                raise ValueError(f"{name} is on cuda:{t.device.index}, the context on cuda:{self.device}")
         m = material(mat)
         self._check(self.lib.nis_shade_points_static(self.h, vol, light, weights, C.byref(m),
                                                      _ptr(points), _ptr(omega), points.shape[0],
@@ -485,6 +495,10 @@ class Server:
             raise NisError(st, f"request {rid} failed")
         _, out = self._keep.pop(rid)
         return out, lat.value
+
+    def inject_failure(self, rid: int, status: int):
+        """nis_server_inject_failure: request rid's shading is treated as failed (host side)."""
+        self.ctx._check(self.lib.nis_server_inject_failure(self.h, rid, status))
 
     def stats(self) -> dict:
         s = ServerStats()

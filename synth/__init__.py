@@ -175,6 +175,16 @@ def unit_vector(seed: int) -> np.ndarray:
             return v / nv
 
 
+def rotating_light(base, frame: int, deg_per_frame: float = 6.0) -> np.ndarray:
+    """The light direction of frame `frame` of an animation: `base` turned about the
+    vertical (+y) axis by frame * deg_per_frame degrees (the 1024^3 plume's 60-frame loop
+    turns it 6 degrees a frame, a full turn over 60 frames)."""
+    a = math.radians(frame * deg_per_frame)
+    c, s = math.cos(a), math.sin(a)
+    b = np.asarray(base, dtype=np.float64)
+    return np.array([c * b[0] + s * b[2], b[1], -s * b[0] + c * b[2]])
+
+
 def material(g: float, albedo, intensity=(1.0, 1.0, 1.0), lobes=None) -> dict:
     """Material: network asymmetry input g, RGB albedo and light intensity; optional MHG
     lobes [(g_i, w_i), ...] (2 or 3, weights summing to 1) for the phase features."""

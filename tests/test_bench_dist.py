@@ -116,3 +116,27 @@ def test_dense_layer_bytes_per_point_hand_count():
     import bench
     for op, st in ((6, 4), (2, 2), (1, 2)):
         assert bench.mlp_bytes_per_point(op, st) == 25160 * op + 26400 * st + 876
+
+
+def test_compact_summary_fits_the_end_of_a_log():
+    # the bench line ends with a summary of its figures; a log that keeps only the last
+    # ~1.5 KB of the output must still hold it whole
+    import json
+    import bench
+    fam = {f: 1.0 for f in ("pyramid", "march", "phase", "hits", "gather", "cnn", "mlp", "other")}
+    sub = {"value": 1e7, "frame_ms": 20.0, "mean_rel_err_vs_fp32": 0.006,
+           "step_breakdown_ms": fam, "roofline": {"frac": 0.3}}
+    serv = {"throughput_req_s": 30.0, "p50_ms": 50.0, "p99_ms": 250.0, "mean_batch_requests": 1.5,
+            "load_sweep": [{"load": 1.0, "throughput_req_s": 40.0, "p50_ms": 60.0, "p99_ms": 300.0,
+                            "mean_batch_requests": 2.0}] * 2}
+    line = {"frame_ms": 36.0, "value": 5.9e6, "step_breakdown_ms": fam,
+            "roofline": {"bound": "tensor", "frac": 0.3}, "gather_roofline": {"frac": 0.2},
+            "e2e": {"value": 5.8e6}, "bf16": sub, "fp8": sub,
+            "paper_template_model": {"frame_ms": 27.0}, "shear_warp": {"frame_ms": 33.0},
+            "serving": serv, "serving_shear_warp": serv,
+            "plume1024_60f": {"shear_warp": {"frames": 60, "frame_ms_median": 80.0, "frame_ms_p99": 90.0},
+                              "march": {"frames": 8, "frame_ms_median": 1200.0, "frame_ms_p99": 1210.0}},
+            "cpu_baseline": {"value": 9.0, "single_thread": {"value": 3.0}}}
+    s = json.dumps({"summary": bench.compact_summary(line)})
+    assert len(s) < 1400, len(s)
+    assert '"bf16"' in s and '"plume_60f"' in s and '"sweep"' in s

@@ -151,3 +151,55 @@ def test_server_budget_admission_and_caches(nis):
     assert st["completed"] == 3 and st["failed"] == 0
     assert st["evictions"] >= 1
     assert st["peak_bytes"] <= budget
+
+
+def test_server_refuses_invalid_material_at_submit_beside_valid_requests(nis):
+    # a material nis_shade_points would refuse (lobe weights that do not sum to 1) is refused
+    # at submit, and nothing of it is queued; the valid requests around it complete with the
+    # images they get alone
+    blob = synth.pack_weights(synth.make_weights(24, 12.0))
+    reqs = _requests(k0=50)[:3]
+    ctx = nis.Context(0, torch_allocator=False)
+    srv = nis.Server(ctx, ctx.load_weights(blob), max_batch_points=1500, max_inflight=8)
+    ids = [srv.submit(reqs[0]["vol"], reqs[0]["key"], reqs[0]["light"], 0.6, reqs[0]["mat"], reqs[0]["cam"])]
+    bad = dict(reqs[1]["mat"], lobes=[(0.5, 0.7), (0.2, 0.7)])
+    with pytest.raises(nis.NisError) as e:
+        srv.submit(reqs[1]["vol"], reqs[1]["key"], reqs[1]["light"], 0.6, bad, reqs[1]["cam"])
+    assert e.value.status == -1
+    ids.append(srv.submit(reqs[2]["vol"], reqs[2]["key"], reqs[2]["light"], 0.6, reqs[2]["mat"], reqs[2]["cam"]))
+    imgs = [srv.wait(i, 60000)[0] for i in ids]
+    st = srv.stats()
+    srv.close()
+    ctx.close()
+    assert st["submitted"] == 2 and st["completed"] == 2 and st["failed"] == 0
+    for img, r in zip(imgs, (reqs[0], reqs[2])):
+        np.testing.assert_array_equal(img, _render_direct(nis, r, blob))
+
+
+def test_server_retires_a_request_whose_shading_failed(nis):
+    # a shading failure made on the host for one request (no GPU fault): that request
+    # completes with the injected status and shades no further points, the others complete
+    # with their solo images, and destroying the server joins its loop
+    blob = synth.pack_weights(synth.make_weights(25, 12.0))
+    reqs = _requests(k0=60)[:4]
+    ctx = nis.Context(0, torch_allocator=False)
+    srv = nis.Server(ctx, ctx.load_weights(blob), max_batch_points=700, max_inflight=8)
+    ids = []
+    for i, r in enumerate(reqs):
+        rid = srv.submit(r["vol"], r["key"], r["light"], 0.6, r["mat"], r["cam"])
+        if i == 1:
+            srv.inject_failure(rid, -5)
+        ids.append(rid)
+    outcome = {}
+    for i, rid in enumerate(ids):
+        try:
+            outcome[i] = srv.wait(rid, 60000)[0]
+        except nis.NisError as e:
+            outcome[i] = e.status
+    st = srv.stats()
+    srv.close()                                    # joins the loop; must not hang
+    ctx.close()
+    assert outcome[1] == -5
+    assert st["completed"] == 3 and st["failed"] == 1
+    for i in (0, 2, 3):
+        np.testing.assert_array_equal(outcome[i], _render_direct(nis, reqs[i], blob))

@@ -106,3 +106,15 @@ def test_workloads_as_documented():
     assert synth.config(2, small=True)["camera"]["width"] == 192
     with pytest.raises(ValueError):
         synth.config(4)
+
+
+def test_rotating_light_turns_about_the_vertical_axis():
+    base = synth.unit_vector(9)
+    for f in (0, 1, 7, 15, 60):
+        l = synth.rotating_light(base, f)
+        assert abs(np.linalg.norm(l) - 1.0) < 1e-12
+        assert abs(l[1] - base[1]) < 1e-15                      # y component kept
+        ang = np.degrees(np.arctan2(l[0] * base[2] - l[2] * base[0],
+                                    l[0] * base[0] + l[2] * base[2]))   # angle in the xz plane
+        assert abs((ang - 6.0 * f + 180.0) % 360.0 - 180.0) < 1e-9
+    np.testing.assert_allclose(synth.rotating_light(base, 60), base, atol=1e-12)   # a full turn

@@ -91,3 +91,43 @@ def test_static_refuses_a_light_older_than_the_pyramid(setup):
     ctx.sync(timeout_ms=60000)
     # the static path's dense layers are FP32 FFMA, shade_points' the FP32 tensor split
     assert _rel(out.cpu().numpy(), ref.cpu().numpy()).max() <= 1e-4
+
+
+def test_static_checks_the_material_like_every_shading_call(setup):
+    # a fourth phase lobe is refused (the material struct holds three) as nis_shade_points
+    # refuses it: invalid argument, before any input is resolved
+    import ctypes as C
+    nis, ctx, v, l, w, mat = setup
+    dev = torch.device("cuda:0")
+    x = torch.zeros((4, 3), dtype=torch.float32, device=dev)
+    m = nis.material(dict(mat, lobes=[(0.5, 0.5), (0.2, 0.5)]))
+    m.n_lobes = 4
+    st = ctx.lib.nis_shade_points_static(ctx.h, v, l, w, C.byref(m), x.data_ptr(), x.data_ptr(), 4,
+                                         x.data_ptr(), None)
+    assert st == -1
+    bad = nis.material(dict(mat, lobes=[(0.5, 0.7), (0.2, 0.7)]))   # weights sum above 1
+    st = ctx.lib.nis_shade_points_static(ctx.h, v, l, w, C.byref(bad), x.data_ptr(), x.data_ptr(), 4,
+                                         x.data_ptr(), None)
+    assert st == -1
+
+
+def test_static_refuses_paper_weights_and_runs_bf16_weights_in_fp32(setup):
+    nis, ctx, v, l, w, mat = setup
+    dev = torch.device("cuda:0")
+    p, o = (torch.from_numpy(a).to(dev) for a in synth.shading_points(96, 19))
+    out = torch.empty((96, 3), dtype=torch.float32, device=dev)
+    wp = ctx.load_weights(synth.pack_weights_paper(synth.make_weights_paper(20, 12.0)))
+    with pytest.raises(nis.NisError) as e:
+        ctx.shade_points_static(v, l, wp, mat, p, o, out)
+    assert e.value.status == -7
+    # weights loaded for BF16 shading: the static path uses their FP32 copy, so the result
+    # is the FP32-loaded weights' result bit for bit
+    wb = ctx.load_weights(synth.pack_weights(synth.make_weights(15, 12.0)), nis.PREC_BF16)
+    ref = torch.empty_like(out)
+    ctx.shade_points_static(v, l, w, mat, p, o, ref)
+    ctx.shade_points_static(v, l, wb, mat, p, o, out)
+    ctx.sync(timeout_ms=60000)
+    assert torch.equal(out, ref)
+    # and the binding checks the output's shape before the library writes into it
+    with pytest.raises(ValueError):
+        ctx.shade_points_static(v, l, w, mat, p, o, out[:50])
