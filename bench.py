@@ -88,6 +88,7 @@ def parse():
     ap.add_argument("--no-paper-model", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=256)
     ap.add_argument("--no-plume-loop", action="store_true")
+    ap.add_argument("--no-split-frame", action="store_true")
     ap.add_argument("--plume-march-frames", type=int, default=8)
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--ncu-case", choices=("f32", "bf16", "simt", "sweep"),
@@ -325,6 +326,9 @@ def compact_summary(line: dict) -> dict:
             if sv.get("load_sweep"):
                 out[k]["sweep"] = [[x["load"], x["throughput_req_s"], x["p50_ms"], x["p99_ms"],
                                     x["mean_batch_requests"]] for x in sv["load_sweep"]]
+    sp = line.get("split_frame")
+    if sp:
+        out["split_frame"] = [sp["parts"], r(sp["frame_ms"]), sp.get("equals_whole_frame")]
     pl = line.get("plume1024_60f")
     if pl:
         out["plume_60f"] = {m: [pl[m]["frames"], pl[m]["frame_ms_median"], pl[m]["frame_ms_p99"]]
@@ -534,6 +538,48 @@ def run_plume_loop(args, nis, local: int) -> dict:
                      "shade_ms_median": round(float(np.median(shade)), 3)}
     ctx.close()
     return out
+
+
+def run_split_frame(args, nis, ctx, v, w, cfg, img, flush, stream, world: int) -> dict:
+    """Strong scaling of one frame: the whole step (pyramid, transmittance, phase table,
+    hits) replicated on every rank, the frame's shading points split into `world` equal
+    ranges (one per rank), the ranges gathered to rank 0 and scattered into the image there.
+    Per frame: barrier, synchronise, time on the host clock, max over ranks.  Rank 0 also
+    checks the assembled image against its own whole-frame render, bit for bit."""
+    import torch
+    from paper_2401_14051_gb300 import frame_split
+    mat, cam, light = cfg["material"], cfg["camera"], cfg["light"]
+    dev = img.device
+    cap = nis.part_capacity(cam["width"] * cam["height"], world)
+    bufs = (torch.empty((cap, 3), dtype=torch.float32, device=dev),
+            torch.empty((cap,), dtype=torch.int32, device=dev))
+    out = torch.empty_like(img)
+
+    def frame():
+        ctx.build_pyramid(v)
+        lt = ctx.build_transmittance(v, light, 0.6)
+        ctx.build_phase_table(mat["g"])
+        return frame_split.render_frame_split(ctx, v, lt, w, mat, cam, out=out, part_bufs=bufs)
+
+    for _ in range(args.warmup):
+        frame()
+    times, info = [], None
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        _, info = frame()
+        torch.cuda.synchronize()
+        times.append(max_over_ranks(time.perf_counter() - t0, world))
+    res = {"parts": world, "scaling": "strong", "precision": "f32",
+           "frame_ms": 1e3 * sum(times) / len(times),
+           "points_per_s": info["n_hits"] * len(times) / sum(times),
+           "max_part_points": info["rows"], "timer": "host clock around a synchronised frame, "
+           "max over ranks", "exchange": "torch.distributed gather of 16 B per point to rank 0"}
+    if world == 1 or dist_env()[0] == 0:
+        res["equals_whole_frame"] = bool(torch.equal(out, img))
+    return res
 
 
 def serving_volumes(args, local: int):
@@ -782,6 +828,10 @@ def run_nis(args):
     e2e_value, e2e_total = whole_job_rate(n_points * args.steps, sum(e2e_times), world)
     ctx.sync(timeout_ms=120000)
 
+    # ---- one frame split across the ranks (strong scaling), beside the replicas above
+    split = None if args.no_split_frame else run_split_frame(args, nis, ctx, v, w, cfg, img,
+                                                             flush, stream, world)
+
     if rank != 0:
         ctx.close()
         return
@@ -863,6 +913,7 @@ def run_nis(args):
             "fp8": fp8,
             "shear_warp": sw,
             "paper_template_model": paper,
+            "split_frame": split,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(vol_np.nbytes),
                     "d2h_bytes_per_step": int(img.numel() * 4),

@@ -222,6 +222,41 @@ nis_status nis_render_frame_lights(nis_ctx *ctx, nis_volume vol, const nis_light
                                    int n_lights, nis_weights w, const nis_material *m,
                                    const nis_camera *cam, float *d_rgb_out, nis_stream stream);
 
+/* ---- one frame split into ranges of shading points ------------------------------------
+ * The paper runs many network instances in parallel over independent shading points
+ * (Sec. III.C.2, input batching).  These calls split one frame's shading points into `parts`
+ * contiguous ranges, one per process (or per GPU), with the volume, light and weights
+ * replicated; each range's radiance is shaded where it lies and the parts are assembled into
+ * one image on one device.  The frame's hits are listed in pixel order, so every process
+ * computes the same list and the ranges cover each hit exactly once. */
+
+/* Range `part` of `parts` equal contiguous ranges over n items: *first = floor(part * n /
+ * parts), *count = floor((part + 1) * n / parts) - *first.  Host only: needs no context and
+ * no device.  NIS_ERR_INVALID_ARG for n < 0, parts < 1, part outside [0, parts) or a NULL
+ * output. */
+nis_status nis_part_range(long long n, int part, int parts, long long *first, long long *count);
+
+/* Range `part` of `parts` of one frame (the frame of nis_render_frame with the same
+ * arguments): finds the frame's hits, lists them in pixel order, and shades hits *first ..
+ * *first + *count - 1 of that list (nis_part_range over the frame's hits).  Writes their
+ * radiance to d_rgb (device float32, count x 3) and their pixel indices y * width + x to d_pix
+ * (device int32, count); both hold `capacity` rows, and ceil(width * height / parts) always
+ * suffices.  *n_hits, *first and *count (host) receive the frame's hit count and the range.
+ * Each hit's radiance is bit-identical to that pixel of nis_render_frame.  NIS_ERR_INVALID_ARG
+ * for part/parts out of range, NULL buffers, or capacity < count (then nothing is shaded),
+ * besides the errors of nis_render_frame.  Waits once on the stream (to read the hit count). */
+nis_status nis_render_frame_part(nis_ctx *ctx, nis_volume vol, nis_light light, nis_weights w,
+                                 const nis_material *m, const nis_camera *cam, int part,
+                                 int parts, float *d_rgb, int *d_pix, int capacity, int *n_hits,
+                                 int *first, int *count, nis_stream stream);
+
+/* Assembles one part into an image: d_image[3 * d_pix[i] + c] = d_rgb[3 * i + c] for i < n and
+ * c < 3 (all device buffers; d_image float32 of n_pixels x 3).  Pixel indices outside
+ * [0, n_pixels) are skipped.  Pixels that no part names keep their value, so the caller
+ * clears the image once before the first part.  Asynchronous on `stream`. */
+nis_status nis_scatter_part(nis_ctx *ctx, const float *d_rgb, const int *d_pix, int n,
+                            float *d_image, int n_pixels, nis_stream stream);
+
 /* Overwrites the density of an existing volume with a grid of the same size (same
  * conventions as nis_upload_volume) without allocating: device sources and page-locked
  * host sources are read in place (a GB300 kernel reads pinned host memory over

@@ -105,6 +105,9 @@ struct Workspace {                    // scratch of nis_shade_points, grow-only
     float *hit_pts = nullptr, *hit_omega = nullptr, *hit_rgb = nullptr;
     int *hit_pix = nullptr, *hit_count = nullptr;
     int *host_count = nullptr;        // pinned
+    int px_cap = 0;                   // pixels: the frame split's per-pixel hit list
+    int *px_flag = nullptr, *px_blk = nullptr, *px_off = nullptr;
+    float *px_pts = nullptr, *px_om = nullptr;
 };
 constexpr int kActBufs = 15;          // e, h0, h1, 6 chain ends, 3 merges, z1, z2, spare
 // Shading points per pipeline pass, at most.  Each dense layer is one launch per pass, and
@@ -1893,6 +1896,46 @@ nis_status nis_find_hits(nis_ctx *ctx, nis_volume vol, const nis_camera *cam, in
     return NIS_OK;
 }
 
+// Hit-list buffers of a frame of `pixels` pixels (grow-only).
+nis_status ensure_hit_ws(nis_ctx *ctx, int pixels, cudaStream_t s) {
+    Workspace &ws = ctx->ws;
+    if (ws.hit_cap >= pixels) return NIS_OK;
+    nis_status st;
+    dev_free(ctx, ws.hit_pts); dev_free(ctx, ws.hit_omega); dev_free(ctx, ws.hit_rgb);
+    dev_free(ctx, ws.hit_pix); dev_free(ctx, ws.hit_count);
+    ws.hit_pts = ws.hit_omega = ws.hit_rgb = nullptr;
+    ws.hit_pix = ws.hit_count = nullptr;
+    ws.hit_cap = 0;
+    if ((st = dev_alloc_t(ctx, 3 * (size_t)pixels, &ws.hit_pts, s))) return st;
+    if ((st = dev_alloc_t(ctx, 3 * (size_t)pixels, &ws.hit_omega, s))) return st;
+    if ((st = dev_alloc_t(ctx, 3 * (size_t)pixels, &ws.hit_rgb, s))) return st;
+    if ((st = dev_alloc_t(ctx, (size_t)pixels, &ws.hit_pix, s))) return st;
+    if ((st = dev_alloc_t(ctx, 1, &ws.hit_count, s))) return st;
+    ws.hit_cap = pixels;
+    return NIS_OK;
+}
+
+// Per-pixel hit list of the frame split (grow-only): flags, points, directions, block counts
+// and their offsets.
+nis_status ensure_px_ws(nis_ctx *ctx, int pixels, cudaStream_t s) {
+    Workspace &ws = ctx->ws;
+    if (ws.px_cap >= pixels) return NIS_OK;
+    nis_status st;
+    dev_free(ctx, ws.px_flag); dev_free(ctx, ws.px_blk); dev_free(ctx, ws.px_off);
+    dev_free(ctx, ws.px_pts); dev_free(ctx, ws.px_om);
+    ws.px_flag = ws.px_blk = ws.px_off = nullptr;
+    ws.px_pts = ws.px_om = nullptr;
+    ws.px_cap = 0;
+    const size_t nb = ((size_t)pixels + 255) / 256;
+    if ((st = dev_alloc_t(ctx, (size_t)pixels, &ws.px_flag, s))) return st;
+    if ((st = dev_alloc_t(ctx, nb, &ws.px_blk, s))) return st;
+    if ((st = dev_alloc_t(ctx, nb + 1, &ws.px_off, s))) return st;
+    if ((st = dev_alloc_t(ctx, 3 * (size_t)pixels, &ws.px_pts, s))) return st;
+    if ((st = dev_alloc_t(ctx, 3 * (size_t)pixels, &ws.px_om, s))) return st;
+    ws.px_cap = pixels;
+    return NIS_OK;
+}
+
 // Frame for one or more lights: the shading points (first hits) do not depend on the light;
 // each light's radiance is shaded with its own transmittance and added to the pixels.
 nis_status render_impl(nis_ctx *ctx, nis_volume vol, const nis_light *lights, int n_lights,
@@ -1917,19 +1960,7 @@ nis_status render_impl(nis_ctx *ctx, nis_volume vol, const nis_light *lights, in
         if ((st = ensure_pairs(ctx, *pv, *l, s))) return st;
     Workspace &ws = ctx->ws;
     int pixels = c.width * c.height;
-    if (ws.hit_cap < pixels) {
-        dev_free(ctx, ws.hit_pts); dev_free(ctx, ws.hit_omega); dev_free(ctx, ws.hit_rgb);
-        dev_free(ctx, ws.hit_pix); dev_free(ctx, ws.hit_count);
-        ws.hit_pts = ws.hit_omega = ws.hit_rgb = nullptr;
-        ws.hit_pix = ws.hit_count = nullptr;
-        ws.hit_cap = 0;
-        if ((st = dev_alloc_t(ctx, 3 * (size_t)pixels, &ws.hit_pts, s))) return st;
-        if ((st = dev_alloc_t(ctx, 3 * (size_t)pixels, &ws.hit_omega, s))) return st;
-        if ((st = dev_alloc_t(ctx, 3 * (size_t)pixels, &ws.hit_rgb, s))) return st;
-        if ((st = dev_alloc_t(ctx, (size_t)pixels, &ws.hit_pix, s))) return st;
-        if ((st = dev_alloc_t(ctx, 1, &ws.hit_count, s))) return st;
-        ws.hit_cap = pixels;
-    }
+    if ((st = ensure_hit_ws(ctx, pixels, s))) return st;
     NIS_CUDA(cudaMemsetAsync(ws.hit_count, 0, sizeof(int), s));
     {
         ProfScope ps(ctx, "hits", s);
@@ -1947,7 +1978,7 @@ nis_status render_impl(nis_ctx *ctx, nis_volume vol, const nis_light *lights, in
                                  nullptr, s)))
                 return st;
             ProfScope ps(ctx, "other", s);
-            launch_scatter_rgb(ws.hit_rgb, ws.hit_pix, count, d_rgb_out, s, q > 0);
+            launch_scatter_rgb(ws.hit_rgb, ws.hit_pix, count, d_rgb_out, pixels, s, q > 0);
         }
         NIS_CUDA(cudaGetLastError());
     }
@@ -1965,6 +1996,79 @@ nis_status nis_render_frame_lights(nis_ctx *ctx, nis_volume vol, const nis_light
                                    const nis_camera *cam, float *d_rgb_out, nis_stream stream) {
     if (ctx && n_lights > 64) return fail(ctx, NIS_ERR_INVALID_ARG, "at most 64 lights");
     return render_impl(ctx, vol, lights, n_lights, w, m, cam, d_rgb_out, stream);
+}
+
+nis_status nis_part_range(long long n, int part, int parts, long long *first, long long *count) {
+    if (n < 0 || parts < 1 || part < 0 || part >= parts || !first || !count)
+        return NIS_ERR_INVALID_ARG;
+    // floor(p * n / parts) without overflow: n = q * parts + r
+    const long long q = n / parts, r = n % parts;
+    auto start = [&](long long p) { return p * q + p * r / parts; };
+    *first = start(part);
+    *count = start(part + 1) - *first;
+    return NIS_OK;
+}
+
+nis_status nis_render_frame_part(nis_ctx *ctx, nis_volume vol, nis_light light, nis_weights w,
+                                 const nis_material *m, const nis_camera *cam, int part,
+                                 int parts, float *d_rgb, int *d_pix, int capacity, int *n_hits,
+                                 int *first, int *count, nis_stream stream) {
+    if (!ctx) return NIS_ERR_INVALID_ARG;
+    if (parts < 1 || part < 0 || part >= parts)
+        return fail(ctx, NIS_ERR_INVALID_ARG, "part outside [0, parts)");
+    if (!d_rgb || !d_pix || !n_hits || !first || !count || capacity < 0)
+        return fail(ctx, NIS_ERR_INVALID_ARG, "NULL output or negative capacity");
+    nis_status st = check_material(ctx, m);
+    if (st) return st;
+    CameraArgs c;
+    if ((st = camera_args(ctx, cam, &c))) return st;
+    Volume *pv; Light *pl; Weights *pw;
+    if ((st = resolve(ctx, vol, light, w, &pv, &pl, &pw))) return st;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if ((st = ensure_pairs(ctx, *pv, *pl, s))) return st;
+    const int pixels = c.width * c.height;
+    if ((st = ensure_hit_ws(ctx, pixels, s)) || (st = ensure_px_ws(ctx, pixels, s))) return st;
+    Workspace &ws = ctx->ws;
+    {
+        ProfScope ps(ctx, "hits", s);
+        launch_find_hits_ordered(pv->data, pv->n, pv->sigma_max, c, ws.px_flag, ws.px_pts,
+                                 ws.px_om, ws.px_blk, ws.px_off, ws.hit_count, s);
+    }
+    NIS_CUDA(cudaGetLastError());
+    NIS_CUDA(cudaMemcpyAsync(ws.host_count, ws.hit_count, sizeof(int), cudaMemcpyDeviceToHost, s));
+    NIS_CUDA(cudaStreamSynchronize(s));
+    const int hits = *ws.host_count;
+    long long f, k;
+    nis_part_range(hits, part, parts, &f, &k);
+    *n_hits = hits;
+    *first = (int)f;
+    *count = (int)k;
+    if (k > capacity) return fail(ctx, NIS_ERR_INVALID_ARG, "capacity below the part's hit count");
+    if (k == 0) return NIS_OK;
+    {
+        ProfScope ps(ctx, "hits", s);
+        launch_hits_range(ws.px_flag, ws.px_pts, ws.px_om, ws.px_off, pixels, f, (int)k,
+                          ws.hit_pts, ws.hit_omega, d_pix, s);
+    }
+    NIS_CUDA(cudaGetLastError());
+    return shade_impl(ctx, *pv, *pl, *pw, m, ws.hit_pts, ws.hit_omega, (int)k, d_rgb, nullptr, s);
+}
+
+nis_status nis_scatter_part(nis_ctx *ctx, const float *d_rgb, const int *d_pix, int n,
+                            float *d_image, int n_pixels, nis_stream stream) {
+    if (!ctx) return NIS_ERR_INVALID_ARG;
+    if (n < 0 || n_pixels < 0 || (n > 0 && (!d_rgb || !d_pix || !d_image)))
+        return fail(ctx, NIS_ERR_INVALID_ARG, "NULL buffer or negative size");
+    if (n == 0) return NIS_OK;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    {
+        ProfScope ps(ctx, "other", s);
+        launch_scatter_rgb(d_rgb, d_pix, n, d_image, n_pixels, s);
+    }
+    NIS_CUDA(cudaGetLastError());
+    return NIS_OK;
 }
 
 nis_status nis_release(nis_ctx *ctx, nis_handle h) {

@@ -415,8 +415,17 @@ struct CameraArgs {
 void launch_find_hits(const float *rho0, int n, const float *sigma_max, const CameraArgs &c,
                       int *hit_flag, float *points, float *omega, int *pix_index,
                       int *counter, cudaStream_t s);
+// Hits in pixel order: per-pixel flag/point/direction, hit counts per 256-pixel block and
+// their exclusive scan (offsets: nb + 1 ints, nb = ceil(pixels / 256); *total = the hits).
+void launch_find_hits_ordered(const float *rho0, int n, const float *sigma_max,
+                              const CameraArgs &c, int *flag, float *pts_px, float *om_px,
+                              int *block_count, int *offsets, int *total, cudaStream_t s);
+// Hits first .. first + count - 1 of that order, compacted into pts/om/pix.
+void launch_hits_range(const int *flag, const float *pts_px, const float *om_px,
+                       const int *offsets, int pixels, long long first, int count, float *pts,
+                       float *om, int *pix, cudaStream_t s);
 void launch_scatter_rgb(const float *rgb, const int *pix_index, int count, float *image,
-                        cudaStream_t s, bool accumulate = false);
+                        int n_pixels, cudaStream_t s, bool accumulate = false);
 
 // ---- tensor-core dense layer (k_mlp_tc.cu) ------------------------------------------------
 constexpr int kEpiPlain = 0, kEpiFc1 = 1, kEpiFc2 = 2, kEpiRelu = 3, kEpiDecode = 4;

@@ -313,7 +313,7 @@ nis_status prepare(nis_server *S, Req *q) {
 // Image of a finished request: scatter the shaded points and copy to page-locked staging.
 nis_status schedule_output(nis_server *S, Req *q) {
     cudaStream_t s = S->shade;
-    launch_scatter_rgb(q->rgb, q->pix, q->n_points, q->img, s);
+    launch_scatter_rgb(q->rgb, q->pix, q->n_points, q->img, q->pixels, s);
     q->h_img_bytes = (size_t)q->pixels * 12;
     if (cudaMallocHost(&q->h_img, q->h_img_bytes) != cudaSuccess ||
         cudaMemcpyAsync(q->h_img, q->img, q->h_img_bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess ||

@@ -109,6 +109,14 @@ _SIGS = {
     "nis_render_frame_lights": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(C.c_uint64), C.c_int,
                                           C.c_uint64, C.POINTER(Material), C.POINTER(Camera),
                                           C.c_void_p, C.c_void_p]),
+    "nis_part_range": (C.c_int, [C.c_longlong, C.c_int, C.c_int, C.POINTER(C.c_longlong),
+                                 C.POINTER(C.c_longlong)]),
+    "nis_render_frame_part": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint64,
+                                        C.POINTER(Material), C.POINTER(Camera), C.c_int, C.c_int,
+                                        C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int),
+                                        C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_void_p]),
+    "nis_scatter_part": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int,
+                                   C.c_void_p]),
     "nis_release": (C.c_int, [C.c_void_p, C.c_uint64]),
     "nis_sync": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "nis_volume_info": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(C.c_int), C.c_int * 16,
@@ -169,6 +177,21 @@ def lib():
             fn.argtypes = args
         _lib = h
     return _lib
+
+
+def part_range(n: int, part: int, parts: int) -> tuple[int, int]:
+    """(first, count) of range `part` of `parts` equal contiguous ranges over n items (host
+    only; no device needed)."""
+    first, count = C.c_longlong(), C.c_longlong()
+    st = lib().nis_part_range(int(n), int(part), int(parts), C.byref(first), C.byref(count))
+    if st != NIS_OK:
+        raise NisError(st, f"bad range request: n={n} part={part} parts={parts}")
+    return first.value, count.value
+
+
+def part_capacity(pixels: int, parts: int) -> int:
+    """Rows a part's buffers need for any frame of `pixels` pixels split `parts` ways."""
+    return -(-int(pixels) // int(parts))
 
 
 def material(m: dict) -> Material:
@@ -409,6 +432,50 @@ class Context:
                                                      C.byref(m), C.byref(c), _ptr(out),
                                                      _stream(stream)))
         return out
+
+    def render_frame_part(self, vol, light, weights, mat: dict, cam: dict, part: int, parts: int,
+                          rgb=None, pix=None, stream=None):
+        """Range `part` of `parts` of the frame's shading points (pixel order): returns
+        (rgb[count, 3], pix[count], n_hits, first).  rgb/pix, if given, are device buffers of
+        at least part_capacity(width * height, parts) rows."""
+        c = camera(cam)
+        cap = part_capacity(c.width * c.height, parts) if parts >= 1 else 1
+        dev = f"cuda:{self.device}"
+        if rgb is None:
+            rgb = torch.empty((cap, 3), dtype=torch.float32, device=dev)
+        if pix is None:
+            pix = torch.empty((cap,), dtype=torch.int32, device=dev)
+        for t, shape, dt in ((rgb, 3, torch.float32), (pix, None, torch.int32)):
+            if (t.dtype != dt or not t.is_cuda or not t.is_contiguous()
+                    or (shape is not None and (t.dim() != 2 or t.shape[1] != shape))
+                    or (shape is None and t.dim() != 1)):
+                raise ValueError("rgb must be contiguous float32 CUDA (rows, 3), pix int32 (rows,)")
+        capacity = min(rgb.shape[0], pix.shape[0])
+        m = material(mat)
+        n_hits, first, count = C.c_int(), C.c_int(), C.c_int()
+        self._check(self.lib.nis_render_frame_part(self.h, vol, light, weights, C.byref(m),
+                                                   C.byref(c), int(part), int(parts), _ptr(rgb),
+                                                   _ptr(pix), capacity, C.byref(n_hits),
+                                                   C.byref(first), C.byref(count),
+                                                   _stream(stream)))
+        k = count.value
+        return rgb[:k], pix[:k], n_hits.value, first.value
+
+    def scatter_part(self, rgb, pix, image, stream=None):
+        """image.view(-1, 3)[pix[i]] = rgb[i] on the device (pixels outside the image are
+        skipped); image is a contiguous float32 CUDA tensor whose last dimension is 3."""
+        n = int(pix.shape[0])
+        if rgb.shape[0] < n:
+            raise ValueError("fewer rgb rows than pixel indices")
+        for t in (rgb, pix, image):
+            if not t.is_cuda or not t.is_contiguous():
+                raise ValueError("scatter_part takes contiguous CUDA tensors")
+        if rgb.dtype != torch.float32 or image.dtype != torch.float32 or pix.dtype != torch.int32:
+            raise ValueError("rgb/image float32, pix int32")
+        n_pixels = image.numel() // 3
+        self._check(self.lib.nis_scatter_part(self.h, _ptr(rgb), _ptr(pix), n, _ptr(image),
+                                              n_pixels, _stream(stream)))
+        return image
 
     def find_hits(self, vol, cam: dict, stream=None):
         c = camera(cam)
