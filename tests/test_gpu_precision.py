@@ -125,3 +125,53 @@ def test_bf16_cnn_against_fp64_on_the_same_inputs(env):
           f"{err.max() / scale:.3g}, mean |d| {err.mean() / scale:.3g} of the output range")
     assert err.max() <= 3e-2 * scale
     assert err.mean() <= 2e-3 * scale
+
+
+def test_precision_study_config3_million_pixels(env):
+    """The precision study as its workload states it: the 64^3 fBm volume seen through a
+    1024x1024 orthographic camera (1,048,576 sampled pixels; the 482,255 that hit the medium
+    are the shading points), rendered in FP32, BF16 and FP8.  BF16 and FP8 are compared with
+    the FP32 path over every hit pixel, and all three with the FP64 oracle on 4096 hit pixels
+    that the oracle finds and shades by itself.  FP32 agreeing with FP64 there to 1e-4 is what
+    lets the comparison against FP32 over all hit pixels stand for one against FP64."""
+    ctx = env["ctx"]
+    cfg = synth.config(3)
+    vol, weights, mat, cam = env["vol"], env["weights"], cfg["material"], cfg["camera"]
+    imgs = {}
+    for name, w in (("f32", env["w32"]), ("bf16", env["wbf"]), ("fp8", env["wf8"])):
+        imgs[name] = ctx.render_frame(env["v"], env["l"], w, mat, cam).cpu().numpy()
+    ctx.sync(timeout_ms=120000)
+    ref32 = imgs["f32"]
+    hit = np.abs(ref32).sum(-1) > 0
+    n_hit = int(hit.sum())
+    assert n_hit >= 400_000, n_hit
+    stats = {}
+    for name in ("bf16", "fp8"):
+        assert np.array_equal(np.abs(imgs[name]).sum(-1) > 0, hit)
+        e = rel_err(imgs[name][hit], ref32[hit])
+        stats[name] = (float(e.mean()), float(np.percentile(e, 99)), float(e.max()))
+        print(f"\n[precision] config 3, {name} vs FP32 over {n_hit} hit pixels of 1024x1024: "
+              f"mean rel {stats[name][0]:.3g}, p99 {stats[name][1]:.3g}, max {stats[name][2]:.3g}")
+    # the oracle's own hits on a seeded sample of pixels, shaded in FP64
+    levels, tl, table = O.prepare(vol, cfg["light"], mat["g"])
+    o, d = O.camera_rays(cam)
+    rng = np.random.default_rng(33)
+    idx = rng.choice(o.shape[0] * o.shape[1], 12000, replace=False)
+    ohit, pts, margin = O.hit_search(levels[0], cfg["sigma_max"], o.reshape(-1, 3)[idx],
+                                     d.reshape(-1, 3)[idx])
+    amb = O.layer_geometry(pts, cfg["light"], cfg["n"])[4].min(axis=1) < 1e-4
+    sel = ohit & (margin > 1e-5) & ~amb
+    sel_idx = idx[sel][:4096]
+    assert len(sel_idx) == 4096
+    ref = O.shade_points(pts[sel][:4096], -d.reshape(-1, 3)[sel_idx], cfg["light"], levels, tl,
+                         table, weights, mat)
+    err64 = {}
+    for name in ("f32", "bf16", "fp8"):
+        got = imgs[name].reshape(-1, 3)[sel_idx]
+        e = rel_err(got, ref)
+        err64[name] = (float(e.mean()), float(e.max()))
+        print(f"[precision] config 3, {name} vs FP64 oracle on 4096 pixels: mean rel "
+              f"{err64[name][0]:.3g}, max {err64[name][1]:.3g}")
+    assert err64["f32"][1] <= 1e-4
+    assert err64["bf16"][0] <= 2e-2 and stats["bf16"][0] <= 2e-2
+    assert err64["fp8"][0] <= 0.25 and stats["fp8"][0] <= 0.25
