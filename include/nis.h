@@ -291,7 +291,7 @@ nis_status nis_update_volume(nis_ctx *ctx, nis_volume vol, const void *density, 
  *   calls whose work overlaps on the GPU (different streams, no ordering) race on it and
  *   give wrong results.  Serialise them (one stream, or events). */
 #define NIS_STATIC_MAX_POINTS 512
-#define NIS_STATIC_SCRATCH_BYTES 24979456
+#define NIS_STATIC_SCRATCH_BYTES 25151488
 nis_status nis_shade_points_static(nis_ctx *ctx, nis_volume vol, nis_light light,
                                    nis_weights w, const nis_material *m,
                                    const float *d_points, const float *d_omega, int n,

@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kThreads, 2) cnn_f32_kernel(const float *__res
 #pragma unroll
         for (int i = 0; i < kXPer; ++i) {
             const int idx = tid + i * kThreads, q = idx / kLat, t = idx % kLat;
-            xr[i] = (idx < kPts * kLat && q < np) ? H_T[((size_t)(p0 + q) * kLayers + k) * kLat + t] : 0.f;
+            xr[i] = (idx < kPts * kLat && q < np) ? H_T[((size_t)(p0 + q) * kLayers + k) * kLatT + t] : 0.f;
         }
         __syncthreads();                                  // weights ready / previous group done
 #pragma unroll

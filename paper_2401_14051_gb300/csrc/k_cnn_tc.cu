@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2)
 #pragma unroll
         for (int i = 0; i < kXPer; ++i) {
             const int idx = tid + i * kThreadsTC, q = idx / kLat, t = idx % kLat;
-            xr[i] = (idx < kGP * kLat && q < np) ? H_T[((size_t)(p0 + q) * kLayers + k) * kLat + t] : 0.f;
+            xr[i] = (idx < kGP * kLat && q < np) ? H_T[((size_t)(p0 + q) * kLayers + k) * kLatT + t] : 0.f;
         }
         __syncthreads();                           // previous group done with x, y1 and TMEM
 #pragma unroll

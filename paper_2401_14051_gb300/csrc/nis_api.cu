@@ -424,7 +424,7 @@ nis_status ensure_workspace(nis_ctx *ctx, int cap, cudaStream_t s) {
     size_t n = (size_t)cap;
     nis_status st;
     if ((st = dev_alloc_t(ctx, n * kLayers * kLat, &w.H_rho, s))) return st;
-    if ((st = dev_alloc_t(ctx, n * kLayers * kLat, &w.H_T, s))) return st;
+    if ((st = dev_alloc_t(ctx, n * kLayers * kLatT, &w.H_T, s))) return st;
     if ((st = dev_alloc_t(ctx, n * kLayers * kLat, &w.H_f, s))) return st;
     if ((st = dev_alloc_t(ctx, n * kLayers * 8, &w.v, s))) return st;
     if ((st = dev_alloc_t(ctx, n * kLayers * 3, &w.w_se, s))) return st;
@@ -464,7 +464,7 @@ nis_status ensure_workspace_tc(nis_ctx *ctx, WorkspaceBf &w, int parts, int cap,
     for (int t = 0; t < 3; ++t)
         if ((st = dev_alloc_t(ctx, P * n * 2 * kWidth, &w.mrg_in[t], s))) return st;
     if ((st = dev_alloc_t(ctx, P * n * 3 * kWidth, &w.head_in, s))) return st;
-    if ((st = dev_alloc_t(ctx, n * kLayers * kLat, &w.H_T, s))) return st;
+    if ((st = dev_alloc_t(ctx, n * kLayers * kLatT, &w.H_T, s))) return st;
     if ((st = dev_alloc_t(ctx, n * kLayers * 3, &w.w_se, s))) return st;
     if ((st = dev_alloc_t(ctx, n * kCfg, &w.cfg, s))) return st;
     if ((st = dev_alloc_t(ctx, n * kLayers * 8, &w.v, s))) return st;
@@ -638,7 +638,7 @@ nis_status ensure_workspace_fp8(nis_ctx *ctx, int cap, cudaStream_t s) {
     }
     if ((st = dev_alloc_t(ctx, n * kWidth, &w.E, s))) return st;
     if ((st = dev_alloc_t(ctx, n * kWidth, &w.H, s))) return st;
-    if ((st = dev_alloc_t(ctx, n * kLayers * kLat, &w.H_T, s))) return st;
+    if ((st = dev_alloc_t(ctx, n * kLayers * kLatT, &w.H_T, s))) return st;
     if ((st = dev_alloc_t(ctx, n * kLayers * 3, &w.w_se, s))) return st;
     if ((st = dev_alloc_t(ctx, n * kCfg, &w.cfg, s))) return st;
     if ((st = dev_alloc_t(ctx, n * kLayers * 8, &w.v, s))) return st;
@@ -668,6 +668,14 @@ struct Mixed {                        // per-point request descriptors of a mixe
     const float *dec_rows;
 };
 
+// The transmittance lattices of points off .. off + cnt - 1 from the workspace (rows of
+// kLatT) to a caller's [n][12][225] buffer.
+cudaError_t copy_ht(float *dst, const float *src, int off, int cnt, cudaStream_t s) {
+    if (!dst || cnt <= 0) return cudaSuccess;
+    return cudaMemcpy2DAsync(dst + (size_t)off * kLayers * kLat, kLat * sizeof(float), src,
+                             kLatT * sizeof(float), kLat * sizeof(float), (size_t)cnt * kLayers,
+                             cudaMemcpyDeviceToDevice, s);
+}
 nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, const Weights &wt,
                            const nis_material *m, const float *table, const float *pts,
                            const float *om, int n, float *rgb, const nis_debug_out *dbg,
@@ -931,7 +939,7 @@ nis_status shade_impl(nis_ctx *ctx, const Volume &vol, const Light &light, const
                                        cudaMemcpyDeviceToDevice, s);
             };
             NIS_CUDA(cp(dbg->H_rho, w.H_rho, (size_t)kLayers * kLat));
-            NIS_CUDA(cp(dbg->H_T, w.H_T, (size_t)kLayers * kLat));
+            NIS_CUDA(copy_ht(dbg->H_T, w.H_T, off, cnt, s));
             NIS_CUDA(cp(dbg->H_f, w.H_f, (size_t)kLayers * kLat));
             NIS_CUDA(cp(dbg->v, w.v, (size_t)kLayers * 8));
             NIS_CUDA(cp(dbg->X_T, w.X_T, (size_t)kLayers * kDT));
@@ -1128,7 +1136,7 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
                 return cudaMemcpyAsync(dst + per * off, src, per * cnt * sizeof(float),
                                        cudaMemcpyDeviceToDevice, s);
             };
-            if (!paper) NIS_CUDA(cp(dbg->H_T, w.H_T, (size_t)kLayers * kLat));   // paper: by the gather
+            if (!paper) NIS_CUDA(copy_ht(dbg->H_T, w.H_T, off, cnt, s));   // paper: by the gather
             NIS_CUDA(cp(dbg->v, w.v, (size_t)kLayers * 8));
             NIS_CUDA(cp(dbg->w_se, w.w_se, (size_t)kLayers * 3));
         }
@@ -1255,7 +1263,7 @@ nis_status shade_impl_fp8(nis_ctx *ctx, const Volume &vol, const Light &light, c
                 return cudaMemcpyAsync(dst + per * off, src, per * cnt * sizeof(float),
                                        cudaMemcpyDeviceToDevice, s);
             };
-            NIS_CUDA(cp(dbg->H_T, w.H_T, (size_t)kLayers * kLat));
+            NIS_CUDA(copy_ht(dbg->H_T, w.H_T, off, cnt, s));
             NIS_CUDA(cp(dbg->v, w.v, (size_t)kLayers * 8));
             NIS_CUDA(cp(dbg->w_se, w.w_se, (size_t)kLayers * 3));
         }
@@ -1960,17 +1968,24 @@ nis_status render_impl(nis_ctx *ctx, nis_volume vol, const nis_light *lights, in
         if ((st = ensure_pairs(ctx, *pv, *l, s))) return st;
     Workspace &ws = ctx->ws;
     int pixels = c.width * c.height;
-    if ((st = ensure_hit_ws(ctx, pixels, s))) return st;
-    NIS_CUDA(cudaMemsetAsync(ws.hit_count, 0, sizeof(int), s));
+    if ((st = ensure_hit_ws(ctx, pixels, s)) || (st = ensure_px_ws(ctx, pixels, s))) return st;
+    // the shading points in pixel order: neighbouring points of the list are neighbouring
+    // pixels, which the gathers' lane mapping relies on for coherent loads
     {
         ProfScope ps(ctx, "hits", s);
-        launch_find_hits(pv->data, pv->n, pv->sigma_max, c, nullptr, ws.hit_pts, ws.hit_omega,
-                         ws.hit_pix, ws.hit_count, s);
+        launch_find_hits_ordered(pv->data, pv->n, pv->sigma_max, c, ws.px_flag, ws.px_pts,
+                                 ws.px_om, ws.px_blk, ws.px_off, ws.hit_count, s);
     }
     NIS_CUDA(cudaGetLastError());
     NIS_CUDA(cudaMemcpyAsync(ws.host_count, ws.hit_count, sizeof(int), cudaMemcpyDeviceToHost, s));
     NIS_CUDA(cudaStreamSynchronize(s));
     int count = *ws.host_count;
+    if (count > 0) {
+        ProfScope ps(ctx, "hits", s);
+        launch_hits_range(ws.px_flag, ws.px_pts, ws.px_om, ws.px_off, pixels, 0, count,
+                          ws.hit_pts, ws.hit_omega, ws.hit_pix, s);
+    }
+    NIS_CUDA(cudaGetLastError());
     NIS_CUDA(cudaMemsetAsync(d_rgb_out, 0, sizeof(float) * 3 * (size_t)pixels, s));
     if (count > 0) {
         for (int q = 0; q < n_lights; ++q) {

@@ -18,7 +18,8 @@ constexpr int kDiffuse = 8;
 constexpr int kHighlight = 4;
 constexpr int kLatA = 5, kLatB = 5, kLatC = 9;
 constexpr int kLat = 225;            // lattice points per layer
-constexpr int kLatPad = 232;         // BF16 feature row per layer, padded to 16 bytes
+constexpr int kLatPad = 240;         // BF16 feature row per layer: 480 bytes, 32-byte aligned
+constexpr int kLatT = 232;           // FP32 transmittance lattice row (H_T): 928 bytes, 32-byte aligned
 constexpr int kPhaseSets = 5;        // all diffuse layers share one set; one per highlight
 constexpr int kAlpha = 1024;         // alpha nodes of the phase table
 constexpr int kRings = 16;           // cap quadrature: rings (angle midpoints) ...
@@ -314,7 +315,8 @@ struct GatherArgs {
     float albedo[3];
     const float *se;                 // FP32 weights base; SE offsets below
     size_t se_w1[kLayers], se_b1[kLayers], se_w2[kLayers], se_b2[kLayers];
-    float *H_rho, *H_T, *H_f;        // [count][12][225] (H_rho, H_f may be null when Hb_* set)
+    float *H_rho, *H_T, *H_f;        // H_T [count][12][kLatT]; H_rho, H_f [count][12][225], may be
+                                     // null when Hb_* are set
     __nv_bfloat16 *Hb_rho, *Hb_f;    // optional BF16 copies [count][12][kLatPad] (pad zeroed)
     uint8_t *H8_rho, *H8_f;          // optional e4m3 copies [count][12][kLatPad8], each layer's
     float *f8_scale;                 // row scaled by f8_scale[count][12][2] = max / 448

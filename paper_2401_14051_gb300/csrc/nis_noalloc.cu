@@ -16,7 +16,7 @@ constexpr size_t round64(size_t n) { return (n + 63) & ~size_t(63); }   // 256-b
 // float offsets of the sub-buffers inside the scratch array
 constexpr size_t kOffHrho = 0;
 constexpr size_t kOffHT = kOffHrho + round64(kMaxPts * kLayers * kLat);
-constexpr size_t kOffHf = kOffHT + round64(kMaxPts * kLayers * kLat);
+constexpr size_t kOffHf = kOffHT + round64(kMaxPts * kLayers * kLatT);
 constexpr size_t kOffV = kOffHf + round64(kMaxPts * kLayers * kLat);
 constexpr size_t kOffW = kOffV + round64(kMaxPts * kLayers * 8);
 constexpr size_t kOffCfg = kOffW + round64(kMaxPts * kLayers * 3);
