@@ -49,6 +49,7 @@ GATHER_BYTES_PER_POINT = 4 * (3 * 12 * 225 + 12 * 8 + 12 * 3 + 5 + 6)
 # transmittance at 12 x 225 template points; FP32) written once, plus the density pyramid
 # and the transmittance pyramid read once per frame (levels sum to ~8/7 of the finest).
 GATHER_FEATURE_BYTES = 4 * 5400
+GATHER_WRITTEN_BYTES_F32 = 12 * (232 * 4 + 3 * 2 * 240 * 2)
 
 
 def gather_algorithmic_bytes(n_points: int, n: int) -> float:
@@ -885,11 +886,20 @@ def run_nis(args):
     g_ms, g_n = fam["gather"]
     g_bytes = gather_algorithmic_bytes(n_points, cfg["n"]) * args.steps / max(g_n, 1)
     g_gbs = g_bytes / (g_ms / 1e3 / max(g_n, 1)) / 1e9
-    gather_roof = {"bound": "hbm", "unit": "GB/s", "kernel": "gather_kernel<0>",
+    # what this launch design writes per point (FP32 frame): H_T rows of 232 FP32 and the
+    # three BF16 parts of the density and phase rows of 240, per layer
+    g_written = GATHER_WRITTEN_BYTES_F32 * n_points * args.steps / max(g_n, 1)
+    gather_roof = {"bound": "hbm", "unit": "GB/s",
+                   "kernel": "gather_kernel<3> (one lane per shading point; FP32 H_T and "
+                             "three-part BF16 density and phase rows)",
                    "achieved": g_gbs, "peak": peaks["hbm_gbs"], "frac": g_gbs / peaks["hbm_gbs"],
                    "work_per_launch": g_bytes, "avg_launch_ms": g_ms / max(g_n, 1),
                    "peak_source": f"{peaks['source']} STREAM copy",
-                   "work": "5400 FP32 features per point + density and transmittance pyramids once"}
+                   "work": "5400 FP32 features per point + density and transmittance pyramids once",
+                   "written": {"bytes_per_point": GATHER_WRITTEN_BYTES_F32,
+                               "gb_s": g_written / (g_ms / 1e3 / max(g_n, 1)) / 1e9,
+                               "note": "bytes this launch design writes (the FP32-accurate "
+                                       "split), not algorithmic bytes"}}
     roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak,
                  "traffic": tr["bytes_per_launch"] if tr else None,
                  "family": dom, "launches": dom_n, "avg_launch_ms": dom_ms / max(dom_n, 1),
