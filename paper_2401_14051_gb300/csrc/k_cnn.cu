@@ -40,6 +40,25 @@ constexpr int kOffW1 = 0, kOffB1 = kOffW1 + 27 * kCnnCh, kOffW2 = kOffB1 + kCnnC
               kOffB2 = kOffW2 + kCnnCh * kW2Ci, kOffX = kOffB2 + kCnnCh,
               kOffY1 = kOffX + kPts * kLat, kSmemFloats = kOffY1 + kPts * kY1;
 static_assert(kOffW2 % 4 == 0 && kW2Ci % 4 == 0, "float4 weight loads need 16-byte alignment");
+
+// Packed FP32 pairs (two output channels): acc += w * (v, v) with fma.rn.f32x2, the same
+// rounding per lane as two scalar fmaf.
+typedef unsigned long long f2_t;
+__device__ __forceinline__ f2_t f2_dup(float v) {
+    f2_t r;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ f2_t f2_make(float a, float b) {
+    f2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_fma(f2_t &acc, f2_t w, f2_t v) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(w), "l"(v));
+}
+__device__ __forceinline__ float f2_lo(f2_t a) { return __uint_as_float((unsigned)a); }
+__device__ __forceinline__ float f2_hi(f2_t a) { return __uint_as_float((unsigned)(a >> 32)); }
 }  // namespace
 
 __global__ void __launch_bounds__(kThreads, 2) cnn_f32_kernel(const float *__restrict__ H_T,
@@ -93,38 +112,42 @@ __global__ void __launch_bounds__(kThreads, 2) cnn_f32_kernel(const float *__res
         {
             const int half = tid & 1, r = tid >> 1;            // 144 (q, d, h) rows
             const int q = r / 9, dh = r % 9, d = dh / 3, h = dh % 3;
-            float acc[7][8];
+            f2_t acc[7][4];                                    // channel pairs
 #pragma unroll
-            for (int w = 0; w < 7; ++w)
+            for (int c = 0; c < 4; ++c) {
+                const f2_t b = f2_make(b1[half * 8 + 2 * c], b1[half * 8 + 2 * c + 1]);
 #pragma unroll
-                for (int c = 0; c < 8; ++c) acc[w][c] = b1[half * 8 + c];
+                for (int w = 0; w < 7; ++w) acc[w][c] = b;
+            }
 #pragma unroll
             for (int kd = 0; kd < 3; ++kd)
 #pragma unroll
                 for (int kh = 0; kh < 3; ++kh) {
                     const float *xr = xin + q * kLat + ((d + kd) * 5 + (h + kh)) * 9;
-                    float row[9];
+                    f2_t row[9];
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) row[i] = xr[i];
+                    for (int i = 0; i < 9; ++i) row[i] = f2_dup(xr[i]);
 #pragma unroll
                     for (int kw = 0; kw < 3; ++kw) {
-                        const float4 *wv =
-                            reinterpret_cast<const float4 *>(w1t + ((kd * 3 + kh) * 3 + kw) * kCnnCh + half * 8);
-                        const float4 wa = wv[0], wb = wv[1];
+                        const ulonglong2 *wv = reinterpret_cast<const ulonglong2 *>(
+                            w1t + ((kd * 3 + kh) * 3 + kw) * kCnnCh + half * 8);
+                        const ulonglong2 wa = wv[0], wb = wv[1];
 #pragma unroll
                         for (int w = 0; w < 7; ++w) {
-                            const float v = row[w + kw];
-                            acc[w][0] += wa.x * v; acc[w][1] += wa.y * v; acc[w][2] += wa.z * v;
-                            acc[w][3] += wa.w * v; acc[w][4] += wb.x * v; acc[w][5] += wb.y * v;
-                            acc[w][6] += wb.z * v; acc[w][7] += wb.w * v;
+                            const f2_t v = row[w + kw];
+                            f2_fma(acc[w][0], wa.x, v); f2_fma(acc[w][1], wa.y, v);
+                            f2_fma(acc[w][2], wb.x, v); f2_fma(acc[w][3], wb.y, v);
                         }
                     }
                 }
             float *yo = y1 + q * kY1 + (d * 3 + h) * 7;        // y1[q][ci][d][h][w]
 #pragma unroll
-            for (int c = 0; c < 8; ++c)
+            for (int c = 0; c < 4; ++c)
 #pragma unroll
-                for (int w = 0; w < 7; ++w) yo[(half * 8 + c) * kY1Ci + w] = fmaxf(acc[w][c], 0.f);
+                for (int w = 0; w < 7; ++w) {
+                    yo[(half * 8 + 2 * c) * kY1Ci + w] = fmaxf(f2_lo(acc[w][c]), 0.f);
+                    yo[(half * 8 + 2 * c + 1) * kY1Ci + w] = fmaxf(f2_hi(acc[w][c]), 0.f);
+                }
         }
         __syncthreads();
         // conv2: warp g = input channels g and g + 8, lane = (channel half, point q);
@@ -133,11 +156,11 @@ __global__ void __launch_bounds__(kThreads, 2) cnn_f32_kernel(const float *__res
         float *part = y1;                                 // [g][lane][kPartLd] partial sums
         if (warp < kCiGroups) {
             const int half = lane >> 4, q = lane & 15;
-            float acc[5][8];
+            f2_t acc[5][4];                                    // channel pairs
 #pragma unroll
             for (int w = 0; w < 5; ++w)
 #pragma unroll
-                for (int c = 0; c < 8; ++c) acc[w][c] = 0.f;
+                for (int c = 0; c < 4; ++c) acc[w][c] = 0ull;
             for (int cc = 0; cc < kCnnCh / kCiGroups; ++cc) {
                 const int ci = warp + kCiGroups * cc;
 #pragma unroll
@@ -145,20 +168,19 @@ __global__ void __launch_bounds__(kThreads, 2) cnn_f32_kernel(const float *__res
 #pragma unroll
                     for (int kh = 0; kh < 3; ++kh) {
                         const float *yr = y1 + q * kY1 + ci * kY1Ci + (kd * 3 + kh) * 7;
-                        float row[7];
+                        f2_t row[7];
 #pragma unroll
-                        for (int i = 0; i < 7; ++i) row[i] = yr[i];
+                        for (int i = 0; i < 7; ++i) row[i] = f2_dup(yr[i]);
 #pragma unroll
                         for (int kw = 0; kw < 3; ++kw) {
-                            const float4 *wv = reinterpret_cast<const float4 *>(
+                            const ulonglong2 *wv = reinterpret_cast<const ulonglong2 *>(
                                 w2t + ci * kW2Ci + ((kd * 3 + kh) * 3 + kw) * kCnnCh + half * 8);
-                            const float4 wa = wv[0], wb = wv[1];
+                            const ulonglong2 wa = wv[0], wb = wv[1];
 #pragma unroll
                             for (int w = 0; w < 5; ++w) {
-                                const float v = row[w + kw];
-                                acc[w][0] += wa.x * v; acc[w][1] += wa.y * v; acc[w][2] += wa.z * v;
-                                acc[w][3] += wa.w * v; acc[w][4] += wb.x * v; acc[w][5] += wb.y * v;
-                                acc[w][6] += wb.z * v; acc[w][7] += wb.w * v;
+                                const f2_t v = row[w + kw];
+                                f2_fma(acc[w][0], wa.x, v); f2_fma(acc[w][1], wa.y, v);
+                                f2_fma(acc[w][2], wb.x, v); f2_fma(acc[w][3], wb.y, v);
                             }
                         }
                     }
@@ -169,7 +191,10 @@ __global__ void __launch_bounds__(kThreads, 2) cnn_f32_kernel(const float *__res
 #pragma unroll
             for (int w = 0; w < 5; ++w)
 #pragma unroll
-                for (int c = 0; c < 8; ++c) part[(warp * 32 + lane) * kPartLd + w * 8 + c] = acc[w][c];
+                for (int c = 0; c < 4; ++c) {
+                    part[(warp * 32 + lane) * kPartLd + w * 8 + 2 * c] = f2_lo(acc[w][c]);
+                    part[(warp * 32 + lane) * kPartLd + w * 8 + 2 * c + 1] = f2_hi(acc[w][c]);
+                }
         }
         __syncthreads();
         // output (point q, entry r = position w x 16 + channel co): the eight groups' partial
