@@ -92,7 +92,7 @@ def parse():
     ap.add_argument("--no-split-frame", action="store_true")
     ap.add_argument("--plume-march-frames", type=int, default=8)
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
-    ap.add_argument("--ncu-case", choices=("f32", "bf16", "simt", "sweep"),
+    ap.add_argument("--ncu-case", choices=("f32", "bf16", "simt", "sweep", "frame_f32", "frame_bf16"),
                     help="small case for ncu captures: shade 32,768 points of the 64^3 fBm "
                          "volume twice at this precision (sweep: one shear-warp "
                          "transmittance of a 512^3 FP16 plume toward a light along x), print "
@@ -896,6 +896,7 @@ def run_nis(args):
                    "work_per_launch": g_bytes, "avg_launch_ms": g_ms / max(g_n, 1),
                    "peak_source": f"{peaks['source']} STREAM copy",
                    "work": "5400 FP32 features per point + density and transmittance pyramids once",
+                   "traffic": (recorded_traffic("gather") or {}).get("bytes_per_launch"),
                    "written": {"bytes_per_point": GATHER_WRITTEN_BYTES_F32,
                                "gb_s": g_written / (g_ms / 1e3 / max(g_n, 1)) / 1e9,
                                "note": "bytes this launch design writes (the FP32-accurate "
@@ -955,6 +956,23 @@ def run_ncu_case(args):
         ctx = nis.Context(0)
         v = ctx.upload_volume(synth.plume_volume_torch(512, 9, 128.0))
         ctx.build_transmittance(v, synth.unit_vector(10), 0.6, method=nis.TRANSMITTANCE_SHEAR_WARP)
+        ctx.sync(timeout_ms=60000)
+        ctx.close()
+        print("ok")
+        return
+    if args.ncu_case in ("frame_f32", "frame_bf16"):
+        # the benchmark's volume and view at 800x450 (about 37,000 shading points: the
+        # features still exceed L2, the device holds a few GB)
+        cfg = synth.config(2)
+        cam = dict(cfg["camera"], width=800, height=450)
+        ctx = nis.Context(0)
+        v = ctx.upload_volume(cfg["volume"]())
+        l = ctx.build_transmittance(v, cfg["light"], 0.6)
+        prec = nis.PREC_F32 if args.ncu_case == "frame_f32" else nis.PREC_BF16
+        w = ctx.load_weights(synth.pack_weights(synth.make_weights(cfg["weights_seed"],
+                                                                   cfg["sigma_max"])), prec)
+        for _ in range(2):
+            ctx.render_frame(v, l, w, cfg["material"], cam)
         ctx.sync(timeout_ms=60000)
         ctx.close()
         print("ok")
