@@ -307,8 +307,14 @@ __device__ __forceinline__ void load_pre(const TcGemmArgs &a, int r, int c0, flo
 }
 }  // namespace
 
+// Threads per CTA: producer, MMA and EPI epilogue warps, plus (FP32 split) two more producer
+// warps, so that each of a stage's three parts is issued by its own thread: loads issued by
+// one thread complete one after another, and a split stage has six of them.
 template <int EPI>
-__global__ void __launch_bounds__(64 + 32 * EPI, 1)
+__host__ __device__ constexpr int tc_threads() { return 64 + 32 * EPI + (EPI == 4 ? 64 : 0); }
+
+template <int EPI>
+__global__ void __launch_bounds__(tc_threads<EPI>(), 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                    const __grid_constant__ CUtensorMap map_o1, const __grid_constant__ CUtensorMap map_o2,
                    const __grid_constant__ CUtensorMap map_pre, const __grid_constant__ TcGemmArgs a) {
@@ -347,7 +353,10 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
     const int kslice = a.fp8 ? 32 : 16;                // K elements per MMA (32 bytes)
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < n_stages; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
+        for (int s = 0; s < n_stages; ++s) {
+            tc::mbar_init(&full[s], split3 ? 3 : 1);      // one arrival per producer thread
+            tc::mbar_init(&empty[s], 1);
+        }
         for (int b = 0; b < 2; ++b) { tc::mbar_init(&acc_full[b], 1); tc::mbar_init(&acc_empty[b], EPI); }
         tc::mbar_init(drain, 1);
         for (int i = 0; i < 2 * EPI; ++i) tc::mbar_init(&pre_full[i], 1);
@@ -396,7 +405,11 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
-    if (warp == 0) {
+    // producer threads: warp 0, and with the split warps 2 + EPI and 3 + EPI; producer pi
+    // loads part pi of each first-sweep slab and slab pi of each second-sweep stage
+    const bool producer = warp == 0 || (split3 && EPI == 4 && warp >= 2 + EPI);
+    if (producer) {
+        const int pi = warp == 0 ? 0 : warp - (1 + EPI);
         if (lane == 0) {
             int it = 0;
             for (int tile = blockIdx.x; tile < n_tiles && !*(volatile int *)abort_flag; tile += gridDim.x) {
@@ -409,23 +422,23 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
                         tc::mbar_expect_tx(&full[s], stage_tx);
                         tc::tma_load_2d(st, &map_a, a.a_col0 + step * tk, tile * TM, &full[s]);
                         tc::tma_load_2d(st + b_off, &map_b, step * tk, 0, &full[s]);
-                    } else if (step < n_sweep1) {              // slab `step`, all three parts
-                        tc::mbar_expect_tx(&full[s], stage_tx);
-                        for (int p = 0; p < 3; ++p) {
-                            tc::tma_load_2d(st + p * A_PART3, &map_a, a.a_col0 + step * tk,
-                                            p * a.a_part_rows + tile * TM, &full[s]);
-                            tc::tma_load_2d(st + b_off + p * B_PART3, &map_b, step * tk,
-                                            p * a.b_part_rows, &full[s]);
-                        }
-                    } else {                                   // up to three slabs of A0 B0
+                    } else if (step < n_sweep1) {              // slab `step`, part pi
+                        tc::mbar_expect_tx(&full[s], slab_tx);
+                        tc::tma_load_2d(st + pi * A_PART3, &map_a, a.a_col0 + step * tk,
+                                        pi * a.a_part_rows + tile * TM, &full[s]);
+                        tc::tma_load_2d(st + b_off + pi * B_PART3, &map_b, step * tk,
+                                        pi * a.b_part_rows, &full[s]);
+                    } else {                                   // slab j0 + pi of A0 B0, if any
                         const int j0 = 3 * (step - n_sweep1);
                         const int nb = a.k_tiles - j0 < 3 ? a.k_tiles - j0 : 3;
-                        tc::mbar_expect_tx(&full[s], nb * slab_tx);
-                        for (int j = 0; j < nb; ++j) {
-                            tc::tma_load_2d(st + j * A_PART3, &map_a, a.a_col0 + (j0 + j) * tk,
+                        if (pi < nb) {
+                            tc::mbar_expect_tx(&full[s], slab_tx);
+                            tc::tma_load_2d(st + pi * A_PART3, &map_a, a.a_col0 + (j0 + pi) * tk,
                                             tile * TM, &full[s]);
-                            tc::tma_load_2d(st + b_off + j * B_PART3, &map_b, (j0 + j) * tk, 0,
+                            tc::tma_load_2d(st + b_off + pi * B_PART3, &map_b, (j0 + pi) * tk, 0,
                                             &full[s]);
+                        } else {
+                            tc::mbar_arrive(&full[s]);
                         }
                     }
                 }
@@ -496,7 +509,7 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
             tc::mma_commit(drain);
             tc::mbar_wait(drain, 0, 1u << 20);
         }
-    } else {
+    } else if (warp < 2 + EPI) {
         const int q = warp & 3;                        // TMEM lane quarter of this warp
         // which 32-column chunks this warp takes: every one (EPI 4) or every other (EPI 8)
         const int half = EPI == 8 ? (warp - 2) >> 2 : 0;
@@ -701,11 +714,11 @@ void launch_tc_gemm(const TcGemmArgs &a, const CUtensorMap &map_a, const CUtenso
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if (a.n_pass > 1) {
-        cfg.blockDim = dim3(64 + 32 * 4);
+        cfg.blockDim = dim3(tc_threads<4>());
         cfg.dynamicSmemBytes = smem_bytes<4>();
         cudaLaunchKernelEx(&cfg, tc_gemm_kernel<4>, map_a, map_b, o1, o2, pr, a);
     } else {
-        cfg.blockDim = dim3(64 + 32 * 8);
+        cfg.blockDim = dim3(tc_threads<8>());
         cfg.dynamicSmemBytes = smem_bytes<8>();
         cudaLaunchKernelEx(&cfg, tc_gemm_kernel<8>, map_a, map_b, o1, o2, pr, a);
     }
