@@ -65,14 +65,44 @@ void paper_template(double unit[kPaperPts][3], double D[kLayers], float q[kPaper
     }
 }
 
-// One CTA per shading point, thread t < 266 owns template point t.  Each samples the
-// density at its layer's level and the transmittance at every level, reads its phase
-// column; the squeeze statistics of each layer are then summed in point order by one thread
-// per layer (deterministic) and the SE excitation follows.
-__global__ void __launch_bounds__(288, 4) gather_paper_kernel(const __grid_constant__ PaperGatherArgs a) {
-    __shared__ float s_rho[kPaperPts], s_f[kPaperPts], s_T[kPaperPts];
-    __shared__ float s_alpha;
-    const int p = blockIdx.x, t = threadIdx.x;
+// 16 bytes to a 16-byte aligned global address; two floats as BF16 (lo at the lower address).
+__device__ __forceinline__ void st_v4p(void *p, uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
+    asm volatile("st.global.v4.b32 [%0], {%1, %2, %3, %4};" :: "l"(p), "r"(x), "r"(y), "r"(z),
+                 "r"(w) : "memory");
+}
+__device__ __forceinline__ uint32_t pack_bf2p(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
+// The BF16 parts of 8 consecutive operand columns (x = x0 + x1 + x2 with three parts, each
+// part the remainder rounded to BF16), one 16-byte store per part.
+__device__ __forceinline__ void store_parts8(__nv_bfloat16 *dst, size_t part, int parts,
+                                             float (&v)[8]) {
+    for (int q = 0; q < parts; ++q) {
+        uint32_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            w[i] = pack_bf2p(v[2 * i], v[2 * i + 1]);
+            v[2 * i] -= __uint_as_float(w[i] << 16);
+            v[2 * i + 1] -= __uint_as_float(w[i] & 0xffff0000u);
+        }
+        st_v4p(dst + q * part, w[0], w[1], w[2], w[3]);
+    }
+}
+
+constexpr int kPWarps = 4;                             // warps per CTA, 32 points each
+
+// One lane per shading point, a warp over 32 consecutive points (neighbouring pixels of a
+// frame, so a warp's samples of one template point touch few cache lines).  Each lane walks
+// its point's 266 template points layer by layer: the density at the layer's level, the
+// transmittance at every level, the phase column; it sums each layer's squeeze statistics
+// in point order in registers, then computes the layer's SE excitation, and writes its BF16
+// operand columns 8 at a time (16-byte stores).
+__global__ void __launch_bounds__(kPWarps * 32, 4) gather_paper_kernel(const __grid_constant__ PaperGatherArgs a) {
+    const int p = (blockIdx.x * kPWarps + (threadIdx.x >> 5)) * 32 + (threadIdx.x & 31);
+    if (p >= a.count) return;
     const float lx = a.lx, ly = a.ly, lz = a.lz;
     const float px = a.points[3 * p], py = a.points[3 * p + 1], pz = a.points[3 * p + 2];
     float ox = a.omega[3 * p], oy = a.omega[3 * p + 1], oz = a.omega[3 * p + 2];
@@ -101,10 +131,16 @@ __global__ void __launch_bounds__(288, 4) gather_paper_kernel(const __grid_const
     float tt = fminf(fmaxf(alpha * ((kAlpha - 1) / 3.14159265358979f), 0.f), (float)(kAlpha - 1));
     const int ja = min((int)floorf(tt), kAlpha - 2);
     const float wa = tt - ja;
+    const float *tab0 = a.table + (size_t)ja * kPaperPts, *tab1 = tab0 + kPaperPts;
     const int N = a.rho.n[0], L = a.rho.levels;
-    if (t < kPaperPts) {
-        const int k = paper_layer_of(t);
-        const float ux = a.unit[t][0], uy = a.unit[t][1], uz = a.unit[t][2];
+    const int nlv = L < kLevelWeights ? L : kLevelWeights;
+    const float lb = __ldg(a.level_b);
+    const bool bf = a.Hb_rho != nullptr;
+    __nv_bfloat16 *row_r = bf ? a.Hb_rho + (size_t)p * a.ld_rf : nullptr;
+    __nv_bfloat16 *row_f = bf ? a.Hb_f + (size_t)p * a.ld_rf : nullptr;
+    __nv_bfloat16 *row_t = bf ? a.Hb_T + (size_t)p * a.ld_t : nullptr;
+
+    for (int k = 0; k < kLayers; ++k) {
         float cx = px, cy = py, cz = pz, radius;
         int m;
         if (k < kDiffuse) {
@@ -119,73 +155,48 @@ __global__ void __launch_bounds__(288, 4) gather_paper_kernel(const __grid_const
             const float z = log2f(radius * a.D[k] * (float)N) + 0.5f;
             m = (int)fminf(fmaxf(floorf(z), 0.f), (float)(L - 1));
         }
-        const float sx = cx + radius * (ux * exx + uy * eyx + uz * ezx);
-        const float sy = cy + radius * (ux * exy + uy * eyy + uz * ezy);
-        const float sz = cz + radius * (ux * exz + uy * eyz + uz * ezz);
-        // the density at the layer's level; the transmission feature weighs the 11 finest
-        // levels (a grid has at most 12).  Plain float grids, not the interleaved pairs: the
-        // transmittance alone is read at every level (measured 2 % faster than the pairs)
-        const float rho = sample_border(a.rho.lv[m], a.rho.n[m], sx, sy, sz, 0.0f);
-        float T = __ldg(a.level_b);
-        for (int lv = 0; lv < L && lv < kLevelWeights; ++lv)
-            T = fmaf(__ldg(a.level_w + lv), sample_border(a.T.lv[lv], a.T.n[lv], sx, sy, sz, 1.0f), T);
-        const float f0 = __ldg(a.table + (size_t)ja * kPaperPts + t);
-        const float f1 = __ldg(a.table + (size_t)(ja + 1) * kPaperPts + t);
-        const float f = f0 + wa * (f1 - f0);
-        if (a.H_rho) {
-            const size_t o = (size_t)p * kPaperPts + t;
-            a.H_rho[o] = rho;
-            a.H_f[o] = f;
-            a.H_T[o] = T;
-        }
-        if (a.Hb_rho) {                        // BF16 parts, the layer's padded columns
-            const int col = paper_first_pad(k) + (t - paper_first(k));
-            __nv_bfloat16 *dr = a.Hb_rho + (size_t)p * a.ld_rf + col;
-            __nv_bfloat16 *df = a.Hb_f + (size_t)p * a.ld_rf + col;
-            __nv_bfloat16 *dt = a.Hb_T + (size_t)p * a.ld_t + col;
-            float r0 = rho, r1 = f, r2 = T;
-            for (int q = 0; q < a.parts; ++q) {
-                const __nv_bfloat16 b0 = __float2bfloat16_rn(r0), b1 = __float2bfloat16_rn(r1),
-                                    b2 = __float2bfloat16_rn(r2);
-                dr[q * a.part_rf] = b0;
-                df[q * a.part_rf] = b1;
-                dt[q * a.part_t] = b2;
-                r0 -= __bfloat162float(b0);
-                r1 -= __bfloat162float(b1);
-                r2 -= __bfloat162float(b2);
-            }
-        }
-        s_rho[t] = rho; s_f[t] = f; s_T[t] = T;
-    } else if (a.Hb_rho) {
-        // zeros in the layers' padding columns and the tail: the MMAs read whole operand
-        // boxes (32 or 64 columns), whose columns beyond a layer meet zero weights and so
-        // must hold finite values
-        for (int z = t - kPaperPts; z < kPaperPadTail - kPaperPts; z += blockDim.x - kPaperPts) {
-            int col = -1, seen = 0;
-            for (int k = 0; k < kLayers && col < 0; ++k) {
-                const int padn = paper_count_pad(k) - paper_count(k);
-                if (z < seen + padn) col = paper_first_pad(k) + paper_count(k) + (z - seen);
-                seen += padn;
-            }
-            if (col < 0) col = kPaperPad + (z - seen);
-            for (int q = 0; q < a.parts; ++q) {
-                a.Hb_rho[(size_t)p * a.ld_rf + col + q * a.part_rf] = __float2bfloat16_rn(0.f);
-                a.Hb_f[(size_t)p * a.ld_rf + col + q * a.part_rf] = __float2bfloat16_rn(0.f);
-                a.Hb_T[(size_t)p * a.ld_t + col + q * a.part_t] = __float2bfloat16_rn(0.f);
-            }
-        }
-    }
-    if (t == 0) s_alpha = alpha;
-    __syncthreads();
-    if (t < kLayers) {
-        const int k = t, f0 = paper_first(k), n = paper_count(k);
+        const float *rho_lv = a.rho.lv[m];
+        const int rho_n = a.rho.n[m];
+        const int f0 = paper_first(k), n = paper_count(k), c0 = paper_first_pad(k);
         float s0 = 0.f, s1 = 0.f, s2 = 0.f, m0 = -3.0e38f, m1 = -3.0e38f, m2 = -3.0e38f;
-        for (int i = f0; i < f0 + n; ++i) {
-            s0 += s_rho[i]; s1 += s_f[i]; s2 += s_T[i];
-            m0 = fmaxf(m0, s_rho[i]); m1 = fmaxf(m1, s_f[i]); m2 = fmaxf(m2, s_T[i]);
+        for (int i0 = 0; i0 < n; i0 += 8) {
+            float vr[8], vf[8], vt[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                vr[j] = vf[j] = vt[j] = 0.f;
+                if (i0 + j < n) {                  // uniform over the warp
+                    const int t = f0 + i0 + j;
+                    const float ux = a.unit[t][0], uy = a.unit[t][1], uz = a.unit[t][2];
+                    const float sx = cx + radius * (ux * exx + uy * eyx + uz * ezx);
+                    const float sy = cy + radius * (ux * exy + uy * eyy + uz * ezy);
+                    const float sz = cz + radius * (ux * exz + uy * eyz + uz * ezz);
+                    // the density at the layer's level; the transmission feature weighs the
+                    // 11 finest levels (a grid has at most 12)
+                    const float rho = sample_border(rho_lv, rho_n, sx, sy, sz, 0.0f);
+                    float T = lb;
+                    for (int lv = 0; lv < nlv; ++lv)
+                        T = fmaf(__ldg(a.level_w + lv), sample_border(a.T.lv[lv], a.T.n[lv], sx, sy, sz, 1.0f), T);
+                    const float fa = __ldg(tab0 + t), fb = __ldg(tab1 + t);
+                    const float f = fa + wa * (fb - fa);
+                    if (a.H_rho) {
+                        const size_t o = (size_t)p * kPaperPts + t;
+                        a.H_rho[o] = rho;
+                        a.H_f[o] = f;
+                        a.H_T[o] = T;
+                    }
+                    s0 += rho; s1 += f; s2 += T;
+                    m0 = fmaxf(m0, rho); m1 = fmaxf(m1, f); m2 = fmaxf(m2, T);
+                    vr[j] = rho; vf[j] = f; vt[j] = T;
+                }
+            }
+            if (bf) {                              // columns c0 + i0 .. + 7 (zeros past n)
+                store_parts8(row_r + c0 + i0, a.part_rf, a.parts, vr);
+                store_parts8(row_f + c0 + i0, a.part_rf, a.parts, vf);
+                store_parts8(row_t + c0 + i0, a.part_t, a.parts, vt);
+            }
         }
         const float inv_n = 1.0f / (float)n;
-        const float v[8] = {s0 * inv_n, s1 * inv_n, s2 * inv_n, m0, m1, m2, a.g, s_alpha};
+        const float v[8] = {s0 * inv_n, s1 * inv_n, s2 * inv_n, m0, m1, m2, a.g, alpha};
         if (a.v)
             for (int q = 0; q < 8; ++q) a.v[((size_t)p * kLayers + k) * 8 + q] = v[q];
         const float *w1 = a.se + a.se_w1[k], *b1 = a.se + a.se_b1[k];
@@ -201,15 +212,25 @@ __global__ void __launch_bounds__(288, 4) gather_paper_kernel(const __grid_const
                 sigmoidf_p(b2[r] + w2[r * 2] * z[0] + w2[r * 2 + 1] * z[1]);
         if (k == 0) {
             float *c = a.cfg + (size_t)p * kCfg;
-            c[0] = a.g; c[1] = a.albedo[0]; c[2] = a.albedo[1]; c[3] = a.albedo[2]; c[4] = s_alpha;
+            c[0] = a.g; c[1] = a.albedo[0]; c[2] = a.albedo[1]; c[3] = a.albedo[2]; c[4] = alpha;
         }
+    }
+    if (bf) {
+        // the zero tail after the last layer: the MMAs read whole operand boxes, whose
+        // columns beyond a layer meet zero weights and so must hold finite values
+        for (int c = kPaperPad; c < kPaperPadTail; c += 8)
+            for (int q = 0; q < a.parts; ++q) {
+                st_v4p(row_r + c + q * a.part_rf, 0u, 0u, 0u, 0u);
+                st_v4p(row_f + c + q * a.part_rf, 0u, 0u, 0u, 0u);
+                st_v4p(row_t + c + q * a.part_t, 0u, 0u, 0u, 0u);
+            }
     }
 }
 
 void launch_gather_paper(const PaperGatherArgs &a, cudaStream_t s) {
     if (a.count <= 0) return;
     note_launch();
-    gather_paper_kernel<<<a.count, 288, 0, s>>>(a);
+    gather_paper_kernel<<<(a.count + 32 * kPWarps - 1) / (32 * kPWarps), 32 * kPWarps, 0, s>>>(a);
 }
 
 }  // namespace nis
