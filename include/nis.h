@@ -66,7 +66,9 @@ typedef int nis_status;
                                     residual < 2^-24 |x|) and the six products that matter
                                     accumulated in FP32; everything else in FP32 */
 #define NIS_PREC_BF16 1          /* CNN output, features and dense layers in BF16, FP32 accumulation */
-#define NIS_PREC_FP8 2           /* as BF16 with e4m3 operands and per-channel scales */
+#define NIS_PREC_FP8 2           /* as BF16, FC-1 of the density and phase chains on e4m3 operands
+                                    (per-layer scales); mixed batches: e4m3 dense layers with
+                                    per-channel weight scales */
 #define NIS_PREC_F32_SIMT 3      /* FP32 everywhere on the FP32 FFMA pipes (reference path) */
 
 #define NIS_CAMERA_ORTHO 0

@@ -132,6 +132,11 @@ __device__ __forceinline__ uint32_t pack_bf2(float lo, float hi) {
 __device__ __forceinline__ float bf_lo(uint32_t r) { return __uint_as_float(r << 16); }
 __device__ __forceinline__ float bf_hi(uint32_t r) { return __uint_as_float(r & 0xffff0000u); }
 
+// 16 bytes to a 16-byte aligned global address.
+__device__ __forceinline__ void st_v4(void *p, uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
+    asm volatile("st.global.v4.b32 [%0], {%1, %2, %3, %4};" :: "l"(p), "r"(x), "r"(y), "r"(z),
+                 "r"(w) : "memory");
+}
 // 32 bytes to a 32-byte aligned global address.
 __device__ __forceinline__ void st_v8(void *p, const uint32_t (&v)[8]) {
     asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
@@ -212,8 +217,9 @@ __device__ __forceinline__ float4 lattice_offset(int t) {
 
 constexpr int kGWarps = 4;                       // layers (warps) per gather_kernel CTA
 
-// kParts 1: BF16 feature rows; 3: the three-part BF16 split.  Rows are written in chunks of 16
-// BF16 columns (8 FP32 for H_T), one 32-byte store each.
+// kParts 1: BF16 feature rows; 3: the three-part BF16 split; 8: e4m3 rows of the fused
+// network's e4m3 mode.  Rows are written in chunks of 16 BF16 columns (32 e4m3; 8 FP32 for
+// H_T), one 32-byte store each.
 template <int kParts>
 __global__ void __launch_bounds__(kGWarps * 32, 4) gather_kernel(const __grid_constant__ GatherArgs a) {
     __shared__ float4 s_lat[kLat];
@@ -248,6 +254,20 @@ __global__ void __launch_bounds__(kGWarps * 32, 4) gather_kernel(const __grid_co
     __nv_bfloat16 *bR = a.Hb_rho ? a.Hb_rho + rk * kLatPad : nullptr;
     __nv_bfloat16 *bF = a.Hb_f ? a.Hb_f + rk * kLatPad : nullptr;
     const size_t part = a.part;
+    // e4m3 mode: x / s with s = sigma_max / 448 (density) and the phase set's table maximum /
+    // 448 (phase); both bound their feature from above, so nothing saturates
+    uint8_t *qR = kParts == 8 ? a.F8_rho + rk * kF8LatLd : nullptr;
+    uint8_t *qF = kParts == 8 ? a.F8_f + rk * kF8LatLd : nullptr;
+    float s_r = 1.f, s_f = 1.f;
+    if (kParts == 8) {
+        const float sg = __ldg(a.f8_sigma), tm = __ldg(a.f8_tabmax + lg.set);
+        if (sg > 0.f) s_r = sg * (1.0f / 448.f);
+        if (tm > 0.f) s_f = tm * (1.0f / 448.f);
+    }
+    const float inv_r = 1.0f / s_r, inv_f = 1.0f / s_f;
+    auto q2 = [](float x0, float x1) -> uint32_t {   // two values as e4m3, x0 in the low byte
+        return (uint32_t)__nv_cvt_float2_to_fp8x2(make_float2(x0, x1), __NV_SATFINITE, __NV_E4M3);
+    };
 
     float s0 = 0.f, s1 = 0.f, s2 = 0.f;
     float m0 = -3.0e38f, m1 = -3.0e38f, m2 = -3.0e38f;
@@ -274,9 +294,10 @@ __global__ void __launch_bounds__(kGWarps * 32, 4) gather_kernel(const __grid_co
             out[2] = pack_bf2(x0, x1);
         }
     };
-    constexpr int CH = 16;                                  // BF16 columns per 32-byte store
+    constexpr int CH = 16;                                  // columns per chunk
     for (int t0 = 0; t0 < kLat - 1; t0 += CH) {             // lattice points 0..223
-        // kParts 1: packed BF16 pairs; kParts 3: the FP32 values, split after the chunk
+        // kParts 1: packed BF16 pairs; kParts 3: the FP32 values, split after the chunk;
+        // kParts 8: packed e4m3 quadruples (16 bytes per chunk)
         uint32_t rb[CH / 2], fb[CH / 2];
         float rv[kParts == 3 ? CH : 1], fvv[kParts == 3 ? CH : 1];
         float tb[8];
@@ -296,12 +317,19 @@ __global__ void __launch_bounds__(kGWarps * 32, 4) gather_kernel(const __grid_co
             if constexpr (kParts == 1) {
                 rb[u / 2] = pack_bf2(r0, r1);
                 fb[u / 2] = pack_bf2(f0, f1);
+            } else if constexpr (kParts == 8) {
+                const uint32_t qr = q2(r0 * inv_r, r1 * inv_r), qf = q2(f0 * inv_f, f1 * inv_f);
+                if ((u & 2) == 0) { rb[u / 4] = qr; fb[u / 4] = qf; }
+                else { rb[u / 4] |= qr << 16; fb[u / 4] |= qf << 16; }
             } else {
                 rv[u] = r0; rv[u + 1] = r1;
                 fvv[u] = f0; fvv[u + 1] = f1;
             }
         }
-        if (bR) {
+        if constexpr (kParts == 8) {
+            st_v4(qR + t0, rb[0], rb[1], rb[2], rb[3]);
+            st_v4(qF + t0, fb[0], fb[1], fb[2], fb[3]);
+        } else if (bR) {
             if constexpr (kParts == 1) {
                 st_v8(bR + t0, rb);
                 st_v8(bF + t0, fb);
@@ -333,7 +361,30 @@ __global__ void __launch_bounds__(kGWarps * 32, 4) gather_kernel(const __grid_co
     }
     float wse[3];
     se_epilogue(a, d, p, k, s0, s1, s2, m0, m1, m2, gg, f.alpha, wse);
-    if (bR) {
+    if constexpr (kParts == 8) {
+        // the e4m3 rows' tails (columns 224..255), the configuration operands c / u and 1 / u
+        // of density and phase (u = w_se s S_w) and of the transmittance (u = w_se), and the
+        // epilogue's row factors u
+        {
+            uint32_t vr[8] = {q2(rl * inv_r, 0.f), 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+            uint32_t vf[8] = {q2(fl * inv_f, 0.f), 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+            st_v8(qR + kLat - 1, vr);
+            st_v8(qF + kLat - 1, vf);
+        }
+        const float *alb = d ? d->albedo : a.albedo;
+        const float u_r = fmaxf(wse[0] * s_r * a.f8_sw[k][0], kSeFloor);
+        const float u_f = fmaxf(wse[1] * s_f * a.f8_sw[k][1], kSeFloor);
+        uint32_t row[8];
+        fused_cfg_row(gg, alb, f.alpha, u_r, row);
+        st_v8(a.F8_cfg + rk * kF8CfgLd, row);
+        fused_cfg_row(gg, alb, f.alpha, u_f, row);
+        st_v8(a.F8_cfg + rk * kF8CfgLd + 16, row);
+        fused_cfg_row(gg, alb, f.alpha, wse[2], row);
+        st_v8(a.XT_cfg + rk * kFuseXtLd + kDT, row);
+        a.fc1_scale[rk * 3] = u_r;
+        a.fc1_scale[rk * 3 + 1] = u_f;
+        a.fc1_scale[rk * 3 + 2] = fmaxf(wse[2], kSeFloor);
+    } else if (bR) {
         if (a.fused) {                                       // BF16 only (kParts 1)
             const float *alb = d ? d->albedo : a.albedo;
             uint32_t row[8], out[8];
@@ -446,7 +497,8 @@ void launch_gather(const GatherArgs &a, cudaStream_t s) {
         gather8_kernel<<<a.count, kLayers * 32, 0, s>>>(a);
     } else {
         const dim3 grid((a.count + 31) / 32, kLayers / kGWarps);
-        if (a.Hb_rho && a.split) gather_kernel<3><<<grid, kGWarps * 32, 0, s>>>(a);
+        if (a.F8_rho) gather_kernel<8><<<grid, kGWarps * 32, 0, s>>>(a);
+        else if (a.Hb_rho && a.split) gather_kernel<3><<<grid, kGWarps * 32, 0, s>>>(a);
         else gather_kernel<1><<<grid, kGWarps * 32, 0, s>>>(a);
     }
 }
@@ -475,6 +527,40 @@ void launch_fill_segments(const int *seg_start, const int *seg_desc, int nseg, i
     note_launch();
     fill_segments_kernel<<<(count + 255) / 256, 256, 0, s>>>(seg_start, seg_desc, nseg, count,
                                                              req_of_point, dec_rows, descs);
+}
+
+}  // namespace nis
+
+namespace nis {
+
+// Largest value of each of the phase table's point sets ([kAlpha][kPhaseSets][kLat], all
+// entries >= 0): blocks of 256 threads over slices of the alpha nodes, a shared-memory
+// reduction, then an atomic max on the value's bits (order-preserving for non-negative
+// floats) into out[set], cleared first.
+constexpr int kTabSlices = 64;
+__global__ void __launch_bounds__(256) table_set_max_kernel(const float *__restrict__ table,
+                                                            float *__restrict__ out) {
+    __shared__ float red[256];
+    const int set = blockIdx.y;
+    constexpr int per = kAlpha / kTabSlices;
+    float m = 0.f;
+    for (int i = threadIdx.x; i < per * kLat; i += 256) {
+        const int al = blockIdx.x * per + i / kLat, t = i % kLat;
+        m = fmaxf(m, table[((size_t)al * kPhaseSets + set) * kLat + t]);
+    }
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicMax(reinterpret_cast<int *>(out) + set, __float_as_int(fmaxf(red[0], 0.f)));
+}
+
+void launch_table_set_max(const float *table, float *out, cudaStream_t s) {
+    cudaMemsetAsync(out, 0, kPhaseSets * sizeof(float), s);
+    note_launch();
+    table_set_max_kernel<<<dim3(kTabSlices, kPhaseSets), 256, 0, s>>>(table, out);
 }
 
 }  // namespace nis

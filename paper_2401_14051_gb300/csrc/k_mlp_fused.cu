@@ -35,6 +35,7 @@
 // Every mbarrier wait is bounded: on a time-out the kernel records kErrTimeout in the
 // context's error word and winds down (draining its MMAs and copies before releasing TMEM).
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "nis_internal.h"
 #include "tc_common.h"
@@ -77,6 +78,11 @@ __device__ __forceinline__ void record_timeout(unsigned *err, int *abort_flag) {
     if (err) atomicOr(err, kErrTimeout);
 }
 __device__ __forceinline__ bool aborted(const int *abort_flag) { return *(const volatile int *)abort_flag != 0; }
+
+// An op's weight/operand blocks: 64-column blocks of its K, or, for an e4m3 FC-1, two
+// 128-column e4m3 blocks and the 16-column configuration block.
+// column of an e4m3 FC-1's configuration operand in the [rows][12 x 2 x 16] source
+__device__ __forceinline__ int cfg8_col(const FusedOp &op) { return (op.layer * 2 + op.type) * 16; }
 
 // 8 floats as BF16, one 16-byte word
 __device__ __forceinline__ uint4 pack8(const float *v) {
@@ -287,6 +293,9 @@ __device__ __forceinline__ void epi_tail(const FusedOp &op, int c, uint32_t acc_
 }
 }  // namespace
 
+// kF8: the e4m3 mode (a separate instantiation, so that the BF16 kernel's issue loops carry
+// none of its branches)
+template <bool kF8>
 __global__ void __launch_bounds__(kThreads, 1)
     mlp_fused_kernel(const __grid_constant__ FusedMaps maps, const __grid_constant__ FusedArgs a) {
     extern __shared__ uint8_t smem_raw[];
@@ -314,8 +323,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
-    if (warp == 0 && lane == 0)
+    if (warp == 0 && lane == 0) {
         for (int i = 0; i < kFuseSrcs; ++i) tc::prefetch_tmap(&maps.m64[i]);
+        if (kF8) tc::prefetch_tmap(&maps.cfg8);
+    }
     if (warp == 1) {
         tc::tmem_alloc(tmem_slot, 512);
         tc::tmem_relinquish();
@@ -346,8 +357,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             auto prefetch = [&](int i, int y, int j) {
                 const FusedOp &op = ops[i];
                 if (op.src > kSrcT) return;
-                for (int b = 0; b < (op.k + 63) / 64; ++b)
-                    if (j < 0 || b == j) tc::tma_prefetch_2d(&maps.m64[op.src], op.a_col0 + 64 * b, y);
+                const bool f8 = kF8 && (op.flags & kFuseF8Flag) != 0;
+                for (int b = 0; b < (f8 ? 3 : (op.k + 63) / 64); ++b)
+                    if (j < 0 || b == j) {
+                        if (f8 && b == 2) tc::tma_prefetch_2d(&maps.cfg8, cfg8_col(op), y);
+                        else tc::tma_prefetch_2d(&maps.m64[op.src], op.a_col0 + (f8 ? 128 : 64) * b, y);
+                    }
             };
             if (!ring_g && blockIdx.x < n_tiles)
                 for (int i = 0; i < kPrefetchOps && i < n_ops; ++i) prefetch(i, blockIdx.x * FM, -1);
@@ -369,9 +384,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                         ++cnt;
                     }
                     const uint8_t *src = a.wpack + op.b_off;
-                    const int nblk = (op.k + 63) / 64;
+                    const bool f8 = kF8 && (op.flags & kFuseF8Flag) != 0;
+                    const int nblk = f8 ? 3 : (op.k + 63) / 64;
                     for (int j = 0; j < nblk; ++j, ++it) {
-                        const bool tail = !a_glob && op.k - 64 * j == 16;
+                        // 32-byte rows: the s buffer's 16-column tail, or an e4m3 op's
+                        // configuration block
+                        const bool tail = f8 ? j == 2 : (!a_glob && op.k - 64 * j == 16);
                         const uint32_t bbytes = (uint32_t)op.n_mma * (tail ? 32u : 128u);
                         const int ss = it % ns;
                         if (aborted(abort_flag)) { ok = false; break; }
@@ -389,9 +407,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 else if (tile + (int)gridDim.x < n_tiles)
                                     prefetch(i + kPrefetchOps - n_ops, y + gridDim.x * FM, j);
                             }
+                        } else if (f8 && j == 2) {
+                            tc::mbar_expect_tx(&bar[full + ss], FM * 32);
+                            tc::tma_load_2d_hint(dst + B_SLOT, &maps.cfg8, cfg8_col(op), y, &bar[full + ss], once);
                         } else {
                             tc::mbar_expect_tx(&bar[full + ss], A_SLOT);
-                            tc::tma_load_2d_hint(dst + B_SLOT, &maps.m64[op.src], op.a_col0 + 64 * j, y, &bar[full + ss], once);
+                            tc::tma_load_2d_hint(dst + B_SLOT, &maps.m64[op.src], op.a_col0 + (f8 ? 128 : 64) * j, y,
+                                                 &bar[full + ss], once);
                         }
                         src += bbytes;
                     }
@@ -417,10 +439,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint32_t d = tmem_base + (on_y ? 256u : 0u);
                     const uint32_t idesc = tc::idesc_bf16_f32(FM, op.n_mma);
                     const bool a_glob = op.src != kSrcS;
-                    const int nblk = (op.k + 63) / 64;
+                    const bool f8 = kF8 && (op.flags & kFuseF8Flag) != 0;
+                    const int nblk = f8 ? 3 : (op.k + 63) / 64;
                     for (int j = 0; j < nblk; ++j) {
                         const int w = op.k - 64 * j < 64 ? op.k - 64 * j : 64;
-                        const bool tail = !a_glob && w == 16;
+                        const bool tail = f8 ? j == 2 : (!a_glob && w == 16);
                         uint32_t a_addr, b_addr;
                         uint64_t *freed;
                         if (a_glob) {
@@ -444,6 +467,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                         if (tail) {
                             tc::mma_f16(d, tc::smem_desc_sw32(a_addr), tc::smem_desc_sw32(b_addr), idesc, j != 0);
+                        } else if (f8) {
+                            // e4m3 x e4m3, K = 32 per MMA: four MMAs per 128-byte row block
+                            const uint32_t idesc8 = tc::idesc_e4m3_f32(FM, op.n_mma);
+                            const uint64_t ad = tc::smem_desc_sw128(a_addr), bd = tc::smem_desc_sw128(b_addr);
+                            for (int k = 0; k < 4; ++k) tc::mma_f8(d, ad + 2 * k, bd + 2 * k, idesc8, (j | k) != 0);
                         } else {
                             const uint64_t ad = tc::smem_desc_sw128(a_addr), bd = tc::smem_desc_sw128(b_addr);
                             tc::mma_f16(d, ad, bd, idesc, j != 0);
@@ -489,7 +517,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t acc_tm = lane_tm + (on_y ? 256u : 0u);
                 float sc = 1.f;
                 if (op.kind == kFuseFc1 && live)
-                    sc = fmaxf(a.w_se[(size_t)r * (kLayers * 3) + op.layer * 3 + op.type], kSeFloor);
+                    sc = fmaxf((kF8 ? a.fc1_scale : a.w_se)[(size_t)r * (kLayers * 3) + op.layer * 3 + op.type],
+                               kSeFloor);
                 for (int c = hf; 32 * c < op.n_mma; c += 2) {
                     if (32 * c + 32 <= op.n_mma) epi_chunk32(op, c, acc_tm, lane_tm, smem, bar, rl, r, live, sc, a, lane);
                     else epi_tail(op, c, acc_tm, smem, bar, rl, r, live, sc, a, lane);
@@ -522,8 +551,61 @@ __global__ void __launch_bounds__(kThreads, 1)
 // BF16 parts at k_main and k_main + 1 when bias_main); FC-1's configuration columns k_main +
 // 0..12 are [W_c (5), W_c (5), b_hi, b_lo, b_hi] against the operand [c/w hi (5), c/w lo (5),
 // 1/w hi, 1/w hi, 1/w lo].
+// An e4m3 op (fp8): two [n_mma][128] e4m3 blocks of W / S_w (128-byte swizzle, 16 values per
+// unit) and the [n_mma][16] BF16 configuration block (32-byte swizzle).
+__device__ void fused_pack_f8(const FusedPackOp &p, uint8_t *__restrict__ dst) {
+    const int u8 = 2 * p.n_mma * 8;
+    const int units = u8 + p.n_mma * 2;
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < units; u += gridDim.x * blockDim.x) {
+        if (u < u8) {
+            const int j = u / (p.n_mma * 8), rem = u - j * p.n_mma * 8;
+            const int n = rem >> 3, pu = rem & 7, lu = pu ^ (n & 7);
+            uint32_t w[4] = {0u, 0u, 0u, 0u};
+            for (int e = 0; e < 16; e += 2) {
+                const int kk = 128 * j + 16 * lu + e;
+                float x0 = 0.f, x1 = 0.f;
+                if (n < p.n_out) {
+                    const float *wr = p.W + (size_t)n * p.ld;
+                    if (kk < p.k_main) x0 = wr[kk] * p.f8_inv;
+                    if (kk + 1 < p.k_main) x1 = wr[kk + 1] * p.f8_inv;
+                }
+                const uint32_t q = __nv_cvt_float2_to_fp8x2(make_float2(x0, x1), __NV_SATFINITE, __NV_E4M3);
+                w[e >> 2] |= q << (8 * (e & 3));        // bytes e, e + 1 of the unit
+            }
+            *reinterpret_cast<uint4 *>(dst + p.b_off + (size_t)j * p.n_mma * 128 + n * 128 + pu * 16) =
+                make_uint4(w[0], w[1], w[2], w[3]);
+        } else {
+            const int rem = u - u8, n = rem >> 1, pu = rem & 1, lu = pu ^ ((n >> 2) & 1);
+            float v[8];
+            float bh = 0.f, bl = 0.f;
+            if (n < p.n_out) {
+                const float b = p.bias[n];
+                bh = __bfloat162float(__float2bfloat16_rn(b));
+                bl = b - bh;
+            }
+            for (int e = 0; e < 8; ++e) {
+                const int kc = 8 * lu + e;
+                float x = 0.f;
+                if (n < p.n_out) {
+                    const float *wr = p.W + (size_t)n * p.ld;
+                    if (kc < 5) x = wr[p.k_main + kc];
+                    else if (kc < 10) x = wr[p.k_main + kc - 5];
+                    else if (kc == 10 || kc == 12) x = bh;
+                    else if (kc == 11) x = bl;
+                }
+                v[e] = x;
+            }
+            *reinterpret_cast<uint4 *>(dst + p.b_off + (size_t)2 * p.n_mma * 128 + n * 32 + pu * 16) = pack8(v);
+        }
+    }
+}
+
 __global__ void fused_pack_kernel(const FusedPackOp *__restrict__ pk, uint8_t *__restrict__ dst) {
     const FusedPackOp p = pk[blockIdx.y];
+    if (p.fp8) {
+        fused_pack_f8(p, dst);
+        return;
+    }
     const int nblk = (p.k + 63) / 64;
     const int full = p.s_tail ? nblk - 1 : nblk;            // 128-byte-row blocks
     const int u128 = full * p.n_mma * 8;                     // their 16-byte units
@@ -576,11 +658,11 @@ __global__ void fused_pack_kernel(const FusedPackOp *__restrict__ pk, uint8_t *_
 }
 
 void fused_program(const WeightOffsets &o, const float *W, FusedOp *ops, FusedPackOp *pack, int *n_ops,
-                   size_t *bytes) {
+                   size_t *bytes, const float (*sw)[2]) {
     int n = 0;
     uint32_t off = 0;
     auto add = [&](int kind, int src, int type, int layer, int chain, int flags, int col0, int k, int n_mma,
-                   const float *w, int ld, int n_out, int k_main, const float *b) {
+                   const float *w, int ld, int n_out, int k_main, const float *b, float f8_inv = 0.f) {
         FusedOp f{};
         f.kind = (uint8_t)kind; f.src = (uint8_t)src; f.type = (uint8_t)type; f.layer = (uint8_t)layer;
         f.chain = (uint8_t)chain; f.flags = (uint8_t)(flags | ((n & 1) ? 4 : 0));   // X, Y alternate
@@ -591,8 +673,14 @@ void fused_program(const WeightOffsets &o, const float *W, FusedOp *ops, FusedPa
         p.bias_main = kind == kFuseFc1 ? 0 : 1;
         p.k = k; p.n_mma = n_mma; p.s_tail = src == kSrcS ? 1 : 0;
         f.b_off = p.b_off = off;
-        const int nblk = (k + 63) / 64;
-        off += (uint32_t)n_mma * (p.s_tail ? 128u * (nblk - 1) + 32u : 128u * nblk);
+        if (flags & kFuseF8Flag) {
+            p.fp8 = 1;
+            p.f8_inv = f8_inv;
+            off += (uint32_t)n_mma * (2u * 128u + 32u);
+        } else {
+            const int nblk = (k + 63) / 64;
+            off += (uint32_t)n_mma * (p.s_tail ? 128u * (nblk - 1) + 32u : 128u * nblk);
+        }
         ops[n] = f;
         pack[n] = p;
         ++n;
@@ -603,8 +691,12 @@ void fused_program(const WeightOffsets &o, const float *W, FusedOp *ops, FusedPa
             for (int k = k0; k < k1; ++k) {
                 const int d = feat_dim(t);
                 const int ld = t == 2 ? kFuseXtLd : kFuseLatLd;
-                add(kFuseFc1, t, t, k, chain, k == k0 ? 1 : 0, k * ld, ld, 208, W + o.blk_w1[t][k], d + kCfg,
-                    kWidth, d, W + o.blk_b1[t][k]);
+                if (sw && t < 2)        // e4m3 features: columns k * kF8LatLd of their source
+                    add(kFuseFc1, t, t, k, chain, (k == k0 ? 1 : 0) | kFuseF8Flag, k * kF8LatLd, kF8LatLd + 16,
+                        208, W + o.blk_w1[t][k], d + kCfg, kWidth, d, W + o.blk_b1[t][k], 1.0f / sw[k][t]);
+                else
+                    add(kFuseFc1, t, t, k, chain, k == k0 ? 1 : 0, k * ld, ld, 208, W + o.blk_w1[t][k], d + kCfg,
+                        kWidth, d, W + o.blk_b1[t][k]);
                 const int fl = (k == k1 - 1 ? 2 : 0) | (k == k1 - 1 && chain == 1 ? 8 : 0);
                 add(kFuseFc2, kSrcS, t, k, chain, fl, 0, 208, 208, W + o.blk_w2[t][k], kWidth, kWidth, kWidth,
                     W + o.blk_b2[t][k]);
@@ -631,13 +723,15 @@ void launch_mlp_fused(const FusedArgs &a, const FusedMaps &maps, int num_sms, cu
     if (a.M <= 0 || a.n_ops <= 0 || a.n_ops > kFuseMaxOps) return;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(mlp_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_FUSED);
+        cudaFuncSetAttribute(mlp_fused_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_FUSED);
+        cudaFuncSetAttribute(mlp_fused_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_FUSED);
         attr_set = true;
     }
     const int tiles = (a.M + FM - 1) / FM;
     const int grid = tiles < num_sms ? tiles : num_sms;
     note_launch();
-    mlp_fused_kernel<<<grid, kThreads, SMEM_FUSED, s>>>(maps, a);
+    if (a.fc1_scale) mlp_fused_kernel<true><<<grid, kThreads, SMEM_FUSED, s>>>(maps, a);
+    else mlp_fused_kernel<false><<<grid, kThreads, SMEM_FUSED, s>>>(maps, a);
 }
 
 }  // namespace nis

@@ -1,5 +1,6 @@
 // The C ABI (include/nis.h): context, handle registries, HBM budget accounting, weight-blob
 // parsing and the stream-ordered orchestration of the kernels of the inference path.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -62,11 +63,13 @@ struct Weights {
     uint8_t *f8 = nullptr;
     float *f8_scales = nullptr;
     const float *sc_fc1[3][kLayers] = {}, *sc_fc2[3][kLayers] = {}, *sc_mrg[3] = {}, *sc_head[3] = {};
-    // BF16: the fused backbone's op program and pre-swizzled weight slabs
+    // BF16 and FP8: the fused backbone's op program and pre-swizzled weight slabs (FP8: its
+    // e4m3 mode, with the FC-1 weight scales of the density and phase chains)
     uint8_t *fused_w = nullptr;
     FusedOp *fused_ops = nullptr;
     FusedPackOp *fused_pack = nullptr;
     int fused_n_ops = 0;
+    float f8_sw[kLayers][2] = {};
 };
 
 struct WorkspaceF8 {                  // scratch of the FP8 path, grow-only
@@ -94,6 +97,14 @@ struct WorkspaceBf {                  // scratch of the tensor-core paths, grow-
     // (the features in Hb_rho, Hb_f and XTb with rows of kFuseLatLd / kFuseXtLd per layer)
     __nv_bfloat16 *mrg_f = nullptr, *head_f = nullptr;
     FusedMaps fmaps{};
+    // the fused backbone's e4m3 mode (FP8): e4m3 density and phase rows, their configuration
+    // operands, the FC-1 row factors, the phase table's set maxima, and the operand maps
+    // (rho, f and the configuration operands of their own; the rest shared with fmaps)
+    int f8_cap = 0;
+    uint8_t *F8_rho = nullptr, *F8_f = nullptr;
+    __nv_bfloat16 *F8_cfg = nullptr;
+    float *fc1_scale = nullptr, *tabmax = nullptr;
+    FusedMaps f8maps{};
 };
 
 struct Workspace {                    // scratch of nis_shade_points, grow-only
@@ -512,9 +523,59 @@ nis_status ensure_workspace_tc(nis_ctx *ctx, WorkspaceBf &w, int parts, int cap,
     return NIS_OK;
 }
 
+// The e4m3 mode's buffers and operand maps (the BF16 workspace must already hold cap rows).
+nis_status ensure_f8_fused(nis_ctx *ctx, WorkspaceBf &w, int cap, cudaStream_t s) {
+    const size_t n = (size_t)cap;
+    nis_status st;
+    if (w.f8_cap < cap) {
+        for (auto **b : {&w.F8_rho, &w.F8_f}) { dev_free(ctx, *b); *b = nullptr; }
+        dev_free(ctx, w.F8_cfg); w.F8_cfg = nullptr;
+        for (float **f : {&w.fc1_scale, &w.tabmax}) { dev_free(ctx, *f); *f = nullptr; }
+        w.f8_cap = 0;
+        if ((st = dev_alloc_t(ctx, n * kLayers * kF8LatLd, &w.F8_rho, s))) return st;
+        if ((st = dev_alloc_t(ctx, n * kLayers * kF8LatLd, &w.F8_f, s))) return st;
+        if ((st = dev_alloc_t(ctx, n * kLayers * kF8CfgLd, &w.F8_cfg, s))) return st;
+        if ((st = dev_alloc_t(ctx, n * kLayers * 3, &w.fc1_scale, s))) return st;
+        if ((st = dev_alloc_t(ctx, (size_t)kPhaseSets, &w.tabmax, s))) return st;
+        w.f8_cap = cap;
+    }
+    // rebuilt every call: the shared sources move when the BF16 workspace grows
+    w.f8maps = w.fmaps;
+    const uint64_t rows = (uint64_t)w.f8_cap;
+    const bool ok =
+        make_tmap_u8(&w.f8maps.m64[kSrcRho], w.F8_rho, kLayers * kF8LatLd, rows, kLayers * kF8LatLd, 128, 128) &&
+        make_tmap_u8(&w.f8maps.m64[kSrcF], w.F8_f, kLayers * kF8LatLd, rows, kLayers * kF8LatLd, 128, 128) &&
+        make_tmap_bf16(&w.f8maps.cfg8, w.F8_cfg, kLayers * kF8CfgLd, rows, kLayers * kF8CfgLd * 2, 16, 128);
+    if (!ok) return fail(ctx, NIS_ERR_CUDA, "cuTensorMapEncodeTiled failed for the e4m3 operands");
+    return NIS_OK;
+}
+
 int n_mma_of(int n) { return (n + 15) / 16 * 16; }
 
 int k_pad_of(int k) { return (k + 63) / 64 * 64; }
+
+// The fused backbone (lattice model): its op program and weight slabs; with sw, its e4m3 mode.
+nis_status pack_fused(nis_ctx *ctx, Weights &w, const float (*sw)[2], cudaStream_t s) {
+    FusedOp ops[kFuseMaxOps];
+    FusedPackOp pk[kFuseMaxOps];
+    int n_ops = 0;
+    size_t bytes = 0;
+    nis_status st;
+    fused_program(w.off, w.f32, ops, pk, &n_ops, &bytes, sw);
+    if ((st = dev_alloc_t(ctx, bytes, &w.fused_w, s))) return st;
+    if ((st = dev_alloc_t(ctx, (size_t)n_ops, &w.fused_ops, s))) return st;
+    if ((st = dev_alloc_t(ctx, (size_t)n_ops, &w.fused_pack, s))) return st;
+    NIS_CUDA(cudaMemcpyAsync(w.fused_ops, ops, n_ops * sizeof(FusedOp), cudaMemcpyHostToDevice, s));
+    NIS_CUDA(cudaMemcpyAsync(w.fused_pack, pk, n_ops * sizeof(FusedPackOp), cudaMemcpyHostToDevice, s));
+    {
+        ProfScope ps(ctx, "other", s);
+        launch_fused_pack(w.fused_pack, n_ops, w.fused_w, s);
+    }
+    // the host arrays above are read by the copies before this returns
+    NIS_CUDA(cudaStreamSynchronize(s));
+    w.fused_n_ops = n_ops;
+    return NIS_OK;
+}
 
 // Tensor-core weight pack: per dense layer `parts` zero-padded [n_mma][Kp] BF16 matrices
 // stacked along the rows (1 part: BF16; 3 parts: the three-way split), one tensor map each.
@@ -550,27 +611,7 @@ nis_status pack_weights_tc(nis_ctx *ctx, Weights &w, int parts, cudaStream_t s) 
             return fail(ctx, NIS_ERR_CUDA, "cuTensorMapEncodeTiled failed for a weight matrix");
         off += (size_t)parts * np * kp;
     }
-    if (parts == 1 && o.model == kModelLattice) {
-        // the fused backbone: its op program and weight slabs
-        FusedOp ops[kFuseMaxOps];
-        FusedPackOp pk[kFuseMaxOps];
-        int n_ops = 0;
-        size_t bytes = 0;
-        fused_program(o, w.f32, ops, pk, &n_ops, &bytes);
-        if ((st = dev_alloc_t(ctx, bytes, &w.fused_w, s))) return st;
-        if ((st = dev_alloc_t(ctx, (size_t)n_ops, &w.fused_ops, s))) return st;
-        if ((st = dev_alloc_t(ctx, (size_t)n_ops, &w.fused_pack, s))) return st;
-        NIS_CUDA(cudaMemcpyAsync(w.fused_ops, ops, n_ops * sizeof(FusedOp), cudaMemcpyHostToDevice, s));
-        NIS_CUDA(cudaMemcpyAsync(w.fused_pack, pk, n_ops * sizeof(FusedPackOp), cudaMemcpyHostToDevice, s));
-        {
-            ProfScope ps(ctx, "other", s);
-            launch_fused_pack(w.fused_pack, n_ops, w.fused_w, s);
-        }
-
-        // the host arrays above are read by the copies before this returns
-        NIS_CUDA(cudaStreamSynchronize(s));
-        w.fused_n_ops = n_ops;
-    }
+    if (parts == 1 && o.model == kModelLattice && (st = pack_fused(ctx, w, nullptr, s))) return st;
     NIS_CUDA(cudaGetLastError());
     return NIS_OK;
 }
@@ -830,7 +871,8 @@ nis_status shade_impl(nis_ctx *ctx, const Volume &vol, const Light &light, const
     }
     if (!mx && (st = ensure_phase(ctx, phase_spec(m), s, &table))) return st;
     if (n <= 0) return NIS_OK;
-    if (wt.precision == NIS_PREC_FP8)
+    // FP8: the fused backbone's e4m3 mode; mixed batches take the layered FP8 path
+    if (wt.precision == NIS_PREC_FP8 && (mx || wt.fused_n_ops == 0))
         return shade_impl_fp8(ctx, vol, light, wt, m, table, pts, om, n, rgb, dbg, s, mx);
     if (wt.precision != NIS_PREC_F32_SIMT)
         return shade_impl_bf16(ctx, vol, light, wt, m, table, pts, om, n, rgb, dbg, s, mx);
@@ -980,8 +1022,15 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
         launch_tc_gemm(a, ma, mb, ctx->num_sms, s, o1, o2, pre);
     };
     const int k_e = split ? kOutF32 : kOutBf16;     // kind of e and h
-    // BF16 lattice model: the whole network after the features in one fused kernel
+    // BF16 lattice model: the whole network after the features in one fused kernel; FP8 (no
+    // mixed batch): the same kernel in its e4m3 mode
     const bool fused = !split && !paper && wt.fused_n_ops > 0;
+    const bool f8 = wt.precision == NIS_PREC_FP8;
+    if (f8 && (st = ensure_f8_fused(ctx, w, chunk, s))) return st;
+    if (f8) {
+        ProfScope ps(ctx, "gather", s);
+        launch_table_set_max(table, w.tabmax, s);
+    }
     for (int off = 0; off < n; off += chunk) {
         int cnt = n - off < chunk ? n - off : chunk;
         GatherArgs ga{};
@@ -1008,6 +1057,13 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
         }
         ga.v = dbg ? w.v : nullptr; ga.w_se = w.w_se; ga.cfg = w.cfg;
         if (fused) { ga.fused = 1; ga.XT_cfg = w.XTb; }
+        if (f8) {
+            ga.Hb_rho = ga.Hb_f = nullptr;
+            ga.F8_rho = w.F8_rho; ga.F8_f = w.F8_f; ga.F8_cfg = w.F8_cfg; ga.fc1_scale = w.fc1_scale;
+            ga.f8_sigma = vol.sigma_max; ga.f8_tabmax = w.tabmax;
+            for (int k = 0; k < kLayers; ++k)
+                for (int t = 0; t < 2; ++t) ga.f8_sw[k][t] = wt.f8_sw[k][t];
+        }
         if (mx) { ga.descs = mx->descs; ga.req_of_point = mx->req_of_point + off; }
         if (paper) {
             // the paper model: its gathers write the operands of all three types (the
@@ -1048,7 +1104,8 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
             fa.dec_rows = mx ? mx->dec_rows + 3 * (size_t)off : nullptr;
             for (int c = 0; c < 3; ++c) fa.dec_scale[c] = dec_scale[c];
             fa.err = ctx->d_err;
-            launch_mlp_fused(fa, w.fmaps, ctx->num_sms, s);
+            fa.fc1_scale = f8 ? w.fc1_scale : nullptr;
+            launch_mlp_fused(fa, f8 ? w.f8maps : w.fmaps, ctx->num_sms, s);
         } else {
             ProfScope pm(ctx, "mlp", s);   // the pass's dense layers as one timed block
             for (int t = 0; t < 3; ++t) {
@@ -1844,8 +1901,26 @@ nis_status nis_load_weights(nis_ctx *ctx, const void *blob, size_t bytes, int pr
     cudaError_t e = cudaMemcpyAsync(w.f32, words, o.total * 4, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the caller may free the blob
     if (e != cudaSuccess) { dev_free(ctx, w.f32); return cuda_fail(ctx, e, "weights upload"); }
-    if (precision == NIS_PREC_FP8) st = pack_weights_fp8(ctx, w, s);
-    else if (precision != NIS_PREC_F32_SIMT) st = pack_weights_tc(ctx, w, precision == NIS_PREC_F32 ? 3 : 1, s);
+    if (precision == NIS_PREC_FP8) {
+        st = pack_weights_fp8(ctx, w, s);
+        if (!st) {
+            // the fused backbone's e4m3 mode: per layer, the FC-1 weight scale of the density and
+            // phase features (largest magnitude / 448, the e4m3 maximum)
+            for (int k = 0; k < kLayers; ++k)
+                for (int t = 0; t < 2; ++t) {
+                    const int d = feat_dim(t);
+                    float mx = 0.f;
+                    for (int n = 0; n < kWidth; ++n)
+                        for (int kk = 0; kk < d; ++kk) {
+                            float x;
+                            std::memcpy(&x, words + o.blk_w1[t][k] + (size_t)n * (d + kCfg) + kk, 4);
+                            mx = std::max(mx, std::fabs(x));
+                        }
+                    w.f8_sw[k][t] = mx > 0.f ? mx / 448.f : 1.f;
+                }
+            st = pack_fused(ctx, w, w.f8_sw, s);
+        }
+    } else if (precision != NIS_PREC_F32_SIMT) st = pack_weights_tc(ctx, w, precision == NIS_PREC_F32 ? 3 : 1, s);
     if (st) {
         dev_free(ctx, w.f32);
         dev_free(ctx, w.bf);

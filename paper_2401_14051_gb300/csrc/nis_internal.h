@@ -329,8 +329,19 @@ struct GatherArgs {
     // kFuseXtLd per layer, columns 80..92) ahead of the CNN's outputs
     int fused;
     __nv_bfloat16 *XT_cfg;
+    // e4m3 mode of the fused network: the density and phase rows as e4m3 [count][12][kF8LatLd]
+    // scaled by 448 / sigma_max and 448 / the phase set's table maximum, their configuration
+    // operands [count][12][kF8CfgLd] BF16 and the FC-1 row factors [count][12][3]
+    uint8_t *F8_rho, *F8_f;
+    __nv_bfloat16 *F8_cfg;
+    float *fc1_scale;
+    const float *f8_sigma;                   // device: sigma_max of the volume
+    const float *f8_tabmax;                  // device: [5] maxima of the phase table's sets
+    float f8_sw[kLayers][2];                 // weight scales of FC-1 (rho, f)
 };
 void launch_gather(const GatherArgs &a, cudaStream_t s);
+// out[set] = the largest entry of the phase table's point set (kPhaseSets of them)
+void launch_table_set_max(const float *table, float *out, cudaStream_t s);
 
 // ---- paper-template model (k_gather_paper.cu) -----------------------------------------------
 // Unit-radius point sets of the 12 layers (light-frame coordinates; Fibonacci sphere,
@@ -525,7 +536,8 @@ struct FusedOp {
     uint8_t kind, src, type, layer;
     uint8_t chain, flags;                    // flags: 1 first layer of its chain, 2 last, 4 on
                                              // accumulator Y, 8 merge operand complete,
-                                             // 16 head operand complete
+                                             // 16 head operand complete, 32 e4m3 features
+                                             // (kFuseF8Flag)
     uint16_t a_col0, n_mma, k;               // operand column; 208 or 16 outputs; K (x16)
     uint32_t b_off;                          // byte offset of the op's weight blocks
 };
@@ -540,10 +552,24 @@ struct FusedPackOp {
                                              // features) and the bias in columns k_main..+12
     int k, n_mma, s_tail;                    // K; outputs; last block 16 wide (s buffer tail)
     uint32_t b_off;
+    int fp8;                                 // e4m3 feature blocks (see kFuseF8Flag)
+    float f8_inv;                            // 1 / the layer's weight scale S_w
 };
 struct FusedMaps {                           // per TMA source: 64-column boxes of 128 rows,
-    CUtensorMap m64[kFuseSrcs];              // 128-byte swizzle
+    CUtensorMap m64[kFuseSrcs];              // 128-byte swizzle (with e4m3 features: 128
+                                             // columns of rho and f)
+    CUtensorMap cfg8;                        // e4m3 mode: the configuration operands [rows][12
+                                             // layers x 2 types x 16] BF16, 16-column boxes
 };
+// e4m3 mode of the fused network (the FP8 precision): FC-1 of the density and phase chains
+// reads the layer's features as e4m3 (x / s, s the layer's activation scale) in two
+// 128-column blocks against e4m3 weights (W / S_w, S_w the layer's weight scale), then a
+// 16-column BF16 block of configuration columns c / u and 1 / u (u = w_se s S_w) against
+// [W_c; W_c; b_hi; b_lo; b_hi]; the accumulator times u is W1 [w_se x; c] + b1, and the
+// epilogue's row factor is u (FusedArgs::fc1_scale) instead of w_se.
+constexpr int kFuseF8Flag = 32;
+constexpr int kF8LatLd = 256;                  // e4m3 feature row per layer (225 + zeros)
+constexpr int kF8CfgLd = 32;                   // configuration columns per layer: 2 types x 16
 struct FusedArgs {
     int M, n_ops;
     const FusedOp *ops;                      // device, n_ops <= kFuseMaxOps
@@ -556,11 +582,14 @@ struct FusedArgs {
     const float *dec_rows;                   // optional per-row decode scales [M][3]
     float dec_scale[3];                      // I * albedo^4
     unsigned *err;
+    const float *fc1_scale;                  // e4m3 mode: FC-1 row factors [M][12][3], else null
 };
 // The op program and the pack list of a weight set (lattice model: feature columns
 // k * kFuseLatLd for rho and f, k * kFuseXtLd for T).
+// With sw (e4m3 mode), FC-1 of the density and phase chains takes e4m3 feature blocks with
+// the weight scales sw[k][t] (host values, computed by the caller).
 void fused_program(const WeightOffsets &o, const float *W, FusedOp *ops, FusedPackOp *pack,
-                   int *n_ops, size_t *bytes);
+                   int *n_ops, size_t *bytes, const float (*sw)[2] = nullptr);
 void launch_fused_pack(const FusedPackOp *pack_dev, int n_ops, uint8_t *dst, cudaStream_t s);
 void launch_mlp_fused(const FusedArgs &a, const FusedMaps &maps, int num_sms, cudaStream_t s);
 // SE weights are floored at kSeFloor where the configuration operand divides by them.

@@ -84,10 +84,10 @@ def test_bf16_render_frame(env):
 
 
 def test_fp8_against_fp64_oracle_and_fp32(env):
-    # FP8 e4m3 operands with per-output-channel weight scales and per-(point, layer) feature
-    # scales, FP32 accumulation.  The error is stated (printed) with a loose sanity bound:
-    # e4m3 keeps 3 mantissa bits, and the residual chains carry the rounding of ~60
-    # dependent layers.
+    # FP8: the fused network's e4m3 mode, the wide FC-1 operands of the density and phase
+    # chains in e4m3 (per-layer activation and weight scales, the product's scale applied per
+    # row in the epilogue), the rest of the network in BF16, FP32 accumulation.  Measured
+    # mean 0.0156 against FP64; bounded like BF16.
     ctx, cfg = env["ctx"], env["cfg"]
     p, om = synth.shading_points(2048, 404, 0.05, 0.95)
     dev = torch.device("cuda:0")
@@ -102,7 +102,8 @@ def test_fp8_against_fp64_oracle_and_fp32(env):
     print(f"\n[precision] FP8 vs FP64 oracle, 2048 points: mean rel {e.mean():.3g}, max {e.max():.3g}; "
           f"vs FP32 path mean {e32.mean():.3g}")
     assert np.isfinite(rf8.cpu().numpy()).all()
-    assert e.mean() <= 0.3
+    assert e.mean() <= 2e-2
+    assert e32.mean() <= 2e-2
 
 
 def test_bf16_cnn_against_fp64_on_the_same_inputs(env):
@@ -174,4 +175,4 @@ def test_precision_study_config3_million_pixels(env):
               f"{err64[name][0]:.3g}, max {err64[name][1]:.3g}")
     assert err64["f32"][1] <= 1e-4
     assert err64["bf16"][0] <= 2e-2 and stats["bf16"][0] <= 2e-2
-    assert err64["fp8"][0] <= 0.25 and stats["fp8"][0] <= 0.25
+    assert err64["fp8"][0] <= 2e-2 and stats["fp8"][0] <= 2e-2
