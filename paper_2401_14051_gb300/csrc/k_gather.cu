@@ -174,31 +174,39 @@ __device__ __forceinline__ float2 lerp2(float2 a, float2 b, float f) {
     return r;
 }
 
+// One 32-byte PairView entry (two float4: the y0 and y1 rows of a cell's z slice) in one
+// full-sector load.
+__device__ __forceinline__ void ld_entry(const float4 *p, float4 &a, float4 &b) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(p));
+}
+
 // Trilinear (density, transmittance) at grid coordinates (gx, gy, gz) = position * n - 1/2 of
-// a level stored as interleaved voxel pairs (entry x + 1 of a (z, y) row holds voxels x and
-// x + 1; rows of n + 1 entries), zero density and unit transmittance outside the grid.
+// a PairView level (entry (z, j, i) holds both fields at y = j - 1, j and x = i - 1, i), zero
+// density and unit transmittance outside the grid: two 32-byte loads, one per z slice.
 __device__ __forceinline__ float2 sample_pair_grid(const float4 *__restrict__ g, int n, float gx,
                                                    float gy, float gz) {
     int ix = __float2int_rd(gx), iy = __float2int_rd(gy), iz = __float2int_rd(gz);
     const float fx = gx - (float)ix, fy = gy - (float)iy, fz = gz - (float)iz;
-    const int row = n + 1;
+    const int m = n + 1;
     float4 q[4];                                 // (y, z) corners; .x .y at ix, .z .w at ix + 1
-    if ((unsigned)ix < (unsigned)(n - 1) && (unsigned)iy < (unsigned)(n - 1) &&
-        (unsigned)iz < (unsigned)(n - 1) && n <= 1024) {
-        const float4 *p = g + ((unsigned)iz * (unsigned)n + (unsigned)iy) * (unsigned)row + (unsigned)(ix + 1);
-        const unsigned zs = (unsigned)n * (unsigned)row;
-        q[0] = __ldg(p);
-        q[1] = __ldg(p + row);
-        q[2] = __ldg(p + zs);
-        q[3] = __ldg(p + zs + row);
+    // entry (z, iy + 1, ix + 1) exists for iy, ix in [-1, n - 1]
+    const bool xy_in = (unsigned)(ix + 1) <= (unsigned)n && (unsigned)(iy + 1) <= (unsigned)n;
+    if (xy_in && (unsigned)iz < (unsigned)(n - 1) && n <= 1024) {
+        const float4 *p = g + 2 * (((unsigned)iz * (unsigned)m + (unsigned)(iy + 1)) * (unsigned)m + (unsigned)(ix + 1));
+        ld_entry(p, q[0], q[1]);
+        ld_entry(p + 2 * (unsigned)m * (unsigned)m, q[2], q[3]);
     } else {
-        ix = min(max(ix, -2), n + 1); iy = min(max(iy, -2), n + 1); iz = min(max(iz, -2), n + 1);
+        iz = min(max(iz, -2), n + 1);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            int cy = iy + (c & 1), cz = iz + (c >> 1);
-            bool in = (unsigned)cy < (unsigned)n && (unsigned)cz < (unsigned)n && ix >= -1 && ix < n;
-            q[c] = in ? __ldg(g + ((size_t)cz * n + cy) * row + (ix + 1))
-                      : make_float4(0.0f, 1.0f, 0.0f, 1.0f);
+        for (int c = 0; c < 2; ++c) {
+            const int cz = iz + c;
+            if (xy_in && (unsigned)cz < (unsigned)n) {
+                ld_entry(g + 2 * (((size_t)cz * m + (iy + 1)) * m + (ix + 1)), q[2 * c], q[2 * c + 1]);
+            } else {
+                q[2 * c] = q[2 * c + 1] = make_float4(0.0f, 1.0f, 0.0f, 1.0f);
+            }
         }
     }
     const float2 c00 = lerp2(make_float2(q[0].x, q[0].y), make_float2(q[0].z, q[0].w), fx);

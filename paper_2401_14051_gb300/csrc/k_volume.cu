@@ -118,28 +118,34 @@ void launch_transpose(const float *in, size_t R, size_t C, float *out, cudaStrea
     transpose_kernel<<<(unsigned)(tiles_r * tiles_c), 256, 0, s>>>(in, R, C, tiles_c, out);
 }
 
-// PairView level: entry (z, y, i) = {rho, T} at x = i - 1 and x = i (borders 0 and 1).
+// PairView level: entry (z, j, i) = {rho, T} at (y, x) in {j - 1, j} x {i - 1, i} (borders 0
+// and 1), as two float4 (row y = j - 1, then y = j).
 __global__ void pack_pairs_kernel(const float *__restrict__ rho, const float *__restrict__ T, int n,
                                   float4 *__restrict__ out) {
-    const size_t total = (size_t)n * n * (n + 1);
+    const size_t m = (size_t)n + 1, total = (size_t)n * m * m;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
          e += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(e % (n + 1));
-        const size_t row = e / (n + 1);                   // z * n + y
-        const float *r = rho + row * n, *t = T + row * n;
+        const int i = (int)(e % m), j = (int)((e / m) % m);
+        const size_t z = e / (m * m);
         const int x0 = i - 1, x1 = i;
-        float4 q;
-        q.x = x0 >= 0 ? r[x0] : 0.0f;
-        q.y = x0 >= 0 ? t[x0] : 1.0f;
-        q.z = x1 < n ? r[x1] : 0.0f;
-        q.w = x1 < n ? t[x1] : 1.0f;
-        out[e] = q;
+        float4 q[2];
+        for (int r = 0; r < 2; ++r) {
+            const int y = j - 1 + r;
+            const bool yin = y >= 0 && y < n;
+            const float *rr = rho + (z * n + (size_t)(yin ? y : 0)) * n, *tt = T + (z * n + (size_t)(yin ? y : 0)) * n;
+            q[r].x = yin && x0 >= 0 ? rr[x0] : 0.0f;
+            q[r].y = yin && x0 >= 0 ? tt[x0] : 1.0f;
+            q[r].z = yin && x1 < n ? rr[x1] : 0.0f;
+            q[r].w = yin && x1 < n ? tt[x1] : 1.0f;
+        }
+        out[2 * e] = q[0];
+        out[2 * e + 1] = q[1];
     }
 }
 
 void launch_pack_pairs(const float *rho, const float *T, int n, float4 *out, cudaStream_t s) {
-    const size_t total = (size_t)n * n * (n + 1);
-    const int blocks = (int)((total + 255) / 256 < 8192 ? (total + 255) / 256 : 8192);
+    const size_t total = (size_t)n * ((size_t)n + 1) * ((size_t)n + 1);
+    const int blocks = (int)((total + 255) / 256 < 16384 ? (total + 255) / 256 : 16384);
     note_launch();
     pack_pairs_kernel<<<blocks, 256, 0, s>>>(rho, T, n, out);
 }

@@ -331,7 +331,7 @@ nis_status ensure_pairs(nis_ctx *ctx, const Volume &v, Light &L, cudaStream_t s)
         size_t total = 0;
         for (int m = 0; m < v.levels; ++m) {
             L.pair_off[m] = total;
-            total += (size_t)v.sizes[m] * v.sizes[m] * (v.sizes[m] + 1);
+            total += pair_level_float4(v.sizes[m]);
         }
         nis_status st = dev_alloc_t(ctx, total, &L.pairs, s);
         if (st) return st;

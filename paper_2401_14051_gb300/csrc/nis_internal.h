@@ -153,59 +153,6 @@ __device__ __forceinline__ float sample_border(const float *__restrict__ g, int 
     return c0 + fz * (c1 - c0);
 }
 
-// sample_border of density and transmittance (borders 0 and 1) at once, from a PairView
-// level: four 16-byte loads instead of sixteen scalar ones, the same arithmetic.  A cell
-// whose eight corners all lie inside the grid (the common case) skips the per-corner bounds
-// tests; levels up to 1024^3 index in 32 bits.
-__device__ __forceinline__ float2 sample_pair(const float4 *__restrict__ g, int n, float x, float y,
-                                              float z) {
-    float gx = x * n - 0.5f, gy = y * n - 0.5f, gz = z * n - 0.5f;
-    float flx = floorf(gx), fly = floorf(gy), flz = floorf(gz);
-    float fx = gx - flx, fy = gy - fly, fz = gz - flz;
-    int ix = (int)fminf(fmaxf(flx, -2.0f), (float)n + 1.0f);
-    int iy = (int)fminf(fmaxf(fly, -2.0f), (float)n + 1.0f);
-    int iz = (int)fminf(fmaxf(flz, -2.0f), (float)n + 1.0f);
-    float4 q[4];                                 // (y, z) corners; .x .y at ix, .z .w at ix + 1
-    const int row = n + 1;                       // pair entries per (z, y) row
-    if ((unsigned)ix < (unsigned)(n - 1) && (unsigned)iy < (unsigned)(n - 1) &&
-        (unsigned)iz < (unsigned)(n - 1) && n <= 1024) {
-        const float4 *p = g + ((unsigned)iz * (unsigned)n + (unsigned)iy) * (unsigned)row + (unsigned)(ix + 1);
-        const unsigned zs = (unsigned)n * (unsigned)row;
-        q[0] = __ldg(p);
-        q[1] = __ldg(p + row);
-        q[2] = __ldg(p + zs);
-        q[3] = __ldg(p + zs + row);
-    } else {
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            int cy = iy + (c & 1), cz = iz + (c >> 1);
-            bool in = (unsigned)cy < (unsigned)n && (unsigned)cz < (unsigned)n && ix >= -1 && ix < n;
-            q[c] = in ? __ldg(g + ((size_t)cz * n + cy) * row + (ix + 1))
-                      : make_float4(0.0f, 1.0f, 0.0f, 1.0f);
-        }
-    }
-    float2 r;
-    {
-        float c00 = q[0].x + fx * (q[0].z - q[0].x);
-        float c01 = q[1].x + fx * (q[1].z - q[1].x);
-        float c10 = q[2].x + fx * (q[2].z - q[2].x);
-        float c11 = q[3].x + fx * (q[3].z - q[3].x);
-        float c0 = c00 + fy * (c01 - c00);
-        float c1 = c10 + fy * (c11 - c10);
-        r.x = c0 + fz * (c1 - c0);
-    }
-    {
-        float c00 = q[0].y + fx * (q[0].w - q[0].y);
-        float c01 = q[1].y + fx * (q[1].w - q[1].y);
-        float c10 = q[2].y + fx * (q[2].w - q[2].y);
-        float c11 = q[3].y + fx * (q[3].w - q[3].y);
-        float c0 = c00 + fy * (c01 - c00);
-        float c1 = c10 + fy * (c11 - c10);
-        r.y = c0 + fz * (c1 - c0);
-    }
-    return r;
-}
-
 // Distance from (x, y, z) along unit u to the boundary of the unit cube (>= 0).
 __device__ __forceinline__ float exit_distance(float x, float y, float z, float ux, float uy,
                                                float uz) {
@@ -229,6 +176,8 @@ void launch_convert_density(const void *src, int dtype, float scale, size_t coun
 void launch_downsample(const float *src, int n, float *dst, int m, cudaStream_t s);
 // one PairView level of size n from the density and transmittance levels
 void launch_pack_pairs(const float *rho, const float *T, int n, float4 *out, cudaStream_t s);
+// float4 count of a PairView level of size n
+inline size_t pair_level_float4(int n) { return 2 * (size_t)n * (size_t)(n + 1) * (size_t)(n + 1); }
 // occupancy of the trilinear cells of an n^3 level, one byte per base voxel (i, j, k):
 // occ = 0 guarantees that the cell's corners (i..min(i+1, n-1), likewise j, k) are all zero
 void launch_occupancy(const float *level, int n, unsigned char *occ, cudaStream_t s);
@@ -281,9 +230,11 @@ struct PyramidView {                 // device pointers of all levels of a pyram
 };
 
 // Density and transmittance of a (volume, light) pair side by side for the gathers: entry
-// (z, y, i) of a level of size n, i = 0..n, holds {rho, T} at x = i - 1 and at x = i, each
-// outside the volume as its border value (rho 0, T 1), so that one 16-byte load brings the
-// two x-neighbours of a trilinear cell for both fields.  [z][y][n + 1] float4 per level.
+// (z, j, i) of a level of size n, j, i = 0..n, holds {rho, T} at the four (y, x) of y = j - 1,
+// j and x = i - 1, i (each outside the volume as its border value, rho 0 and T 1), ordered
+// (y0 x0, y0 x1, y1 x0, y1 x1): 32 bytes, so that one full-sector load brings a trilinear
+// cell's four corners of one z slice for both fields.  [z][n + 1][n + 1] entries per level,
+// each two float4.
 struct PairView {
     const float4 *lv[kMaxLevels];
     int n[kMaxLevels];

@@ -94,7 +94,7 @@ size_t level_floats(int n) {
 size_t light_bytes(int n) {
     size_t pairs = 0;
     for (int sz = n;; sz = (sz + 1) / 2) {
-        pairs += (size_t)sz * sz * (sz + 1);
+        pairs += pair_level_float4(sz);
         if (sz == 1) break;
     }
     return level_floats(n) * 4 + pairs * 16;

@@ -129,7 +129,7 @@ def test_server_budget_admission_and_caches(nis):
     # context first (weights, shading workspace for a full batch, phase table, mixed-batch
     # buffers) so that the budget is measured above that base.  One request holds its
     # volume pyramid (1.2 MB), the light's transmittance (1.2 MB) and density/transmittance
-    # pairs (4.9 MB), about 7.4 MB with its image buffers; two do not fit in 10 MB.
+    # cell entries (9.9 MB), about 12.4 MB with its image buffers; two do not fit in 18 MB.
     ctx = nis.Context(0, torch_allocator=False)
     w = ctx.load_weights(blob)
     dev = torch.device("cuda:0")
@@ -140,7 +140,7 @@ def test_server_budget_admission_and_caches(nis):
     ctx.shade_segments(w, [(v0, l0, mat, pt, ot, torch.empty_like(pt))])
     ctx.sync(timeout_ms=60000)
     base = ctx.bytes_in_use()
-    budget = base + 10 * 2 ** 20
+    budget = base + 18 * 2 ** 20
     srv = nis.Server(ctx, w, budget_bytes=budget, max_batch_points=4096, max_inflight=4)
     ids = [srv.submit(v, 900 + i, l, 0.6, mat, cam) for i, v in enumerate(other)]
     for i in ids:
