@@ -32,12 +32,13 @@ constexpr uint32_t kY1Point = 2 * 63 * 16;    // conv1 output per point: 2 chann
 constexpr uint32_t kB1 = 0;                   // [2 co groups][4 k groups][8][8] BF16
 constexpr uint32_t kB2 = kB1 + 1024;          // [27 taps][2 co groups][2 ci groups][8][8] BF16
 constexpr uint32_t kBias = kB2 + 27 * 512;    // b1[16], b2[16] FP32
-constexpr uint32_t kX = kBias + 128;          // [16 points][225] FP32
-constexpr uint32_t kA1 = 29696;               // 4 conv1 tiles
+constexpr uint32_t kX = kBias + 128;          // [16 points][kLatT] FP32, one TMA box
+constexpr uint32_t kXBytes = kGP * kLatT * 4;
+constexpr uint32_t kA1 = 30720;               // 4 conv1 tiles
 constexpr uint32_t kY1 = kA1 + 4 * kTileA1;   // [16 points][2][63][16 B] + read-past pad
 constexpr uint32_t kBar = kY1 + kGP * kY1Point + 256;
 constexpr uint32_t kSmemTC = kBar + 64;
-static_assert(kX + kGP * kLat * 4 <= kA1, "conv1 input overlaps the operand tiles");
+static_assert(kX + kXBytes <= kA1 && kX % 16 == 0, "conv1 input overlaps the operand tiles");
 static_assert(kA1 % 1024 == 0 && kY1 % 16 == 0 && kBar % 8 == 0, "alignment");
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
@@ -47,7 +48,7 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
 }  // namespace
 
 __global__ void __launch_bounds__(kThreadsTC, 2)
-    cnn_tc_kernel(const float *__restrict__ H_T, int count, const float *__restrict__ wbase,
+    cnn_tc_kernel(const __grid_constant__ CUtensorMap map_ht, int count, const float *__restrict__ wbase,
                   const __grid_constant__ WeightOffsets o, float *__restrict__ X_T,
                   __nv_bfloat16 *__restrict__ X_T_bf, uint8_t *__restrict__ X_T_f8, unsigned *err, int xt_ld) {
     extern __shared__ __align__(1024) uint8_t sm[];
@@ -58,6 +59,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2)
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + kBar);      // [0] MMA done, [1] drain
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + kBar + 16);
     int *abort_flag = reinterpret_cast<int *>(sm + kBar + 20);
+    uint64_t *xbar = reinterpret_cast<uint64_t *>(sm + kBar + 24);  // a group's inputs landed
     const uint32_t sbase = tc::smem_u32(sm);
 
     // this layer's weights as BF16 core matrices, and the biases
@@ -83,6 +85,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2)
     if (tid == 0) {
         tc::mbar_init(&bar[0], 1);
         tc::mbar_init(&bar[1], 1);
+        tc::mbar_init(xbar, 1);
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
@@ -113,21 +116,28 @@ __global__ void __launch_bounds__(kThreadsTC, 2)
     };
 
     const int n_groups = (count + kGP - 1) / kGP;
+    // a group's inputs: rows (p0 .. p0 + 15, layer k) of H_T as one TMA box [16][kLatT], issued
+    // as soon as the previous group's conv1 operands are built, so that it lands while that
+    // group's MMAs and epilogues run (rows past the points are read but never written out)
+    uint32_t xphase = 0, x_issued = 0;
+    if (tid == 0 && (int)blockIdx.x < n_groups) {
+        tc::mbar_expect_tx(xbar, kXBytes);
+        tc::tma_load_3d(x, &map_ht, 0, k, blockIdx.x * kGP, xbar);
+        x_issued = 1;
+    }
     for (int grp = blockIdx.x; grp < n_groups && ok; grp += gridDim.x) {
         const int p0 = grp * kGP, np = min(kGP, count - p0);
-        // the group's inputs: every load issued before the stores
-        constexpr int kXPer = (kGP * kLat + kThreadsTC - 1) / kThreadsTC;
-        float xr[kXPer];
-#pragma unroll
-        for (int i = 0; i < kXPer; ++i) {
-            const int idx = tid + i * kThreadsTC, q = idx / kLat, t = idx % kLat;
-            xr[i] = (idx < kGP * kLat && q < np) ? H_T[((size_t)(p0 + q) * kLayers + k) * kLatT + t] : 0.f;
+        __syncthreads();                           // previous group done with y1 and TMEM
+        {
+            const bool got = tc::mbar_wait(xbar, xphase & 1);
+            ++xphase;
+            if (!got) {
+                atomicOr(err, kErrTimeout);
+                *abort_flag = 1;
+            }
+            __syncthreads();
+            if (*(volatile int *)abort_flag) break;
         }
-        __syncthreads();                           // previous group done with x, y1 and TMEM
-#pragma unroll
-        for (int i = 0; i < kXPer; ++i)
-            if (tid + i * kThreadsTC < kGP * kLat) x[tid + i * kThreadsTC] = xr[i];
-        __syncthreads();
         // conv1, in two halves of four tiles
         for (int half = 0; half < 2 && ok; ++half) {
             for (int rl = tid; rl < 512; rl += kThreadsTC) {
@@ -136,7 +146,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2)
                 if (r < kRows1) {
                     const int p = r / 63, pos = r % 63;
                     const int d = pos / 21, h = (pos / 7) % 3, w = pos % 7;
-                    const float *xp = x + p * kLat + d * 45 + h * 9 + w;
+                    const float *xp = x + p * kLatT + d * 45 + h * 9 + w;
                     float v[32];
 #pragma unroll
                     for (int kk = 0; kk < 32; ++kk) {
@@ -160,6 +170,12 @@ __global__ void __launch_bounds__(kThreadsTC, 2)
             __syncthreads();
             if (tid == 0) {
                 tc::fence_after_sync();
+                if (half == 1 && grp + (int)gridDim.x < n_groups) {   // x is free: the next group
+                    tc::fence_async_smem();
+                    tc::mbar_expect_tx(xbar, kXBytes);
+                    tc::tma_load_3d(x, &map_ht, 0, k, (grp + gridDim.x) * kGP, xbar);
+                    ++x_issued;
+                }
                 for (int tt = 0; tt < 4; ++tt)
 #pragma unroll
                     for (int s = 0; s < 2; ++s)
@@ -243,11 +259,13 @@ __global__ void __launch_bounds__(kThreadsTC, 2)
         }
         tc::fence_before_sync();
     }
-    // MMAs issued before a time-out complete before TMEM is released
+    // MMAs issued before a time-out complete before TMEM is released, and an input load in
+    // flight lands before the CTA's shared memory goes away
     __syncthreads();
     if (tid == 0) {
         tc::mma_commit(&bar[1]);
         tc::mbar_wait(&bar[1], 0, 1u << 20);
+        if (x_issued > xphase) tc::mbar_wait(xbar, xphase & 1, 1u << 20);
     }
     __syncthreads();
     if (warp == 0) {
@@ -256,7 +274,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2)
     }
 }
 
-void launch_cnn_tc(const float *H_T, int count, const float *wbase, const WeightOffsets &o,
+void launch_cnn_tc(const CUtensorMap &map_ht, int count, const float *wbase, const WeightOffsets &o,
                    float *X_T, __nv_bfloat16 *X_T_bf, uint8_t *X_T_f8, unsigned *err, int num_sms,
                    cudaStream_t s, int xt_ld) {
     if (count <= 0) return;
@@ -271,7 +289,7 @@ void launch_cnn_tc(const float *H_T, int count, const float *wbase, const Weight
     if (per_layer < 1) per_layer = 1;
     if (per_layer > n_groups) per_layer = n_groups;
     note_launch();
-    cnn_tc_kernel<<<dim3(per_layer, kLayers), kThreadsTC, kSmemTC, s>>>(H_T, count, wbase, o, X_T,
+    cnn_tc_kernel<<<dim3(per_layer, kLayers), kThreadsTC, kSmemTC, s>>>(map_ht, count, wbase, o, X_T,
                                                                         X_T_bf, X_T_f8, err, xt_ld);
 }
 

@@ -79,6 +79,7 @@ struct WorkspaceF8 {                  // scratch of the FP8 path, grow-only
     __nv_bfloat16 *E = nullptr, *H = nullptr;
     float *H_T = nullptr, *w_se = nullptr, *cfg = nullptr, *v = nullptr, *fscale = nullptr;
     CUtensorMap map_rho, map_f, map_xt, map_s, map_mrg[3], map_head, map_z1, map_z2;
+    CUtensorMap map_ht;               // the tensor-core CNN's input boxes over H_T
 };
 
 struct WorkspaceBf {                  // scratch of the tensor-core paths, grow-only
@@ -90,6 +91,7 @@ struct WorkspaceBf {                  // scratch of the tensor-core paths, grow-
                   *Z1 = nullptr, *Z2 = nullptr;
     float *H_T = nullptr, *w_se = nullptr, *cfg = nullptr, *v = nullptr;
     CUtensorMap map_rho, map_f, map_xt, map_s, map_mrg[3], map_head, map_z1, map_z2;
+    CUtensorMap map_ht;               // the tensor-core CNN's input boxes over H_T
     // epilogue output maps (TMA stores): e, h (FP32 with the split), s, the chain ends
     // (per type and chain), the merges (per type) and the head activations
     CUtensorMap out_e, out_h, out_s, out_mrg[3][2], out_head[3], out_z1, out_z2;
@@ -481,7 +483,8 @@ nis_status ensure_workspace_tc(nis_ctx *ctx, WorkspaceBf &w, int parts, int cap,
     if ((st = dev_alloc_t(ctx, n * kLayers * 8, &w.v, s))) return st;
     const uint64_t rows = P * n;      // the parts of a tensor stack along the row dimension
     const uint32_t bx = tc_box_k(parts);
-    bool ok = make_tmap_bf16(&w.map_rho, w.Hb_rho, kLayers * kLatPad, rows, kLayers * kLatPad * 2, bx, 128) &&
+    bool ok = make_tmap_ht(&w.map_ht, w.H_T, n) &&
+              make_tmap_bf16(&w.map_rho, w.Hb_rho, kLayers * kLatPad, rows, kLayers * kLatPad * 2, bx, 128) &&
               make_tmap_bf16(&w.map_f, w.Hb_f, kLayers * kLatPad, rows, kLayers * kLatPad * 2, bx, 128) &&
               make_tmap_bf16(&w.map_xt, w.XTb, kLayers * kDT, rows, kLayers * kDT * 2, bx, 128) &&
               make_tmap_bf16(&w.map_s, w.S, kWidth, rows, kWidth * 2, bx, 128) &&
@@ -684,7 +687,8 @@ nis_status ensure_workspace_fp8(nis_ctx *ctx, int cap, cudaStream_t s) {
     if ((st = dev_alloc_t(ctx, n * kCfg, &w.cfg, s))) return st;
     if ((st = dev_alloc_t(ctx, n * kLayers * 8, &w.v, s))) return st;
     if ((st = dev_alloc_t(ctx, n * kLayers * 2, &w.fscale, s))) return st;
-    bool ok = make_tmap_u8(&w.map_rho, w.H8_rho, kLayers * kLatPad8, n, kLayers * kLatPad8, 128, 128) &&
+    bool ok = make_tmap_ht(&w.map_ht, w.H_T, n) &&
+              make_tmap_u8(&w.map_rho, w.H8_rho, kLayers * kLatPad8, n, kLayers * kLatPad8, 128, 128) &&
               make_tmap_u8(&w.map_f, w.H8_f, kLayers * kLatPad8, n, kLayers * kLatPad8, 128, 128) &&
               make_tmap_u8(&w.map_xt, w.XT8, kLayers * kDT, n, kLayers * kDT, 128, 128) &&
               make_tmap_u8(&w.map_s, w.S8, kWidth8, n, kWidth8, 128, 128) &&
@@ -1091,7 +1095,7 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
             if (split)      // FP32: the FP32 CNN, its output split into three BF16 parts
                 launch_cnn_f32(w.H_T, cnt, W, o, xt_dbg, w.XTb, s, cap * kLayers * kDT);
             else            // BF16: the CNN with BF16 operands on the tensor cores
-                launch_cnn_tc(w.H_T, cnt, W, o, xt_dbg, w.XTb, nullptr, ctx->d_err, ctx->num_sms, s,
+                launch_cnn_tc(w.map_ht, cnt, W, o, xt_dbg, w.XTb, nullptr, ctx->d_err, ctx->num_sms, s,
                               fused ? kFuseXtLd : kDT);
         }
         if (fused) {
@@ -1253,7 +1257,7 @@ nis_status shade_impl_fp8(nis_ctx *ctx, const Volume &vol, const Light &light, c
         }
         {
             ProfScope ps(ctx, "cnn", s);
-            launch_cnn_tc(w.H_T, cnt, W, o, (dbg && dbg->X_T) ? dbg->X_T + (size_t)off * kLayers * kDT : nullptr,
+            launch_cnn_tc(w.map_ht, cnt, W, o, (dbg && dbg->X_T) ? dbg->X_T + (size_t)off * kLayers * kDT : nullptr,
                           nullptr, w.XT8, ctx->d_err, ctx->num_sms, s);
         }
         {
@@ -1454,6 +1458,18 @@ bool make_tmap_u8(CUtensorMap *map, const void *base, uint64_t inner, uint64_t o
     cuuint32_t estr[2] = {1, 1};
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(base), dims, strides, box,
               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool make_tmap_ht(CUtensorMap *map, const float *H_T, uint64_t points) {
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn || (reinterpret_cast<uintptr_t>(H_T) & 15)) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)kLatT, (cuuint64_t)kLayers, points};
+    cuuint64_t strides[2] = {(cuuint64_t)kLatT * 4, (cuuint64_t)kLayers * kLatT * 4};
+    cuuint32_t box[3] = {(cuuint32_t)kLatT, 1, 16};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(H_T), dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 

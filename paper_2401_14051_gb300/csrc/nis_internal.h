@@ -333,7 +333,7 @@ void launch_cnn_f32(const float *H_T, int count, const float *wbase, const Weigh
                     float *X_T, __nv_bfloat16 *X_T_bf, cudaStream_t s, size_t split_part = 0);
 // The same CNN with BF16 operands on the tensor cores (FP32 accumulation): outputs X_T
 // (FP32, optional), X_T_bf (BF16, optional), X_T_f8 (e4m3, optional), [count][12][80].
-void launch_cnn_tc(const float *H_T, int count, const float *wbase, const WeightOffsets &o,
+void launch_cnn_tc(const CUtensorMap &map_ht, int count, const float *wbase, const WeightOffsets &o,
                    float *X_T, __nv_bfloat16 *X_T_bf, uint8_t *X_T_f8, unsigned *err, int num_sms,
                    cudaStream_t s, int xt_ld = kDT);   // xt_ld: X_T_bf row per layer
 // FP8 weights: scale[n] = max_k |W[n][k]| / 448 (1 for empty rows), dst = e4m3(W / scale)
@@ -455,6 +455,9 @@ constexpr int kSplitSlabK = 32;
 inline uint32_t tc_box_k(int parts) { return parts > 1 ? kSplitSlabK : 64; }
 // 2-D BF16 tensor map, inner dimension contiguous, box = box_inner x box_outer; box_inner 64,
 // 32 or 16 gives 128-, 64- or 32-byte swizzled rows (other widths are refused).
+// The tensor-core CNN's input map over H_T [count][12][kLatT] FP32: boxes of one layer's rows
+// of 16 consecutive points (3-D: columns, layers, points; no swizzle).
+bool make_tmap_ht(CUtensorMap *map, const float *H_T, uint64_t points);
 bool make_tmap_bf16(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer,
                     uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer);
 // 3-D output map of the tensor-core epilogue: [parts][rows][cols] FP32 (f32 = true, 128-byte
