@@ -17,6 +17,7 @@
 #include <cuda_fp8.h>
 
 #include "nis_internal.h"
+#include "tc_common.h"
 
 namespace nis {
 
@@ -35,10 +36,12 @@ constexpr int kPartLd = 41;                      // conv2 partial sums: stride p
 static_assert(kCiGroups * 32 * kPartLd <= kPts * kY1, "partial sums alias the conv1 output");
 constexpr int kW2Ci = 436;                       // per-input-channel stride of w2t (27 x 16, padded)
 // shared memory (floats): w1t [27 taps][16 co], b1 [16], w2t [16 ci][kW2Ci: 27 taps x 16 co],
-// b2 [16], x [kPts][225], y1 [kPts][16 ci][kY1Ci]
+// b2 [16], x [kPts][kLatT] (one TMA box), y1 [kPts][16 ci][kY1Ci], an mbarrier
 constexpr int kOffW1 = 0, kOffB1 = kOffW1 + 27 * kCnnCh, kOffW2 = kOffB1 + kCnnCh,
-              kOffB2 = kOffW2 + kCnnCh * kW2Ci, kOffX = kOffB2 + kCnnCh,
-              kOffY1 = kOffX + kPts * kLat, kSmemFloats = kOffY1 + kPts * kY1;
+              kOffB2 = kOffW2 + kCnnCh * kW2Ci, kOffX = (kOffB2 + kCnnCh + 31) & ~31,
+              kOffY1 = kOffX + kPts * kLatT, kOffBar = (kOffY1 + kPts * kY1 + 1) & ~1,
+              kSmemFloats = kOffBar + 4;
+static_assert(kOffX % 32 == 0, "a TMA box lands at a 128-byte aligned shared-memory address");
 static_assert(kOffW2 % 4 == 0 && kW2Ci % 4 == 0, "float4 weight loads need 16-byte alignment");
 
 // Packed FP32 pairs (two output channels): acc += w * (v, v) with fma.rn.f32x2, the same
@@ -61,16 +64,23 @@ __device__ __forceinline__ float f2_lo(f2_t a) { return __uint_as_float((unsigne
 __device__ __forceinline__ float f2_hi(f2_t a) { return __uint_as_float((unsigned)(a >> 32)); }
 }  // namespace
 
-__global__ void __launch_bounds__(kThreads, 2) cnn_f32_kernel(const float *__restrict__ H_T,
+// kTma: a group's inputs arrive as one TMA box ([16 points][kLatT] of one layer), issued once
+// the previous group's conv1 has read its own, so that the load overlaps conv2; otherwise
+// they are plain loads.
+template <bool kTma>
+__global__ void __launch_bounds__(kThreads, 2) cnn_f32_kernel(const __grid_constant__ CUtensorMap map_ht,
+                                                           const float *__restrict__ H_T,
                                                            int count,
                                                            const float *__restrict__ wbase,
                                                            const __grid_constant__ WeightOffsets o,
                                                            float *__restrict__ X_T,
                                                            __nv_bfloat16 *__restrict__ X_T_bf,
-                                                           size_t split_part) {
-    extern __shared__ __align__(16) float sm[];
+                                                           size_t split_part, unsigned *err) {
+    extern __shared__ __align__(128) float sm[];
     float *w1t = sm + kOffW1, *b1 = sm + kOffB1, *w2t = sm + kOffW2, *b2 = sm + kOffB2;
     float *xin = sm + kOffX, *y1 = sm + kOffY1;
+    uint64_t *xbar = reinterpret_cast<uint64_t *>(sm + kOffBar);
+    int *abort_flag = reinterpret_cast<int *>(sm + kOffBar + 2);
     const int k = blockIdx.y;
     const int tid = threadIdx.x;
     {
@@ -90,24 +100,49 @@ __global__ void __launch_bounds__(kThreads, 2) cnn_f32_kernel(const float *__res
         }
     }
     const int n_groups = (count + kPts - 1) / kPts;
-    for (int grp = blockIdx.x * kGroupsPerCta;
-         grp < n_groups && grp < (blockIdx.x + 1) * kGroupsPerCta; ++grp) {
+    const int g_end = min(n_groups, (int)(blockIdx.x + 1) * kGroupsPerCta);
+    uint32_t xphase = 0, x_issued = 0;
+    if (kTma && tid == 0) {
+        tc::mbar_init(xbar, 1);
+        *abort_flag = 0;
+        tc::fence_mbar_init();
+        if ((int)blockIdx.x * kGroupsPerCta < g_end) {
+            tc::mbar_expect_tx(xbar, kPts * kLatT * 4);
+            tc::tma_load_3d(xin, &map_ht, 0, k, blockIdx.x * kGroupsPerCta * kPts, xbar);
+            x_issued = 1;
+        }
+    }
+    for (int grp = blockIdx.x * kGroupsPerCta; grp < g_end; ++grp) {
         const int p0 = grp * kPts;
         const int np = min(kPts, count - p0);
-        // the group's input: all of this thread's loads issued before any store, so that
-        // their latencies overlap (a load-store loop waits for each load in turn)
-        constexpr int kXPer = (kPts * kLat + kThreads - 1) / kThreads;
-        float xr[kXPer];
+        if constexpr (kTma) {
+            __syncthreads();                              // weights ready / previous group done
+            const bool got = tc::mbar_wait(xbar, xphase & 1);
+            ++xphase;
+            if (!got) {
+                *abort_flag = 1;
+                if (err) atomicOr(err, kErrTimeout);
+            }
+            __syncthreads();
+            if (*(volatile int *)abort_flag) break;
+        } else {
+            // the group's input: all of this thread's loads issued before any store, so that
+            // their latencies overlap (a load-store loop waits for each load in turn)
+            constexpr int kXPer = (kPts * kLat + kThreads - 1) / kThreads;
+            float xr[kXPer];
 #pragma unroll
-        for (int i = 0; i < kXPer; ++i) {
-            const int idx = tid + i * kThreads, q = idx / kLat, t = idx % kLat;
-            xr[i] = (idx < kPts * kLat && q < np) ? H_T[((size_t)(p0 + q) * kLayers + k) * kLatT + t] : 0.f;
+            for (int i = 0; i < kXPer; ++i) {
+                const int idx = tid + i * kThreads, q = idx / kLat, t = idx % kLat;
+                xr[i] = (idx < kPts * kLat && q < np) ? H_T[((size_t)(p0 + q) * kLayers + k) * kLatT + t] : 0.f;
+            }
+            __syncthreads();                              // weights ready / previous group done
+#pragma unroll
+            for (int i = 0; i < kXPer; ++i) {
+                const int idx = tid + i * kThreads, q = idx / kLat, t = idx % kLat;
+                if (idx < kPts * kLat) xin[q * kLatT + t] = xr[i];
+            }
+            __syncthreads();
         }
-        __syncthreads();                                  // weights ready / previous group done
-#pragma unroll
-        for (int i = 0; i < kXPer; ++i)
-            if (tid + i * kThreads < kPts * kLat) xin[tid + i * kThreads] = xr[i];
-        __syncthreads();
         // conv1: thread = (point q, row d, row h, channel half); 7 outputs x 8 channels
         {
             const int half = tid & 1, r = tid >> 1;            // 144 (q, d, h) rows
@@ -123,7 +158,7 @@ __global__ void __launch_bounds__(kThreads, 2) cnn_f32_kernel(const float *__res
             for (int kd = 0; kd < 3; ++kd)
 #pragma unroll
                 for (int kh = 0; kh < 3; ++kh) {
-                    const float *xr = xin + q * kLat + ((d + kd) * 5 + (h + kh)) * 9;
+                    const float *xr = xin + q * kLatT + ((d + kd) * 5 + (h + kh)) * 9;
                     f2_t row[9];
 #pragma unroll
                     for (int i = 0; i < 9; ++i) row[i] = f2_dup(xr[i]);
@@ -150,6 +185,12 @@ __global__ void __launch_bounds__(kThreads, 2) cnn_f32_kernel(const float *__res
                 }
         }
         __syncthreads();
+        if (kTma && tid == 0 && grp + 1 < g_end) {        // conv1 is done with x: the next group
+            tc::fence_async_smem();
+            tc::mbar_expect_tx(xbar, kPts * kLatT * 4);
+            tc::tma_load_3d(xin, &map_ht, 0, k, (grp + 1) * kPts, xbar);
+            ++x_issued;
+        }
         // conv2: warp g = input channels g and g + 8, lane = (channel half, point q);
         // 5 outputs x 8 channels, partial sums over 2 input channels
         const int warp = tid >> 5, lane = tid & 31;
@@ -221,21 +262,31 @@ __global__ void __launch_bounds__(kThreads, 2) cnn_f32_kernel(const float *__res
             if (X_T) X_T[o] = v;
         }
     }
+    // an input load still in flight (after a time-out) lands before the CTA exits
+    if (kTma && tid == 0 && x_issued > xphase) tc::mbar_wait(xbar, xphase & 1, 1u << 20);
 }
 
 void launch_cnn_f32(const float *H_T, int count, const float *wbase, const WeightOffsets &o,
-                    float *X_T, __nv_bfloat16 *X_T_bf, cudaStream_t s, size_t split_part) {
+                    float *X_T, __nv_bfloat16 *X_T_bf, cudaStream_t s, size_t split_part,
+                    const CUtensorMap *map_ht, unsigned *err) {
     if (count <= 0) return;
     size_t smem = kSmemFloats * sizeof(float);
     static bool attr_set = false;   // per process; the attribute is per function
     if (!attr_set) {
-        cudaFuncSetAttribute(cnn_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(cnn_f32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(cnn_f32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr_set = true;
     }
+    static const CUtensorMap unused{};
     int n_groups = (count + kPts - 1) / kPts;
     dim3 grid((n_groups + kGroupsPerCta - 1) / kGroupsPerCta, kLayers);
     note_launch();
-    cnn_f32_kernel<<<grid, kThreads, smem, s>>>(H_T, count, wbase, o, X_T, X_T_bf, split_part);
+    if (map_ht)
+        cnn_f32_kernel<true><<<grid, kThreads, smem, s>>>(*map_ht, H_T, count, wbase, o, X_T, X_T_bf,
+                                                          split_part, err);
+    else
+        cnn_f32_kernel<false><<<grid, kThreads, smem, s>>>(unused, H_T, count, wbase, o, X_T, X_T_bf,
+                                                           split_part, err);
 }
 
 }  // namespace nis

@@ -38,7 +38,8 @@ constexpr uint32_t kA1 = 30720;               // 4 conv1 tiles
 constexpr uint32_t kY1 = kA1 + 4 * kTileA1;   // [16 points][2][63][16 B] + read-past pad
 constexpr uint32_t kBar = kY1 + kGP * kY1Point + 256;
 constexpr uint32_t kSmemTC = kBar + 64;
-static_assert(kX + kXBytes <= kA1 && kX % 16 == 0, "conv1 input overlaps the operand tiles");
+static_assert(kX + kXBytes <= kA1, "conv1 input overlaps the operand tiles");
+static_assert(kX % 128 == 0, "a TMA box lands at a 128-byte aligned shared-memory address");
 static_assert(kA1 % 1024 == 0 && kY1 % 16 == 0 && kBar % 8 == 0, "alignment");
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {

@@ -1093,7 +1093,7 @@ nis_status shade_impl_bf16(nis_ctx *ctx, const Volume &vol, const Light &light, 
             ProfScope ps(ctx, "cnn", s);
             float *xt_dbg = (dbg && dbg->X_T) ? dbg->X_T + (size_t)off * kLayers * kDT : nullptr;
             if (split)      // FP32: the FP32 CNN, its output split into three BF16 parts
-                launch_cnn_f32(w.H_T, cnt, W, o, xt_dbg, w.XTb, s, cap * kLayers * kDT);
+                launch_cnn_f32(w.H_T, cnt, W, o, xt_dbg, w.XTb, s, cap * kLayers * kDT, &w.map_ht, ctx->d_err);
             else            // BF16: the CNN with BF16 operands on the tensor cores
                 launch_cnn_tc(w.map_ht, cnt, W, o, xt_dbg, w.XTb, nullptr, ctx->d_err, ctx->num_sms, s,
                               fused ? kFuseXtLd : kDT);

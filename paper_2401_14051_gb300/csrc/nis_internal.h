@@ -330,7 +330,8 @@ void launch_phase_points(const PhaseSpec &ph, const float (*q)[3], int n_pts, fl
 // FP32 CNN (FP32 FFMA): outputs X_T (FP32, optional) and X_T_bf (BF16, optional; three
 // split parts `split_part` elements apart when split_part != 0), [count][12][80].
 void launch_cnn_f32(const float *H_T, int count, const float *wbase, const WeightOffsets &o,
-                    float *X_T, __nv_bfloat16 *X_T_bf, cudaStream_t s, size_t split_part = 0);
+                    float *X_T, __nv_bfloat16 *X_T_bf, cudaStream_t s, size_t split_part = 0,
+                    const CUtensorMap *map_ht = nullptr, unsigned *err = nullptr);
 // The same CNN with BF16 operands on the tensor cores (FP32 accumulation): outputs X_T
 // (FP32, optional), X_T_bf (BF16, optional), X_T_f8 (e4m3, optional), [count][12][80].
 void launch_cnn_tc(const CUtensorMap &map_ht, int count, const float *wbase, const WeightOffsets &o,
