@@ -163,17 +163,6 @@ __device__ __forceinline__ void fused_cfg_row(float gg, const float *alb, float 
     for (int q = 0; q < 8; ++q) row[q] = pack_bf2(x[2 * q], x[2 * q + 1]);
 }
 
-// (a + f (b - a)) for the two lanes of a pair at once (packed FP32: sub.rn / fma.rn .f32x2,
-// the same roundings as the scalar form).
-__device__ __forceinline__ float2 lerp2(float2 a, float2 b, float f) {
-    float2 r;
-    asm("{\n\t.reg .b64 A, B, F, D;\n\t"
-        "mov.b64 A, {%2, %3};\n\tmov.b64 B, {%4, %5};\n\tmov.b64 F, {%6, %6};\n\t"
-        "sub.rn.f32x2 D, B, A;\n\tfma.rn.f32x2 D, F, D, A;\n\tmov.b64 {%0, %1}, D;\n\t}"
-        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(f));
-    return r;
-}
-
 // One 32-byte PairView entry (two float4: the y0 and y1 rows of a cell's z slice) in one
 // full-sector load.
 __device__ __forceinline__ void ld_entry(const float4 *p, float4 &a, float4 &b) {

@@ -153,6 +153,17 @@ __device__ __forceinline__ float sample_border(const float *__restrict__ g, int 
     return c0 + fz * (c1 - c0);
 }
 
+// (a + f (b - a)) for the two lanes of a pair at once (packed FP32: sub.rn / fma.rn .f32x2,
+// the same roundings as the scalar form).
+__device__ __forceinline__ float2 lerp2(float2 a, float2 b, float f) {
+    float2 r;
+    asm("{\n\t.reg .b64 A, B, F, D;\n\t"
+        "mov.b64 A, {%2, %3};\n\tmov.b64 B, {%4, %5};\n\tmov.b64 F, {%6, %6};\n\t"
+        "sub.rn.f32x2 D, B, A;\n\tfma.rn.f32x2 D, F, D, A;\n\tmov.b64 {%0, %1}, D;\n\t}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(f));
+    return r;
+}
+
 // Distance from (x, y, z) along unit u to the boundary of the unit cube (>= 0).
 __device__ __forceinline__ float exit_distance(float x, float y, float z, float ux, float uy,
                                                float uz) {
