@@ -325,7 +325,10 @@ nis_status nis_shade_segments(nis_ctx *ctx, nis_weights w, const nis_segment *se
  * allow; an admitted request's volume upload, pyramid, transmittance and first-hit
  * search run on a preparation stream while earlier requests shade on a second stream; the
  * shading points of all ready requests are shaded together in mixed batches
- * (nis_shade_segments), so requests that arrive while others run join the next batch.
+ * (nis_shade_segments), so requests that arrive while others run join the next batch: of a
+ * batch's max_batch_points the oldest ready request takes up to half and the other ready
+ * requests share the rest equally; what a request cannot use goes to the others in
+ * admission order.
  * Pyramids are cached per volume_key and transmittance fields per (volume_key, light,
  * lambda), kept on the device and evicted least-recently-used (unreferenced only) when the
  * budget needs room.  Each request's image is written to its rgb_out (host, H x W x 3

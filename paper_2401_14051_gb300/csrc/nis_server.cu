@@ -7,10 +7,12 @@
 //      enqueues their preparation on the prep stream: upload + pyramid (cache miss),
 //      transmittance (cache miss), compacted first hits, hit count read-back;
 //   2. marks requests whose preparation event completed as ready;
-//   3. when the previous batch has drained, shades up to max_batch_points points taken from
-//      the ready requests in admission order as one mixed batch on the shade stream; a
-//      request whose last points are in the batch gets its image scattered and copied to a
-//      page-locked staging buffer behind the batch;
+//   3. when the previous batch has drained, shades up to max_batch_points points as one mixed
+//      batch on the shade stream: the oldest ready request takes up to half of the room and
+//      the other ready requests share the rest equally (so every ready request advances in
+//      every batch, and the oldest at least half as fast as alone); what a request cannot use
+//      goes to the others in admission order; a request whose last points are in the batch
+//      gets its image scattered and copied to a page-locked staging buffer behind the batch;
 //   4. retires requests whose image copy completed: copies it to rgb_out, records the
 //      latency, releases its buffers (stream-ordered frees) and its cache references.
 #include <algorithm>
@@ -389,14 +391,16 @@ void loop(nis_server *S) {
             std::vector<nis_segment> segs;
             std::vector<Req *> last, in_batch;
             int room = S->cfg.max_batch_points;
+            std::vector<Req *> ready;
             for (Req *q : S->active) {
-                if (room <= 0) break;
                 if (q->state == kReady && q->err) {   // an earlier batch failed: shade no more
                     q->state = kFailing;              // of it; retired after its batches drain
                     continue;
                 }
-                if (q->state != kReady || q->shaded >= q->n_points) continue;
-                int take = std::min(q->n_points - q->shaded, room);
+                if (q->state == kReady && q->shaded < q->n_points) ready.push_back(q);
+            }
+            // the next `take` points of q as a segment of the batch
+            auto add = [&](Req *q, int take) {
                 nis_segment sg{};
                 sg.vol = q->vol; sg.light = q->light; sg.material = q->r.material;
                 sg.d_points = q->pts + 3 * (size_t)q->shaded;
@@ -404,10 +408,23 @@ void loop(nis_server *S) {
                 sg.n = take;
                 sg.d_rgb_out = q->rgb + 3 * (size_t)q->shaded;
                 segs.push_back(sg);
-                in_batch.push_back(q);
+                if (std::find(in_batch.begin(), in_batch.end(), q) == in_batch.end()) in_batch.push_back(q);
                 q->shaded += take;
                 room -= take;
                 if (q->shaded == q->n_points) last.push_back(q);
+            };
+            if (!ready.empty()) {
+                // the oldest ready request takes up to half of the room, the others an equal
+                // share of the rest; then what is left, in admission order
+                Req *head = ready.front();
+                add(head, std::min(head->n_points - head->shaded, ready.size() > 1 ? room / 2 : room));
+                if (ready.size() > 1) {
+                    const int share = (room + (int)ready.size() - 2) / ((int)ready.size() - 1);
+                    for (size_t i = 1; i < ready.size() && room > 0; ++i)
+                        add(ready[i], std::min({ready[i]->n_points - ready[i]->shaded, share, room}));
+                }
+                for (Req *q : ready)
+                    if (room > 0 && q->shaded < q->n_points) add(q, std::min(q->n_points - q->shaded, room));
             }
             if (!segs.empty()) {
                 nis_status rc = nis_shade_segments(S->ctx, S->w, segs.data(), (int)segs.size(),
@@ -429,7 +446,7 @@ void loop(nis_server *S) {
                 S->batch_in_flight = true;
                 ++S->batches;
                 S->batch_points_sum += S->cfg.max_batch_points - room;
-                S->batch_reqs_sum += segs.size();
+                S->batch_reqs_sum += in_batch.size();
                 S->points += S->cfg.max_batch_points - room;
                 worked = true;
             }
