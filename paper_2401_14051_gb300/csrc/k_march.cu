@@ -93,29 +93,40 @@ void launch_march(const float *level, const unsigned char *occ, int n, int m, fl
 // (counted from the light side) at rho - k r, r = u_perp / |u_a|.  Every ray keeps its
 // optical depth and its length inside the cube from its crossing toward the light.  Step
 // k advances every ray from slice k-1 to slice k (the part of that move inside the cube,
-// its density taken at the part's midpoint) and, in the same launch, fills slice k-1: a
-// voxel centre lies between four rays and takes their bilinearly weighted mean density
-// (depth / length; for a ray that has not met the cube, the density at its crossing)
-// times its own exit distance.  The interpolation happens once per voxel, so its error
-// does not build up along the rays; a light along an axis gives the march's sums and a
-// homogeneous medium the exact depth.
+// its density taken at the part's midpoint); once a ray has crossed slice k, slice k can
+// be filled: a voxel centre lies between four rays and takes their bilinearly weighted mean
+// density (depth / length; for a ray that has not met the cube, the density at its
+// crossing) times its own exit distance.  The interpolation happens once per voxel, so its
+// error does not build up along the rays; a light along an axis gives the march's sums and
+// a homogeneous medium the exact depth.
+//
+// A ray's state depends on nothing but its own previous state, so the sweep runs in chunks
+// of S steps with two launches each: one thread per ray advances it through the S steps in
+// registers, storing its state after each; then one thread per voxel fills the chunk's S
+// slices from those states.  2 ceil(N / S) launches instead of one per step.
 namespace {
 
-constexpr int kSwMaxSeg = 2 * kMaxLevels;
-
-// the work of one step: per level, a ray segment (k < n) and a voxel segment (1 <= k <= n).
-// A ray segment covers the window of rays whose crossing of slice k-1 or k lies within
-// two voxels of the cube; the others keep their state (rays move monotonically across the
-// window: one not yet in it has not met the cube, and one past it is read no more).
-struct SwStep {
-    int k, n_seg;
+// the work of one chunk (steps k0 .. k0 + steps - 1), per level: for the ray launch the
+// window of rays whose crossing of any slice k0 - 1 .. k0 + steps - 1 lies within two
+// voxels of the cube (the others are read by no voxel of the chunk and keep their state:
+// rays move monotonically across the windows, so one not yet in it has not met the cube
+// and one past it is read no more); for the voxel launch the chunk's slices
+struct SwChunk {
+    int k0, n_seg;
     unsigned total;
-    unsigned start[kSwMaxSeg];
-    int width[kSwMaxSeg];             // threads per row: window width (rays) or n (voxels)
-    float inv_width[kSwMaxSeg];
-    int ip0[kSwMaxSeg], iq0[kSwMaxSeg];   // ray index of the window's first row and column
-    unsigned char level[kSwMaxSeg], voxels[kSwMaxSeg];
+    unsigned start[kMaxLevels];
+    int width[kMaxLevels];            // threads per row: window width (rays) or n (voxels)
+    float inv_width[kMaxLevels];
+    int ip0[kMaxLevels], iq0[kMaxLevels];   // ray index of the window's first row and column
+    int steps[kMaxLevels];
+    unsigned char level[kMaxLevels];
 };
+
+__device__ __forceinline__ int sw_segment(const SwChunk &c, unsigned t) {
+    int s = 0;
+    while (s + 1 < c.n_seg && t >= c.start[s + 1]) ++s;
+    return s;
+}
 
 // (i / w, i % w) for i < 2^24 through a float reciprocal, corrected by one step
 __device__ __forceinline__ void sw_divmod(unsigned i, int w, float inv_w, int &q, int &r) {
@@ -153,31 +164,39 @@ __device__ __forceinline__ float sw_exit(const ShearWarpArgs &a, float gx, float
     return fmaxf(t, 0.f) * inv_n;
 }
 
+// rays: ray (lo_p + ip, lo_q + iq) from its crossing of slice k-1 one step along
+// (-sgn, -r_p, -r_q) to slice k, for each step k of the chunk.  Stored per step: (depth,
+// length) once it has met the cube, (density at the crossing, 0) before.
 template <typename Index>
-__global__ void __launch_bounds__(256) shear_warp_kernel(const __grid_constant__ ShearWarpArgs a,
-                                                         const __grid_constant__ SwStep st) {
-    // programmatic dependent launch: the previous step's rays are read only after it ends
+__global__ void __launch_bounds__(256) sw_rays_kernel(const __grid_constant__ ShearWarpArgs a,
+                                                      const __grid_constant__ SwChunk c) {
+    // programmatic dependent launch: the previous launch's rays are read and its voxels'
+    // reads of this buffer end before anything here touches it
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= st.total) return;
-    int s = 0;
-    while (s + 1 < st.n_seg && t >= st.start[s + 1]) ++s;
-    const ShearWarpLevel &L = a.lv[st.level[s]];
-    const unsigned i = t - st.start[s];
-    const int k = st.k, n = L.n;
+    if (t >= c.total) return;
+    const int s = sw_segment(c, t);
+    const ShearWarpLevel &L = a.lv[c.level[s]];
+    const int n = L.n;
     const Index N = (Index)n, d1 = n > 1 ? 1 : 0, dn = n > 1 ? N : 0, dnn = n > 1 ? N * N : 0;
     const float hi = (float)(n - 1), top = (float)(n > 1 ? n - 2 : 0);
-    if (!st.voxels[s]) {
-        // ray (lo_p + ip, lo_q + iq): from its crossing of slice k-1 one step along
-        // (-sgn, -r_p, -r_q) to slice k.  Stored: (depth, length) once it has met the cube,
-        // (density at the crossing, 0) before.
-        int ip, iq;
-        sw_divmod(i, st.width[s], st.inv_width[s], iq, ip);
-        ip += st.ip0[s];
-        iq += st.iq0[s];
-        const unsigned ri = (unsigned)iq * (unsigned)L.P + (unsigned)ip;
-        const float sg = (float)a.sgn, nhi = (float)n - 0.5f;
+    int ip, iq;
+    sw_divmod(t - c.start[s], c.width[s], c.inv_width[s], iq, ip);
+    ip += c.ip0[s];
+    iq += c.iq0[s];
+    const size_t ri = (size_t)iq * (size_t)L.P + (size_t)ip, slot = (size_t)L.P * (size_t)L.Q;
+    const float sg = (float)a.sgn, nhi = (float)n - 0.5f;
+    // the state after step k0 - 1: the last slot of the previous chunk (zeros: not met)
+    float tau = 0.f, ell = 0.f;
+    if (c.k0 > 0) {
+        const float2 old = L.ray[(size_t)(a.slices - 1) * slot + ri];
+        tau = old.x;
+        ell = old.y;
+    }
+    for (int j = 0; j < c.steps[s]; ++j) {
+        const int k = c.k0 + j;
+        if (!(ell > 0.f)) { tau = 0.f; ell = 0.f; }     // not met: nothing carried
         const float ga = a.sgn > 0 ? (float)(n - k) : (float)(k - 1);
         const float gp = (float)(L.lo_p + ip) - (float)(k - 1) * L.r_p;
         const float gq = (float)(L.lo_q + iq) - (float)(k - 1) * L.r_q;
@@ -185,11 +204,6 @@ __global__ void __launch_bounds__(256) shear_warp_kernel(const __grid_constant__
         sw_clip(ga, -sg, nhi, t0, t1);
         sw_clip(gp, -L.inv_rp, nhi, t0, t1);
         sw_clip(gq, -L.inv_rq, nhi, t0, t1);
-        float tau = 0.f, ell = 0.f;
-        if (k > 0) {
-            const float2 old = L.ray[(k - 1) & 1][ri];
-            if (old.y > 0.f) { tau = old.x; ell = old.y; }
-        }
         if (t1 > t0) {
             const float tm = 0.5f * (t0 + t1), len = (t1 - t0) * L.ts;
             float x, y, z;
@@ -208,32 +222,46 @@ __global__ void __launch_bounds__(256) shear_warp_kernel(const __grid_constant__
             }
             ell = 0.f;
         }
-        L.ray[k & 1][ri] = make_float2(tau, ell);
-    } else {
-        // voxel (jp, jq) of slice k-1 between the rays floor(j + (k-1) r) and the next one
-        const int kk = k - 1;
-        int jp, jq;
-        sw_divmod(i, n, st.inv_width[s], jq, jp);
-        const float fp = (float)jp + (float)kk * L.r_p, fq = (float)jq + (float)kk * L.r_q;
-        const float p0 = floorf(fp), q0 = floorf(fq);
-        const float wp = fp - p0, wq = fq - q0;
-        const float2 *ray = L.ray[kk & 1];
-        float mean = 0.f;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int dp = c & 1, dq = c >> 1;
-            const float w = (dp ? wp : 1.f - wp) * (dq ? wq : 1.f - wq);
-            const int ip = min(max((int)p0 + dp - L.lo_p, 0), L.P - 1);
-            const int iq = min(max((int)q0 + dq - L.lo_q, 0), L.Q - 1);
-            const float2 rv = ray[(size_t)iq * L.P + ip];
-            mean += w * (rv.y > 0.f ? __fdividef(rv.x, rv.y) : rv.x);
-        }
-        const float ga = a.sgn > 0 ? (float)(n - 1 - kk) : (float)kk;
-        float x, y, z;
-        sw_xyz(a, ga, (float)jp, (float)jq, x, y, z);
-        const float d = sw_exit(a, x, y, z, (float)n - 0.5f, 1.0f / (float)n);
-        L.T[((Index)z * N + (Index)y) * N + (Index)x] = expf(-L.scale * d * mean);
+        L.ray[(size_t)j * slot + ri] = make_float2(tau, ell);
     }
+}
+
+// voxels: voxel (jp, jq) of slice k0 + j between the rays floor(j_p + (k0 + j) r) and the
+// next ones, from their states after step k0 + j
+template <typename Index>
+__global__ void __launch_bounds__(256) sw_voxels_kernel(const __grid_constant__ ShearWarpArgs a,
+                                                        const __grid_constant__ SwChunk c) {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= c.total) return;
+    const int s = sw_segment(c, t);
+    const ShearWarpLevel &L = a.lv[c.level[s]];
+    const int n = L.n;
+    const Index N = (Index)n;
+    int row, jp, j, jq;
+    sw_divmod(t - c.start[s], n, c.inv_width[s], row, jp);
+    sw_divmod((unsigned)row, n, c.inv_width[s], j, jq);
+    const int kk = c.k0 + j;
+    const float fp = (float)jp + (float)kk * L.r_p, fq = (float)jq + (float)kk * L.r_q;
+    const float p0 = floorf(fp), q0 = floorf(fq);
+    const float wp = fp - p0, wq = fq - q0;
+    const float2 *ray = L.ray + (size_t)j * (size_t)L.P * (size_t)L.Q;
+    float mean = 0.f;
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+        const int dp = cc & 1, dq = cc >> 1;
+        const float w = (dp ? wp : 1.f - wp) * (dq ? wq : 1.f - wq);
+        const int ip = min(max((int)p0 + dp - L.lo_p, 0), L.P - 1);
+        const int iq = min(max((int)q0 + dq - L.lo_q, 0), L.Q - 1);
+        const float2 rv = ray[(size_t)iq * L.P + ip];
+        mean += w * (rv.y > 0.f ? __fdividef(rv.x, rv.y) : rv.x);
+    }
+    const float ga = a.sgn > 0 ? (float)(n - 1 - kk) : (float)kk;
+    float x, y, z;
+    sw_xyz(a, ga, (float)jp, (float)jq, x, y, z);
+    const float d = sw_exit(a, x, y, z, (float)n - 0.5f, 1.0f / (float)n);
+    L.T[((Index)z * N + (Index)y) * N + (Index)x] = expf(-L.scale * d * mean);
 }
 
 }  // namespace
@@ -245,6 +273,7 @@ void shear_warp_setup(ShearWarpArgs &a, const int *sizes, int levels, float ux, 
     for (int c = 1; c < 3; ++c)
         if (std::fabs(u[c]) > std::fabs(u[ax])) ax = c;
     a.levels = levels;
+    a.slices = sw_slices(sizes[0]);
     a.sgn = u[ax] > 0 ? 1 : -1;
     a.ax_a = ax;
     a.ax_p = ax == 0 ? 1 : 0;
@@ -271,67 +300,68 @@ void shear_warp_setup(ShearWarpArgs &a, const int *sizes, int levels, float ux, 
         L.inv_rq = rq != 0.0 ? (float)(1.0 / rq) : 0.f;
         L.ts = (float)(1.0 / (n * ua));
         L.scale = powf(lam, (float)(m + 1));
-        ray_floats[m] = 4 * (size_t)L.P * L.Q;
+        ray_floats[m] = 2 * (size_t)a.slices * L.P * L.Q;
     }
 }
 
 void launch_shear_warp(const ShearWarpArgs &a, cudaStream_t s) {
-    const int n0 = a.lv[0].n;
+    const int n0 = a.lv[0].n, S = a.slices;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
-    for (int k = 0; k <= n0; ++k) {
-        SwStep st{};
-        st.k = k;
-        unsigned total = 0;
-        int ns = 0;
-        for (int m = 0; m < a.levels; ++m) {
-            const ShearWarpLevel &L = a.lv[m];
-            if (k < L.n) {
-                // rays whose crossing of slice k-1 or k is within [-2, n+1]
-                auto window = [&](double r, int lo, int count, int &first, int &width) {
-                    const double a0 = std::min((k - 1) * r, k * r), a1 = std::max((k - 1) * r, k * r);
-                    const int r0 = std::max(lo, (int)std::floor(-2.0 + a0));
-                    const int r1 = std::min(lo + count - 1, (int)std::ceil(L.n + 1.0 + a1));
-                    first = r0 - lo;
-                    width = std::max(0, r1 - r0 + 1);
-                };
-                int fp, wp, fq, wq;
-                window(L.r_p, L.lo_p, L.P, fp, wp);
-                window(L.r_q, L.lo_q, L.Q, fq, wq);
-                if (wp > 0 && wq > 0) {
-                    st.start[ns] = total;
-                    st.level[ns] = (unsigned char)m;
-                    st.width[ns] = wp;
-                    st.inv_width[ns] = 1.0f / (float)wp;
-                    st.ip0[ns] = fp;
-                    st.iq0[ns] = fq;
-                    st.voxels[ns++] = 0;
-                    total += (unsigned)wp * (unsigned)wq;
-                }
-            }
-            if (k >= 1 && k <= L.n) {
-                st.start[ns] = total;
-                st.level[ns] = (unsigned char)m;
-                st.width[ns] = L.n;
-                st.inv_width[ns] = 1.0f / (float)L.n;
-                st.voxels[ns++] = 1;
-                total += (unsigned)L.n * (unsigned)L.n;
-            }
-        }
-        st.n_seg = ns;
-        st.total = total;
+    auto launch = [&](bool rays, const SwChunk &c) {
+        if (c.total == 0) return;
         cudaLaunchConfig_t cfg{};
-        cfg.gridDim = dim3((total + 255) / 256);
+        cfg.gridDim = dim3((c.total + 255) / 256);
         cfg.blockDim = dim3(256);
         cfg.stream = s;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         note_launch();
         if (n0 <= 1024)
-            cudaLaunchKernelEx(&cfg, shear_warp_kernel<unsigned>, a, st);
+            cudaLaunchKernelEx(&cfg, rays ? sw_rays_kernel<unsigned> : sw_voxels_kernel<unsigned>, a, c);
         else
-            cudaLaunchKernelEx(&cfg, shear_warp_kernel<size_t>, a, st);
+            cudaLaunchKernelEx(&cfg, rays ? sw_rays_kernel<size_t> : sw_voxels_kernel<size_t>, a, c);
+    };
+    for (int k0 = 0; k0 < n0; k0 += S) {
+        SwChunk rc{}, vc{};
+        rc.k0 = vc.k0 = k0;
+        for (int m = 0; m < a.levels; ++m) {
+            const ShearWarpLevel &L = a.lv[m];
+            if (k0 >= L.n) continue;
+            const int steps = std::min(S, L.n - k0), k1 = k0 + steps - 1;
+            // rays whose crossing of a slice k0 - 1 .. k1 is within [-2, n + 1]
+            auto window = [&](double r, int lo, int count, int &first, int &width) {
+                const double a0 = std::min((k0 - 1) * r, k1 * r), a1 = std::max((k0 - 1) * r, k1 * r);
+                const int r0 = std::max(lo, (int)std::floor(-2.0 + a0));
+                const int r1 = std::min(lo + count - 1, (int)std::ceil(L.n + 1.0 + a1));
+                first = r0 - lo;
+                width = std::max(0, r1 - r0 + 1);
+            };
+            int fp, wp, fq, wq;
+            window(L.r_p, L.lo_p, L.P, fp, wp);
+            window(L.r_q, L.lo_q, L.Q, fq, wq);
+            if (wp > 0 && wq > 0) {
+                const int i = rc.n_seg++;
+                rc.start[i] = rc.total;
+                rc.level[i] = (unsigned char)m;
+                rc.width[i] = wp;
+                rc.inv_width[i] = 1.0f / (float)wp;
+                rc.ip0[i] = fp;
+                rc.iq0[i] = fq;
+                rc.steps[i] = steps;
+                rc.total += (unsigned)wp * (unsigned)wq;
+            }
+            const int i = vc.n_seg++;
+            vc.start[i] = vc.total;
+            vc.level[i] = (unsigned char)m;
+            vc.width[i] = L.n;
+            vc.inv_width[i] = 1.0f / (float)L.n;
+            vc.steps[i] = steps;
+            vc.total += (unsigned)steps * (unsigned)L.n * (unsigned)L.n;
+        }
+        launch(true, rc);
+        launch(false, vc);
     }
 }
 

@@ -1857,8 +1857,7 @@ nis_status nis_build_transmittance_method(nis_ctx *ctx, nis_volume vol, const fl
             Lm.rho = (xmajor ? v->xmaj : v->data) + v->off[m];
             Lm.occ = (xmajor ? v->xmaj_occ : v->occ) + v->occ_off[m];
             Lm.T = (xmajor ? ctx->sw_T : L.data) + v->off[m];
-            Lm.ray[0] = reinterpret_cast<float2 *>(r);
-            Lm.ray[1] = reinterpret_cast<float2 *>(r + rays[m] / 2);
+            Lm.ray = reinterpret_cast<float2 *>(r);
             r += rays[m];
         }
         launch_shear_warp(sw, s);

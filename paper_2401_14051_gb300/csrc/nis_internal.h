@@ -207,24 +207,38 @@ struct ShearWarpLevel {
     const float *rho;             // density level, [z][y][x]
     const unsigned char *occ;     // its cell occupancy
     float *T;                     // transmittance out, [z][y][x]
-    float2 *ray[2];               // ray (depth, length) [q][p], ping-pong by step parity
+    float2 *ray;                  // ray (depth, length) [slice of the chunk][q][p]
     int n, P, Q, lo_p, lo_q;      // P x Q rays, ray (lo_p + ip, lo_q + iq) at index iq P + ip
     float r_p, r_q, ts, scale;    // shifts per slice, step length 1/(n |u_a|), lambda^(m+1)
     float inv_rp, inv_rq;         // 1 / r (0 where r = 0)
 };
 struct ShearWarpArgs {
     int levels, sgn;              // sgn = sign(u_a): slice a-index of step k is n-1-k or k
+    int slices;                   // steps per launch pair (sw_slices of the finest size)
     int ax_a, ax_p, ax_q;         // coordinate (0 x, 1 y, 2 z) of the axes a, p < q in the
                                   // arrays the kernel reads and writes
     float ux, uy, uz;             // unit direction toward the light, in those coordinates
     float iux, iuy, iuz;          // 1 / |u| per coordinate (0 where u = 0)
     ShearWarpLevel lv[kMaxLevels];
 };
-// fills the geometry of `a` (axes, shifts, ray ranges; not the pointers) for levels of the
-// given sizes and returns the ray-buffer floats each level needs (4 per ray) in ray_floats
+// Steps the sweep takes per pair of launches for a finest level of n voxels a side: the
+// ray states of every step of a chunk are kept (2 n + 3 rays a side at most), up to 256 MB
+// of them at the finest level, 2 to 32 steps, and a chunk's voxel indices stay below 2^24
+// (the kernels split indices through a float reciprocal).
+inline int sw_slices(int n) {
+    const double side = 2.0 * n + 3.0;
+    int s = (int)((256.0 * 1024 * 1024) / (8.0 * side * side));
+    s = s < 2 ? 2 : (s > 32 ? 32 : s);
+    const long long cap = ((1LL << 24) - 1) / ((long long)n * n);
+    return (int)(cap < 1 ? 1 : (cap < s ? cap : s));
+}
+// fills the geometry of `a` (axes, shifts, ray ranges, slices; not the pointers) for levels
+// of the given sizes and returns the ray-buffer floats each level needs (2 per ray and step
+// of a chunk) in ray_floats
 void shear_warp_setup(ShearWarpArgs &a, const int *sizes, int levels, float ux, float uy,
                       float uz, float lam, size_t *ray_floats);
-// enqueues the n_0 + 1 sweep steps (the ray pointers of `a` set by the caller)
+// enqueues the sweep: per chunk of a.slices steps one launch that advances the rays through
+// them and one that fills those slices' voxels (the ray pointers of `a` set by the caller)
 void launch_shear_warp(const ShearWarpArgs &a, cudaStream_t s);
 // phase function of the phase features: one HG lobe, or a mixture of up to 3 (Eq. 6)
 struct PhaseSpec {

@@ -106,8 +106,9 @@ size_t light_bytes(int n) {
 // this grid's size)
 size_t sweep_bytes(int n, bool new_volume) {
     size_t rays = 0;
+    const size_t slices = (size_t)sw_slices(n);         // ray states kept per step of a chunk
     for (int sz = n;; sz = (sz + 1) / 2) {
-        rays += 2 * (size_t)(2 * sz + 3) * (2 * sz + 3) * 8;
+        rays += slices * (size_t)(2 * sz + 3) * (2 * sz + 3) * 8;
         if (sz == 1) break;
     }
     return (new_volume ? level_floats(n) * 5 : 0) + level_floats(n) * 4 + rays;
