@@ -6,8 +6,12 @@ namespace nis {
 
 // Per pixel: ray from the camera, clipped to the unit cube; samples at t_in + (j + 1/2) *
 // 0.5/n; the first whose zero-border trilinear level-0 density reaches kHitFraction *
-// sigma_max is the shading point x; d is the ray direction.
-__device__ __forceinline__ bool first_hit(const float *__restrict__ rho0, int n,
+// sigma_max is the shading point x; d is the ray direction.  With the level's cell
+// occupancy (occ0, built with the pyramid; null otherwise) a sample in an interior cell
+// whose eight corners are all zero reads one byte instead of eight corners: its density is
+// exactly zero, so the test gives the same answer.
+__device__ __forceinline__ bool first_hit(const float *__restrict__ rho0,
+                                          const unsigned char *__restrict__ occ0, int n,
                                           const float *__restrict__ sigma_max,
                                           const CameraArgs &c, int idx, float (&x)[3],
                                           float (&d)[3]) {
@@ -48,7 +52,7 @@ __device__ __forceinline__ bool first_hit(const float *__restrict__ rho0, int n,
             float t = t0 + (j + 0.5f) * step;
             if (!(t < t1)) break;
             for (int q = 0; q < 3; ++q) x[q] = o[q] + t * d[q];
-            if (sample_border(rho0, n, x[0], x[1], x[2], 0.0f) >= thr) { hit = true; break; }
+            if (sample_border(rho0, n, x[0], x[1], x[2], 0.0f, occ0) >= thr) { hit = true; break; }
         }
     }
     return hit;
@@ -57,7 +61,8 @@ __device__ __forceinline__ bool first_hit(const float *__restrict__ rho0, int n,
 // Compacted output (pix_index != null): slot from an atomic counter; otherwise one entry per
 // pixel, and with block_count != null the number of hits among the block's 256 pixels goes to
 // block_count[blockIdx.x].
-__global__ void __launch_bounds__(256) find_hits_kernel(const float *__restrict__ rho0, int n,
+__global__ void __launch_bounds__(256) find_hits_kernel(const float *__restrict__ rho0,
+                                 const unsigned char *__restrict__ occ0, int n,
                                  const float *__restrict__ sigma_max,
                                  const __grid_constant__ CameraArgs c,
                                  int *hit_flag, float *points, float *omega, int *pix_index,
@@ -66,7 +71,7 @@ __global__ void __launch_bounds__(256) find_hits_kernel(const float *__restrict_
     bool hit = false;
     if (idx < c.width * c.height) {
         float x[3], d[3];
-        hit = first_hit(rho0, n, sigma_max, c, idx, x, d);
+        hit = first_hit(rho0, occ0, n, sigma_max, c, idx, x, d);
         if (pix_index) {
             if (hit) {
                 int slot = atomicAdd(counter, 1);
@@ -87,12 +92,12 @@ __global__ void __launch_bounds__(256) find_hits_kernel(const float *__restrict_
     }
 }
 
-void launch_find_hits(const float *rho0, int n, const float *sigma_max, const CameraArgs &c,
-                      int *hit_flag, float *points, float *omega, int *pix_index, int *counter,
-                      cudaStream_t s) {
+void launch_find_hits(const float *rho0, const unsigned char *occ0, int n, const float *sigma_max,
+                      const CameraArgs &c, int *hit_flag, float *points, float *omega,
+                      int *pix_index, int *counter, cudaStream_t s) {
     int total = c.width * c.height;
     note_launch();
-    find_hits_kernel<<<(total + 255) / 256, 256, 0, s>>>(rho0, n, sigma_max, c, hit_flag, points,
+    find_hits_kernel<<<(total + 255) / 256, 256, 0, s>>>(rho0, occ0, n, sigma_max, c, hit_flag, points,
                                                          omega, pix_index, counter, nullptr);
 }
 
@@ -174,12 +179,13 @@ __global__ void __launch_bounds__(256) hits_range_kernel(const int *__restrict__
     }
 }
 
-void launch_find_hits_ordered(const float *rho0, int n, const float *sigma_max,
-                              const CameraArgs &c, int *flag, float *pts_px, float *om_px,
-                              int *block_count, int *offsets, int *total, cudaStream_t s) {
+void launch_find_hits_ordered(const float *rho0, const unsigned char *occ0, int n,
+                              const float *sigma_max, const CameraArgs &c, int *flag,
+                              float *pts_px, float *om_px, int *block_count, int *offsets,
+                              int *total, cudaStream_t s) {
     const int pixels = c.width * c.height, nb = (pixels + 255) / 256;
     note_launch();
-    find_hits_kernel<<<nb, 256, 0, s>>>(rho0, n, sigma_max, c, flag, pts_px, om_px, nullptr,
+    find_hits_kernel<<<nb, 256, 0, s>>>(rho0, occ0, n, sigma_max, c, flag, pts_px, om_px, nullptr,
                                         nullptr, block_count);
     note_launch();
     hit_block_scan_kernel<<<1, 1024, 0, s>>>(block_count, nb, offsets, total);

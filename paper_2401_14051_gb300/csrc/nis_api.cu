@@ -1518,7 +1518,8 @@ nis_status hits_compact(nis_ctx *ctx, nis_volume vol, const nis_camera *cam, flo
     NIS_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int), s));
     {
         ProfScope ps(ctx, "hits", s);
-        launch_find_hits(v->data, v->n, v->sigma_max, c, nullptr, pts, om, pix, d_count, s);
+        launch_find_hits(v->data, v->pyramid ? v->occ : nullptr, v->n, v->sigma_max, c, nullptr, pts,
+                         om, pix, d_count, s);
     }
     NIS_CUDA(cudaGetLastError());
     return NIS_OK;
@@ -1988,7 +1989,8 @@ nis_status nis_find_hits(nis_ctx *ctx, nis_volume vol, const nis_camera *cam, in
     nis_status st = camera_args(ctx, cam, &c);
     if (st) return st;
     DeviceGuard g(ctx->device);
-    launch_find_hits(v->data, v->n, v->sigma_max, c, d_hit, d_points, d_omega, nullptr, nullptr,
+    launch_find_hits(v->data, v->pyramid ? v->occ : nullptr, v->n, v->sigma_max, c, d_hit, d_points,
+                     d_omega, nullptr, nullptr,
                      reinterpret_cast<cudaStream_t>(stream));
     NIS_CUDA(cudaGetLastError());
     return NIS_OK;
@@ -2063,7 +2065,8 @@ nis_status render_impl(nis_ctx *ctx, nis_volume vol, const nis_light *lights, in
     // pixels, which the gathers' lane mapping relies on for coherent loads
     {
         ProfScope ps(ctx, "hits", s);
-        launch_find_hits_ordered(pv->data, pv->n, pv->sigma_max, c, ws.px_flag, ws.px_pts,
+        launch_find_hits_ordered(pv->data, pv->pyramid ? pv->occ : nullptr, pv->n, pv->sigma_max, c,
+                                 ws.px_flag, ws.px_pts,
                                  ws.px_om, ws.px_blk, ws.px_off, ws.hit_count, s);
     }
     NIS_CUDA(cudaGetLastError());
@@ -2137,7 +2140,8 @@ nis_status nis_render_frame_part(nis_ctx *ctx, nis_volume vol, nis_light light, 
     Workspace &ws = ctx->ws;
     {
         ProfScope ps(ctx, "hits", s);
-        launch_find_hits_ordered(pv->data, pv->n, pv->sigma_max, c, ws.px_flag, ws.px_pts,
+        launch_find_hits_ordered(pv->data, pv->pyramid ? pv->occ : nullptr, pv->n, pv->sigma_max, c,
+                                 ws.px_flag, ws.px_pts,
                                  ws.px_om, ws.px_blk, ws.px_off, ws.hit_count, s);
     }
     NIS_CUDA(cudaGetLastError());

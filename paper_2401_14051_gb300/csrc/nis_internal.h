@@ -127,8 +127,12 @@ __device__ __forceinline__ float sample_clamped(const float *__restrict__ g, int
 }
 
 // Trilinear lookup where voxels outside the grid read `border` (template gathers, hits).
+// occ (optional): the grid's cell occupancy (cell (i, j, k) flagged when one of its eight
+// corners is nonzero); an interior cell that is not flagged returns 0 after one byte load,
+// the value its eight zero corners interpolate to.
 __device__ __forceinline__ float sample_border(const float *__restrict__ g, int n, float x,
-                                               float y, float z, float border) {
+                                               float y, float z, float border,
+                                               const unsigned char *__restrict__ occ = nullptr) {
     float gx = x * n - 0.5f, gy = y * n - 0.5f, gz = z * n - 0.5f;
     float flx = floorf(gx), fly = floorf(gy), flz = floorf(gz);
     float fx = gx - flx, fy = gy - fly, fz = gz - flz;
@@ -136,6 +140,9 @@ __device__ __forceinline__ float sample_border(const float *__restrict__ g, int 
     int ix = (int)fminf(fmaxf(flx, -2.0f), (float)n + 1.0f);
     int iy = (int)fminf(fmaxf(fly, -2.0f), (float)n + 1.0f);
     int iz = (int)fminf(fmaxf(flz, -2.0f), (float)n + 1.0f);
+    if (occ && (unsigned)ix <= (unsigned)(n - 2) && (unsigned)iy <= (unsigned)(n - 2) &&
+        (unsigned)iz <= (unsigned)(n - 2) && !__ldg(occ + ((size_t)iz * n + iy) * n + ix))
+        return 0.f;
     float v[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
@@ -402,14 +409,16 @@ struct CameraArgs {
     float eye[3], fwd[3], right[3], up[3];
     float tan_half, aspect, half_h;
 };
-void launch_find_hits(const float *rho0, int n, const float *sigma_max, const CameraArgs &c,
-                      int *hit_flag, float *points, float *omega, int *pix_index,
-                      int *counter, cudaStream_t s);
+// occ0: level 0's cell occupancy when it matches rho0 (skips empty cells), else null
+void launch_find_hits(const float *rho0, const unsigned char *occ0, int n, const float *sigma_max,
+                      const CameraArgs &c, int *hit_flag, float *points, float *omega,
+                      int *pix_index, int *counter, cudaStream_t s);
 // Hits in pixel order: per-pixel flag/point/direction, hit counts per 256-pixel block and
 // their exclusive scan (offsets: nb + 1 ints, nb = ceil(pixels / 256); *total = the hits).
-void launch_find_hits_ordered(const float *rho0, int n, const float *sigma_max,
-                              const CameraArgs &c, int *flag, float *pts_px, float *om_px,
-                              int *block_count, int *offsets, int *total, cudaStream_t s);
+void launch_find_hits_ordered(const float *rho0, const unsigned char *occ0, int n,
+                              const float *sigma_max, const CameraArgs &c, int *flag,
+                              float *pts_px, float *om_px, int *block_count, int *offsets,
+                              int *total, cudaStream_t s);
 // Hits first .. first + count - 1 of that order, compacted into pts/om/pix.
 void launch_hits_range(const int *flag, const float *pts_px, const float *om_px,
                        const int *offsets, int pixels, long long first, int count, float *pts,

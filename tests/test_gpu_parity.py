@@ -352,6 +352,24 @@ def test_chunked_batch_beyond_one_pass(ctx, w1, gpu1):
 
 
 # ---- support: hits and the frame -------------------------------------------------------
+def test_hit_search_occupancy_skip_is_exact(ctx):
+    # once the pyramid is built the hit search reads level 0's cell occupancy and takes an
+    # unflagged interior cell's density as zero without loading its corners; those corners
+    # are all zero, so every hit and hit point equals the search without it, bit for bit
+    vol = synth.cloud_volume(96, 5, 64.0)
+    cams = [synth.persp_camera(synth.unit_vector(7), 320, 180),
+            synth.ortho_camera(synth.unit_vector(12), 200, 150)]
+    h = ctx.upload_volume(vol)
+    before = [[t.cpu().numpy() for t in ctx.find_hits(h, cam)] for cam in cams]
+    ctx.build_pyramid(h)
+    after = [[t.cpu().numpy() for t in ctx.find_hits(h, cam)] for cam in cams]
+    for a, b in zip(before, after):
+        assert a[0].sum() > 1000                     # the view sees the cloud
+        for x, y in zip(a, b):
+            np.testing.assert_array_equal(x, y)
+    ctx.release(h)
+
+
 def test_find_hits_and_render_frame(ctx, w1, gpu1):
     cfg = w1["cfg"]
     cam = cfg["camera"]
