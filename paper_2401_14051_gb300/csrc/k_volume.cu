@@ -43,14 +43,17 @@ void launch_convert_density(const void *src, int dtype, float scale, size_t coun
                                                           count, dst, err, sigma_max);
 }
 
+// downsample and occupancy take one grid row per block, (j, k) = (blockIdx.x, blockIdx.y),
+// its threads striding over i: no index division (the cell-entry packing's rows of n + 1
+// entries measured faster as a flat grid-stride loop).
+
 // One level coarser: parent (i, j, k) of an m^3 grid averages its in-range children
 // (2i + a, 2j + b, 2k + c) < n of the n^3 grid (reading: box mean, ceil(n/2) for odd n).
 __global__ void downsample_kernel(const float *__restrict__ src, int n, float *__restrict__ dst,
                                   int m) {
-    size_t total = (size_t)m * m * m;
-    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
-         idx += (size_t)gridDim.x * blockDim.x) {
-        int i = (int)(idx % m), j = (int)((idx / m) % m), k = (int)(idx / ((size_t)m * m));
+    const int j = blockIdx.x, k = blockIdx.y;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const size_t idx = ((size_t)k * m + j) * m + i;
         float sum = 0.f;
         int cnt = 0;
 #pragma unroll
@@ -65,21 +68,19 @@ __global__ void downsample_kernel(const float *__restrict__ src, int n, float *_
     }
 }
 
+// threads per row block: the row length rounded up to a warp, at most 256
+static int row_threads(int len) { return len >= 256 ? 256 : ((len + 31) / 32) * 32; }
+
 void launch_downsample(const float *src, int n, float *dst, int m, cudaStream_t s) {
-    const int threads = 256;
-    size_t total = (size_t)m * m * m;
-    size_t want = (total + threads - 1) / threads;
-    int blocks = (int)(want < 152 * 32 ? want : 152 * 32);
     note_launch();
-    downsample_kernel<<<blocks, threads, 0, s>>>(src, n, dst, m);
+    downsample_kernel<<<dim3(m, m), row_threads(m), 0, s>>>(src, n, dst, m);
 }
 
 __global__ void occupancy_kernel(const float *__restrict__ level, int n, unsigned char *occ) {
-    const size_t total = (size_t)n * n * n;
     const size_t nn = (size_t)n * n;
-    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
-         idx += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(idx % n), j = (int)((idx / n) % n), k = (int)(idx / nn);
+    const int j = blockIdx.x, k = blockIdx.y;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const size_t idx = (size_t)k * nn + (size_t)j * n + i;
         const size_t dx = i + 1 < n ? 1 : 0, dy = j + 1 < n ? (size_t)n : 0, dz = k + 1 < n ? nn : 0;
         const float *p = level + idx;
         const bool any = __ldg(p) != 0.f || __ldg(p + dx) != 0.f || __ldg(p + dy) != 0.f ||
@@ -91,10 +92,8 @@ __global__ void occupancy_kernel(const float *__restrict__ level, int n, unsigne
 }
 
 void launch_occupancy(const float *level, int n, unsigned char *occ, cudaStream_t s) {
-    const size_t total = (size_t)n * n * n;
-    int blocks = (int)((total + 255) / 256 < 152 * 32 ? (total + 255) / 256 : 152 * 32);
     note_launch();
-    occupancy_kernel<<<blocks, 256, 0, s>>>(level, n, occ);
+    occupancy_kernel<<<dim3(n, n), row_threads(n), 0, s>>>(level, n, occ);
 }
 
 // out[c][r] = in[r][c] for an R x C row-major matrix, through 32 x 32 shared-memory tiles
