@@ -3,18 +3,6 @@
 
 namespace nis {
 
-// HG (Eq. 5) from omc = 1 - cos(theta) and opc = 1 + cos(theta), both computed without
-// cancellation: 1 + g^2 - 2 g cos = (1 - g)^2 + 2 g omc for g >= 0, (1 + g)^2 - 2 g opc for
-// g < 0, so sharp lobes keep full FP32 precision near their peak.  base^(-3/2) as the cube
-// of the hardware reciprocal square root (a few ulp, far inside the table's use) instead of
-// a correctly rounded square root and division: the table costs ~400 of these per entry.
-__device__ __forceinline__ float hg2(float omc, float opc, float g, float k_g) {
-    float base = g >= 0.f ? (1.f - g) * (1.f - g) + 2.f * g * omc
-                          : (1.f + g) * (1.f + g) - 2.f * g * opc;
-    const float r = rsqrtf(base);
-    return k_g * (r * r * r);
-}
-
 // Mean of the phase function (Eq. 5/6) of the angle theta between b and the directions phi
 // of the cap of half-angle beta around an axis a, where gamma = angle(a, b): rings at
 // psi_i = beta (i + 1/2) / kRings weighted by sin(psi_i), kAzim azimuths phi_j measured
@@ -22,8 +10,17 @@ __device__ __forceinline__ float hg2(float omc, float opc, float g, float k_g) {
 // Eq. 9).  1 -/+ cos(theta) come from the haversine form of the spherical law of cosines,
 //   1 - cos(theta) = 2 [sin^2((psi - gamma)/2) + sin(psi) sin(gamma) sin^2(phi/2)],
 //   1 + cos(theta) = 2 [sin^2((psi + gamma - pi)/2) + sin(psi) sin(gamma) cos^2(phi/2)].
-__device__ float cap_mean(float gamma, float beta, const PhaseSpec &ph, const float *k_g,
-                          const float *__restrict__ az_s2, const float *__restrict__ az_c2) {
+// HG's 1 + g^2 - 2 g cos(theta) is written without cancellation, (1 - g)^2 + 2 g (1 - cos)
+// for g >= 0 and (1 + g)^2 - 2 g (1 + cos) for g < 0, so sharp lobes keep full FP32
+// precision near their peak; on one ring that is A + B t_j with non-negative A, B and t_j
+// = sin^2(phi_j / 2) (g >= 0) or cos^2(phi_j / 2) (g < 0), and each node costs one FMA, a
+// reciprocal square root (base^(-3/2) as its cube; a few ulp) and two multiply-adds.
+__device__ __forceinline__ float cap_mean(float gamma, float beta, const PhaseSpec &ph, const float *k_g,
+                                          const float *__restrict__ az_s2,
+                                          const float *__restrict__ az_c2) {
+    float ts[kAzim], tc[kAzim];
+#pragma unroll
+    for (int j = 0; j < kAzim; ++j) { ts[j] = az_s2[j]; tc[j] = az_c2[j]; }
     const float sg = sinf(gamma);
     float acc = 0.f, wsum = 0.f;
     for (int i = 0; i < kRings; ++i) {
@@ -32,12 +29,25 @@ __device__ float cap_mean(float gamma, float beta, const PhaseSpec &ph, const fl
         const float hm = sinf(0.5f * (psi - gamma)), hp = sinf(0.5f * (psi + gamma) - 1.5707963267949f);
         const float hm2 = hm * hm, hp2 = hp * hp, ss = s * sg;
         float ring = 0.f;
-        for (int j = 0; j < kAzim; ++j) {
-            const float omc = 2.f * (hm2 + ss * az_s2[j]);
-            const float opc = 2.f * (hp2 + ss * az_c2[j]);
-            float v = ph.w[0] * hg2(omc, opc, ph.g[0], k_g[0]);
-            for (int l = 1; l < ph.n; ++l) v += ph.w[l] * hg2(omc, opc, ph.g[l], k_g[l]);
-            ring += v;
+        for (int l = 0; l < ph.n; ++l) {
+            const float g = ph.g[l];
+            float sum = 0.f;
+            if (g >= 0.f) {
+                const float A = fmaf(4.f * g, hm2, (1.f - g) * (1.f - g)), B = 4.f * g * ss;
+#pragma unroll
+                for (int j = 0; j < kAzim; ++j) {
+                    const float r = rsqrtf(fmaf(B, ts[j], A));
+                    sum = fmaf(r * r, r, sum);
+                }
+            } else {
+                const float A = fmaf(-4.f * g, hp2, (1.f + g) * (1.f + g)), B = -4.f * g * ss;
+#pragma unroll
+                for (int j = 0; j < kAzim; ++j) {
+                    const float r = rsqrtf(fmaf(B, tc[j], A));
+                    sum = fmaf(r * r, r, sum);
+                }
+            }
+            ring = fmaf(ph.w[l] * k_g[l], sum, ring);
         }
         acc += s * ring;
         wsum += s * kAzim;
