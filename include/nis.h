@@ -144,9 +144,10 @@ nis_status nis_build_pyramid(nis_ctx *ctx, nis_volume vol, nis_stream stream);
  * scaled optical depth exceeds 30.  lambda in (0, 1] (the paper uses 0.6).  Builds the
  * pyramid first if needed.  A light with the same volume, direction and lambda is
  * re-marched into its existing buffers and its handle returned again.  The light also keeps
- * the density and its transmittance interleaved per voxel pair for the template gathers
- * (about 4x the transmittance pyramid's bytes); shading calls refresh that copy when the
- * pyramid has been rebuilt since. */
+ * a cell-entry copy for the template gathers: per z slice and cell (y, x), the density and
+ * the transmittance at the cell's four (y, x) corners in 32 bytes (about 8x the
+ * transmittance pyramid's bytes: 34 GB for a 1024^3 grid); shading calls refresh that copy
+ * when the pyramid has been rebuilt since. */
 nis_status nis_build_transmittance(nis_ctx *ctx, nis_volume vol, const float light_dir[3],
                                    float lambda, nis_stream stream, nis_light *out);
 
