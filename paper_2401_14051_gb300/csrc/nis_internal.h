@@ -140,7 +140,8 @@ __device__ __forceinline__ float sample_border(const float *__restrict__ g, int 
     int ix = (int)fminf(fmaxf(flx, -2.0f), (float)n + 1.0f);
     int iy = (int)fminf(fmaxf(fly, -2.0f), (float)n + 1.0f);
     int iz = (int)fminf(fmaxf(flz, -2.0f), (float)n + 1.0f);
-    if (occ && (unsigned)ix <= (unsigned)(n - 2) && (unsigned)iy <= (unsigned)(n - 2) &&
+    // interior cells only (0 <= index <= n - 2; a 1^3 grid has none)
+    if (occ && n >= 2 && (unsigned)ix <= (unsigned)(n - 2) && (unsigned)iy <= (unsigned)(n - 2) &&
         (unsigned)iz <= (unsigned)(n - 2) && !__ldg(occ + ((size_t)iz * n + iy) * n + ix))
         return 0.f;
     float v[8];

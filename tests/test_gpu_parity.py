@@ -368,6 +368,17 @@ def test_hit_search_occupancy_skip_is_exact(ctx):
         for x, y in zip(a, b):
             np.testing.assert_array_equal(x, y)
     ctx.release(h)
+    # grids with no interior cell (1^3) or a single one (2^3), and a small odd grid
+    for n, seed in ((1, 3), (2, 4), (3, 5)):
+        v = np.random.default_rng(seed).uniform(0, 4, (n, n, n)).astype(np.float32)
+        v[v < 2] = 0.0
+        h = ctx.upload_volume(v)
+        before = [t.cpu().numpy() for t in ctx.find_hits(h, cams[0])]
+        ctx.build_pyramid(h)
+        after = [t.cpu().numpy() for t in ctx.find_hits(h, cams[0])]
+        for x, y in zip(before, after):
+            np.testing.assert_array_equal(x, y)
+        ctx.release(h)
 
 
 def test_find_hits_and_render_frame(ctx, w1, gpu1):
