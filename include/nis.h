@@ -134,8 +134,12 @@ nis_status nis_upload_volume(nis_ctx *ctx, const void *density, int nx, int ny, 
                              nis_stream stream, nis_volume *out);
 
 /* Builds the density mip pyramid of `vol` (Sec. III.B.1): levels N, ceil(N/2), ..., 1,
- * each voxel the mean of its in-range 2x2x2 children, plus sigma_max of level 0.
- * Rebuilding an already built pyramid recomputes it in place. */
+ * each voxel the mean of its in-range 2x2x2 children, plus sigma_max of level 0, and each
+ * level's cell occupancy (which cells have a nonzero corner).  Rebuilding an already built
+ * pyramid recomputes it in place.  Once it is built, the first-hit search of the calls below
+ * (nis_render_frame*, nis_find_hits, nis_render_frame_part) reads level 0's occupancy to pass
+ * over empty cells (the hits are the same): order those calls after this one when they run
+ * on another stream. */
 nis_status nis_build_pyramid(nis_ctx *ctx, nis_volume vol, nis_stream stream);
 
 /* Marches the graded transmittance fields of `vol` toward a distant light (Eq. 1):
@@ -430,7 +434,8 @@ nis_status nis_shade_points_debug(nis_ctx *ctx, nis_volume vol, nis_light light,
                                   nis_stream stream);
 
 /* First-hit search alone: per pixel, hit flag (int32), shading point and omega (float32
- * x3) into caller device buffers of width*height entries. */
+ * x3) into caller device buffers of width*height entries.  Reads level 0 (and, once the
+ * pyramid is built, its cell occupancy: see nis_build_pyramid). */
 nis_status nis_find_hits(nis_ctx *ctx, nis_volume vol, const nis_camera *cam, int *d_hit,
                          float *d_points, float *d_omega, nis_stream stream);
 
