@@ -415,10 +415,12 @@ void loop(nis_server *S) {
                 if (q->shaded == q->n_points) last.push_back(q);
             };
             if (!ready.empty()) {
-                // the oldest ready request takes up to half of the room, the others an equal
-                // share of the rest; then what is left, in admission order
+                // the oldest ready request takes up to half of the room (at least one point, so
+                // that a batch of one point still serves it first), the others an equal share
+                // of the rest; then what is left, in admission order
                 Req *head = ready.front();
-                add(head, std::min(head->n_points - head->shaded, ready.size() > 1 ? room / 2 : room));
+                add(head, std::min(head->n_points - head->shaded,
+                                   ready.size() > 1 ? std::max(1, room / 2) : room));
                 if (ready.size() > 1) {
                     const int share = (room + (int)ready.size() - 2) / ((int)ready.size() - 1);
                     for (size_t i = 1; i < ready.size() && room > 0; ++i)
